@@ -29,6 +29,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "glu_oracle.c")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _SO = os.path.join(_OUT_DIR, "liboracle.so")
+# a test may point the wrapper at a deliberately broken build of the source
+_SO_OVERRIDE = os.environ.get("GLU_ORACLE_LIB")
 _lock = threading.Lock()
 _lib = None
 
@@ -61,7 +63,7 @@ def _load():
     with _lock:
         if _lib is not None:
             return _lib
-        lib = C.CDLL(build())
+        lib = C.CDLL(_SO_OVERRIDE if _SO_OVERRIDE else build())
         P = C.c_void_p
         i32, i64 = C.c_int32, C.c_int64
         lib.oracle_permute.argtypes = [i32, P, P, P, P, P, P]
