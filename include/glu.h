@@ -1,0 +1,177 @@
+/*
+ * glu.h -- C ABI of the GB300 (sm_103a) sparse LU refactorization library.
+ *
+ * The method is GLU3.0 (Peng & Tan, "GLU3.0: Fast GPU-based Parallel Sparse
+ * LU Factorization for Circuit Simulation"): a statically pivoted,
+ * fill-reduced sparse A = LU is analysed once on the host (fill-in,
+ * relaxed column dependencies, levels) and then refactorized on the GPU
+ * many times with new values (Section III, first paragraph: the numeric part
+ * repeats inside Newton-Raphson loops), level by level, with the hybrid
+ * right-looking column update (Algorithm 2, Algorithm 5, Eqs. 1-3).  x
+ * follows from the two triangular solves (Section I).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Indices are 0-based.  The input matrix is n x n in compressed sparse
+ * column form: colptr[n+1] (colptr[0] = 0, non-decreasing), rowidx[nnz]
+ * with rows sorted ascending and no duplicates inside a column; every
+ * column of P A P^T must hold its diagonal.  perm[n] maps new to old:
+ * the library factors B = P A P^T with B(i,j) = A(perm[i], perm[j]);
+ * NULL means the identity.  The factor is stored as one CSC array over the
+ * filled pattern, A_s = L + U - I (Section II-A): the strict lower part of
+ * each column is L (unit diagonal implied), the rest is U.
+ *
+ * Values, right-hand sides and solutions are double arrays that may live in
+ * host or device memory; the library tells them apart with
+ * cudaPointerGetAttributes.  Multiple right-hand sides are stored one after
+ * the other, each of length n (column-major n x nrhs).
+ *
+ * Execution is stream-ordered on the handle's stream (glu_set_stream,
+ * default: the legacy default stream).  A call given only device pointers
+ * returns once its work is enqueued; errors raised on the GPU (zero or
+ * non-finite pivot, bounded-wait timeout) surface at the next call that
+ * synchronizes: glu_sync, or any call with a host output.  A call with a
+ * host output returns after the result is in host memory.
+ *
+ * Ownership: glu_analyze copies its inputs; the handle owns every array it
+ * hands out, which stays valid until glu_destroy.  One handle must not be
+ * used by two host threads at once; separate handles are independent.
+ *
+ * Return codes: GLU_OK (0) or one of the negative GLU_ERR_* codes below.
+ */
+#ifndef GLU_H_
+#define GLU_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GLU_OK 0
+#define GLU_ERR_INVALID -1          /* malformed CSC, bad permutation, bad argument */
+#define GLU_ERR_STRUCT_SINGULAR -2  /* a column of P A P^T lacks its diagonal */
+#define GLU_ERR_ZERO_PIVOT -3       /* a pivot is exactly zero (column in glu_last_error_info) */
+#define GLU_ERR_NONFINITE -4        /* a pivot is NaN or infinite */
+#define GLU_ERR_OOM -5              /* host or device allocation failed */
+#define GLU_ERR_CUDA -6             /* a CUDA runtime call failed */
+#define GLU_ERR_TIMEOUT -7          /* a bounded device-side wait gave up */
+#define GLU_ERR_NOT_FACTORED -8     /* solve before a successful factorization */
+#define GLU_ERR_INTERNAL -9         /* an internal consistency check failed */
+
+typedef struct glu_handle glu_handle;
+
+/* Tuning knobs.  glu_default_options fills every field; a zero or negative
+ * value in a field means "choose automatically" unless stated otherwise. */
+typedef struct glu_options {
+    int32_t struct_size;      /* sizeof(glu_options); set by glu_default_options */
+    int32_t mode_force;       /* -1 per-level choice; 0 warp-per-column,
+                                 1 block-per-column, 2 pipelined tail, for every level */
+    int32_t tail_threshold;   /* levels with at most this many columns run in the
+                                 pipelined tail mode (the paper's stream-mode
+                                 threshold, 16, Section III-B.2 item 3) */
+    int32_t piece_updates;    /* target-column updates per warp task (work split size) */
+    int32_t wide_threshold;   /* levels with more columns than this run warp-per-column */
+    int32_t use_graph;        /* 1: capture the level sequence in a CUDA graph */
+    int32_t verbose;          /* 1: print analysis statistics to stderr */
+    int32_t host_only;        /* 1: run the host analysis only; no device memory is
+                                 touched and the handle can only report the analysis
+                                 (glu_get_fill / deps / levels / stats) */
+    int32_t reserved[8];
+} glu_options;
+
+/* Analysis statistics (glu_get_stats). */
+typedef struct glu_stats {
+    int32_t n;
+    int32_t nlevels;
+    int64_t nnz_a;
+    int64_t nnz_lu;           /* filled pattern including the diagonal */
+    int64_t nnz_l;            /* strict lower part */
+    int64_t nnz_u;            /* upper part including the diagonal */
+    int64_t n_deps;           /* Algorithm 4 dependency edges */
+    int64_t n_pairs;          /* (source j, target k) column pairs of the updates */
+    int64_t n_updates;        /* multiply-subtract updates per factorization */
+    double flops;             /* sum_j l_j + 2 l_j u_j */
+    int32_t levels_by_mode[3];/* levels run warp-per-column / block-per-column / pipelined */
+    int32_t solve_levels_fwd;
+    int32_t solve_levels_bwd;
+    int32_t max_level_width;
+    int64_t device_bytes;     /* device memory held by the handle */
+    double analyze_ms;        /* host wall time of glu_analyze */
+} glu_stats;
+
+/* Fill every field of *opts with its default. */
+void glu_default_options(glu_options *opts);
+
+/* Symbolic analysis on the host (Section III-A and the flow of Fig. 5):
+ * validates the CSC input, forms B = P A P^T, computes the fill-in of L+U
+ * (Section II-A), the relaxed column dependencies (Algorithm 4), the levels
+ * (Section II-C: columns grouped into levels of mutually independent
+ * columns; level(k) = 0 without dependencies, else 1 + the largest level
+ * among its dependencies) and the per-level update schedule, then uploads the
+ * schedule to the current CUDA device.  On success *out holds a new handle.
+ * Errors: GLU_ERR_INVALID (malformed input), GLU_ERR_STRUCT_SINGULAR,
+ * GLU_ERR_OOM, GLU_ERR_CUDA. */
+int glu_analyze(int32_t n, const int32_t *colptr, const int32_t *rowidx,
+                const int32_t *perm, glu_handle **out);
+
+/* glu_analyze with explicit options (NULL = defaults). */
+int glu_analyze_opts(int32_t n, const int32_t *colptr, const int32_t *rowidx,
+                     const int32_t *perm, const glu_options *opts, glu_handle **out);
+
+/* Stream for all later work of the handle (a cudaStream_t; NULL = legacy
+ * default stream). */
+int glu_set_stream(glu_handle *h, void *cuda_stream);
+
+/* Numeric refactorization in FP64 (Algorithm 2 scheduled by levels,
+ * Algorithm 5 / Eq. 3 for the subcolumn updates).  values[nnz_a] are A's
+ * values in the input CSC order (host or device).  Errors surface as
+ * described above: GLU_ERR_ZERO_PIVOT / GLU_ERR_NONFINITE with the smallest
+ * failing column in glu_last_error_info. */
+int glu_factor(glu_handle *h, const double *values);
+
+/* Wait for the handle's stream and return the first pending device error. */
+int glu_sync(glu_handle *h);
+
+/* Solve A x = b with the last FP64 factorization: c = P b, L y = c (unit L,
+ * forward), U z = y (backward), x = P^T z (Section I).  b and x hold nrhs
+ * vectors of length n each; b and x must not overlap.
+ * Errors: GLU_ERR_NOT_FACTORED, GLU_ERR_INVALID, pending factor errors. */
+int glu_solve(glu_handle *h, const double *b, double *x, int32_t nrhs);
+
+/* Pattern of the fill (Section II-A): lu_colptr[n+1], lu_rowidx[nnz]
+ * (rows ascending per column), host memory owned by the handle. */
+int glu_get_fill(const glu_handle *h, const int64_t **lu_colptr,
+                 const int32_t **lu_rowidx, int64_t *nnz);
+
+/* Algorithm 4's dependency lists: for column k, dep_idx[dep_ptr[k] ..
+ * dep_ptr[k+1]) ascending, each entry a column i < k.  Host memory owned by
+ * the handle. */
+int glu_get_deps(const glu_handle *h, const int64_t **dep_ptr, const int32_t **dep_idx);
+
+/* Levels: level_cols[level_ptr[l] .. level_ptr[l+1]) are the columns of
+ * level l in ascending order; level_ptr has nlevels + 1 entries.  Host
+ * memory owned by the handle. */
+int glu_get_levels(const glu_handle *h, int32_t *nlevels, const int32_t **level_ptr,
+                   const int32_t **level_cols);
+
+/* Copy the FP64 factor values (pattern order, nnz_lu doubles) to host memory;
+ * synchronizes and returns any pending device error. */
+int glu_get_factors(glu_handle *h, double *lu_val_host);
+
+/* Analysis statistics. */
+int glu_get_stats(const glu_handle *h, glu_stats *s);
+
+/* Column of the last zero or non-finite pivot error (-1 if none). */
+int glu_last_error_info(const glu_handle *h, int32_t *column);
+
+/* Free the handle and everything it owns.  NULL is ignored. */
+void glu_destroy(glu_handle *h);
+
+/* Static description of a return code. */
+const char *glu_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GLU_H_ */

@@ -1,0 +1,544 @@
+// analyze.cpp -- host half of glu_analyze (the CPU part of the flow, Fig. 5).
+//
+// Steps: input checks and B = P A P^T; symbolic fill-in of L+U with a
+// depth-first reachability search pruned by symmetric pruning (Eisenstat &
+// Liu), which returns the same pattern as the plain search of Section II-A in
+// less time; the relaxed dependencies of Algorithm 4 by merging two sorted
+// lists per column; levels by longest path (Section II-C); the per-level
+// update schedule of Algorithm 2 / Algorithm 5 (sources of a level, their
+// target columns, the warp tasks); the row views and levels of the two
+// triangular solves.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <numeric>
+
+#include "glu_internal.h"
+
+namespace glu {
+namespace {
+
+double now_ms() {
+    return std::chrono::duration<double, std::milli>(
+               std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// ---------------------------------------------------------------------------
+// Input checks and the symmetric permutation.  Two stable counting sorts
+// (by new row, then by new column) give B's columns with sorted rows.
+int permute_input(HostPlan &P, std::vector<int64_t> &bptr, std::vector<int32_t> &brow,
+                  std::vector<int32_t> &bsrc, std::string &why) {
+    const int32_t n = P.n;
+    const int64_t nnz = P.nnz_a;
+    std::vector<int32_t> cnt((size_t)n + 1, 0);
+    std::vector<int32_t> order1((size_t)nnz);
+    for (int64_t p = 0; p < nnz; p++) cnt[P.iperm[P.a_rowidx[p]] + 1]++;
+    for (int32_t i = 0; i < n; i++) cnt[i + 1] += cnt[i];
+    for (int32_t c = 0; c < n; c++)
+        for (int32_t p = P.a_colptr[c]; p < P.a_colptr[c + 1]; p++)
+            order1[cnt[P.iperm[P.a_rowidx[p]]]++] = p;
+    // column of each A entry in the new numbering
+    std::vector<int32_t> colof((size_t)nnz);
+    for (int32_t c = 0; c < n; c++)
+        for (int32_t p = P.a_colptr[c]; p < P.a_colptr[c + 1]; p++) colof[p] = P.iperm[c];
+    bptr.assign((size_t)n + 1, 0);
+    for (int64_t p = 0; p < nnz; p++) bptr[colof[p] + 1]++;
+    for (int32_t j = 0; j < n; j++) bptr[j + 1] += bptr[j];
+    std::vector<int64_t> fill(bptr.begin(), bptr.end() - 1);
+    brow.resize((size_t)nnz);
+    bsrc.resize((size_t)nnz);
+    for (int64_t q = 0; q < nnz; q++) {
+        int32_t p = order1[q];
+        int64_t dst = fill[colof[p]]++;
+        brow[dst] = P.iperm[P.a_rowidx[p]];
+        bsrc[dst] = p;
+    }
+    for (int32_t j = 0; j < n; j++) {
+        bool diag = false;
+        for (int64_t q = bptr[j]; q < bptr[j + 1]; q++) diag |= (brow[q] == j);
+        if (!diag) {
+            why = "column " + std::to_string(j) + " of P A P^T has no diagonal entry";
+            return GLU_ERR_STRUCT_SINGULAR;
+        }
+    }
+    return GLU_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Symbolic fill-in.  Column j of A_s is the set reached from struct(B(:,j))
+// through the edges k -> i of L(i,k) != 0 with k < j.  After column j is
+// known, every k < j with U(k,j) != 0 and L(j,k) != 0 can drop from its
+// search list the rows of L(:,k) below j: they are reached through j
+// (symmetric pruning); the result is unchanged.
+int symbolic(HostPlan &P, const std::vector<int64_t> &bptr, const std::vector<int32_t> &brow) {
+    const int32_t n = P.n;
+    P.lu_colptr.assign((size_t)n + 1, 0);
+    P.diag_pos.assign((size_t)n, 0);
+    std::vector<int32_t> &rows = P.lu_rowidx;
+    rows.clear();
+    rows.reserve((size_t)bptr[n] * 4 + 16);
+    std::vector<int64_t> lend_pruned((size_t)n);
+    std::vector<uint8_t> pruned((size_t)n, 0);
+    std::vector<int32_t> mark((size_t)n, -1);
+    std::vector<int32_t> stk((size_t)n + 1);
+    std::vector<int64_t> nxt((size_t)n + 1);
+    std::vector<int32_t> found;
+    found.reserve(1024);
+    for (int32_t j = 0; j < n; j++) {
+        found.clear();
+        for (int64_t q = bptr[j]; q < bptr[j + 1]; q++) {
+            int32_t s = brow[q];
+            if (mark[s] == j) continue;
+            mark[s] = j;
+            found.push_back(s);
+            if (s >= j) continue;
+            int32_t top = 0;
+            stk[0] = s;
+            nxt[0] = P.diag_pos[s] + 1;
+            while (top >= 0) {
+                int32_t v = stk[top];
+                int64_t e = lend_pruned[v];
+                int64_t t = nxt[top];
+                while (t < e && mark[rows[t]] == j) t++;
+                if (t == e) { top--; continue; }
+                int32_t w = rows[t];
+                nxt[top] = t + 1;
+                mark[w] = j;
+                found.push_back(w);
+                if (w < j) {
+                    top++;
+                    stk[top] = w;
+                    nxt[top] = P.diag_pos[w] + 1;
+                }
+            }
+        }
+        std::sort(found.begin(), found.end());
+        int64_t base = (int64_t)rows.size();
+        rows.insert(rows.end(), found.begin(), found.end());
+        int64_t end = (int64_t)rows.size();
+        P.lu_colptr[j + 1] = end;
+        int64_t d = base + (std::lower_bound(found.begin(), found.end(), j) - found.begin());
+        P.diag_pos[j] = d;
+        lend_pruned[j] = end;
+        // symmetric pruning of the columns k with U(k,j) != 0
+        for (int64_t q = base; q < d; q++) {
+            int32_t k = rows[q];
+            if (pruned[k]) continue;
+            const int32_t *lb = rows.data() + P.diag_pos[k] + 1;
+            const int32_t *le = rows.data() + P.lu_colptr[k + 1];
+            const int32_t *it = std::lower_bound(lb, le, j);
+            if (it != le && *it == j) {
+                lend_pruned[k] = (it - rows.data()) + 1;
+                pruned[k] = 1;
+            }
+        }
+    }
+    return GLU_OK;
+}
+
+// Compressed-row views of the strict lower and strict upper parts.
+void row_views(HostPlan &P) {
+    const int32_t n = P.n;
+    P.lrow_ptr.assign((size_t)n + 1, 0);
+    P.urow_ptr.assign((size_t)n + 1, 0);
+    for (int32_t j = 0; j < n; j++) {
+        for (int64_t p = P.lu_colptr[j]; p < P.diag_pos[j]; p++) P.urow_ptr[P.lu_rowidx[p] + 1]++;
+        for (int64_t p = P.diag_pos[j] + 1; p < P.lu_colptr[j + 1]; p++) P.lrow_ptr[P.lu_rowidx[p] + 1]++;
+    }
+    for (int32_t i = 0; i < n; i++) {
+        P.lrow_ptr[i + 1] += P.lrow_ptr[i];
+        P.urow_ptr[i + 1] += P.urow_ptr[i];
+    }
+    P.nnz_l = P.lrow_ptr[n];
+    P.nnz_u = P.urow_ptr[n] + n;
+    P.lrow_col.resize((size_t)P.lrow_ptr[n]);
+    P.lrow_pos.resize((size_t)P.lrow_ptr[n]);
+    P.urow_col.resize((size_t)P.urow_ptr[n]);
+    P.urow_pos.resize((size_t)P.urow_ptr[n]);
+    std::vector<int64_t> lf(P.lrow_ptr.begin(), P.lrow_ptr.end() - 1);
+    std::vector<int64_t> uf(P.urow_ptr.begin(), P.urow_ptr.end() - 1);
+    for (int32_t j = 0; j < n; j++) {
+        for (int64_t p = P.lu_colptr[j]; p < P.diag_pos[j]; p++) {
+            int64_t q = uf[P.lu_rowidx[p]]++;
+            P.urow_col[q] = j;
+            P.urow_pos[q] = p;
+        }
+        for (int64_t p = P.diag_pos[j] + 1; p < P.lu_colptr[j + 1]; p++) {
+            int64_t q = lf[P.lu_rowidx[p]]++;
+            P.lrow_col[q] = j;
+            P.lrow_pos[q] = p;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 4: deps(k) = { i < k : U(i,k) != 0 and L(:,i) not empty }
+//                      u { i < k : L(k,i) != 0 }.
+// Both lists are ascending (the rows of column k above the diagonal, and
+// row k of the L view), so one merge gives the sorted, duplicate-free set.
+void dependencies(HostPlan &P) {
+    const int32_t n = P.n;
+    P.dep_ptr.assign((size_t)n + 1, 0);
+    P.dep_idx.clear();
+    P.dep_idx.reserve((size_t)(P.nnz_l + P.nnz_u));
+    auto has_l = [&](int32_t i) { return P.lu_colptr[i + 1] - 1 > P.diag_pos[i]; };
+    for (int32_t k = 0; k < n; k++) {
+        int64_t a = P.lu_colptr[k], ae = P.diag_pos[k];
+        int64_t b = P.lrow_ptr[k], be = P.lrow_ptr[k + 1];
+        while (a < ae || b < be) {
+            // skip up-looking candidates whose L column is empty
+            while (a < ae && !has_l(P.lu_rowidx[a])) a++;
+            int32_t va = a < ae ? P.lu_rowidx[a] : INT32_MAX;
+            int32_t vb = b < be ? P.lrow_col[b] : INT32_MAX;
+            if (va == INT32_MAX && vb == INT32_MAX) break;
+            if (va <= vb) {
+                P.dep_idx.push_back(va);
+                a++;
+                if (va == vb) b++;
+            } else {
+                P.dep_idx.push_back(vb);
+                b++;
+            }
+        }
+        P.dep_ptr[k + 1] = (int64_t)P.dep_idx.size();
+    }
+}
+
+// Longest-path levels; columns of a level ascending.
+void levelize(HostPlan &P) {
+    const int32_t n = P.n;
+    P.level_of.assign((size_t)n, 0);
+    int32_t nl = n > 0 ? 1 : 0;
+    for (int32_t k = 0; k < n; k++) {
+        int32_t lv = 0;
+        for (int64_t p = P.dep_ptr[k]; p < P.dep_ptr[k + 1]; p++)
+            lv = std::max(lv, P.level_of[P.dep_idx[p]] + 1);
+        P.level_of[k] = lv;
+        nl = std::max(nl, lv + 1);
+    }
+    P.level_ptr.assign((size_t)nl + 1, 0);
+    for (int32_t k = 0; k < n; k++) P.level_ptr[P.level_of[k] + 1]++;
+    for (int32_t l = 0; l < nl; l++) P.level_ptr[l + 1] += P.level_ptr[l];
+    P.level_cols.resize((size_t)n);
+    std::vector<int32_t> f(P.level_ptr.begin(), P.level_ptr.end() - 1);
+    for (int32_t k = 0; k < n; k++) P.level_cols[f[P.level_of[k]]++] = k;
+    P.max_level_width = 0;
+    for (int32_t l = 0; l < nl; l++)
+        P.max_level_width = std::max(P.max_level_width, P.level_ptr[l + 1] - P.level_ptr[l]);
+}
+
+// ---------------------------------------------------------------------------
+// The update schedule.  Level l's sources are its columns j with a non-empty
+// L(:,j); each source updates every target k with U(j,k) != 0 (Algorithm 5).
+// The pairs (j,k) of a level are grouped by target; a group with few sources
+// becomes KIND_ROW tasks (split by row ranges when large), a group with many
+// sources becomes one KIND_SRC task per touched 32-position chunk of column
+// k.  Each level's kernel also normalizes the previous level's L columns.
+void schedule(HostPlan &P, const glu_options &opt) {
+    const int32_t n = P.n;
+    const int32_t nl = (int32_t)P.level_ptr.size() - 1;
+    const int64_t piece = opt.piece_updates > 0 ? opt.piece_updates : 2048;
+    const int32_t src_min = 5;   // groups with more sources use KIND_SRC
+    auto lstart = [&](int32_t j) { return P.diag_pos[j] + 1; };
+    auto lcount = [&](int32_t j) { return (int32_t)(P.lu_colptr[j + 1] - P.diag_pos[j] - 1); };
+
+    // pairs, bucketed by the source's level; scanning targets k ascending
+    // (and rows j ascending inside column k) leaves every bucket sorted by
+    // (k, j).
+    std::vector<int64_t> lvl_pair_ptr((size_t)nl + 1, 0);
+    for (int32_t k = 0; k < n; k++)
+        for (int64_t p = P.lu_colptr[k]; p < P.diag_pos[k]; p++) {
+            int32_t j = P.lu_rowidx[p];
+            if (lcount(j) > 0) lvl_pair_ptr[P.level_of[j] + 1]++;
+        }
+    for (int32_t l = 0; l < nl; l++) lvl_pair_ptr[l + 1] += lvl_pair_ptr[l];
+    const int64_t npairs = lvl_pair_ptr[nl];
+    P.pair_j.resize((size_t)npairs);
+    P.pair_k.resize((size_t)npairs);
+    P.pair_pos.resize((size_t)npairs);
+    P.pair_map.resize((size_t)npairs + 1);
+    {
+        std::vector<int64_t> f(lvl_pair_ptr.begin(), lvl_pair_ptr.end() - 1);
+        for (int32_t k = 0; k < n; k++)
+            for (int64_t p = P.lu_colptr[k]; p < P.diag_pos[k]; p++) {
+                int32_t j = P.lu_rowidx[p];
+                if (lcount(j) == 0) continue;
+                int64_t q = f[P.level_of[j]]++;
+                P.pair_j[q] = j;
+                P.pair_k[q] = k;
+                P.pair_pos[q] = p;
+            }
+    }
+    int64_t acc = 0;
+    for (int64_t q = 0; q < npairs; q++) {
+        P.pair_map[q] = acc;
+        acc += lcount(P.pair_j[q]);
+    }
+    P.pair_map[npairs] = acc;
+    P.n_updates = acc;
+
+    P.segs.clear();
+    P.tasks.clear();
+    P.lvl_task_ptr.assign((size_t)nl + 1, 0);
+    P.level_mode.assign((size_t)nl, 0);
+    std::vector<Task> lvl_tasks;
+    // per-chunk scratch for splitting one group
+    std::vector<int64_t> chunk_work;
+    std::vector<std::vector<Seg>> chunk_segs;
+    std::vector<int32_t> touched;
+
+    for (int32_t l = 0; l < nl; l++) {
+        lvl_tasks.clear();
+        int64_t g = lvl_pair_ptr[l];
+        const int64_t ge_l = lvl_pair_ptr[l + 1];
+        while (g < ge_l) {
+            const int32_t k = P.pair_k[g];
+            int64_t ge = g;
+            int64_t work = 0;
+            while (ge < ge_l && P.pair_k[ge] == k) { work += lcount(P.pair_j[ge]); ge++; }
+            const int64_t nsrc = ge - g;
+            if (nsrc < src_min && work <= piece) {
+                Task t{(int32_t)0, 0, KIND_ROW, 0, 0, work};
+                t.seg_begin = (int32_t)P.segs.size();
+                for (int64_t q = g; q < ge; q++)
+                    P.segs.push_back(Seg{(int32_t)q, 0, lcount(P.pair_j[q]), 0});
+                t.seg_end = (int32_t)P.segs.size();
+                lvl_tasks.push_back(t);
+                g = ge;
+                continue;
+            }
+            // Split column k into 32-position chunks; route every source's
+            // rows to the chunks they fall in.
+            const int64_t c0 = P.lu_colptr[k];
+            const int64_t clen = P.lu_colptr[k + 1] - c0;
+            const int64_t nchunks = (clen + SRC_SLOTS - 1) / SRC_SLOTS;
+            if ((int64_t)chunk_work.size() < nchunks) {
+                chunk_work.resize((size_t)nchunks, 0);
+                chunk_segs.resize((size_t)nchunks);
+            }
+            touched.clear();
+            const int32_t *krows = P.lu_rowidx.data() + c0;
+            for (int64_t q = g; q < ge; q++) {
+                const int32_t j = P.pair_j[q];
+                const int32_t *L = P.lu_rowidx.data() + lstart(j);
+                const int32_t lj = lcount(j);
+                int32_t t = 0;
+                while (t < lj) {
+                    // position of row L[t] inside column k
+                    int64_t pos = std::lower_bound(krows, krows + clen, L[t]) - krows;
+                    int64_t ch = pos / SRC_SLOTS;
+                    int64_t chend = std::min<int64_t>((ch + 1) * SRC_SLOTS, clen);
+                    int32_t t1;
+                    if (chend >= clen) {
+                        t1 = lj;
+                    } else {
+                        int32_t endrow = krows[chend];
+                        t1 = (int32_t)(std::lower_bound(L + t, L + lj, endrow) - L);
+                    }
+                    if (chunk_work[ch] == 0 && chunk_segs[ch].empty()) touched.push_back((int32_t)ch);
+                    chunk_segs[ch].push_back(Seg{(int32_t)q, t, t1, 0});
+                    chunk_work[ch] += t1 - t;
+                    t = t1;
+                }
+            }
+            std::sort(touched.begin(), touched.end());
+            if (nsrc >= src_min) {
+                for (int32_t ch : touched) {
+                    Task t{(int32_t)P.segs.size(), 0, KIND_SRC,
+                           (int32_t)std::min<int64_t>(SRC_SLOTS, clen - (int64_t)ch * SRC_SLOTS),
+                           c0 + (int64_t)ch * SRC_SLOTS, chunk_work[ch]};
+                    P.segs.insert(P.segs.end(), chunk_segs[ch].begin(), chunk_segs[ch].end());
+                    t.seg_end = (int32_t)P.segs.size();
+                    lvl_tasks.push_back(t);
+                    chunk_segs[ch].clear();
+                    chunk_work[ch] = 0;
+                }
+            } else {
+                // few sources, much work: consecutive chunks merged into
+                // KIND_ROW pieces of about `piece` updates; inside a piece
+                // the segments of one source are contiguous in t, so they
+                // merge into one, kept in ascending source order.
+                size_t a = 0;
+                while (a < touched.size()) {
+                    size_t b = a;
+                    int64_t w = 0;
+                    while (b < touched.size() && (b == a || w + chunk_work[touched[b]] <= piece)) {
+                        w += chunk_work[touched[b]];
+                        b++;
+                    }
+                    Task t{(int32_t)P.segs.size(), 0, KIND_ROW, 0, 0, w};
+                    for (int64_t q = g; q < ge; q++) {
+                        int32_t lo = INT32_MAX, hi = -1;
+                        for (size_t c = a; c < b; c++)
+                            for (const Seg &s : chunk_segs[touched[c]])
+                                if (s.pair == (int32_t)q) { lo = std::min(lo, s.t0); hi = std::max(hi, s.t1); }
+                        if (hi > lo) P.segs.push_back(Seg{(int32_t)q, lo, hi, 0});
+                    }
+                    t.seg_end = (int32_t)P.segs.size();
+                    lvl_tasks.push_back(t);
+                    a = b;
+                }
+                for (int32_t ch : touched) { chunk_segs[ch].clear(); chunk_work[ch] = 0; }
+            }
+            g = ge;
+        }
+        // largest tasks first: warps take tasks in order
+        std::stable_sort(lvl_tasks.begin(), lvl_tasks.end(),
+                         [](const Task &a, const Task &b) { return a.work > b.work; });
+        P.tasks.insert(P.tasks.end(), lvl_tasks.begin(), lvl_tasks.end());
+        P.lvl_task_ptr[l + 1] = (int32_t)P.tasks.size();
+        const int32_t width = P.level_ptr[l + 1] - P.level_ptr[l];
+        const int32_t tail = opt.tail_threshold > 0 ? opt.tail_threshold : 16;
+        const int32_t wide = opt.wide_threshold > 0 ? opt.wide_threshold : 256;
+        int8_t mode = width <= tail ? 2 : (width > wide ? 0 : 1);
+        if (opt.mode_force >= 0 && opt.mode_force <= 2) mode = (int8_t)opt.mode_force;
+        P.level_mode[l] = mode;
+        P.levels_by_mode[mode]++;
+    }
+
+    // normalization items: level l's columns run in level l+1's kernel; the
+    // last level's columns in the final pass
+    const int32_t nchunk = 1024;
+    P.norms.clear();
+    P.lvl_norm_ptr.assign((size_t)nl + 2, 0);
+    for (int32_t l = 0; l <= nl; l++) {
+        if (l >= 1) {
+            for (int32_t c = P.level_ptr[l - 1]; c < P.level_ptr[l]; c++) {
+                int32_t j = P.level_cols[c];
+                int32_t lj = lcount(j);
+                for (int32_t t = 0; t < lj; t += nchunk)
+                    P.norms.push_back(NormItem{j, t, std::min(lj, t + nchunk), 0});
+            }
+        }
+        P.lvl_norm_ptr[l + 1] = (int32_t)P.norms.size();
+    }
+}
+
+// Solve levels: forward lf(i) = 1 + max lf(j) over L(i,j) != 0 (0 if none);
+// backward lb(i) = 1 + max lb(k) over U(i,k) != 0, k > i (0 if none).
+void solve_levels(HostPlan &P) {
+    const int32_t n = P.n;
+    std::vector<int32_t> lf((size_t)n, 0), lb((size_t)n, 0);
+    int32_t nf = n ? 1 : 0, nb = n ? 1 : 0;
+    for (int32_t i = 0; i < n; i++) {
+        int32_t v = 0;
+        for (int64_t p = P.lrow_ptr[i]; p < P.lrow_ptr[i + 1]; p++) v = std::max(v, lf[P.lrow_col[p]] + 1);
+        lf[i] = v;
+        nf = std::max(nf, v + 1);
+    }
+    for (int32_t i = n - 1; i >= 0; i--) {
+        int32_t v = 0;
+        for (int64_t p = P.urow_ptr[i]; p < P.urow_ptr[i + 1]; p++) v = std::max(v, lb[P.urow_col[p]] + 1);
+        lb[i] = v;
+        nb = std::max(nb, v + 1);
+    }
+    auto group = [n](const std::vector<int32_t> &lv, int32_t nlev, std::vector<int32_t> &ptr,
+                     std::vector<int32_t> &rows) {
+        ptr.assign((size_t)nlev + 1, 0);
+        for (int32_t i = 0; i < n; i++) ptr[lv[i] + 1]++;
+        for (int32_t l = 0; l < nlev; l++) ptr[l + 1] += ptr[l];
+        rows.resize((size_t)n);
+        std::vector<int32_t> f(ptr.begin(), ptr.end() - 1);
+        for (int32_t i = 0; i < n; i++) rows[f[lv[i]]++] = i;
+    };
+    group(lf, nf, P.fwd_ptr, P.fwd_rows);
+    group(lb, nb, P.bwd_ptr, P.bwd_rows);
+}
+
+}  // namespace
+
+int analyze_host(int32_t n, const int32_t *colptr, const int32_t *rowidx, const int32_t *perm,
+                 const glu_options &opt, HostPlan &P, std::string &why) {
+    if (n < 0 || (n > 0 && (!colptr || !rowidx))) { why = "bad arguments"; return GLU_ERR_INVALID; }
+    P.n = n;
+    if (n == 0) {
+        P.lu_colptr.assign(1, 0);
+        P.dep_ptr.assign(1, 0);
+        P.level_ptr.assign(1, 0);
+        P.lvl_task_ptr.assign(1, 0);
+        P.lvl_norm_ptr.assign(2, 0);
+        P.pair_map.assign(1, 0);
+        P.lrow_ptr.assign(1, 0);
+        P.urow_ptr.assign(1, 0);
+        P.fwd_ptr.assign(1, 0);
+        P.bwd_ptr.assign(1, 0);
+        P.acsr_ptr.assign(1, 0);
+        return GLU_OK;
+    }
+    if (colptr[0] != 0) { why = "colptr[0] != 0"; return GLU_ERR_INVALID; }
+    for (int32_t j = 0; j < n; j++) {
+        if (colptr[j + 1] < colptr[j]) { why = "colptr decreases at column " + std::to_string(j); return GLU_ERR_INVALID; }
+        for (int32_t p = colptr[j]; p < colptr[j + 1]; p++) {
+            if (rowidx[p] < 0 || rowidx[p] >= n) { why = "row index out of range in column " + std::to_string(j); return GLU_ERR_INVALID; }
+            if (p > colptr[j] && rowidx[p] <= rowidx[p - 1]) { why = "rows not strictly ascending in column " + std::to_string(j); return GLU_ERR_INVALID; }
+        }
+    }
+    P.nnz_a = colptr[n];
+    P.a_colptr.assign(colptr, colptr + n + 1);
+    P.a_rowidx.assign(rowidx, rowidx + P.nnz_a);
+    P.perm.resize((size_t)n);
+    P.iperm.assign((size_t)n, -1);
+    for (int32_t i = 0; i < n; i++) {
+        int32_t o = perm ? perm[i] : i;
+        if (o < 0 || o >= n || P.iperm[o] != -1) { why = "perm is not a permutation"; return GLU_ERR_INVALID; }
+        P.perm[i] = o;
+        P.iperm[o] = i;
+    }
+    double t0 = now_ms();
+    std::vector<int64_t> bptr;
+    std::vector<int32_t> brow, bsrc;
+    int rc = permute_input(P, bptr, brow, bsrc, why);
+    if (rc != GLU_OK) return rc;
+    rc = symbolic(P, bptr, brow);
+    if (rc != GLU_OK) return rc;
+    // value gather map: each B entry's position in its LU column
+    const int64_t nnz = P.lu_colptr[n];
+    P.gsrc.assign((size_t)nnz, -1);
+    P.max_col_len = 0;
+    for (int32_t j = 0; j < n; j++) {
+        const int32_t *cb = P.lu_rowidx.data() + P.lu_colptr[j];
+        const int32_t *ce = P.lu_rowidx.data() + P.lu_colptr[j + 1];
+        P.max_col_len = std::max<int64_t>(P.max_col_len, ce - cb);
+        for (int64_t q = bptr[j]; q < bptr[j + 1]; q++) {
+            const int32_t *it = std::lower_bound(cb, ce, brow[q]);
+            P.gsrc[it - P.lu_rowidx.data()] = bsrc[q];
+        }
+    }
+    row_views(P);
+    double t1 = now_ms();
+    dependencies(P);
+    double t2 = now_ms();
+    levelize(P);
+    double t3 = now_ms();
+    schedule(P, opt);
+    solve_levels(P);
+    // A in compressed rows (original numbering), for residuals
+    P.acsr_ptr.assign((size_t)n + 1, 0);
+    for (int64_t p = 0; p < P.nnz_a; p++) P.acsr_ptr[P.a_rowidx[p] + 1]++;
+    for (int32_t i = 0; i < n; i++) P.acsr_ptr[i + 1] += P.acsr_ptr[i];
+    P.acsr_col.resize((size_t)P.nnz_a);
+    P.acsr_src.resize((size_t)P.nnz_a);
+    {
+        std::vector<int64_t> f(P.acsr_ptr.begin(), P.acsr_ptr.end() - 1);
+        for (int32_t c = 0; c < n; c++)
+            for (int32_t p = colptr[c]; p < colptr[c + 1]; p++) {
+                int64_t q = f[rowidx[p]]++;
+                P.acsr_col[q] = c;
+                P.acsr_src[q] = p;
+            }
+    }
+    double t4 = now_ms();
+    P.flops = 0.0;
+    for (int32_t j = 0; j < n; j++) {
+        double lj = (double)(P.lu_colptr[j + 1] - P.diag_pos[j] - 1);
+        double uj = (double)(P.urow_ptr[j + 1] - P.urow_ptr[j]);
+        P.flops += lj + 2.0 * lj * uj;
+    }
+    P.ms_symbolic = t1 - t0;
+    P.ms_deps = t2 - t1;
+    P.ms_levels = t3 - t2;
+    P.ms_schedule = t4 - t3;
+    return GLU_OK;
+}
+
+}  // namespace glu

@@ -1,0 +1,493 @@
+// capi.cu -- the C ABI declared in include/glu.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "glu_device.cuh"
+#include "glu_internal.h"
+
+using namespace glu;
+
+struct glu_handle {
+    HostPlan P;
+    glu_options opt{};
+    int device = 0;
+    int num_sms = 152;
+    cudaStream_t stream = nullptr;
+    // device memory: one arena for the schedule, the map apart
+    char *arena = nullptr;
+    size_t arena_bytes = 0;
+    void *map = nullptr;
+    size_t map_total = 0;
+    int map_bytes = 2;
+    double *d_lu = nullptr;
+    double *d_aval = nullptr;
+    int32_t *d_gsrc = nullptr;
+    int64_t *d_diag = nullptr;
+    int32_t *d_pair_j = nullptr;
+    int64_t *d_pair_pos = nullptr;
+    int64_t *d_pair_map = nullptr;
+    Seg *d_segs = nullptr;
+    Task *d_tasks = nullptr;
+    NormItem *d_norms = nullptr;
+    unsigned long long *d_err = nullptr;
+    int64_t *d_lrow_ptr = nullptr, *d_lrow_pos = nullptr, *d_urow_ptr = nullptr, *d_urow_pos = nullptr;
+    int32_t *d_lrow_col = nullptr, *d_urow_col = nullptr;
+    int32_t *d_fwd_rows = nullptr, *d_bwd_rows = nullptr, *d_perm = nullptr;
+    // solve scratch (grown on demand)
+    double *d_work = nullptr;
+    double *d_bstage = nullptr;
+    double *d_xstage = nullptr;
+    int64_t work_elems = 0;
+    bool factored = false;
+    int32_t err_col = -1;
+    double analyze_ms = 0.0;
+    std::string why;
+};
+
+namespace {
+
+int cuda_fail(glu_handle *h, cudaError_t e, const char *what) {
+    if (h) h->why = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return GLU_ERR_OOM;
+    return GLU_ERR_CUDA;
+}
+
+#define CK(call)                                                         \
+    do {                                                                 \
+        cudaError_t e_ = (call);                                         \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call);           \
+    } while (0)
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Arena carving: every sub-buffer 256-byte aligned.
+struct Carve {
+    size_t off = 0;
+    template <typename T>
+    size_t take(size_t count) {
+        size_t o = (off + 255) & ~size_t(255);
+        off = o + count * sizeof(T) + 1;
+        return o;
+    }
+};
+
+template <typename T>
+T *at(char *base, size_t off) { return reinterpret_cast<T *>(base + off); }
+
+template <typename T>
+cudaError_t upload(T *dst, const std::vector<T> &src) {
+    if (src.empty()) return cudaSuccess;
+    return cudaMemcpy(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+int ensure_work(glu_handle *h, int64_t elems) {
+    if (elems <= h->work_elems) return GLU_OK;
+    cudaFree(h->d_work);
+    cudaFree(h->d_bstage);
+    cudaFree(h->d_xstage);
+    h->d_work = h->d_bstage = h->d_xstage = nullptr;
+    h->work_elems = 0;
+    CK(cudaMalloc(&h->d_work, elems * sizeof(double)));
+    CK(cudaMalloc(&h->d_bstage, elems * sizeof(double)));
+    CK(cudaMalloc(&h->d_xstage, elems * sizeof(double)));
+    h->work_elems = elems;
+    return GLU_OK;
+}
+
+int decode_err(glu_handle *h, unsigned long long w) {
+    if (w == ERR_NONE) return GLU_OK;
+    h->err_col = (int32_t)(w >> 8);
+    switch ((unsigned)(w & 0xff)) {
+        case DEVERR_ZERO_PIVOT: return GLU_ERR_ZERO_PIVOT;
+        case DEVERR_NONFINITE: return GLU_ERR_NONFINITE;
+        case DEVERR_TIMEOUT: return GLU_ERR_TIMEOUT;
+        default: return GLU_ERR_INTERNAL;
+    }
+}
+
+int read_err(glu_handle *h) {
+    unsigned long long w = ERR_NONE;
+    CK(cudaMemcpyAsync(&w, h->d_err, sizeof(w), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return decode_err(h, w);
+}
+
+FactorArgs<double> fargs(glu_handle *h) {
+    FactorArgs<double> a;
+    a.lu = h->d_lu;
+    a.diag_pos = h->d_diag;
+    a.pair_j = h->d_pair_j;
+    a.pair_pos = h->d_pair_pos;
+    a.pair_map = h->d_pair_map;
+    a.map = h->map;
+    a.segs = h->d_segs;
+    a.tasks = h->d_tasks;
+    a.norms = h->d_norms;
+    a.err = h->d_err;
+    return a;
+}
+
+SolveArgs<double> sargs(glu_handle *h) {
+    SolveArgs<double> a;
+    a.lu = h->d_lu;
+    a.diag_pos = h->d_diag;
+    a.lrow_ptr = h->d_lrow_ptr;
+    a.lrow_col = h->d_lrow_col;
+    a.lrow_pos = h->d_lrow_pos;
+    a.urow_ptr = h->d_urow_ptr;
+    a.urow_col = h->d_urow_col;
+    a.urow_pos = h->d_urow_pos;
+    a.n = h->P.n;
+    return a;
+}
+
+int upload_plan(glu_handle *h) {
+    HostPlan &P = h->P;
+    const int32_t n = P.n;
+    const int64_t nnz = P.lu_colptr[n];
+    Carve c;
+    size_t o_lu = c.take<double>(nnz), o_aval = c.take<double>(P.nnz_a), o_gsrc = c.take<int32_t>(nnz),
+           o_diag = c.take<int64_t>(n), o_pj = c.take<int32_t>(P.pair_j.size()),
+           o_ppos = c.take<int64_t>(P.pair_pos.size()), o_pmap = c.take<int64_t>(P.pair_map.size()),
+           o_segs = c.take<Seg>(P.segs.size()), o_tasks = c.take<Task>(P.tasks.size()),
+           o_norms = c.take<NormItem>(P.norms.size()), o_err = c.take<unsigned long long>(1),
+           o_lrp = c.take<int64_t>(n + 1), o_lrc = c.take<int32_t>(P.lrow_col.size()),
+           o_lrpos = c.take<int64_t>(P.lrow_pos.size()), o_urp = c.take<int64_t>(n + 1),
+           o_urc = c.take<int32_t>(P.urow_col.size()), o_urpos = c.take<int64_t>(P.urow_pos.size()),
+           o_fwd = c.take<int32_t>(P.fwd_rows.size()), o_bwd = c.take<int32_t>(P.bwd_rows.size()),
+           o_perm = c.take<int32_t>(n), o_pk = c.take<int32_t>(P.pair_k.size()),
+           o_lcp = c.take<int64_t>(n + 1), o_lri = c.take<int32_t>(nnz);
+    h->arena_bytes = c.off + 256;
+    CK(cudaMalloc(&h->arena, h->arena_bytes));
+    char *A = h->arena;
+    h->d_lu = at<double>(A, o_lu);
+    h->d_aval = at<double>(A, o_aval);
+    h->d_gsrc = at<int32_t>(A, o_gsrc);
+    h->d_diag = at<int64_t>(A, o_diag);
+    h->d_pair_j = at<int32_t>(A, o_pj);
+    h->d_pair_pos = at<int64_t>(A, o_ppos);
+    h->d_pair_map = at<int64_t>(A, o_pmap);
+    h->d_segs = at<Seg>(A, o_segs);
+    h->d_tasks = at<Task>(A, o_tasks);
+    h->d_norms = at<NormItem>(A, o_norms);
+    h->d_err = at<unsigned long long>(A, o_err);
+    h->d_lrow_ptr = at<int64_t>(A, o_lrp);
+    h->d_lrow_col = at<int32_t>(A, o_lrc);
+    h->d_lrow_pos = at<int64_t>(A, o_lrpos);
+    h->d_urow_ptr = at<int64_t>(A, o_urp);
+    h->d_urow_col = at<int32_t>(A, o_urc);
+    h->d_urow_pos = at<int64_t>(A, o_urpos);
+    h->d_fwd_rows = at<int32_t>(A, o_fwd);
+    h->d_bwd_rows = at<int32_t>(A, o_bwd);
+    h->d_perm = at<int32_t>(A, o_perm);
+    int32_t *d_pair_k = at<int32_t>(A, o_pk);
+    int64_t *d_lcp = at<int64_t>(A, o_lcp);
+    int32_t *d_lri = at<int32_t>(A, o_lri);
+    CK(upload(h->d_gsrc, P.gsrc));
+    CK(upload(h->d_diag, P.diag_pos));
+    CK(upload(h->d_pair_j, P.pair_j));
+    CK(upload(h->d_pair_pos, P.pair_pos));
+    CK(upload(h->d_pair_map, P.pair_map));
+    CK(upload(h->d_segs, P.segs));
+    CK(upload(h->d_tasks, P.tasks));
+    CK(upload(h->d_norms, P.norms));
+    CK(upload(h->d_lrow_ptr, P.lrow_ptr));
+    CK(upload(h->d_lrow_col, P.lrow_col));
+    CK(upload(h->d_lrow_pos, P.lrow_pos));
+    CK(upload(h->d_urow_ptr, P.urow_ptr));
+    CK(upload(h->d_urow_col, P.urow_col));
+    CK(upload(h->d_urow_pos, P.urow_pos));
+    CK(upload(h->d_fwd_rows, P.fwd_rows));
+    CK(upload(h->d_bwd_rows, P.bwd_rows));
+    CK(upload(h->d_perm, P.perm));
+    CK(upload(d_pair_k, P.pair_k));
+    CK(upload(d_lcp, P.lu_colptr));
+    CK(upload(d_lri, P.lu_rowidx));
+    // position map, built on the device
+    h->map_bytes = (P.max_col_len <= 65536) ? 2 : 4;
+    h->map_total = (size_t)std::max<int64_t>(P.n_updates, 1) * h->map_bytes;
+    CK(cudaMalloc(&h->map, h->map_total));
+    CK(launch_reset_err(h->d_err, h->stream));
+    MapBuildArgs mb;
+    mb.lu_colptr = d_lcp;
+    mb.lu_rowidx = d_lri;
+    mb.diag_pos = h->d_diag;
+    mb.pair_j = h->d_pair_j;
+    mb.pair_k = d_pair_k;
+    mb.pair_pos = h->d_pair_pos;
+    mb.pair_map = h->d_pair_map;
+    mb.map = h->map;
+    mb.npairs = (int64_t)P.pair_j.size();
+    mb.err = h->d_err;
+    CK(launch_map_build(mb, h->map_bytes, h->stream));
+    int rc = read_err(h);
+    if (rc != GLU_OK) {
+        h->why = "position map build found a row outside its target column";
+        return GLU_ERR_INTERNAL;
+    }
+    return GLU_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void glu_default_options(glu_options *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->struct_size = (int32_t)sizeof(glu_options);
+    o->mode_force = -1;
+    o->tail_threshold = 16;
+    o->piece_updates = 2048;
+    o->wide_threshold = 256;
+    o->use_graph = 0;
+    o->verbose = 0;
+}
+
+int glu_analyze_opts(int32_t n, const int32_t *colptr, const int32_t *rowidx, const int32_t *perm,
+                     const glu_options *opts, glu_handle **out) {
+    if (!out) return GLU_ERR_INVALID;
+    *out = nullptr;
+    auto t0 = std::chrono::steady_clock::now();
+    glu_handle *h = new (std::nothrow) glu_handle();
+    if (!h) return GLU_ERR_OOM;
+    glu_default_options(&h->opt);
+    if (opts) {
+        if (opts->struct_size != (int32_t)sizeof(glu_options)) { delete h; return GLU_ERR_INVALID; }
+        h->opt = *opts;
+    }
+    int rc;
+    try {
+        rc = analyze_host(n, colptr, rowidx, perm, h->opt, h->P, h->why);
+    } catch (const std::bad_alloc &) {
+        rc = GLU_ERR_OOM;
+    }
+    if (rc != GLU_OK) {
+        if (h->opt.verbose) std::fprintf(stderr, "glu_analyze: %s\n", h->why.c_str());
+        delete h;
+        return rc;
+    }
+    if (h->opt.verbose) {
+        const HostPlan &P = h->P;
+        std::fprintf(stderr,
+                     "glu_analyze: n=%d nnzA=%lld nnzLU=%lld levels=%d pairs=%zu updates=%lld tasks=%zu segs=%zu "
+                     "flops=%.4g map=%dB  ms: symbolic %.1f deps %.1f levels %.1f schedule %.1f total %.1f\n",
+                     P.n, (long long)P.nnz_a, (long long)P.lu_colptr[P.n], (int)P.level_ptr.size() - 1,
+                     P.pair_j.size(), (long long)P.n_updates, P.tasks.size(), P.segs.size(), P.flops,
+                     (P.max_col_len <= 65536) ? 2 : 4, P.ms_symbolic, P.ms_deps, P.ms_levels, P.ms_schedule, std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
+    }
+    if (h->opt.host_only) {
+        h->analyze_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        *out = h;
+        return GLU_OK;
+    }
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) { glu_destroy(h); return e == cudaErrorMemoryAllocation ? GLU_ERR_OOM : GLU_ERR_CUDA; }
+    rc = upload_plan(h);
+    if (rc != GLU_OK) {
+        if (h->opt.verbose) std::fprintf(stderr, "glu_analyze: %s\n", h->why.c_str());
+        glu_destroy(h);
+        return rc;
+    }
+    h->analyze_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = h;
+    return GLU_OK;
+}
+
+int glu_analyze(int32_t n, const int32_t *colptr, const int32_t *rowidx, const int32_t *perm, glu_handle **out) {
+    return glu_analyze_opts(n, colptr, rowidx, perm, nullptr, out);
+}
+
+int glu_set_stream(glu_handle *h, void *s) {
+    if (!h) return GLU_ERR_INVALID;
+    h->stream = static_cast<cudaStream_t>(s);
+    return GLU_OK;
+}
+
+int glu_factor(glu_handle *h, const double *values) {
+    if (!h || h->opt.host_only) return GLU_ERR_INVALID;
+    HostPlan &P = h->P;
+    if (P.nnz_a > 0 && !values) return GLU_ERR_INVALID;
+    CK(cudaSetDevice(h->device));
+    h->err_col = -1;
+    const double *av = values;
+    if (P.nnz_a > 0 && !is_device_ptr(values)) {
+        CK(cudaMemcpyAsync(h->d_aval, values, P.nnz_a * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        av = h->d_aval;
+    }
+    CK(launch_reset_err(h->d_err, h->stream));
+    CK(launch_gather<double>(h->d_lu, av, h->d_gsrc, P.lu_colptr[P.n], h->stream));
+    FactorArgs<double> a = fargs(h);
+    const int32_t nl = (int32_t)P.level_ptr.size() - 1;
+    for (int32_t l = 0; l <= nl; l++) {
+        int32_t tb = l < nl ? P.lvl_task_ptr[l] : 0, te = l < nl ? P.lvl_task_ptr[l + 1] : 0;
+        CK(launch_level<double>(a, h->map_bytes, tb, te, P.lvl_norm_ptr[l], P.lvl_norm_ptr[l + 1], h->num_sms,
+                                h->stream));
+    }
+    CK(launch_pivot_check<double>(h->d_lu, h->d_diag, P.n, h->d_err, h->stream));
+    h->factored = true;
+    if (!is_device_ptr(values) && P.nnz_a > 0) {
+        // host input: the host buffer was staged; report errors now
+        return glu_sync(h);
+    }
+    return GLU_OK;
+}
+
+int glu_sync(glu_handle *h) {
+    if (!h) return GLU_ERR_INVALID;
+    if (h->opt.host_only) return GLU_OK;
+    CK(cudaSetDevice(h->device));
+    int rc = read_err(h);
+    if (rc != GLU_OK && rc != GLU_ERR_CUDA) h->factored = (rc == GLU_OK);
+    return rc;
+}
+
+int glu_solve(glu_handle *h, const double *b, double *x, int32_t nrhs) {
+    if (!h || nrhs < 0) return GLU_ERR_INVALID;
+    if (!h->factored) return GLU_ERR_NOT_FACTORED;
+    HostPlan &P = h->P;
+    const int32_t n = P.n;
+    const int64_t elems = (int64_t)n * nrhs;
+    if (elems == 0) return GLU_OK;
+    if (!b || !x) return GLU_ERR_INVALID;
+    CK(cudaSetDevice(h->device));
+    int rc = ensure_work(h, elems);
+    if (rc != GLU_OK) return rc;
+    const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
+    const double *db = b;
+    if (!bdev) {
+        CK(cudaMemcpyAsync(h->d_bstage, b, elems * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        db = h->d_bstage;
+    }
+    double *y = h->d_work;
+    CK(launch_permute_in<double>(y, db, h->d_perm, n, nrhs, h->stream));
+    SolveArgs<double> a = sargs(h);
+    for (size_t l = 0; l + 1 < P.fwd_ptr.size(); l++)
+        CK(launch_lsolve_level<double>(a, y, nrhs, h->d_fwd_rows + P.fwd_ptr[l], P.fwd_ptr[l + 1] - P.fwd_ptr[l],
+                                       h->stream));
+    for (size_t l = 0; l + 1 < P.bwd_ptr.size(); l++)
+        CK(launch_usolve_level<double>(a, y, nrhs, h->d_bwd_rows + P.bwd_ptr[l], P.bwd_ptr[l + 1] - P.bwd_ptr[l],
+                                       h->stream));
+    double *dx = xdev ? x : h->d_xstage;
+    CK(launch_permute_out<double>(dx, y, h->d_perm, n, nrhs, h->stream));
+    if (!xdev) {
+        CK(cudaMemcpyAsync(x, dx, elems * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        return glu_sync(h);
+    }
+    return GLU_OK;
+}
+
+int glu_get_fill(const glu_handle *h, const int64_t **cp, const int32_t **ri, int64_t *nnz) {
+    if (!h) return GLU_ERR_INVALID;
+    if (cp) *cp = h->P.lu_colptr.data();
+    if (ri) *ri = h->P.lu_rowidx.data();
+    if (nnz) *nnz = h->P.lu_colptr.empty() ? 0 : h->P.lu_colptr.back();
+    return GLU_OK;
+}
+
+int glu_get_deps(const glu_handle *h, const int64_t **dp, const int32_t **di) {
+    if (!h) return GLU_ERR_INVALID;
+    if (dp) *dp = h->P.dep_ptr.data();
+    if (di) *di = h->P.dep_idx.data();
+    return GLU_OK;
+}
+
+int glu_get_levels(const glu_handle *h, int32_t *nlevels, const int32_t **lp, const int32_t **lc) {
+    if (!h) return GLU_ERR_INVALID;
+    if (nlevels) *nlevels = (int32_t)h->P.level_ptr.size() - 1;
+    if (lp) *lp = h->P.level_ptr.data();
+    if (lc) *lc = h->P.level_cols.data();
+    return GLU_OK;
+}
+
+int glu_get_factors(glu_handle *h, double *out) {
+    if (!h || !out) return GLU_ERR_INVALID;
+    if (!h->factored) return GLU_ERR_NOT_FACTORED;
+    const int64_t nnz = h->P.lu_colptr[h->P.n];
+    if (nnz == 0) return GLU_OK;
+    CK(cudaSetDevice(h->device));
+    CK(cudaMemcpyAsync(out, h->d_lu, nnz * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return glu_sync(h);
+}
+
+int glu_get_stats(const glu_handle *h, glu_stats *s) {
+    if (!h || !s) return GLU_ERR_INVALID;
+    const HostPlan &P = h->P;
+    std::memset(s, 0, sizeof(*s));
+    s->n = P.n;
+    s->nlevels = (int32_t)P.level_ptr.size() - 1;
+    s->nnz_a = P.nnz_a;
+    s->nnz_lu = P.lu_colptr[P.n];
+    s->nnz_l = P.nnz_l;
+    s->nnz_u = P.nnz_u;
+    s->n_deps = P.dep_ptr[P.n];
+    s->n_pairs = (int64_t)P.pair_j.size();
+    s->n_updates = P.n_updates;
+    s->flops = P.flops;
+    for (int i = 0; i < 3; i++) s->levels_by_mode[i] = P.levels_by_mode[i];
+    s->solve_levels_fwd = (int32_t)P.fwd_ptr.size() - 1;
+    s->solve_levels_bwd = (int32_t)P.bwd_ptr.size() - 1;
+    s->max_level_width = P.max_level_width;
+    s->device_bytes = (int64_t)(h->arena_bytes + h->map_total + 3 * h->work_elems * sizeof(double));
+    s->analyze_ms = h->analyze_ms;
+    return GLU_OK;
+}
+
+int glu_last_error_info(const glu_handle *h, int32_t *column) {
+    if (!h || !column) return GLU_ERR_INVALID;
+    *column = h->err_col;
+    return GLU_OK;
+}
+
+void glu_destroy(glu_handle *h) {
+    if (!h) return;
+    if (h->opt.host_only) {
+        delete h;
+        return;
+    }
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    cudaFree(h->arena);
+    cudaFree(h->map);
+    cudaFree(h->d_work);
+    cudaFree(h->d_bstage);
+    cudaFree(h->d_xstage);
+    delete h;
+}
+
+const char *glu_strerror(int code) {
+    switch (code) {
+        case GLU_OK: return "ok";
+        case GLU_ERR_INVALID: return "invalid argument or malformed input";
+        case GLU_ERR_STRUCT_SINGULAR: return "structurally singular: a column of P A P^T lacks its diagonal";
+        case GLU_ERR_ZERO_PIVOT: return "zero pivot";
+        case GLU_ERR_NONFINITE: return "non-finite pivot";
+        case GLU_ERR_OOM: return "out of memory";
+        case GLU_ERR_CUDA: return "CUDA runtime error";
+        case GLU_ERR_TIMEOUT: return "bounded device wait timed out";
+        case GLU_ERR_NOT_FACTORED: return "no successful factorization to solve with";
+        case GLU_ERR_INTERNAL: return "internal consistency check failed";
+        default: return "unknown error code";
+    }
+}
+
+}  // extern "C"

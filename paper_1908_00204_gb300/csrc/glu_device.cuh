@@ -1,0 +1,82 @@
+// glu_device.cuh -- device-side argument blocks and launch helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "glu_internal.h"
+
+namespace glu {
+
+// Pending device error: the smallest (column << 8 | code) wins.
+constexpr unsigned long long ERR_NONE = ~0ull;
+enum : unsigned { DEVERR_ZERO_PIVOT = 1, DEVERR_NONFINITE = 2, DEVERR_TIMEOUT = 3, DEVERR_INTERNAL = 4 };
+
+template <typename T>
+struct FactorArgs {
+    T *lu;                       // values over the filled pattern
+    const int64_t *diag_pos;     // n
+    const int32_t *pair_j;       // source column of each (j,k) pair
+    const int64_t *pair_pos;     // position of U(j,k)
+    const int64_t *pair_map;     // first map entry of the pair
+    const void *map;             // per update: offset of the target row past pair_pos+1
+    const Seg *segs;
+    const Task *tasks;
+    const NormItem *norms;
+    unsigned long long *err;
+};
+
+struct MapBuildArgs {
+    const int64_t *lu_colptr;
+    const int32_t *lu_rowidx;
+    const int64_t *diag_pos;
+    const int32_t *pair_j;
+    const int32_t *pair_k;
+    const int64_t *pair_pos;
+    const int64_t *pair_map;
+    void *map;
+    int64_t npairs;
+    unsigned long long *err;
+};
+
+template <typename T>
+struct SolveArgs {
+    const T *lu;
+    const int64_t *diag_pos;
+    const int64_t *lrow_ptr;
+    const int32_t *lrow_col;
+    const int64_t *lrow_pos;
+    const int64_t *urow_ptr;
+    const int32_t *urow_col;
+    const int64_t *urow_pos;
+    int32_t n;
+};
+
+// launchers (kernels_factor.cu)
+template <typename T>
+cudaError_t launch_gather(T *lu, const double *aval, const int32_t *gsrc, int64_t nnz, cudaStream_t s);
+template <typename T>
+cudaError_t launch_level(const FactorArgs<T> &a, int map_bytes, int32_t t_begin, int32_t t_end,
+                         int32_t n_begin, int32_t n_end, int num_sms, cudaStream_t s);
+template <typename T>
+cudaError_t launch_pivot_check(const T *lu, const int64_t *diag_pos, int32_t n,
+                               unsigned long long *err, cudaStream_t s);
+cudaError_t launch_map_build(const MapBuildArgs &a, int map_bytes, cudaStream_t s);
+cudaError_t launch_reset_err(unsigned long long *err, cudaStream_t s);
+
+// launchers (kernels_solve.cu)
+template <typename T>
+cudaError_t launch_permute_in(T *y, const double *b, const int32_t *perm, int32_t n, int32_t nrhs,
+                              cudaStream_t s);
+template <typename T>
+cudaError_t launch_permute_out(double *x, const T *y, const int32_t *perm, int32_t n, int32_t nrhs,
+                               cudaStream_t s);
+template <typename T>
+cudaError_t launch_lsolve_level(const SolveArgs<T> &a, T *y, int32_t nrhs, const int32_t *rows,
+                                int32_t nrows, cudaStream_t s);
+template <typename T>
+cudaError_t launch_usolve_level(const SolveArgs<T> &a, T *y, int32_t nrhs, const int32_t *rows,
+                                int32_t nrows, cudaStream_t s);
+
+}  // namespace glu

@@ -1,0 +1,97 @@
+// glu_internal.h -- shared declarations of the library (not part of the ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/glu.h"
+
+namespace glu {
+
+// Item kinds of a level's work list.
+enum : int32_t { KIND_ROW = 0, KIND_SRC = 1 };
+
+// A segment of one (source j, target k) column pair: the rows t0..t1-1 of
+// L(:,j) (t counts from the first row below the diagonal).
+struct Seg {
+    int32_t pair;
+    int32_t t0;
+    int32_t t1;
+    int32_t spare;
+};
+
+// Normalization item: rows t0..t1-1 of L(:,j) divided by the pivot.
+struct NormItem {
+    int32_t col;
+    int32_t t0;
+    int32_t t1;
+    int32_t spare;
+};
+
+// A task of a level: segments [seg_begin, seg_end).
+//   KIND_ROW: one warp applies the segments one after the other (ascending
+//             source), lanes over the rows of each segment.
+//   KIND_SRC: one warp, lanes over segments; the products land in per-lane
+//             shared-memory accumulators for the 32 target positions
+//             base .. base+nslots-1, reduced in a fixed order at the end.
+struct Task {
+    int32_t seg_begin;
+    int32_t seg_end;
+    int32_t kind;
+    int32_t nslots;
+    int64_t base;
+    int64_t work;   // host only: number of updates (for ordering)
+};
+
+constexpr int SRC_SLOTS = 32;
+
+// Everything glu_analyze computes on the host.
+struct HostPlan {
+    int32_t n = 0;
+    int64_t nnz_a = 0;
+    // input copy (original numbering) and permutation
+    std::vector<int32_t> a_colptr, a_rowidx, perm, iperm;
+    // filled pattern of A_s = L + U - I (new numbering)
+    std::vector<int64_t> lu_colptr;
+    std::vector<int32_t> lu_rowidx;
+    std::vector<int64_t> diag_pos;
+    std::vector<int32_t> gsrc;          // per LU position: index into A's values, -1 = fill
+    int64_t max_col_len = 0;
+    // dependencies (Algorithm 4) and levels
+    std::vector<int64_t> dep_ptr;
+    std::vector<int32_t> dep_idx;
+    std::vector<int32_t> level_of, level_ptr, level_cols;
+    // update schedule
+    std::vector<int32_t> pair_j, pair_k;
+    std::vector<int64_t> pair_pos, pair_map;
+    int64_t n_updates = 0;
+    std::vector<Seg> segs;
+    std::vector<Task> tasks;
+    std::vector<int32_t> lvl_task_ptr;  // nlevels + 1
+    std::vector<NormItem> norms;
+    std::vector<int32_t> lvl_norm_ptr;  // nlevels + 2: level l's kernel runs [l, l+1); [L, L+1) is the final pass
+    std::vector<int8_t> level_mode;
+    // solve schedule (row views of L and U, levels)
+    std::vector<int64_t> lrow_ptr, urow_ptr;
+    std::vector<int32_t> lrow_col, urow_col;
+    std::vector<int64_t> lrow_pos, urow_pos;
+    std::vector<int32_t> fwd_ptr, fwd_rows, bwd_ptr, bwd_rows;
+    // A in compressed rows (original numbering) for residuals
+    std::vector<int64_t> acsr_ptr;
+    std::vector<int32_t> acsr_col;
+    std::vector<int64_t> acsr_src;
+    // statistics
+    int64_t nnz_l = 0, nnz_u = 0;
+    double flops = 0.0;
+    int32_t max_level_width = 0;
+    int32_t levels_by_mode[3] = {0, 0, 0};
+    double ms_symbolic = 0, ms_deps = 0, ms_levels = 0, ms_schedule = 0;
+};
+
+// Runs every host step of glu_analyze.  Returns a GLU_ code.
+int analyze_host(int32_t n, const int32_t *colptr, const int32_t *rowidx, const int32_t *perm,
+                 const glu_options &opt, HostPlan &P, std::string &why);
+
+}  // namespace glu

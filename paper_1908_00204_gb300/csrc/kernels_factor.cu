@@ -1,0 +1,245 @@
+// kernels_factor.cu -- numeric refactorization kernels (sm_103a).
+//
+// One launch per level runs that level's work list:
+//   * normalization items of the previous level: L(i,j) = A_s(i,j) / A_s(j,j)
+//     (Algorithm 2, the first inner loop), deferred by one level so that a
+//     level needs a single launch: column j is read raw while it is a source
+//     and divided afterwards;
+//   * update tasks: the submatrix update of Algorithm 5 / Eq. 3 for every
+//     (source j, target k) pair of the level, as
+//     A_s(i,k) -= A_s(i,j) * (A_s(j,k) / A_s(j,j))   for i in L(:,j).
+// Every target entry is written by exactly one warp per level (no atomics);
+// the order of the updates of an entry depends only on the pattern, so a
+// refactorization is deterministic run to run.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "glu_device.cuh"
+
+namespace glu {
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ T fma_t(T a, T b, T c);
+template <>
+__device__ __forceinline__ double fma_t<double>(double a, double b, double c) { return fma(a, b, c); }
+template <>
+__device__ __forceinline__ float fma_t<float>(float a, float b, float c) { return fmaf(a, b, c); }
+
+__device__ __forceinline__ void raise_err(unsigned long long *err, int32_t col, unsigned code) {
+    atomicMin(err, ((unsigned long long)(uint32_t)col << 8) | code);
+}
+
+// ----------------------------------------------------------------- gather
+template <typename T>
+__global__ void k_gather(T *__restrict__ lu, const double *__restrict__ aval,
+                         const int32_t *__restrict__ gsrc, int64_t nnz) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (; i < nnz; i += stride) {
+        int32_t s = gsrc[i];
+        lu[i] = s >= 0 ? (T)aval[s] : (T)0;
+    }
+}
+
+// ------------------------------------------------------------- level work
+template <typename T>
+__device__ __forceinline__ void norm_item(const FactorArgs<T> &a, const NormItem it, int lane) {
+    const int64_t dj = a.diag_pos[it.col];
+    const T d = a.lu[dj];
+    T *L = a.lu + dj + 1;
+    for (int32_t t = it.t0 + lane; t < it.t1; t += 32) L[t] = L[t] / d;
+}
+
+// KIND_ROW: the warp applies the segments in order; lanes over rows.
+template <typename T, typename M>
+__device__ __forceinline__ void row_task(const FactorArgs<T> &a, const Task &tk, int lane) {
+    const M *__restrict__ map = static_cast<const M *>(a.map);
+    for (int32_t s = tk.seg_begin; s < tk.seg_end; s++) {
+        const Seg sg = a.segs[s];
+        const int32_t j = a.pair_j[sg.pair];
+        const int64_t pos = a.pair_pos[sg.pair];
+        const int64_t mb = a.pair_map[sg.pair];
+        const int64_t dj = a.diag_pos[j];
+        const T f = a.lu[pos] / a.lu[dj];
+        const T *__restrict__ L = a.lu + dj + 1;
+        T *tgt = a.lu + pos + 1;
+        const M *__restrict__ mp = map + mb;
+        for (int32_t t = sg.t0 + lane; t < sg.t1; t += 32) {
+            const uint32_t off = mp[t];
+            tgt[off] = fma_t<T>(-L[t], f, tgt[off]);
+        }
+        __syncwarp();
+    }
+}
+
+// KIND_SRC: lanes over segments; lane l accumulates its products into row l
+// of a 32 x 33 shared-memory tile (slot = target position - base); then lane
+// s sums column s over the 32 lanes in order and applies it.
+template <typename T, typename M>
+__device__ __forceinline__ void src_task(const FactorArgs<T> &a, const Task &tk, int lane, T *acc) {
+    const M *__restrict__ map = static_cast<const M *>(a.map);
+    T *row = acc + lane * (SRC_SLOTS + 1);
+#pragma unroll
+    for (int s = 0; s < SRC_SLOTS; s++) row[s] = (T)0;
+    for (int32_t s = tk.seg_begin + lane; s < tk.seg_end; s += 32) {
+        const Seg sg = a.segs[s];
+        const int32_t j = a.pair_j[sg.pair];
+        const int64_t pos = a.pair_pos[sg.pair];
+        const int64_t mb = a.pair_map[sg.pair];
+        const int64_t dj = a.diag_pos[j];
+        const T f = a.lu[pos] / a.lu[dj];
+        const T *__restrict__ L = a.lu + dj + 1;
+        const M *__restrict__ mp = map + mb;
+        const int32_t rel = (int32_t)(pos + 1 - tk.base);
+        for (int32_t t = sg.t0; t < sg.t1; t++) {
+            const int32_t slot = rel + (int32_t)mp[t];
+            row[slot] = fma_t<T>(L[t], f, row[slot]);
+        }
+    }
+    __syncwarp();
+    if (lane < tk.nslots) {
+        T sum = (T)0;
+#pragma unroll 8
+        for (int l = 0; l < 32; l++) sum += acc[l * (SRC_SLOTS + 1) + lane];
+        a.lu[tk.base + lane] -= sum;
+    }
+    __syncwarp();
+}
+
+constexpr int LEVEL_WARPS = 4;
+
+template <typename T, typename M>
+__global__ void __launch_bounds__(LEVEL_WARPS * 32)
+k_level(const FactorArgs<T> a, int32_t t_begin, int32_t t_end, int32_t n_begin, int32_t n_end) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    T *acc = reinterpret_cast<T *>(smem_raw) + wib * (32 * (SRC_SLOTS + 1));
+    const int64_t nw = (int64_t)gridDim.x * LEVEL_WARPS;
+    const int64_t nn = n_end - n_begin;
+    const int64_t total = nn + (t_end - t_begin);
+    for (int64_t it = (int64_t)blockIdx.x * LEVEL_WARPS + wib; it < total; it += nw) {
+        if (it < nn) {
+            norm_item<T>(a, a.norms[n_begin + it], lane);
+        } else {
+            const Task tk = a.tasks[t_begin + (it - nn)];
+            if (tk.kind == KIND_ROW) row_task<T, M>(a, tk, lane);
+            else src_task<T, M>(a, tk, lane, acc);
+        }
+    }
+}
+
+// Final check of every pivot: zero or non-finite raises an error for the
+// smallest such column.
+template <typename T>
+__global__ void k_pivot_check(const T *__restrict__ lu, const int64_t *__restrict__ diag_pos, int32_t n,
+                              unsigned long long *err) {
+    int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const T d = lu[diag_pos[j]];
+    if (d == (T)0) raise_err(err, j, DEVERR_ZERO_PIVOT);
+    else if (!isfinite(d)) raise_err(err, j, DEVERR_NONFINITE);
+}
+
+__global__ void k_reset_err(unsigned long long *err) { *err = ERR_NONE; }
+
+// ---------------------------------------------------------------- map build
+// For every (j,k) pair and every row L(t,j), the offset of that row inside
+// column k past the position of U(j,k); a binary search over the rows of
+// column k below j.  Built once at analysis.
+template <typename M>
+__global__ void k_map_build(const MapBuildArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    M *map = static_cast<M *>(a.map);
+    for (int64_t p = w; p < a.npairs; p += nw) {
+        const int32_t j = a.pair_j[p];
+        const int32_t k = a.pair_k[p];
+        const int64_t pos = a.pair_pos[p];
+        const int64_t mb = a.pair_map[p];
+        const int64_t dj = a.diag_pos[j];
+        const int32_t lj = (int32_t)(a.lu_colptr[j + 1] - dj - 1);
+        const int32_t *rows = a.lu_rowidx + pos + 1;
+        const int64_t len = a.lu_colptr[k + 1] - pos - 1;
+        for (int32_t t = lane; t < lj; t += 32) {
+            const int32_t r = a.lu_rowidx[dj + 1 + t];
+            int64_t lo = 0, hi = len;
+            while (lo < hi) {
+                int64_t mid = (lo + hi) >> 1;
+                if (rows[mid] < r) lo = mid + 1;
+                else hi = mid;
+            }
+            if (lo >= len || rows[lo] != r) {
+                raise_err(a.err, k, DEVERR_INTERNAL);
+                lo = 0;
+            }
+            map[mb + t] = (M)lo;
+        }
+    }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_gather(T *lu, const double *aval, const int32_t *gsrc, int64_t nnz, cudaStream_t s) {
+    if (nnz == 0) return cudaSuccess;
+    int64_t blocks = (nnz + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_gather<T><<<(unsigned)blocks, 256, 0, s>>>(lu, aval, gsrc, nnz);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_level(const FactorArgs<T> &a, int map_bytes, int32_t t_begin, int32_t t_end,
+                         int32_t n_begin, int32_t n_end, int num_sms, cudaStream_t s) {
+    const int64_t items = (int64_t)(t_end - t_begin) + (n_end - n_begin);
+    if (items <= 0) return cudaSuccess;
+    int64_t blocks = (items + LEVEL_WARPS - 1) / LEVEL_WARPS;
+    const int64_t cap = (int64_t)num_sms * 8;
+    if (blocks > cap) blocks = cap;
+    const size_t smem = sizeof(T) * LEVEL_WARPS * 32 * (SRC_SLOTS + 1);
+    if (map_bytes == 2)
+        k_level<T, uint16_t><<<(unsigned)blocks, LEVEL_WARPS * 32, smem, s>>>(a, t_begin, t_end, n_begin, n_end);
+    else
+        k_level<T, uint32_t><<<(unsigned)blocks, LEVEL_WARPS * 32, smem, s>>>(a, t_begin, t_end, n_begin, n_end);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_pivot_check(const T *lu, const int64_t *diag_pos, int32_t n, unsigned long long *err,
+                               cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_pivot_check<T><<<(n + 255) / 256, 256, 0, s>>>(lu, diag_pos, n, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reset_err(unsigned long long *err, cudaStream_t s) {
+    k_reset_err<<<1, 1, 0, s>>>(err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_map_build(const MapBuildArgs &a, int map_bytes, cudaStream_t s) {
+    if (a.npairs == 0) return cudaSuccess;
+    int64_t blocks = (a.npairs * 32 + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    if (map_bytes == 2) k_map_build<uint16_t><<<(unsigned)blocks, 256, 0, s>>>(a);
+    else k_map_build<uint32_t><<<(unsigned)blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_gather<double>(double *, const double *, const int32_t *, int64_t, cudaStream_t);
+template cudaError_t launch_gather<float>(float *, const double *, const int32_t *, int64_t, cudaStream_t);
+template cudaError_t launch_level<double>(const FactorArgs<double> &, int, int32_t, int32_t, int32_t, int32_t,
+                                          int, cudaStream_t);
+template cudaError_t launch_level<float>(const FactorArgs<float> &, int, int32_t, int32_t, int32_t, int32_t,
+                                         int, cudaStream_t);
+template cudaError_t launch_pivot_check<double>(const double *, const int64_t *, int32_t, unsigned long long *,
+                                                cudaStream_t);
+template cudaError_t launch_pivot_check<float>(const float *, const int64_t *, int32_t, unsigned long long *,
+                                               cudaStream_t);
+
+}  // namespace glu
