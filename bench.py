@@ -1,0 +1,302 @@
+#!/usr/bin/env python
+"""Benchmark: FP64 numeric refactorization + solve of the 200k-unknown
+synthetic power-grid matrix (400x500 mesh, 64 supply nets, 2% controlled
+sources, nested-dissection order), one Newton-style step = new values ->
+glu_factor -> glu_solve (1 right-hand side).
+
+Prints one JSON line.  ``--impl reference`` times the CPU oracle (plain
+Gilbert-Peierls LU + solves) on the same workload instead.  Under torchrun
+every rank runs an independent replica on its own GPU (a single
+factorization does not shard); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = "mesh400x500_nets64"
+VALUE_SEEDS = list(range(1001, 1011))      # ten re-drawn value sets
+METRIC = "FP64 numeric refactor + solve throughput (n=200,064 synthetic power grid)"
+UNIT = "refactor+solve/s"
+FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 (derived in the design doc)
+L2_BYTES = 129 * 2**20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "200"], stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        self.out.flush()
+        try:
+            lines = open(self.out.name).read().strip().splitlines()
+        except OSError:
+            lines = []
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.out.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# -------------------------------------------------------------- CPU oracle
+def cpu_oracle_steps(m, values, b, min_seconds=10.0, max_reps=5):
+    """The oracle as it stands: single-threaded G/P factor + solves."""
+    import oracle
+    f = oracle.Factorization(m.n, m.colptr, m.rowidx, m.perm)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        f.factor(values[reps % len(values)])
+        f.solve(b)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds or reps >= max_reps:
+            break
+    return reps / el, reps, el
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for fn in ("kernels_factor.cu", "glu_device.cuh", "glu_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1908_00204_gb300", "csrc", fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(workload):
+    """DRAM bytes per refactorization's level sweep from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", f"k_level_fp64_{workload}.traffic.json")
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return d.get("dram_bytes_per_factor")
+
+
+# ------------------------------------------------------------------- arms
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    m = synth.make(args.workload, 1)
+    values = [m.values(s) for s in VALUE_SEEDS]
+    b = synth.rhs(m.n, args.nrhs, 7)
+    f = oracle.Factorization(m.n, m.colptr, m.rowidx, m.perm)
+    for w in range(args.warmup):
+        f.factor(values[w % len(values)])
+        f.solve(b)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        f.factor(values[k % len(values)])
+        f.solve(b)
+    el = time.perf_counter() - t0
+    v = args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "n": m.n, "nrhs": args.nrhs},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} full refactor+solve steps of the workload, single thread"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import paper_1908_00204_gb300 as g
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    g.build.build()
+    g.load_library()
+    dev = torch.device("cuda", local)
+
+    m = synth.make(args.workload, 1)
+    vals_host = [m.values(s) for s in VALUE_SEEDS]
+    b_host = synth.rhs(m.n, args.nrhs, 7)
+    t0 = time.perf_counter()
+    h = g.glu_analyze(m.n, m.colptr, m.rowidx, m.perm)
+    analyze_s = time.perf_counter() - t0
+    st = g.glu_get_stats(h)
+    stream = torch.cuda.current_stream(dev)
+    g.glu_set_stream(h, stream)
+    vals = [torch.from_numpy(v).to(dev) for v in vals_host]
+    b = torch.from_numpy(b_host).to(dev)
+    x = torch.empty_like(b)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    for w in range(max(args.warmup, 3)):
+        g.glu_factor(h, vals[w % len(vals)])
+        g.glu_solve(h, b, x)
+    g.glu_sync(h)
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = g.glu_get_stats(h)["kernel_launches"]
+    with ClockSampler(local) as clk:
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()                      # L2 flushed between steps (outside the events)
+            e0, e1, e2 = ev[k]
+            e0.record(stream)
+            g.glu_factor(h, vals[k % len(vals)])
+            e1.record(stream)
+            g.glu_solve(h, b, x)
+            e2.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+        if dist is not None:
+            dist.barrier()
+    g.glu_sync(h)
+    launches = g.glu_get_stats(h)["kernel_launches"] - launches0
+    clocks = clk.summary()
+    fac = [e0.elapsed_time(e1) for e0, e1, _ in ev]
+    sol = [e1.elapsed_time(e2) for _, e1, e2 in ev]
+    total_ms = float(sum(f + s for f, s in zip(fac, sol)))
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1e3)
+    fac_ms = float(np.mean(fac))
+    flops = st["flops"]
+    achieved = flops / (fac_ms * 1e-3) / 1e12
+
+    e2e = None
+    if not args.no_e2e:
+        vp = [torch.from_numpy(v).pin_memory() for v in vals_host]
+        bp = torch.from_numpy(b_host).pin_memory()
+        xp = torch.empty_like(bp).pin_memory()
+        g.glu_factor(h, vp[0].numpy())
+        g.glu_solve(h, bp.numpy(), xp.numpy())
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            g.glu_factor(h, vp[k % len(vp)].numpy())      # H2D of the values inside
+            g.glu_solve(h, bp.numpy(), xp.numpy())        # H2D of b, D2H of x inside
+        e2e_s = time.perf_counter() - t0
+        e2e = {"value": world * args.steps / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(m.nnz * 8 + b_host.size * 8),
+               "d2h_bytes_per_step": int(b_host.size * 8 + 2 * 8)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, reps, el = cpu_oracle_steps(m, vals_host, b_host)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{reps} full refactor+solve steps of the same workload ({el:.1f} s), single thread"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n": m.n, "nnz_a": m.nnz, "nnz_lu": st["nnz_lu"],
+                       "levels": st["nlevels"], "flops_per_factor": flops, "nrhs": args.nrhs,
+                       "value_sets": len(VALUE_SEEDS), "l2": "flushed between steps",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "refactor_ms": fac_ms, "solve_ms": float(np.mean(sol)),
+            "gflops_refactor": flops / (fac_ms * 1e-3) / 1e9,
+            "analyze_s": analyze_s, "wall_s_timed_loop": wall,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic_for(args.workload),
+                         "kernel": "k_level (FP64 level sweep of one refactorization)",
+                         "peak_source": "nominal GB300 FP64 rate (the measured peaks cover HBM and bf16 only)"},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

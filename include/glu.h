@@ -98,6 +98,7 @@ typedef struct glu_stats {
     int32_t max_level_width;
     int64_t device_bytes;     /* device memory held by the handle */
     double analyze_ms;        /* host wall time of glu_analyze */
+    int64_t kernel_launches;  /* CUDA kernels this handle has launched so far */
 } glu_stats;
 
 /* Fill every field of *opts with its default. */

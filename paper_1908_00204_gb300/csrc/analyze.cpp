@@ -343,18 +343,43 @@ void schedule(HostPlan &P, const glu_options &opt) {
             }
             std::sort(touched.begin(), touched.end());
             if (nsrc >= src_min) {
+                // Chunks reached by two or more segments become KIND_SRC
+                // tasks.  A chunk reached by one segment holds rows that no
+                // other source of this group updates: those segments need no
+                // ordering, so consecutive ones of a source merge and are
+                // packed into KIND_ROW tasks of about `piece` updates.
+                std::vector<Seg> priv;
                 for (int32_t ch : touched) {
-                    Task t{(int32_t)P.segs.size(), 0, KIND_SRC,
-                           (int32_t)std::min<int64_t>(SRC_SLOTS, clen - (int64_t)ch * SRC_SLOTS),
-                           c0 + (int64_t)ch * SRC_SLOTS, chunk_work[ch]};
-                    P.segs.insert(P.segs.end(), chunk_segs[ch].begin(), chunk_segs[ch].end());
-                    t.seg_end = (int32_t)P.segs.size();
-                    lvl_tasks.push_back(t);
-                    chunk_segs[ch].clear();
+                    std::vector<Seg> &cs = chunk_segs[ch];
+                    if (cs.size() >= 2) {
+                        Task t{(int32_t)P.segs.size(), 0, KIND_SRC,
+                               (int32_t)std::min<int64_t>(SRC_SLOTS, clen - (int64_t)ch * SRC_SLOTS),
+                               c0 + (int64_t)ch * SRC_SLOTS, chunk_work[ch]};
+                        P.segs.insert(P.segs.end(), cs.begin(), cs.end());
+                        t.seg_end = (int32_t)P.segs.size();
+                        lvl_tasks.push_back(t);
+                    } else {
+                        const Seg &sg = cs[0];
+                        if (!priv.empty() && priv.back().pair == sg.pair && priv.back().t1 == sg.t0)
+                            priv.back().t1 = sg.t1;
+                        else
+                            priv.push_back(sg);
+                    }
+                    cs.clear();
                     chunk_work[ch] = 0;
                 }
-            } else {
-                // few sources, much work: consecutive chunks merged into
+                size_t a = 0;
+                while (a < priv.size()) {
+                    Task t{(int32_t)P.segs.size(), 0, KIND_ROW, 0, 0, 0};
+                    while (a < priv.size() && (t.work == 0 || t.work + (priv[a].t1 - priv[a].t0) <= piece)) {
+                        t.work += priv[a].t1 - priv[a].t0;
+                        P.segs.push_back(priv[a]);
+                        a++;
+                    }
+                    t.seg_end = (int32_t)P.segs.size();
+                    lvl_tasks.push_back(t);
+                }
+            } else {                // few sources, much work: consecutive chunks merged into
                 // KIND_ROW pieces of about `piece` updates; inside a piece
                 // the segments of one source are contiguous in t, so they
                 // merge into one, kept in ascending source order.
@@ -443,6 +468,31 @@ void solve_levels(HostPlan &P) {
     };
     group(lf, nf, P.fwd_ptr, P.fwd_rows);
     group(lb, nb, P.bwd_ptr, P.bwd_rows);
+    // rows with more than SOLVE_CHUNK entries: their dot products are split
+    // into chunks, summed later in chunk order
+    auto items = [](const std::vector<int32_t> &ptr, const std::vector<int32_t> &rows,
+                    const std::vector<int64_t> &rptr, std::vector<SolveRow> &it, std::vector<SolveChunk> &ch,
+                    std::vector<int32_t> &chp) {
+        const size_t nlev = ptr.size() - 1;
+        it.clear();
+        ch.clear();
+        chp.assign(nlev + 1, 0);
+        for (size_t l = 0; l < nlev; l++) {
+            for (int32_t q = ptr[l]; q < ptr[l + 1]; q++) {
+                const int32_t i = rows[q];
+                const int64_t b = rptr[i], e = rptr[i + 1];
+                SolveRow r{i, (int32_t)ch.size(), (int32_t)ch.size(), 0};
+                if (e - b > SOLVE_CHUNK) {
+                    for (int64_t p = b; p < e; p += SOLVE_CHUNK) ch.push_back(SolveChunk{p, std::min(e, p + SOLVE_CHUNK)});
+                    r.ce = (int32_t)ch.size();
+                }
+                it.push_back(r);
+            }
+            chp[l + 1] = (int32_t)ch.size();
+        }
+    };
+    items(P.fwd_ptr, P.fwd_rows, P.lrow_ptr, P.fwd_items, P.fwd_chunks, P.fwd_chunk_ptr);
+    items(P.bwd_ptr, P.bwd_rows, P.urow_ptr, P.bwd_items, P.bwd_chunks, P.bwd_chunk_ptr);
 }
 
 }  // namespace
@@ -462,6 +512,8 @@ int analyze_host(int32_t n, const int32_t *colptr, const int32_t *rowidx, const 
         P.urow_ptr.assign(1, 0);
         P.fwd_ptr.assign(1, 0);
         P.bwd_ptr.assign(1, 0);
+        P.fwd_chunk_ptr.assign(1, 0);
+        P.bwd_chunk_ptr.assign(1, 0);
         P.acsr_ptr.assign(1, 0);
         return GLU_OK;
     }

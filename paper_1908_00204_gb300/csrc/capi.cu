@@ -41,14 +41,27 @@ struct glu_handle {
     int64_t *d_lrow_ptr = nullptr, *d_lrow_pos = nullptr, *d_urow_ptr = nullptr, *d_urow_pos = nullptr;
     int32_t *d_lrow_col = nullptr, *d_urow_col = nullptr;
     int32_t *d_fwd_rows = nullptr, *d_bwd_rows = nullptr, *d_perm = nullptr;
-    // solve scratch (grown on demand)
+    SolveRow *d_fwd_items = nullptr, *d_bwd_items = nullptr;
+    SolveChunk *d_fwd_chunks = nullptr, *d_bwd_chunks = nullptr;
+    // solve scratch (grown on demand): permuted vector, staging, partials
     double *d_work = nullptr;
     double *d_bstage = nullptr;
     double *d_xstage = nullptr;
+    double *d_partial = nullptr;
     int64_t work_elems = 0;
+    int32_t work_nrhs = 0;
+    // CUDA graphs of the factor and solve sequences (captured on cap_stream)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t fgraph = nullptr;
+    int64_t fgraph_launches = 0;
+    std::vector<std::pair<int32_t, cudaGraphExec_t>> sgraphs;
+    std::vector<int64_t> sgraph_launches;
+    // per-level timing diagnostic (GLU_LEVEL_TIMES=path)
+    std::string level_times_path;
     bool factored = false;
     int32_t err_col = -1;
     double analyze_ms = 0.0;
+    int64_t launches = 0;
     std::string why;
 };
 
@@ -64,6 +77,14 @@ int cuda_fail(glu_handle *h, cudaError_t e, const char *what) {
     do {                                                                 \
         cudaError_t e_ = (call);                                         \
         if (e_ != cudaSuccess) return cuda_fail(h, e_, #call);           \
+    } while (0)
+
+// a kernel launch through one of the launch_* helpers (counted)
+#define CKL(n_launched, call)                                            \
+    do {                                                                 \
+        cudaError_t e_ = (call);                                         \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call);           \
+        h->launches += (n_launched);                                     \
     } while (0)
 
 bool is_device_ptr(const void *p) {
@@ -97,17 +118,94 @@ cudaError_t upload(T *dst, const std::vector<T> &src) {
     return cudaMemcpy(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
 }
 
-int ensure_work(glu_handle *h, int64_t elems) {
-    if (elems <= h->work_elems) return GLU_OK;
+FactorArgs<double> fargs(glu_handle *h);
+SolveArgs<double> sargs(glu_handle *h);
+
+int ensure_work(glu_handle *h, int32_t nrhs) {
+    if (nrhs <= h->work_nrhs) return GLU_OK;
+    const int64_t elems = (int64_t)h->P.n * nrhs;
+    const int64_t nch = (int64_t)std::max(h->P.fwd_chunks.size(), h->P.bwd_chunks.size()) * nrhs;
+    // graphs captured with the old buffers are stale
+    for (auto &g : h->sgraphs) cudaGraphExecDestroy(g.second);
+    h->sgraphs.clear();
+    h->sgraph_launches.clear();
     cudaFree(h->d_work);
     cudaFree(h->d_bstage);
     cudaFree(h->d_xstage);
-    h->d_work = h->d_bstage = h->d_xstage = nullptr;
+    cudaFree(h->d_partial);
+    h->d_work = h->d_bstage = h->d_xstage = h->d_partial = nullptr;
     h->work_elems = 0;
+    h->work_nrhs = 0;
     CK(cudaMalloc(&h->d_work, elems * sizeof(double)));
     CK(cudaMalloc(&h->d_bstage, elems * sizeof(double)));
     CK(cudaMalloc(&h->d_xstage, elems * sizeof(double)));
+    CK(cudaMalloc(&h->d_partial, std::max<int64_t>(nch, 1) * sizeof(double)));
     h->work_elems = elems;
+    h->work_nrhs = nrhs;
+    return GLU_OK;
+}
+
+// The factor sequence: error reset, value gather, one kernel per level (the
+// last one only normalizes), pivot check.
+int enqueue_factor(glu_handle *h, const double *av, cudaStream_t st, std::vector<cudaEvent_t> *lev_events) {
+    HostPlan &P = h->P;
+    CKL(1, launch_reset_err(h->d_err, st));
+    CKL(P.lu_colptr[P.n] > 0, launch_gather<double>(h->d_lu, av, h->d_gsrc, P.lu_colptr[P.n], st));
+    FactorArgs<double> a = fargs(h);
+    const int32_t nl = (int32_t)P.level_ptr.size() - 1;
+    if (lev_events) CK(cudaEventRecord((*lev_events)[0], st));
+    for (int32_t l = 0; l <= nl; l++) {
+        int32_t tb = l < nl ? P.lvl_task_ptr[l] : 0, te = l < nl ? P.lvl_task_ptr[l + 1] : 0;
+        CKL((te - tb) + (P.lvl_norm_ptr[l + 1] - P.lvl_norm_ptr[l]) > 0,
+            launch_level<double>(a, h->map_bytes, tb, te, P.lvl_norm_ptr[l], P.lvl_norm_ptr[l + 1], h->num_sms, st));
+        if (lev_events) CK(cudaEventRecord((*lev_events)[l + 1], st));
+    }
+    CKL(P.n > 0, launch_pivot_check<double>(h->d_lu, h->d_diag, P.n, h->d_err, st));
+    return GLU_OK;
+}
+
+// The solve sequence from device b to device x.
+int enqueue_solve(glu_handle *h, const double *db, double *dx, int32_t nrhs, cudaStream_t st) {
+    HostPlan &P = h->P;
+    const int32_t n = P.n;
+    double *y = h->d_work;
+    CKL(1, launch_permute_in<double>(y, db, h->d_perm, n, nrhs, st));
+    SolveArgs<double> a = sargs(h);
+    int launched = 0;
+    for (size_t l = 0; l + 1 < P.fwd_ptr.size(); l++) {
+        CK(launch_solve_level<double>(a, false, y, nrhs, h->d_fwd_items + P.fwd_ptr[l], P.fwd_ptr[l + 1] - P.fwd_ptr[l],
+                                      h->d_fwd_chunks, P.fwd_chunk_ptr[l], P.fwd_chunk_ptr[l + 1], h->d_partial, st,
+                                      &launched));
+        h->launches += launched;
+    }
+    for (size_t l = 0; l + 1 < P.bwd_ptr.size(); l++) {
+        CK(launch_solve_level<double>(a, true, y, nrhs, h->d_bwd_items + P.bwd_ptr[l], P.bwd_ptr[l + 1] - P.bwd_ptr[l],
+                                      h->d_bwd_chunks, P.bwd_chunk_ptr[l], P.bwd_chunk_ptr[l + 1], h->d_partial, st,
+                                      &launched));
+        h->launches += launched;
+    }
+    CKL(1, launch_permute_out<double>(dx, y, h->d_perm, n, nrhs, st));
+    return GLU_OK;
+}
+
+// Capture `fn` (which enqueues on the given stream) into an executable graph.
+template <typename F>
+int capture(glu_handle *h, F &&fn, cudaGraphExec_t *exec, int64_t *launches) {
+    cudaGraph_t g = nullptr;
+    const int64_t before = h->launches;
+    CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = fn(h->cap_stream);
+    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+    if (rc != GLU_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+    *launches = h->launches - before;
+    h->launches = before;
     return GLU_OK;
 }
 
@@ -173,7 +271,9 @@ int upload_plan(glu_handle *h) {
            o_urc = c.take<int32_t>(P.urow_col.size()), o_urpos = c.take<int64_t>(P.urow_pos.size()),
            o_fwd = c.take<int32_t>(P.fwd_rows.size()), o_bwd = c.take<int32_t>(P.bwd_rows.size()),
            o_perm = c.take<int32_t>(n), o_pk = c.take<int32_t>(P.pair_k.size()),
-           o_lcp = c.take<int64_t>(n + 1), o_lri = c.take<int32_t>(nnz);
+           o_lcp = c.take<int64_t>(n + 1), o_lri = c.take<int32_t>(nnz),
+           o_fi = c.take<SolveRow>(P.fwd_items.size()), o_bi = c.take<SolveRow>(P.bwd_items.size()),
+           o_fc = c.take<SolveChunk>(P.fwd_chunks.size()), o_bc = c.take<SolveChunk>(P.bwd_chunks.size());
     h->arena_bytes = c.off + 256;
     CK(cudaMalloc(&h->arena, h->arena_bytes));
     char *A = h->arena;
@@ -197,6 +297,10 @@ int upload_plan(glu_handle *h) {
     h->d_fwd_rows = at<int32_t>(A, o_fwd);
     h->d_bwd_rows = at<int32_t>(A, o_bwd);
     h->d_perm = at<int32_t>(A, o_perm);
+    h->d_fwd_items = at<SolveRow>(A, o_fi);
+    h->d_bwd_items = at<SolveRow>(A, o_bi);
+    h->d_fwd_chunks = at<SolveChunk>(A, o_fc);
+    h->d_bwd_chunks = at<SolveChunk>(A, o_bc);
     int32_t *d_pair_k = at<int32_t>(A, o_pk);
     int64_t *d_lcp = at<int64_t>(A, o_lcp);
     int32_t *d_lri = at<int32_t>(A, o_lri);
@@ -218,6 +322,10 @@ int upload_plan(glu_handle *h) {
     CK(upload(h->d_bwd_rows, P.bwd_rows));
     CK(upload(h->d_perm, P.perm));
     CK(upload(d_pair_k, P.pair_k));
+    CK(upload(h->d_fwd_items, P.fwd_items));
+    CK(upload(h->d_bwd_items, P.bwd_items));
+    CK(upload(h->d_fwd_chunks, P.fwd_chunks));
+    CK(upload(h->d_bwd_chunks, P.bwd_chunks));
     CK(upload(d_lcp, P.lu_colptr));
     CK(upload(d_lri, P.lu_rowidx));
     // position map, built on the device
@@ -257,7 +365,7 @@ void glu_default_options(glu_options *o) {
     o->tail_threshold = 16;
     o->piece_updates = 2048;
     o->wide_threshold = 256;
-    o->use_graph = 0;
+    o->use_graph = 1;
     o->verbose = 0;
 }
 
@@ -286,6 +394,11 @@ int glu_analyze_opts(int32_t n, const int32_t *colptr, const int32_t *rowidx, co
     }
     if (h->opt.verbose) {
         const HostPlan &P = h->P;
+        int64_t cnt[2] = {0, 0}, sg[2] = {0, 0}, wk[2] = {0, 0};
+        for (const Task &t : P.tasks) { cnt[t.kind]++; sg[t.kind] += t.seg_end - t.seg_begin; wk[t.kind] += t.work; }
+        std::fprintf(stderr, "glu_analyze: ROW tasks %lld segs %lld updates %lld | SRC tasks %lld segs %lld updates %lld\n",
+                     (long long)cnt[0], (long long)sg[0], (long long)wk[0], (long long)cnt[1], (long long)sg[1],
+                     (long long)wk[1]);
         std::fprintf(stderr,
                      "glu_analyze: n=%d nnzA=%lld nnzLU=%lld levels=%d pairs=%zu updates=%lld tasks=%zu segs=%zu "
                      "flops=%.4g map=%dB  ms: symbolic %.1f deps %.1f levels %.1f schedule %.1f total %.1f\n",
@@ -301,6 +414,9 @@ int glu_analyze_opts(int32_t n, const int32_t *colptr, const int32_t *rowidx, co
     cudaError_t e = cudaGetDevice(&h->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e != cudaSuccess) { glu_destroy(h); return e == cudaErrorMemoryAllocation ? GLU_ERR_OOM : GLU_ERR_CUDA; }
+    e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { glu_destroy(h); return GLU_ERR_CUDA; }
+    if (const char *lt = std::getenv("GLU_LEVEL_TIMES")) h->level_times_path = lt;
     rc = upload_plan(h);
     if (rc != GLU_OK) {
         if (h->opt.verbose) std::fprintf(stderr, "glu_analyze: %s\n", h->why.c_str());
@@ -328,26 +444,48 @@ int glu_factor(glu_handle *h, const double *values) {
     if (P.nnz_a > 0 && !values) return GLU_ERR_INVALID;
     CK(cudaSetDevice(h->device));
     h->err_col = -1;
-    const double *av = values;
-    if (P.nnz_a > 0 && !is_device_ptr(values)) {
-        CK(cudaMemcpyAsync(h->d_aval, values, P.nnz_a * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-        av = h->d_aval;
+    const bool dev = P.nnz_a > 0 && is_device_ptr(values);
+    if (h->opt.use_graph) {
+        // the graph reads the values from the handle's staging buffer
+        if (P.nnz_a > 0)
+            CK(cudaMemcpyAsync(h->d_aval, values, P.nnz_a * sizeof(double),
+                               dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+        if (!h->fgraph) {
+            int rc = capture(h, [&](cudaStream_t st) { return enqueue_factor(h, h->d_aval, st, nullptr); },
+                             &h->fgraph, &h->fgraph_launches);
+            if (rc != GLU_OK) return rc;
+        }
+        CK(cudaGraphLaunch(h->fgraph, h->stream));
+        h->launches += h->fgraph_launches;
+    } else {
+        const double *av = values;
+        if (P.nnz_a > 0 && !dev) {
+            CK(cudaMemcpyAsync(h->d_aval, values, P.nnz_a * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+            av = h->d_aval;
+        }
+        if (!h->level_times_path.empty()) {
+            const size_t nev = P.level_ptr.size() + 1;
+            std::vector<cudaEvent_t> ev(nev);
+            for (auto &e : ev) CK(cudaEventCreate(&e));
+            int rc = enqueue_factor(h, av, h->stream, &ev);
+            if (rc != GLU_OK) return rc;
+            CK(cudaEventSynchronize(ev.back()));
+            if (FILE *fp = std::fopen(h->level_times_path.c_str(), "w")) {
+                for (size_t l = 0; l + 1 < nev; l++) {
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, ev[l], ev[l + 1]);
+                    std::fprintf(fp, "%zu %.6f\n", l, ms);
+                }
+                std::fclose(fp);
+            }
+            for (auto &e : ev) cudaEventDestroy(e);
+        } else {
+            int rc = enqueue_factor(h, av, h->stream, nullptr);
+            if (rc != GLU_OK) return rc;
+        }
     }
-    CK(launch_reset_err(h->d_err, h->stream));
-    CK(launch_gather<double>(h->d_lu, av, h->d_gsrc, P.lu_colptr[P.n], h->stream));
-    FactorArgs<double> a = fargs(h);
-    const int32_t nl = (int32_t)P.level_ptr.size() - 1;
-    for (int32_t l = 0; l <= nl; l++) {
-        int32_t tb = l < nl ? P.lvl_task_ptr[l] : 0, te = l < nl ? P.lvl_task_ptr[l + 1] : 0;
-        CK(launch_level<double>(a, h->map_bytes, tb, te, P.lvl_norm_ptr[l], P.lvl_norm_ptr[l + 1], h->num_sms,
-                                h->stream));
-    }
-    CK(launch_pivot_check<double>(h->d_lu, h->d_diag, P.n, h->d_err, h->stream));
     h->factored = true;
-    if (!is_device_ptr(values) && P.nnz_a > 0) {
-        // host input: the host buffer was staged; report errors now
-        return glu_sync(h);
-    }
+    if (P.nnz_a > 0 && !dev) return glu_sync(h);   // host input: report errors now
     return GLU_OK;
 }
 
@@ -356,12 +494,12 @@ int glu_sync(glu_handle *h) {
     if (h->opt.host_only) return GLU_OK;
     CK(cudaSetDevice(h->device));
     int rc = read_err(h);
-    if (rc != GLU_OK && rc != GLU_ERR_CUDA) h->factored = (rc == GLU_OK);
+    if (rc != GLU_OK && rc != GLU_ERR_CUDA) h->factored = false;
     return rc;
 }
 
 int glu_solve(glu_handle *h, const double *b, double *x, int32_t nrhs) {
-    if (!h || nrhs < 0) return GLU_ERR_INVALID;
+    if (!h || nrhs < 0 || h->opt.host_only) return GLU_ERR_INVALID;
     if (!h->factored) return GLU_ERR_NOT_FACTORED;
     HostPlan &P = h->P;
     const int32_t n = P.n;
@@ -369,25 +507,38 @@ int glu_solve(glu_handle *h, const double *b, double *x, int32_t nrhs) {
     if (elems == 0) return GLU_OK;
     if (!b || !x) return GLU_ERR_INVALID;
     CK(cudaSetDevice(h->device));
-    int rc = ensure_work(h, elems);
+    int rc = ensure_work(h, nrhs);
     if (rc != GLU_OK) return rc;
     const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
+    if (h->opt.use_graph) {
+        CK(cudaMemcpyAsync(h->d_bstage, b, elems * sizeof(double),
+                           bdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+        size_t gi = 0;
+        while (gi < h->sgraphs.size() && h->sgraphs[gi].first != nrhs) gi++;
+        if (gi == h->sgraphs.size()) {
+            cudaGraphExec_t ex = nullptr;
+            int64_t nl = 0;
+            rc = capture(h, [&](cudaStream_t st) { return enqueue_solve(h, h->d_bstage, h->d_xstage, nrhs, st); },
+                         &ex, &nl);
+            if (rc != GLU_OK) return rc;
+            h->sgraphs.emplace_back(nrhs, ex);
+            h->sgraph_launches.push_back(nl);
+        }
+        CK(cudaGraphLaunch(h->sgraphs[gi].second, h->stream));
+        h->launches += h->sgraph_launches[gi];
+        CK(cudaMemcpyAsync(x, h->d_xstage, elems * sizeof(double),
+                           xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+        if (!xdev) return glu_sync(h);
+        return GLU_OK;
+    }
     const double *db = b;
     if (!bdev) {
         CK(cudaMemcpyAsync(h->d_bstage, b, elems * sizeof(double), cudaMemcpyHostToDevice, h->stream));
         db = h->d_bstage;
     }
-    double *y = h->d_work;
-    CK(launch_permute_in<double>(y, db, h->d_perm, n, nrhs, h->stream));
-    SolveArgs<double> a = sargs(h);
-    for (size_t l = 0; l + 1 < P.fwd_ptr.size(); l++)
-        CK(launch_lsolve_level<double>(a, y, nrhs, h->d_fwd_rows + P.fwd_ptr[l], P.fwd_ptr[l + 1] - P.fwd_ptr[l],
-                                       h->stream));
-    for (size_t l = 0; l + 1 < P.bwd_ptr.size(); l++)
-        CK(launch_usolve_level<double>(a, y, nrhs, h->d_bwd_rows + P.bwd_ptr[l], P.bwd_ptr[l + 1] - P.bwd_ptr[l],
-                                       h->stream));
     double *dx = xdev ? x : h->d_xstage;
-    CK(launch_permute_out<double>(dx, y, h->d_perm, n, nrhs, h->stream));
+    rc = enqueue_solve(h, db, dx, nrhs, h->stream);
+    if (rc != GLU_OK) return rc;
     if (!xdev) {
         CK(cudaMemcpyAsync(x, dx, elems * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
         return glu_sync(h);
@@ -446,8 +597,11 @@ int glu_get_stats(const glu_handle *h, glu_stats *s) {
     s->solve_levels_fwd = (int32_t)P.fwd_ptr.size() - 1;
     s->solve_levels_bwd = (int32_t)P.bwd_ptr.size() - 1;
     s->max_level_width = P.max_level_width;
-    s->device_bytes = (int64_t)(h->arena_bytes + h->map_total + 3 * h->work_elems * sizeof(double));
+    s->device_bytes = (int64_t)(h->arena_bytes + h->map_total + 3 * h->work_elems * sizeof(double) +
+                                (int64_t)std::max(P.fwd_chunks.size(), P.bwd_chunks.size()) * h->work_nrhs *
+                                    sizeof(double));
     s->analyze_ms = h->analyze_ms;
+    s->kernel_launches = h->launches;
     return GLU_OK;
 }
 
@@ -466,11 +620,15 @@ void glu_destroy(glu_handle *h) {
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
+    if (h->fgraph) cudaGraphExecDestroy(h->fgraph);
+    for (auto &g : h->sgraphs) cudaGraphExecDestroy(g.second);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     cudaFree(h->arena);
     cudaFree(h->map);
     cudaFree(h->d_work);
     cudaFree(h->d_bstage);
     cudaFree(h->d_xstage);
+    cudaFree(h->d_partial);
     delete h;
 }
 

@@ -73,10 +73,8 @@ template <typename T>
 cudaError_t launch_permute_out(double *x, const T *y, const int32_t *perm, int32_t n, int32_t nrhs,
                                cudaStream_t s);
 template <typename T>
-cudaError_t launch_lsolve_level(const SolveArgs<T> &a, T *y, int32_t nrhs, const int32_t *rows,
-                                int32_t nrows, cudaStream_t s);
-template <typename T>
-cudaError_t launch_usolve_level(const SolveArgs<T> &a, T *y, int32_t nrhs, const int32_t *rows,
-                                int32_t nrows, cudaStream_t s);
+cudaError_t launch_solve_level(const SolveArgs<T> &a, bool backward, T *y, int32_t nrhs, const SolveRow *items,
+                               int32_t nitems, const SolveChunk *chunks, int32_t c0, int32_t c1, T *partial,
+                               cudaStream_t s, int *launched);
 
 }  // namespace glu

@@ -47,6 +47,20 @@ struct Task {
 
 constexpr int SRC_SLOTS = 32;
 
+// Triangular-solve work: a row of a solve level; rows with many entries get
+// their dot product split into chunks computed first (partials cb..ce-1).
+struct SolveRow {
+    int32_t row;
+    int32_t cb;
+    int32_t ce;
+    int32_t spare;
+};
+struct SolveChunk {
+    int64_t p0;
+    int64_t p1;
+};
+constexpr int64_t SOLVE_CHUNK = 512;
+
 // Everything glu_analyze computes on the host.
 struct HostPlan {
     int32_t n = 0;
@@ -78,6 +92,10 @@ struct HostPlan {
     std::vector<int32_t> lrow_col, urow_col;
     std::vector<int64_t> lrow_pos, urow_pos;
     std::vector<int32_t> fwd_ptr, fwd_rows, bwd_ptr, bwd_rows;
+    // per solve level: rows (with their chunk ranges) and chunks
+    std::vector<SolveRow> fwd_items, bwd_items;
+    std::vector<SolveChunk> fwd_chunks, bwd_chunks;
+    std::vector<int32_t> fwd_chunk_ptr, bwd_chunk_ptr;   // nlevels + 1
     // A in compressed rows (original numbering) for residuals
     std::vector<int64_t> acsr_ptr;
     std::vector<int32_t> acsr_col;

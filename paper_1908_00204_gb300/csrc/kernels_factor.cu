@@ -53,51 +53,134 @@ __device__ __forceinline__ void norm_item(const FactorArgs<T> &a, const NormItem
     for (int32_t t = it.t0 + lane; t < it.t1; t += 32) L[t] = L[t] / d;
 }
 
-// KIND_ROW: the warp applies the segments in order; lanes over rows.
+// Everything a segment needs, gathered once: the position of U(j,k), the
+// first map entry, the first row of L(:,j) and the multiplier
+// f = A_s(j,k) / A_s(j,j).  All of them are final when the level starts:
+// U(j,k) and the pivot of a source are only written by earlier levels.
+template <typename T>
+struct SegMeta {
+    int64_t pos;
+    int64_t mb;
+    int64_t lstart;
+    int32_t t0;
+    int32_t t1;
+    T f;
+};
+
+template <typename T>
+__device__ __forceinline__ void load_meta(const FactorArgs<T> &a, int32_t s, SegMeta<T> &m) {
+    const Seg sg = a.segs[s];
+    m.t0 = sg.t0;
+    m.t1 = sg.t1;
+    const int32_t j = a.pair_j[sg.pair];
+    m.pos = a.pair_pos[sg.pair];
+    m.mb = a.pair_map[sg.pair];
+    const int64_t dj = a.diag_pos[j];
+    m.lstart = dj + 1;
+    m.f = a.lu[m.pos] / a.lu[dj];
+}
+
+template <typename T>
+__device__ __forceinline__ SegMeta<T> shfl_meta(const SegMeta<T> &m, int src) {
+    SegMeta<T> o;
+    o.pos = __shfl_sync(0xffffffffu, m.pos, src);
+    o.mb = __shfl_sync(0xffffffffu, m.mb, src);
+    o.lstart = __shfl_sync(0xffffffffu, m.lstart, src);
+    o.t0 = __shfl_sync(0xffffffffu, m.t0, src);
+    o.t1 = __shfl_sync(0xffffffffu, m.t1, src);
+    o.f = __shfl_sync(0xffffffffu, m.f, src);
+    return o;
+}
+
+constexpr int ROW_UNROLL = 8;
+
+// Rows t0..t1-1 of one segment, lanes over rows.  Within a segment every row
+// hits a different target entry, so all loads of a batch go out before any
+// store.
+template <typename T, typename M>
+__device__ __forceinline__ void row_segment(T *__restrict__ lu, const M *__restrict__ map, const SegMeta<T> &m,
+                                            int lane) {
+    const M *__restrict__ mp = map + m.mb;
+    const T *__restrict__ L = lu + m.lstart;
+    T *tgt = lu + m.pos + 1;
+    for (int32_t tb = m.t0 + lane; tb < m.t1; tb += 32 * ROW_UNROLL) {
+        uint32_t off[ROW_UNROLL];
+        T lv[ROW_UNROLL], tv[ROW_UNROLL];
+#pragma unroll
+        for (int u = 0; u < ROW_UNROLL; u++) {
+            const int32_t t = tb + 32 * u;
+            if (t < m.t1) {
+                off[u] = mp[t];
+                lv[u] = L[t];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < ROW_UNROLL; u++)
+            if (tb + 32 * u < m.t1) tv[u] = tgt[off[u]];
+#pragma unroll
+        for (int u = 0; u < ROW_UNROLL; u++)
+            if (tb + 32 * u < m.t1) tgt[off[u]] = fma_t<T>(-lv[u], m.f, tv[u]);
+    }
+}
+
+// KIND_ROW: lanes fetch the metadata of up to 32 segments at once, then the
+// warp applies the segments in order (ascending source), lanes over rows.
 template <typename T, typename M>
 __device__ __forceinline__ void row_task(const FactorArgs<T> &a, const Task &tk, int lane) {
     const M *__restrict__ map = static_cast<const M *>(a.map);
-    for (int32_t s = tk.seg_begin; s < tk.seg_end; s++) {
-        const Seg sg = a.segs[s];
-        const int32_t j = a.pair_j[sg.pair];
-        const int64_t pos = a.pair_pos[sg.pair];
-        const int64_t mb = a.pair_map[sg.pair];
-        const int64_t dj = a.diag_pos[j];
-        const T f = a.lu[pos] / a.lu[dj];
-        const T *__restrict__ L = a.lu + dj + 1;
-        T *tgt = a.lu + pos + 1;
-        const M *__restrict__ mp = map + mb;
-        for (int32_t t = sg.t0 + lane; t < sg.t1; t += 32) {
-            const uint32_t off = mp[t];
-            tgt[off] = fma_t<T>(-L[t], f, tgt[off]);
+    for (int32_t base = tk.seg_begin; base < tk.seg_end; base += 32) {
+        const int cnt = min(32, tk.seg_end - base);
+        SegMeta<T> mine;
+        if (lane < cnt) load_meta<T>(a, base + lane, mine);
+        for (int q = 0; q < cnt; q++) {
+            const SegMeta<T> m = shfl_meta<T>(mine, q);
+            row_segment<T, M>(a.lu, map, m, lane);
+            __syncwarp();
         }
-        __syncwarp();
     }
 }
 
 // KIND_SRC: lanes over segments; lane l accumulates its products into row l
 // of a 32 x 33 shared-memory tile (slot = target position - base); then lane
-// s sums column s over the 32 lanes in order and applies it.
+// s sums column s over the 32 lanes in order and applies it.  The next
+// segment's metadata is fetched before the current one's rows.
 template <typename T, typename M>
-__device__ __forceinline__ void src_task(const FactorArgs<T> &a, const Task &tk, int lane, T *acc) {
+__device__ __forceinline__ void src_task(const FactorArgs<T> &a, const Task &tk, int lane, T *__restrict__ acc) {
     const M *__restrict__ map = static_cast<const M *>(a.map);
-    T *row = acc + lane * (SRC_SLOTS + 1);
+    T *__restrict__ row = acc + lane * (SRC_SLOTS + 1);
 #pragma unroll
     for (int s = 0; s < SRC_SLOTS; s++) row[s] = (T)0;
-    for (int32_t s = tk.seg_begin + lane; s < tk.seg_end; s += 32) {
-        const Seg sg = a.segs[s];
-        const int32_t j = a.pair_j[sg.pair];
-        const int64_t pos = a.pair_pos[sg.pair];
-        const int64_t mb = a.pair_map[sg.pair];
-        const int64_t dj = a.diag_pos[j];
-        const T f = a.lu[pos] / a.lu[dj];
-        const T *__restrict__ L = a.lu + dj + 1;
-        const M *__restrict__ mp = map + mb;
-        const int32_t rel = (int32_t)(pos + 1 - tk.base);
-        for (int32_t t = sg.t0; t < sg.t1; t++) {
-            const int32_t slot = rel + (int32_t)mp[t];
-            row[slot] = fma_t<T>(L[t], f, row[slot]);
+    int32_t s = tk.seg_begin + lane;
+    SegMeta<T> cur;
+    bool have = s < tk.seg_end;
+    if (have) load_meta<T>(a, s, cur);
+    while (have) {
+        SegMeta<T> nxt;
+        const int32_t s2 = s + 32;
+        const bool have2 = s2 < tk.seg_end;
+        if (have2) load_meta<T>(a, s2, nxt);
+        const M *__restrict__ mp = map + cur.mb;
+        const T *__restrict__ L = a.lu + cur.lstart;
+        const int32_t rel = (int32_t)(cur.pos + 1 - tk.base);
+        for (int32_t tb = cur.t0; tb < cur.t1; tb += ROW_UNROLL) {
+            uint32_t off[ROW_UNROLL];
+            T lv[ROW_UNROLL];
+#pragma unroll
+            for (int u = 0; u < ROW_UNROLL; u++)
+                if (tb + u < cur.t1) {
+                    off[u] = mp[tb + u];
+                    lv[u] = L[tb + u];
+                }
+#pragma unroll
+            for (int u = 0; u < ROW_UNROLL; u++)
+                if (tb + u < cur.t1) {
+                    const int32_t slot = rel + (int32_t)off[u];
+                    row[slot] = fma_t<T>(lv[u], cur.f, row[slot]);
+                }
         }
+        cur = nxt;
+        s = s2;
+        have = have2;
     }
     __syncwarp();
     if (lane < tk.nslots) {

@@ -41,7 +41,8 @@ class glu_stats(C.Structure):
                 ("nnz_l", C.c_int64), ("nnz_u", C.c_int64), ("n_deps", C.c_int64), ("n_pairs", C.c_int64),
                 ("n_updates", C.c_int64), ("flops", C.c_double), ("levels_by_mode", C.c_int32 * 3),
                 ("solve_levels_fwd", C.c_int32), ("solve_levels_bwd", C.c_int32),
-                ("max_level_width", C.c_int32), ("device_bytes", C.c_int64), ("analyze_ms", C.c_double)]
+                ("max_level_width", C.c_int32), ("device_bytes", C.c_int64), ("analyze_ms", C.c_double),
+                ("kernel_launches", C.c_int64)]
 
 
 _lock = threading.Lock()
