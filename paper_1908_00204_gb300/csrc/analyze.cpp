@@ -237,7 +237,7 @@ void levelize(HostPlan &P) {
 void schedule(HostPlan &P, const glu_options &opt) {
     const int32_t n = P.n;
     const int32_t nl = (int32_t)P.level_ptr.size() - 1;
-    const int64_t piece = opt.piece_updates > 0 ? opt.piece_updates : 2048;
+    const int64_t piece = opt.piece_updates > 0 ? opt.piece_updates : 1024;
     const int32_t src_min = 5;   // groups with more sources use KIND_SRC
     auto lstart = [&](int32_t j) { return P.diag_pos[j] + 1; };
     auto lcount = [&](int32_t j) { return (int32_t)(P.lu_colptr[j + 1] - P.diag_pos[j] - 1); };
@@ -277,14 +277,17 @@ void schedule(HostPlan &P, const glu_options &opt) {
     P.pair_map[npairs] = acc;
     P.n_updates = acc;
 
-    P.segs.clear();
+    std::vector<PSeg> psegs;
     P.tasks.clear();
     P.lvl_task_ptr.assign((size_t)nl + 1, 0);
+    P.lvl_row_ptr.assign((size_t)nl, 0);
+    P.lvl_lane_ptr.assign((size_t)nl, 0);
+    const int64_t lane_max = 64;    // tasks up to this many updates run on one lane
     P.level_mode.assign((size_t)nl, 0);
     std::vector<Task> lvl_tasks;
     // per-chunk scratch for splitting one group
     std::vector<int64_t> chunk_work;
-    std::vector<std::vector<Seg>> chunk_segs;
+    std::vector<std::vector<PSeg>> chunk_segs;
     std::vector<int32_t> touched;
 
     for (int32_t l = 0; l < nl; l++) {
@@ -299,10 +302,10 @@ void schedule(HostPlan &P, const glu_options &opt) {
             const int64_t nsrc = ge - g;
             if (nsrc < src_min && work <= piece) {
                 Task t{(int32_t)0, 0, KIND_ROW, 0, 0, work};
-                t.seg_begin = (int32_t)P.segs.size();
+                t.seg_begin = (int32_t)psegs.size();
                 for (int64_t q = g; q < ge; q++)
-                    P.segs.push_back(Seg{(int32_t)q, 0, lcount(P.pair_j[q]), 0});
-                t.seg_end = (int32_t)P.segs.size();
+                    psegs.push_back(PSeg{(int32_t)q, 0, lcount(P.pair_j[q]), 0});
+                t.seg_end = (int32_t)psegs.size();
                 lvl_tasks.push_back(t);
                 g = ge;
                 continue;
@@ -336,7 +339,7 @@ void schedule(HostPlan &P, const glu_options &opt) {
                         t1 = (int32_t)(std::lower_bound(L + t, L + lj, endrow) - L);
                     }
                     if (chunk_work[ch] == 0 && chunk_segs[ch].empty()) touched.push_back((int32_t)ch);
-                    chunk_segs[ch].push_back(Seg{(int32_t)q, t, t1, 0});
+                    chunk_segs[ch].push_back(PSeg{(int32_t)q, t, t1, 0});
                     chunk_work[ch] += t1 - t;
                     t = t1;
                 }
@@ -348,18 +351,18 @@ void schedule(HostPlan &P, const glu_options &opt) {
                 // other source of this group updates: those segments need no
                 // ordering, so consecutive ones of a source merge and are
                 // packed into KIND_ROW tasks of about `piece` updates.
-                std::vector<Seg> priv;
+                std::vector<PSeg> priv;
                 for (int32_t ch : touched) {
-                    std::vector<Seg> &cs = chunk_segs[ch];
+                    std::vector<PSeg> &cs = chunk_segs[ch];
                     if (cs.size() >= 2) {
-                        Task t{(int32_t)P.segs.size(), 0, KIND_SRC,
+                        Task t{(int32_t)psegs.size(), 0, KIND_SRC,
                                (int32_t)std::min<int64_t>(SRC_SLOTS, clen - (int64_t)ch * SRC_SLOTS),
                                c0 + (int64_t)ch * SRC_SLOTS, chunk_work[ch]};
-                        P.segs.insert(P.segs.end(), cs.begin(), cs.end());
-                        t.seg_end = (int32_t)P.segs.size();
+                        psegs.insert(psegs.end(), cs.begin(), cs.end());
+                        t.seg_end = (int32_t)psegs.size();
                         lvl_tasks.push_back(t);
                     } else {
-                        const Seg &sg = cs[0];
+                        const PSeg &sg = cs[0];
                         if (!priv.empty() && priv.back().pair == sg.pair && priv.back().t1 == sg.t0)
                             priv.back().t1 = sg.t1;
                         else
@@ -370,13 +373,13 @@ void schedule(HostPlan &P, const glu_options &opt) {
                 }
                 size_t a = 0;
                 while (a < priv.size()) {
-                    Task t{(int32_t)P.segs.size(), 0, KIND_ROW, 0, 0, 0};
+                    Task t{(int32_t)psegs.size(), 0, KIND_ROW, 0, 0, 0};
                     while (a < priv.size() && (t.work == 0 || t.work + (priv[a].t1 - priv[a].t0) <= piece)) {
                         t.work += priv[a].t1 - priv[a].t0;
-                        P.segs.push_back(priv[a]);
+                        psegs.push_back(priv[a]);
                         a++;
                     }
-                    t.seg_end = (int32_t)P.segs.size();
+                    t.seg_end = (int32_t)psegs.size();
                     lvl_tasks.push_back(t);
                 }
             } else {                // few sources, much work: consecutive chunks merged into
@@ -391,15 +394,15 @@ void schedule(HostPlan &P, const glu_options &opt) {
                         w += chunk_work[touched[b]];
                         b++;
                     }
-                    Task t{(int32_t)P.segs.size(), 0, KIND_ROW, 0, 0, w};
+                    Task t{(int32_t)psegs.size(), 0, KIND_ROW, 0, 0, w};
                     for (int64_t q = g; q < ge; q++) {
                         int32_t lo = INT32_MAX, hi = -1;
                         for (size_t c = a; c < b; c++)
-                            for (const Seg &s : chunk_segs[touched[c]])
+                            for (const PSeg &s : chunk_segs[touched[c]])
                                 if (s.pair == (int32_t)q) { lo = std::min(lo, s.t0); hi = std::max(hi, s.t1); }
-                        if (hi > lo) P.segs.push_back(Seg{(int32_t)q, lo, hi, 0});
+                        if (hi > lo) psegs.push_back(PSeg{(int32_t)q, lo, hi, 0});
                     }
-                    t.seg_end = (int32_t)P.segs.size();
+                    t.seg_end = (int32_t)psegs.size();
                     lvl_tasks.push_back(t);
                     a = b;
                 }
@@ -407,11 +410,30 @@ void schedule(HostPlan &P, const glu_options &opt) {
             }
             g = ge;
         }
-        // largest tasks first: warps take tasks in order
-        std::stable_sort(lvl_tasks.begin(), lvl_tasks.end(),
-                         [](const Task &a, const Task &b) { return a.work > b.work; });
+        // kinds: small tasks run on one lane; a chunk task with short
+        // segments keeps lanes over segments; the rest lanes over rows
+        for (Task &t : lvl_tasks) {
+            const int32_t ns = t.seg_end - t.seg_begin;
+            if (t.work <= lane_max) t.kind = KIND_LANE;
+            else if (t.kind == KIND_SRC && !(ns >= 16 && t.work <= 16 * (int64_t)ns)) t.kind = KIND_ROW;
+        }
+        // grouped by kind, largest first inside a kind: warps take tasks in order
+        std::stable_sort(lvl_tasks.begin(), lvl_tasks.end(), [](const Task &a, const Task &b) {
+            const int ka = a.kind == KIND_SRC ? 0 : (a.kind == KIND_ROW ? 1 : 2);
+            const int kb = b.kind == KIND_SRC ? 0 : (b.kind == KIND_ROW ? 1 : 2);
+            if (ka != kb) return ka < kb;
+            return a.work > b.work;
+        });
+        const int32_t tb = (int32_t)P.tasks.size();
         P.tasks.insert(P.tasks.end(), lvl_tasks.begin(), lvl_tasks.end());
         P.lvl_task_ptr[l + 1] = (int32_t)P.tasks.size();
+        int32_t r = tb, ln = tb;
+        for (int32_t q = tb; q < P.lvl_task_ptr[l + 1]; q++) {
+            if (P.tasks[q].kind == KIND_SRC) { r = q + 1; ln = q + 1; }
+            else if (P.tasks[q].kind == KIND_ROW) ln = q + 1;
+        }
+        P.lvl_row_ptr[l] = r;
+        P.lvl_lane_ptr[l] = ln;
         const int32_t width = P.level_ptr[l + 1] - P.level_ptr[l];
         const int32_t tail = opt.tail_threshold > 0 ? opt.tail_threshold : 16;
         const int32_t wide = opt.wide_threshold > 0 ? opt.wide_threshold : 256;
@@ -419,6 +441,18 @@ void schedule(HostPlan &P, const glu_options &opt) {
         if (opt.mode_force >= 0 && opt.mode_force <= 2) mode = (int8_t)opt.mode_force;
         P.level_mode[l] = mode;
         P.levels_by_mode[mode]++;
+    }
+
+    // flatten the segments into self-contained records
+    P.segs.resize(psegs.size());
+    for (size_t q = 0; q < psegs.size(); q++) {
+        const PSeg &ps = psegs[q];
+        Seg &sg = P.segs[q];
+        sg.pos = P.pair_pos[ps.pair];
+        sg.dj = P.diag_pos[P.pair_j[ps.pair]];
+        sg.mb = P.pair_map[ps.pair];
+        sg.t0 = ps.t0;
+        sg.t1 = ps.t1;
     }
 
     // normalization items: level l's columns run in level l+1's kernel; the

@@ -155,9 +155,14 @@ int enqueue_factor(glu_handle *h, const double *av, cudaStream_t st, std::vector
     const int32_t nl = (int32_t)P.level_ptr.size() - 1;
     if (lev_events) CK(cudaEventRecord((*lev_events)[0], st));
     for (int32_t l = 0; l <= nl; l++) {
-        int32_t tb = l < nl ? P.lvl_task_ptr[l] : 0, te = l < nl ? P.lvl_task_ptr[l + 1] : 0;
-        CKL((te - tb) + (P.lvl_norm_ptr[l + 1] - P.lvl_norm_ptr[l]) > 0,
-            launch_level<double>(a, h->map_bytes, tb, te, P.lvl_norm_ptr[l], P.lvl_norm_ptr[l + 1], h->num_sms, st));
+        LevelRange r;
+        r.t_begin = l < nl ? P.lvl_task_ptr[l] : 0;
+        r.row_begin = l < nl ? P.lvl_row_ptr[l] : 0;
+        r.lane_begin = l < nl ? P.lvl_lane_ptr[l] : 0;
+        r.t_end = l < nl ? P.lvl_task_ptr[l + 1] : 0;
+        r.n_begin = P.lvl_norm_ptr[l];
+        r.n_end = P.lvl_norm_ptr[l + 1];
+        CKL((r.t_end - r.t_begin) + (r.n_end - r.n_begin) > 0, launch_level<double>(a, h->map_bytes, r, h->num_sms, st));
         if (lev_events) CK(cudaEventRecord((*lev_events)[l + 1], st));
     }
     CKL(P.n > 0, launch_pivot_check<double>(h->d_lu, h->d_diag, P.n, h->d_err, st));
@@ -231,9 +236,6 @@ FactorArgs<double> fargs(glu_handle *h) {
     FactorArgs<double> a;
     a.lu = h->d_lu;
     a.diag_pos = h->d_diag;
-    a.pair_j = h->d_pair_j;
-    a.pair_pos = h->d_pair_pos;
-    a.pair_map = h->d_pair_map;
     a.map = h->map;
     a.segs = h->d_segs;
     a.tasks = h->d_tasks;
@@ -394,17 +396,41 @@ int glu_analyze_opts(int32_t n, const int32_t *colptr, const int32_t *rowidx, co
     }
     if (h->opt.verbose) {
         const HostPlan &P = h->P;
-        int64_t cnt[2] = {0, 0}, sg[2] = {0, 0}, wk[2] = {0, 0};
+        int64_t cnt[3] = {0, 0, 0}, sg[3] = {0, 0, 0}, wk[3] = {0, 0, 0};
         for (const Task &t : P.tasks) { cnt[t.kind]++; sg[t.kind] += t.seg_end - t.seg_begin; wk[t.kind] += t.work; }
-        std::fprintf(stderr, "glu_analyze: ROW tasks %lld segs %lld updates %lld | SRC tasks %lld segs %lld updates %lld\n",
+        std::fprintf(stderr, "glu_analyze: ROW tasks %lld segs %lld updates %lld | SRC tasks %lld segs %lld updates %lld"
+                     " | LANE tasks %lld segs %lld updates %lld\n",
                      (long long)cnt[0], (long long)sg[0], (long long)wk[0], (long long)cnt[1], (long long)sg[1],
-                     (long long)wk[1]);
+                     (long long)wk[1], (long long)cnt[2], (long long)sg[2], (long long)wk[2]);
         std::fprintf(stderr,
                      "glu_analyze: n=%d nnzA=%lld nnzLU=%lld levels=%d pairs=%zu updates=%lld tasks=%zu segs=%zu "
                      "flops=%.4g map=%dB  ms: symbolic %.1f deps %.1f levels %.1f schedule %.1f total %.1f\n",
                      P.n, (long long)P.nnz_a, (long long)P.lu_colptr[P.n], (int)P.level_ptr.size() - 1,
                      P.pair_j.size(), (long long)P.n_updates, P.tasks.size(), P.segs.size(), P.flops,
                      (P.max_col_len <= 65536) ? 2 : 4, P.ms_symbolic, P.ms_deps, P.ms_levels, P.ms_schedule, std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
+    }
+    if (const char *dump = std::getenv("GLU_DUMP_SCHEDULE")) {
+        // per level: width, ROW tasks/segs/updates, SRC tasks/segs/updates,
+        // largest task (updates, segments)
+        if (FILE *fp = std::fopen(dump, "w")) {
+            const HostPlan &P = h->P;
+            for (size_t l = 0; l + 1 < P.level_ptr.size(); l++) {
+                int64_t c[3] = {0, 0, 0}, sg[3] = {0, 0, 0}, wk[3] = {0, 0, 0}, mw = 0, ms = 0;
+                for (int32_t t = P.lvl_task_ptr[l]; t < P.lvl_task_ptr[l + 1]; t++) {
+                    const Task &tk = P.tasks[t];
+                    c[tk.kind]++;
+                    sg[tk.kind] += tk.seg_end - tk.seg_begin;
+                    wk[tk.kind] += tk.work;
+                    mw = std::max<int64_t>(mw, tk.work);
+                    ms = std::max<int64_t>(ms, tk.seg_end - tk.seg_begin);
+                }
+                std::fprintf(fp, "%zu %d %lld %lld %lld %lld %lld %lld %lld %lld %lld %lld %lld\n", l,
+                             P.level_ptr[l + 1] - P.level_ptr[l], (long long)c[0], (long long)sg[0],
+                             (long long)wk[0], (long long)c[1], (long long)sg[1], (long long)wk[1], (long long)c[2],
+                             (long long)sg[2], (long long)wk[2], (long long)mw, (long long)ms);
+            }
+            std::fclose(fp);
+        }
     }
     if (h->opt.host_only) {
         h->analyze_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

@@ -13,13 +13,16 @@ namespace glu {
 constexpr unsigned long long ERR_NONE = ~0ull;
 enum : unsigned { DEVERR_ZERO_PIVOT = 1, DEVERR_NONFINITE = 2, DEVERR_TIMEOUT = 3, DEVERR_INTERNAL = 4 };
 
+// The work list of one level (indices into tasks / norms).
+struct LevelRange {
+    int32_t t_begin, row_begin, lane_begin, t_end;
+    int32_t n_begin, n_end;
+};
+
 template <typename T>
 struct FactorArgs {
     T *lu;                       // values over the filled pattern
     const int64_t *diag_pos;     // n
-    const int32_t *pair_j;       // source column of each (j,k) pair
-    const int64_t *pair_pos;     // position of U(j,k)
-    const int64_t *pair_map;     // first map entry of the pair
     const void *map;             // per update: offset of the target row past pair_pos+1
     const Seg *segs;
     const Task *tasks;
@@ -57,8 +60,7 @@ struct SolveArgs {
 template <typename T>
 cudaError_t launch_gather(T *lu, const double *aval, const int32_t *gsrc, int64_t nnz, cudaStream_t s);
 template <typename T>
-cudaError_t launch_level(const FactorArgs<T> &a, int map_bytes, int32_t t_begin, int32_t t_end,
-                         int32_t n_begin, int32_t n_end, int num_sms, cudaStream_t s);
+cudaError_t launch_level(const FactorArgs<T> &a, int map_bytes, const LevelRange &r, int num_sms, cudaStream_t s);
 template <typename T>
 cudaError_t launch_pivot_check(const T *lu, const int64_t *diag_pos, int32_t n,
                                unsigned long long *err, cudaStream_t s);

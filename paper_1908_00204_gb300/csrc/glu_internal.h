@@ -10,12 +10,27 @@
 
 namespace glu {
 
-// Item kinds of a level's work list.
-enum : int32_t { KIND_ROW = 0, KIND_SRC = 1 };
+// Task kinds of a level's work list.
+//   KIND_SRC:  many short segments on one 32-position chunk: lanes over
+//              segments, shared-memory accumulators, fixed-order reduction;
+//   KIND_ROW:  a warp applies the segments in order, lanes over rows;
+//   KIND_LANE: a small task run start to finish by a single lane.
+enum : int32_t { KIND_ROW = 0, KIND_SRC = 1, KIND_LANE = 2 };
 
-// A segment of one (source j, target k) column pair: the rows t0..t1-1 of
-// L(:,j) (t counts from the first row below the diagonal).
-struct Seg {
+// A segment of one (source j, target k) column pair: rows t0..t1-1 of L(:,j)
+// (t counts from the first row below the diagonal), with everything needed
+// to apply it in one record: pos = position of U(j,k), dj = position of the
+// pivot of j, mb = the pair's first position-map entry.
+struct alignas(16) Seg {
+    int64_t pos;
+    int64_t dj;
+    int64_t mb;
+    int32_t t0;
+    int32_t t1;
+};
+
+// Scheduling-time segment (pair index + row range).
+struct PSeg {
     int32_t pair;
     int32_t t0;
     int32_t t1;
@@ -84,6 +99,9 @@ struct HostPlan {
     std::vector<Seg> segs;
     std::vector<Task> tasks;
     std::vector<int32_t> lvl_task_ptr;  // nlevels + 1
+    // inside level l: [lvl_task_ptr[l], lvl_row_ptr[l]) KIND_SRC,
+    // [lvl_row_ptr[l], lvl_lane_ptr[l]) KIND_ROW, [lvl_lane_ptr[l], lvl_task_ptr[l+1]) KIND_LANE
+    std::vector<int32_t> lvl_row_ptr, lvl_lane_ptr;
     std::vector<NormItem> norms;
     std::vector<int32_t> lvl_norm_ptr;  // nlevels + 2: level l's kernel runs [l, l+1); [L, L+1) is the final pass
     std::vector<int8_t> level_mode;

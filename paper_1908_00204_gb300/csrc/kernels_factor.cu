@@ -69,13 +69,13 @@ struct SegMeta {
 
 template <typename T>
 __device__ __forceinline__ void load_meta(const FactorArgs<T> &a, int32_t s, SegMeta<T> &m) {
-    const Seg sg = a.segs[s];
-    m.t0 = sg.t0;
-    m.t1 = sg.t1;
-    const int32_t j = a.pair_j[sg.pair];
-    m.pos = a.pair_pos[sg.pair];
-    m.mb = a.pair_map[sg.pair];
-    const int64_t dj = a.diag_pos[j];
+    const int4 *r = reinterpret_cast<const int4 *>(a.segs + s);
+    const int4 v0 = r[0], v1 = r[1];
+    m.pos = ((int64_t)(uint32_t)v0.y << 32) | (uint32_t)v0.x;
+    const int64_t dj = ((int64_t)(uint32_t)v0.w << 32) | (uint32_t)v0.z;
+    m.mb = ((int64_t)(uint32_t)v1.y << 32) | (uint32_t)v1.x;
+    m.t0 = v1.z;
+    m.t1 = v1.w;
     m.lstart = dj + 1;
     m.f = a.lu[m.pos] / a.lu[dj];
 }
@@ -192,26 +192,72 @@ __device__ __forceinline__ void src_task(const FactorArgs<T> &a, const Task &tk,
     __syncwarp();
 }
 
+// KIND_LANE: one lane applies the task's segments in order, rows batched.
+template <typename T, typename M>
+__device__ __forceinline__ void lane_task(const FactorArgs<T> &a, const Task &tk) {
+    const M *__restrict__ map = static_cast<const M *>(a.map);
+    for (int32_t s = tk.seg_begin; s < tk.seg_end; s++) {
+        SegMeta<T> m;
+        load_meta<T>(a, s, m);
+        const M *__restrict__ mp = map + m.mb;
+        const T *__restrict__ L = a.lu + m.lstart;
+        T *tgt = a.lu + m.pos + 1;
+        for (int32_t tb = m.t0; tb < m.t1; tb += ROW_UNROLL) {
+            uint32_t off[ROW_UNROLL];
+            T lv[ROW_UNROLL], tv[ROW_UNROLL];
+#pragma unroll
+            for (int u = 0; u < ROW_UNROLL; u++)
+                if (tb + u < m.t1) {
+                    off[u] = mp[tb + u];
+                    lv[u] = L[tb + u];
+                }
+#pragma unroll
+            for (int u = 0; u < ROW_UNROLL; u++)
+                if (tb + u < m.t1) tv[u] = tgt[off[u]];
+#pragma unroll
+            for (int u = 0; u < ROW_UNROLL; u++)
+                if (tb + u < m.t1) tgt[off[u]] = fma_t<T>(-lv[u], m.f, tv[u]);
+        }
+    }
+}
+
 constexpr int LEVEL_WARPS = 4;
 
+// One level.  Work items, in order: normalization items, KIND_SRC tasks and
+// KIND_ROW tasks (one warp each), then KIND_LANE tasks, 32 per warp.
 template <typename T, typename M>
 __global__ void __launch_bounds__(LEVEL_WARPS * 32)
-k_level(const FactorArgs<T> a, int32_t t_begin, int32_t t_end, int32_t n_begin, int32_t n_end) {
+k_level(const FactorArgs<T> a, LevelRange r) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     T *acc = reinterpret_cast<T *>(smem_raw) + wib * (32 * (SRC_SLOTS + 1));
     const int64_t nw = (int64_t)gridDim.x * LEVEL_WARPS;
-    const int64_t nn = n_end - n_begin;
-    const int64_t total = nn + (t_end - t_begin);
+    const int64_t nn = r.n_end - r.n_begin;
+    const int64_t nsrc = r.row_begin - r.t_begin;
+    const int64_t nrow = r.lane_begin - r.row_begin;
+    const int64_t nlane = r.t_end - r.lane_begin;
+    const int64_t total = nn + nsrc + nrow + (nlane + 31) / 32;
     for (int64_t it = (int64_t)blockIdx.x * LEVEL_WARPS + wib; it < total; it += nw) {
-        if (it < nn) {
-            norm_item<T>(a, a.norms[n_begin + it], lane);
-        } else {
-            const Task tk = a.tasks[t_begin + (it - nn)];
-            if (tk.kind == KIND_ROW) row_task<T, M>(a, tk, lane);
-            else src_task<T, M>(a, tk, lane, acc);
+        int64_t k = it;
+        if (k < nn) {
+            norm_item<T>(a, a.norms[r.n_begin + k], lane);
+            continue;
         }
+        k -= nn;
+        if (k < nsrc) {
+            src_task<T, M>(a, a.tasks[r.t_begin + k], lane, acc);
+            continue;
+        }
+        k -= nsrc;
+        if (k < nrow) {
+            row_task<T, M>(a, a.tasks[r.row_begin + k], lane);
+            continue;
+        }
+        k -= nrow;
+        const int64_t q = r.lane_begin + k * 32 + lane;
+        if (q < r.t_end) lane_task<T, M>(a, a.tasks[q]);
+        __syncwarp();
     }
 }
 
@@ -277,18 +323,18 @@ cudaError_t launch_gather(T *lu, const double *aval, const int32_t *gsrc, int64_
 }
 
 template <typename T>
-cudaError_t launch_level(const FactorArgs<T> &a, int map_bytes, int32_t t_begin, int32_t t_end,
-                         int32_t n_begin, int32_t n_end, int num_sms, cudaStream_t s) {
-    const int64_t items = (int64_t)(t_end - t_begin) + (n_end - n_begin);
+cudaError_t launch_level(const FactorArgs<T> &a, int map_bytes, const LevelRange &r, int num_sms, cudaStream_t s) {
+    const int64_t items = (int64_t)(r.lane_begin - r.t_begin) + (r.t_end - r.lane_begin + 31) / 32 +
+                          (r.n_end - r.n_begin);
     if (items <= 0) return cudaSuccess;
     int64_t blocks = (items + LEVEL_WARPS - 1) / LEVEL_WARPS;
     const int64_t cap = (int64_t)num_sms * 8;
     if (blocks > cap) blocks = cap;
     const size_t smem = sizeof(T) * LEVEL_WARPS * 32 * (SRC_SLOTS + 1);
     if (map_bytes == 2)
-        k_level<T, uint16_t><<<(unsigned)blocks, LEVEL_WARPS * 32, smem, s>>>(a, t_begin, t_end, n_begin, n_end);
+        k_level<T, uint16_t><<<(unsigned)blocks, LEVEL_WARPS * 32, smem, s>>>(a, r);
     else
-        k_level<T, uint32_t><<<(unsigned)blocks, LEVEL_WARPS * 32, smem, s>>>(a, t_begin, t_end, n_begin, n_end);
+        k_level<T, uint32_t><<<(unsigned)blocks, LEVEL_WARPS * 32, smem, s>>>(a, r);
     return cudaGetLastError();
 }
 
@@ -316,10 +362,8 @@ cudaError_t launch_map_build(const MapBuildArgs &a, int map_bytes, cudaStream_t 
 
 template cudaError_t launch_gather<double>(double *, const double *, const int32_t *, int64_t, cudaStream_t);
 template cudaError_t launch_gather<float>(float *, const double *, const int32_t *, int64_t, cudaStream_t);
-template cudaError_t launch_level<double>(const FactorArgs<double> &, int, int32_t, int32_t, int32_t, int32_t,
-                                          int, cudaStream_t);
-template cudaError_t launch_level<float>(const FactorArgs<float> &, int, int32_t, int32_t, int32_t, int32_t,
-                                         int, cudaStream_t);
+template cudaError_t launch_level<double>(const FactorArgs<double> &, int, const LevelRange &, int, cudaStream_t);
+template cudaError_t launch_level<float>(const FactorArgs<float> &, int, const LevelRange &, int, cudaStream_t);
 template cudaError_t launch_pivot_check<double>(const double *, const int64_t *, int32_t, unsigned long long *,
                                                 cudaStream_t);
 template cudaError_t launch_pivot_check<float>(const float *, const int64_t *, int32_t, unsigned long long *,
