@@ -371,10 +371,12 @@ void schedule(HostPlan &P, const glu_options &opt) {
                     cs.clear();
                     chunk_work[ch] = 0;
                 }
+                // (private segments are independent: small packs run on one
+                // lane each, a large segment alone on a warp)
                 size_t a = 0;
                 while (a < priv.size()) {
                     Task t{(int32_t)psegs.size(), 0, KIND_ROW, 0, 0, 0};
-                    while (a < priv.size() && (t.work == 0 || t.work + (priv[a].t1 - priv[a].t0) <= piece)) {
+                    while (a < priv.size() && (t.work == 0 || t.work + (priv[a].t1 - priv[a].t0) <= lane_max)) {
                         t.work += priv[a].t1 - priv[a].t0;
                         psegs.push_back(priv[a]);
                         a++;
@@ -412,10 +414,12 @@ void schedule(HostPlan &P, const glu_options &opt) {
         }
         // kinds: small tasks run on one lane; a chunk task with short
         // segments keeps lanes over segments; the rest lanes over rows
+        // (a chunk task's segments hold at most 32 rows each, so lanes over
+        // rows would leave most lanes idle and pay one round trip per segment)
         for (Task &t : lvl_tasks) {
             const int32_t ns = t.seg_end - t.seg_begin;
             if (t.work <= lane_max) t.kind = KIND_LANE;
-            else if (t.kind == KIND_SRC && !(ns >= 16 && t.work <= 16 * (int64_t)ns)) t.kind = KIND_ROW;
+            else if (t.kind == KIND_SRC && ns < 4) t.kind = KIND_ROW;
         }
         // grouped by kind, largest first inside a kind: warps take tasks in order
         std::stable_sort(lvl_tasks.begin(), lvl_tasks.end(), [](const Task &a, const Task &b) {
