@@ -376,7 +376,9 @@ void schedule(HostPlan &P, const glu_options &opt) {
                 size_t a = 0;
                 while (a < priv.size()) {
                     Task t{(int32_t)psegs.size(), 0, KIND_ROW, 0, 0, 0};
-                    while (a < priv.size() && (t.work == 0 || t.work + (priv[a].t1 - priv[a].t0) <= lane_max)) {
+                    while (a < priv.size() &&
+                           (t.work == 0 || (t.work + (priv[a].t1 - priv[a].t0) <= lane_max &&
+                                            (int32_t)psegs.size() - t.seg_begin < 2))) {
                         t.work += priv[a].t1 - priv[a].t0;
                         psegs.push_back(priv[a]);
                         a++;
@@ -416,10 +418,13 @@ void schedule(HostPlan &P, const glu_options &opt) {
         // segments keeps lanes over segments; the rest lanes over rows
         // (a chunk task's segments hold at most 32 rows each, so lanes over
         // rows would leave most lanes idle and pay one round trip per segment)
+        // The level's time is the longest serial chain of one work item, and
+        // every segment applied in sequence adds a few dependent memory round
+        // trips, so a lane task holds at most 4 segments.
         for (Task &t : lvl_tasks) {
             const int32_t ns = t.seg_end - t.seg_begin;
-            if (t.work <= lane_max) t.kind = KIND_LANE;
-            else if (t.kind == KIND_SRC && ns < 4) t.kind = KIND_ROW;
+            if (t.kind == KIND_SRC && ns >= 4) continue;
+            t.kind = (t.work <= lane_max && ns <= 4) ? KIND_LANE : KIND_ROW;
         }
         // grouped by kind, largest first inside a kind: warps take tasks in order
         std::stable_sort(lvl_tasks.begin(), lvl_tasks.end(), [](const Task &a, const Task &b) {

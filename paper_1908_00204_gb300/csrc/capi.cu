@@ -416,18 +416,21 @@ int glu_analyze_opts(int32_t n, const int32_t *colptr, const int32_t *rowidx, co
             const HostPlan &P = h->P;
             for (size_t l = 0; l + 1 < P.level_ptr.size(); l++) {
                 int64_t c[3] = {0, 0, 0}, sg[3] = {0, 0, 0}, wk[3] = {0, 0, 0}, mw = 0, ms = 0;
+                int64_t mseg[3] = {0, 0, 0};
                 for (int32_t t = P.lvl_task_ptr[l]; t < P.lvl_task_ptr[l + 1]; t++) {
                     const Task &tk = P.tasks[t];
+                    mseg[tk.kind] = std::max<int64_t>(mseg[tk.kind], tk.seg_end - tk.seg_begin);
                     c[tk.kind]++;
                     sg[tk.kind] += tk.seg_end - tk.seg_begin;
                     wk[tk.kind] += tk.work;
                     mw = std::max<int64_t>(mw, tk.work);
                     ms = std::max<int64_t>(ms, tk.seg_end - tk.seg_begin);
                 }
-                std::fprintf(fp, "%zu %d %lld %lld %lld %lld %lld %lld %lld %lld %lld %lld %lld\n", l,
+                std::fprintf(fp, "%zu %d %lld %lld %lld %lld %lld %lld %lld %lld %lld %lld %lld %lld %lld %lld\n", l,
                              P.level_ptr[l + 1] - P.level_ptr[l], (long long)c[0], (long long)sg[0],
                              (long long)wk[0], (long long)c[1], (long long)sg[1], (long long)wk[1], (long long)c[2],
-                             (long long)sg[2], (long long)wk[2], (long long)mw, (long long)ms);
+                             (long long)sg[2], (long long)wk[2], (long long)mw, (long long)ms, (long long)mseg[0],
+                             (long long)mseg[1], (long long)mseg[2]);
             }
             std::fclose(fp);
         }

@@ -92,7 +92,8 @@ __device__ __forceinline__ SegMeta<T> shfl_meta(const SegMeta<T> &m, int src) {
     return o;
 }
 
-constexpr int ROW_UNROLL = 8;
+constexpr int ROW_UNROLL = 4;   // rows per lane batch, lanes over rows
+constexpr int LANE_UNROLL = 4;  // rows per batch when one lane walks a segment
 
 // Rows t0..t1-1 of one segment, lanes over rows.  Within a segment every row
 // hits a different target entry, so all loads of a batch go out before any
@@ -162,17 +163,17 @@ __device__ __forceinline__ void src_task(const FactorArgs<T> &a, const Task &tk,
         const M *__restrict__ mp = map + cur.mb;
         const T *__restrict__ L = a.lu + cur.lstart;
         const int32_t rel = (int32_t)(cur.pos + 1 - tk.base);
-        for (int32_t tb = cur.t0; tb < cur.t1; tb += ROW_UNROLL) {
-            uint32_t off[ROW_UNROLL];
-            T lv[ROW_UNROLL];
+        for (int32_t tb = cur.t0; tb < cur.t1; tb += LANE_UNROLL) {
+            uint32_t off[LANE_UNROLL];
+            T lv[LANE_UNROLL];
 #pragma unroll
-            for (int u = 0; u < ROW_UNROLL; u++)
+            for (int u = 0; u < LANE_UNROLL; u++)
                 if (tb + u < cur.t1) {
                     off[u] = mp[tb + u];
                     lv[u] = L[tb + u];
                 }
 #pragma unroll
-            for (int u = 0; u < ROW_UNROLL; u++)
+            for (int u = 0; u < LANE_UNROLL; u++)
                 if (tb + u < cur.t1) {
                     const int32_t slot = rel + (int32_t)off[u];
                     row[slot] = fma_t<T>(lv[u], cur.f, row[slot]);
@@ -192,30 +193,33 @@ __device__ __forceinline__ void src_task(const FactorArgs<T> &a, const Task &tk,
     __syncwarp();
 }
 
-// KIND_LANE: one lane applies the task's segments in order, rows batched.
+// KIND_LANE: one lane applies the task's segments in order, rows batched;
+// the next segment's metadata is fetched before the current one's rows.
 template <typename T, typename M>
 __device__ __forceinline__ void lane_task(const FactorArgs<T> &a, const Task &tk) {
     const M *__restrict__ map = static_cast<const M *>(a.map);
+    SegMeta<T> nxt;
+    load_meta<T>(a, tk.seg_begin, nxt);
     for (int32_t s = tk.seg_begin; s < tk.seg_end; s++) {
-        SegMeta<T> m;
-        load_meta<T>(a, s, m);
+        const SegMeta<T> m = nxt;
+        if (s + 1 < tk.seg_end) load_meta<T>(a, s + 1, nxt);
         const M *__restrict__ mp = map + m.mb;
         const T *__restrict__ L = a.lu + m.lstart;
         T *tgt = a.lu + m.pos + 1;
-        for (int32_t tb = m.t0; tb < m.t1; tb += ROW_UNROLL) {
-            uint32_t off[ROW_UNROLL];
-            T lv[ROW_UNROLL], tv[ROW_UNROLL];
+        for (int32_t tb = m.t0; tb < m.t1; tb += LANE_UNROLL) {
+            uint32_t off[LANE_UNROLL];
+            T lv[LANE_UNROLL], tv[LANE_UNROLL];
 #pragma unroll
-            for (int u = 0; u < ROW_UNROLL; u++)
+            for (int u = 0; u < LANE_UNROLL; u++)
                 if (tb + u < m.t1) {
                     off[u] = mp[tb + u];
                     lv[u] = L[tb + u];
                 }
 #pragma unroll
-            for (int u = 0; u < ROW_UNROLL; u++)
+            for (int u = 0; u < LANE_UNROLL; u++)
                 if (tb + u < m.t1) tv[u] = tgt[off[u]];
 #pragma unroll
-            for (int u = 0; u < ROW_UNROLL; u++)
+            for (int u = 0; u < LANE_UNROLL; u++)
                 if (tb + u < m.t1) tgt[off[u]] = fma_t<T>(-lv[u], m.f, tv[u]);
         }
     }
@@ -226,7 +230,7 @@ constexpr int LEVEL_WARPS = 4;
 // One level.  Work items, in order: normalization items, KIND_SRC tasks and
 // KIND_ROW tasks (one warp each), then KIND_LANE tasks, 32 per warp.
 template <typename T, typename M>
-__global__ void __launch_bounds__(LEVEL_WARPS * 32)
+__global__ void __launch_bounds__(LEVEL_WARPS * 32, 4)
 k_level(const FactorArgs<T> a, LevelRange r) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
