@@ -58,6 +58,11 @@ extern "C" {
 #define GLU_ERR_TIMEOUT -7          /* a bounded device-side wait gave up */
 #define GLU_ERR_NOT_FACTORED -8     /* solve before a successful factorization */
 #define GLU_ERR_INTERNAL -9         /* an internal consistency check failed */
+#define GLU_ERR_TOO_LARGE -10       /* the problem does not fit glu_solve_noalloc's fixed scratch */
+
+/* Size, in doubles, of the fixed device scratch array behind
+ * glu_solve_noalloc (32 MiB). */
+#define GLU_NOALLOC_SCRATCH_DOUBLES 4194304
 
 typedef struct glu_handle glu_handle;
 
@@ -165,6 +170,33 @@ int glu_get_stats(const glu_handle *h, glu_stats *s);
 
 /* Column of the last zero or non-finite pivot error (-1 if none). */
 int glu_last_error_info(const glu_handle *h, int32_t *column);
+
+/* glu_solve without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that must not allocate device memory
+ * once they are running, for example a simulator's time-stepping loop whose
+ * memory is all reserved up front under a fixed budget (where a cudaMalloc
+ * could fail, or stall the device while it runs), or code that hands the
+ * library memory owned by someone else's allocator.
+ *
+ * Same computation and result as glu_solve (one scratch vector of n * nrhs
+ * values plus the partial sums of the long rows), but the scratch is a
+ * fixed, file-scope device array of GLU_NOALLOC_SCRATCH_DOUBLES doubles,
+ * which every GPU where the library's device code gets loaded holds until
+ * the process exits.  b and x must
+ * be device pointers (no staging); the call is stream-ordered on the
+ * handle's stream and returns once enqueued.
+ *
+ * Needs n * nrhs + (longest-row chunks) * nrhs doubles; a larger problem is
+ * rejected with GLU_ERR_TOO_LARGE before anything is launched.  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current); make that first call before any stream capture.
+ * All calls share the one array and it keeps the last call's contents (the
+ * solve writes every scratch value before reading it, so nothing has to
+ * start at zero); calls whose work overlaps on the GPU, from any handle or
+ * stream, race on the array and must be serialized by the caller.
+ * Errors: GLU_ERR_INVALID (host pointers, nrhs < 0), GLU_ERR_NOT_FACTORED,
+ * GLU_ERR_TOO_LARGE, GLU_ERR_CUDA. */
+int glu_solve_noalloc(glu_handle *h, const double *b, double *x, int32_t nrhs);
 
 /* Free the handle and everything it owns.  NULL is ignored. */
 void glu_destroy(glu_handle *h);

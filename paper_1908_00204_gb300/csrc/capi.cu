@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -673,8 +674,77 @@ const char *glu_strerror(int code) {
         case GLU_ERR_TIMEOUT: return "bounded device wait timed out";
         case GLU_ERR_NOT_FACTORED: return "no successful factorization to solve with";
         case GLU_ERR_INTERNAL: return "internal consistency check failed";
+        case GLU_ERR_TOO_LARGE: return "problem exceeds the fixed scratch array of glu_solve_noalloc";
         default: return "unknown error code";
     }
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// glu_solve_noalloc: the solve with its scratch in a fixed file-scope device
+// array instead of handle-owned allocations.  In host code the array's name
+// is only a stand-in for the symbol; its device address comes from
+// cudaGetSymbolAddress, looked up once per device with that device current.
+namespace {
+
+__device__ __align__(256) double g_noalloc_scratch[GLU_NOALLOC_SCRATCH_DOUBLES];
+
+std::mutex g_noalloc_mu;
+std::vector<double *> g_noalloc_addr;   // per device; nullptr until looked up
+
+cudaError_t noalloc_scratch_address(int device, double **out) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if ((int)g_noalloc_addr.size() <= device) g_noalloc_addr.resize((size_t)device + 1, nullptr);
+    if (!g_noalloc_addr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[device] = static_cast<double *>(p);
+    }
+    *out = g_noalloc_addr[device];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" int glu_solve_noalloc(glu_handle *h, const double *b, double *x, int32_t nrhs) {
+    if (!h || nrhs < 0 || h->opt.host_only) return GLU_ERR_INVALID;
+    if (!h->factored) return GLU_ERR_NOT_FACTORED;
+    HostPlan &P = h->P;
+    const int32_t n = P.n;
+    const int64_t elems = (int64_t)n * nrhs;
+    if (elems == 0) return GLU_OK;
+    if (!b || !x || !is_device_ptr(b) || !is_device_ptr(x)) return GLU_ERR_INVALID;
+    // y (n * nrhs values) then the partial sums, 32-value aligned
+    const int64_t yelems = (elems + 31) / 32 * 32;
+    const int64_t nch = (int64_t)std::max(P.fwd_chunks.size(), P.bwd_chunks.size()) * nrhs;
+    if (yelems + nch > (int64_t)GLU_NOALLOC_SCRATCH_DOUBLES) {
+        h->why = "glu_solve_noalloc: needs " + std::to_string(yelems + nch) + " doubles of scratch, the array holds " +
+                 std::to_string((long long)GLU_NOALLOC_SCRATCH_DOUBLES);
+        return GLU_ERR_TOO_LARGE;
+    }
+    CK(cudaSetDevice(h->device));
+    double *scratch = nullptr;
+    CK(noalloc_scratch_address(h->device, &scratch));
+    double *y = scratch;
+    double *partial = scratch + yelems;
+    cudaStream_t st = h->stream;
+    CKL(1, launch_permute_in<double>(y, b, h->d_perm, n, nrhs, st));
+    SolveArgs<double> a = sargs(h);
+    int launched = 0;
+    for (size_t l = 0; l + 1 < P.fwd_ptr.size(); l++) {
+        CK(launch_solve_level<double>(a, false, y, nrhs, h->d_fwd_items + P.fwd_ptr[l], P.fwd_ptr[l + 1] - P.fwd_ptr[l],
+                                      h->d_fwd_chunks, P.fwd_chunk_ptr[l], P.fwd_chunk_ptr[l + 1], partial, st,
+                                      &launched));
+        h->launches += launched;
+    }
+    for (size_t l = 0; l + 1 < P.bwd_ptr.size(); l++) {
+        CK(launch_solve_level<double>(a, true, y, nrhs, h->d_bwd_items + P.bwd_ptr[l], P.bwd_ptr[l + 1] - P.bwd_ptr[l],
+                                      h->d_bwd_chunks, P.bwd_chunk_ptr[l], P.bwd_chunk_ptr[l + 1], partial, st,
+                                      &launched));
+        h->launches += launched;
+    }
+    CKL(1, launch_permute_out<double>(x, y, h->d_perm, n, nrhs, st));
+    return GLU_OK;
+}

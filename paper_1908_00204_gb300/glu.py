@@ -28,6 +28,8 @@ GLU_ERR_CUDA = -6
 GLU_ERR_TIMEOUT = -7
 GLU_ERR_NOT_FACTORED = -8
 GLU_ERR_INTERNAL = -9
+GLU_ERR_TOO_LARGE = -10
+GLU_NOALLOC_SCRATCH_DOUBLES = 4194304
 
 
 class glu_options(C.Structure):
@@ -68,6 +70,7 @@ def load_library(path: Optional[str] = None):
             "glu_factor": (C.c_int, [P, P]),
             "glu_sync": (C.c_int, [P]),
             "glu_solve": (C.c_int, [P, P, P, i32]),
+            "glu_solve_noalloc": (C.c_int, [P, P, P, i32]),
             "glu_get_fill": (C.c_int, [P, C.POINTER(P), C.POINTER(P), C.POINTER(i64)]),
             "glu_get_deps": (C.c_int, [P, C.POINTER(P), C.POINTER(P)]),
             "glu_get_levels": (C.c_int, [P, C.POINTER(i32), C.POINTER(P), C.POINTER(P)]),
@@ -209,6 +212,14 @@ def glu_solve(h: Handle, b, x=None, nrhs: Optional[int] = None):
         else:
             x = b.new_empty(b.shape)
     _check(load_library().glu_solve(h._ptr, _ptr(b, np.float64), _ptr(x, np.float64), int(k)), "glu_solve", h)
+    return x
+
+
+def glu_solve_noalloc(h: Handle, b, x, nrhs: Optional[int] = None):
+    """glu_solve with the library's fixed scratch array: b and x must be CUDA tensors."""
+    k = _nrhs(b, h.n) if nrhs is None else nrhs
+    _check(load_library().glu_solve_noalloc(h._ptr, _ptr(b, np.float64), _ptr(x, np.float64), int(k)),
+           "glu_solve_noalloc", h)
     return x
 
 
