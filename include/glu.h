@@ -82,7 +82,14 @@ typedef struct glu_options {
     int32_t host_only;        /* 1: run the host analysis only; no device memory is
                                  touched and the handle can only report the analysis
                                  (glu_get_fill / deps / levels / stats) */
-    int32_t reserved[8];
+    int32_t solve_mode;       /* 1 (default): dataflow solve, one launch with per-row
+                                 ready flags; 0: one launch per solve level */
+    int32_t spin_limit_us;    /* bound on any device-side wait, microseconds
+                                 (default 2,000,000); past it GLU_ERR_TIMEOUT */
+    int32_t fault_row;        /* testing only: in the dataflow solve this row never
+                                 publishes its result, so waits on it time out
+                                 (-1: off) */
+    int32_t reserved[5];
 } glu_options;
 
 /* Analysis statistics (glu_get_stats). */

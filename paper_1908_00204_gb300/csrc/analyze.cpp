@@ -536,6 +536,46 @@ void solve_levels(HostPlan &P) {
     };
     items(P.fwd_ptr, P.fwd_rows, P.lrow_ptr, P.fwd_items, P.fwd_chunks, P.fwd_chunk_ptr);
     items(P.bwd_ptr, P.bwd_rows, P.urow_ptr, P.bwd_items, P.bwd_chunks, P.bwd_chunk_ptr);
+
+    // Dataflow order: a chunk of a long row only reads rows of lower levels,
+    // so it goes at level 1 + (highest level it reads), before the rows of
+    // that level; far ahead of its row when it covers early columns.
+    P.df_items.clear();
+    auto emit = [&](bool bwd, const std::vector<int32_t> &lv, int32_t nlev, const std::vector<SolveRow> &it,
+                    const std::vector<SolveChunk> &ch, const std::vector<int32_t> &colv,
+                    const std::vector<int32_t> &ptr) {
+        std::vector<int32_t> chlev(ch.size(), 0), chrow(ch.size(), 0);
+        for (const SolveRow &r : it)
+            for (int32_t c = r.cb; c < r.ce; c++) chrow[c] = r.row;
+        for (size_t c = 0; c < ch.size(); c++) {
+            int32_t m = 0;
+            for (int64_t p = ch[c].p0; p < ch[c].p1; p++) m = std::max(m, lv[colv[p]] + 1);
+            chlev[c] = m;
+        }
+        std::vector<int32_t> cnt((size_t)nlev + 2, 0);
+        for (size_t c = 0; c < ch.size(); c++) cnt[chlev[c] + 1]++;
+        for (int32_t l = 0; l <= nlev; l++) cnt[l + 1] += cnt[l];
+        std::vector<int32_t> byl(ch.size());
+        {
+            std::vector<int32_t> f(cnt.begin(), cnt.end() - 1);
+            for (size_t c = 0; c < ch.size(); c++) byl[f[chlev[c]]++] = (int32_t)c;
+        }
+        const int32_t fl = bwd ? 1 : 0;
+        for (int32_t l = 0; l < nlev; l++) {
+            for (int32_t q = cnt[l]; q < cnt[l + 1]; q++) {
+                const int32_t c = byl[q];
+                const int32_t rec[8] = {chrow[c], 0, 0, c, fl | 2, 0, 0, 0};
+                P.df_items.insert(P.df_items.end(), rec, rec + 8);
+            }
+            for (int32_t q = ptr[l]; q < ptr[l + 1]; q++) {
+                const SolveRow &r = it[q];
+                const int32_t rec[8] = {r.row, r.cb, r.ce, -1, fl, 0, 0, 0};
+                P.df_items.insert(P.df_items.end(), rec, rec + 8);
+            }
+        }
+    };
+    emit(false, lf, nf, P.fwd_items, P.fwd_chunks, P.lrow_col, P.fwd_ptr);
+    emit(true, lb, nb, P.bwd_items, P.bwd_chunks, P.urow_col, P.bwd_ptr);
 }
 
 }  // namespace

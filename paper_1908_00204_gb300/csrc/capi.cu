@@ -44,6 +44,15 @@ struct glu_handle {
     int32_t *d_fwd_rows = nullptr, *d_bwd_rows = nullptr, *d_perm = nullptr;
     SolveRow *d_fwd_items = nullptr, *d_bwd_items = nullptr;
     SolveChunk *d_fwd_chunks = nullptr, *d_bwd_chunks = nullptr;
+    // dataflow solve: items, ready flags (forward rows, backward rows, forward
+    // chunks, backward chunks, contiguous), ticket, abort word, error word
+    DFItem *d_df_items = nullptr;
+    int32_t *d_flags = nullptr;
+    int64_t n_flags = 0;
+    unsigned *d_ticket = nullptr;
+    unsigned *d_abort = nullptr;
+    unsigned long long *d_serr = nullptr;
+    long long spin_cycles = 0;
     // solve scratch (grown on demand): permuted vector, staging, partials
     double *d_work = nullptr;
     double *d_bstage = nullptr;
@@ -125,7 +134,7 @@ SolveArgs<double> sargs(glu_handle *h);
 int ensure_work(glu_handle *h, int32_t nrhs) {
     if (nrhs <= h->work_nrhs) return GLU_OK;
     const int64_t elems = (int64_t)h->P.n * nrhs;
-    const int64_t nch = (int64_t)std::max(h->P.fwd_chunks.size(), h->P.bwd_chunks.size()) * nrhs;
+    const int64_t nch = (int64_t)(h->P.fwd_chunks.size() + h->P.bwd_chunks.size()) * nrhs;
     // graphs captured with the old buffers are stale
     for (auto &g : h->sgraphs) cudaGraphExecDestroy(g.second);
     h->sgraphs.clear();
@@ -177,6 +186,30 @@ int enqueue_solve(glu_handle *h, const double *db, double *dx, int32_t nrhs, cud
     double *y = h->d_work;
     CKL(1, launch_permute_in<double>(y, db, h->d_perm, n, nrhs, st));
     SolveArgs<double> a = sargs(h);
+    if (h->opt.solve_mode == 1) {
+        CK(cudaMemsetAsync(h->d_flags, 0, h->n_flags * sizeof(int32_t), st));
+        CK(cudaMemsetAsync(h->d_serr, 0xff, sizeof(unsigned long long), st));
+        DFSolveArgs d;
+        d.items = h->d_df_items;
+        d.nitems = (int32_t)(P.df_items.size() / 8);
+        d.epoch = 1;
+        d.fault_row = h->opt.fault_row;
+        d.fchunks = h->d_fwd_chunks;
+        d.bchunks = h->d_bwd_chunks;
+        d.fpartial_v = h->d_partial;
+        d.bpartial_v = h->d_partial + (int64_t)P.fwd_chunks.size() * nrhs;
+        d.fready = h->d_flags;
+        d.bready = h->d_flags + n;
+        d.fchunk_ready = h->d_flags + 2 * (int64_t)n;
+        d.bchunk_ready = d.fchunk_ready + P.fwd_chunks.size();
+        d.ticket = h->d_ticket;
+        d.abort = h->d_abort;
+        d.err = h->d_serr;
+        d.spin_limit_cycles = h->spin_cycles;
+        CKL(d.nitems > 0, launch_solve_df<double>(a, d, y, nrhs, h->num_sms, st));
+        CKL(1, launch_permute_out<double>(dx, y, h->d_perm, n, nrhs, st));
+        return GLU_OK;
+    }
     int launched = 0;
     for (size_t l = 0; l + 1 < P.fwd_ptr.size(); l++) {
         CK(launch_solve_level<double>(a, false, y, nrhs, h->d_fwd_items + P.fwd_ptr[l], P.fwd_ptr[l + 1] - P.fwd_ptr[l],
@@ -227,10 +260,12 @@ int decode_err(glu_handle *h, unsigned long long w) {
 }
 
 int read_err(glu_handle *h) {
-    unsigned long long w = ERR_NONE;
+    unsigned long long w = ERR_NONE, ws = ERR_NONE;
     CK(cudaMemcpyAsync(&w, h->d_err, sizeof(w), cudaMemcpyDeviceToHost, h->stream));
+    if (h->d_serr) CK(cudaMemcpyAsync(&ws, h->d_serr, sizeof(ws), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    return decode_err(h, w);
+    int rc = decode_err(h, w);          // a factorization error takes precedence
+    return rc != GLU_OK ? rc : decode_err(h, ws);
 }
 
 FactorArgs<double> fargs(glu_handle *h) {
@@ -276,7 +311,10 @@ int upload_plan(glu_handle *h) {
            o_perm = c.take<int32_t>(n), o_pk = c.take<int32_t>(P.pair_k.size()),
            o_lcp = c.take<int64_t>(n + 1), o_lri = c.take<int32_t>(nnz),
            o_fi = c.take<SolveRow>(P.fwd_items.size()), o_bi = c.take<SolveRow>(P.bwd_items.size()),
-           o_fc = c.take<SolveChunk>(P.fwd_chunks.size()), o_bc = c.take<SolveChunk>(P.bwd_chunks.size());
+           o_fc = c.take<SolveChunk>(P.fwd_chunks.size()), o_bc = c.take<SolveChunk>(P.bwd_chunks.size()),
+           o_dfi = c.take<int32_t>(P.df_items.size()),
+           o_flags = c.take<int32_t>(2 * (size_t)n + P.fwd_chunks.size() + P.bwd_chunks.size()),
+           o_ticket = c.take<unsigned>(1), o_abort = c.take<unsigned>(1), o_serr = c.take<unsigned long long>(1);
     h->arena_bytes = c.off + 256;
     CK(cudaMalloc(&h->arena, h->arena_bytes));
     char *A = h->arena;
@@ -304,6 +342,12 @@ int upload_plan(glu_handle *h) {
     h->d_bwd_items = at<SolveRow>(A, o_bi);
     h->d_fwd_chunks = at<SolveChunk>(A, o_fc);
     h->d_bwd_chunks = at<SolveChunk>(A, o_bc);
+    h->d_df_items = at<DFItem>(A, o_dfi);
+    h->d_flags = at<int32_t>(A, o_flags);
+    h->n_flags = 2 * (int64_t)n + (int64_t)P.fwd_chunks.size() + (int64_t)P.bwd_chunks.size();
+    h->d_ticket = at<unsigned>(A, o_ticket);
+    h->d_abort = at<unsigned>(A, o_abort);
+    h->d_serr = at<unsigned long long>(A, o_serr);
     int32_t *d_pair_k = at<int32_t>(A, o_pk);
     int64_t *d_lcp = at<int64_t>(A, o_lcp);
     int32_t *d_lri = at<int32_t>(A, o_lri);
@@ -329,6 +373,15 @@ int upload_plan(glu_handle *h) {
     CK(upload(h->d_bwd_items, P.bwd_items));
     CK(upload(h->d_fwd_chunks, P.fwd_chunks));
     CK(upload(h->d_bwd_chunks, P.bwd_chunks));
+    CK(upload(reinterpret_cast<int32_t *>(h->d_df_items), P.df_items));
+    CK(cudaMemset(h->d_flags, 0, std::max<int64_t>(h->n_flags, 1) * sizeof(int32_t)));
+    CK(cudaMemset(h->d_serr, 0xff, sizeof(unsigned long long)));
+    {
+        int khz = 0;
+        CK(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, h->device));
+        const long long us = h->opt.spin_limit_us > 0 ? h->opt.spin_limit_us : 2000000;
+        h->spin_cycles = us * (long long)(khz > 0 ? khz : 2000000) / 1000;
+    }
     CK(upload(d_lcp, P.lu_colptr));
     CK(upload(d_lri, P.lu_rowidx));
     // position map, built on the device
@@ -370,6 +423,9 @@ void glu_default_options(glu_options *o) {
     o->wide_threshold = 256;
     o->use_graph = 1;
     o->verbose = 0;
+    o->solve_mode = 1;
+    o->spin_limit_us = 2000000;
+    o->fault_row = -1;
 }
 
 int glu_analyze_opts(int32_t n, const int32_t *colptr, const int32_t *rowidx, const int32_t *perm,
@@ -524,7 +580,7 @@ int glu_sync(glu_handle *h) {
     if (h->opt.host_only) return GLU_OK;
     CK(cudaSetDevice(h->device));
     int rc = read_err(h);
-    if (rc != GLU_OK && rc != GLU_ERR_CUDA) h->factored = false;
+    if (rc == GLU_ERR_ZERO_PIVOT || rc == GLU_ERR_NONFINITE) h->factored = false;
     return rc;
 }
 

@@ -56,6 +56,32 @@ struct SolveArgs {
     int32_t n;
 };
 
+// Dataflow solve: one work item per row or long-row chunk, in topological
+// order (forward items, then backward items).
+enum : int32_t { DF_BACKWARD = 1, DF_CHUNK = 2 };
+struct DFItem {
+    int32_t row;
+    int32_t cb;      // row item: its chunks cb..ce-1 (none if equal)
+    int32_t ce;
+    int32_t chunk;   // chunk item: index into the chunk list
+    int32_t flags;
+    int32_t spare[3];
+};
+
+struct DFSolveArgs {
+    const DFItem *items;
+    int32_t nitems;
+    int32_t epoch;
+    int32_t fault_row;            // test hook: this row never publishes (-1: none)
+    const SolveChunk *fchunks, *bchunks;
+    void *fpartial_v, *bpartial_v;
+    int32_t *fready, *bready, *fchunk_ready, *bchunk_ready;
+    unsigned *ticket;
+    unsigned *abort;
+    unsigned long long *err;
+    long long spin_limit_cycles;
+};
+
 // launchers (kernels_factor.cu)
 template <typename T>
 cudaError_t launch_gather(T *lu, const double *aval, const int32_t *gsrc, int64_t nnz, cudaStream_t s);
@@ -74,6 +100,9 @@ cudaError_t launch_permute_in(T *y, const double *b, const int32_t *perm, int32_
 template <typename T>
 cudaError_t launch_permute_out(double *x, const T *y, const int32_t *perm, int32_t n, int32_t nrhs,
                                cudaStream_t s);
+template <typename T>
+cudaError_t launch_solve_df(const SolveArgs<T> &s, const DFSolveArgs &a, T *y, int32_t nrhs, int num_sms,
+                            cudaStream_t st);
 template <typename T>
 cudaError_t launch_solve_level(const SolveArgs<T> &a, bool backward, T *y, int32_t nrhs, const SolveRow *items,
                                int32_t nitems, const SolveChunk *chunks, int32_t c0, int32_t c1, T *partial,

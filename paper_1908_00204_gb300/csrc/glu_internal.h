@@ -114,6 +114,9 @@ struct HostPlan {
     std::vector<SolveRow> fwd_items, bwd_items;
     std::vector<SolveChunk> fwd_chunks, bwd_chunks;
     std::vector<int32_t> fwd_chunk_ptr, bwd_chunk_ptr;   // nlevels + 1
+    // dataflow solve: items in topological order, packed as int32 x 8
+    // {row, cb, ce, chunk, flags, 0, 0, 0}
+    std::vector<int32_t> df_items;
     // A in compressed rows (original numbering) for residuals
     std::vector<int64_t> acsr_ptr;
     std::vector<int32_t> acsr_col;

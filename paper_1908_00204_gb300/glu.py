@@ -35,7 +35,8 @@ GLU_NOALLOC_SCRATCH_DOUBLES = 4194304
 class glu_options(C.Structure):
     _fields_ = [("struct_size", C.c_int32), ("mode_force", C.c_int32), ("tail_threshold", C.c_int32),
                 ("piece_updates", C.c_int32), ("wide_threshold", C.c_int32), ("use_graph", C.c_int32),
-                ("verbose", C.c_int32), ("host_only", C.c_int32), ("reserved", C.c_int32 * 8)]
+                ("verbose", C.c_int32), ("host_only", C.c_int32), ("solve_mode", C.c_int32),
+                ("spin_limit_us", C.c_int32), ("fault_row", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class glu_stats(C.Structure):
