@@ -146,7 +146,7 @@ int ensure_work(glu_handle *h, int32_t nrhs) {
     h->d_work = h->d_bstage = h->d_xstage = h->d_partial = nullptr;
     h->work_elems = 0;
     h->work_nrhs = 0;
-    CK(cudaMalloc(&h->d_work, elems * sizeof(double)));
+    CK(cudaMalloc(&h->d_work, 2 * elems * sizeof(double)));   // y, and z of the dataflow solve
     CK(cudaMalloc(&h->d_bstage, elems * sizeof(double)));
     CK(cudaMalloc(&h->d_xstage, elems * sizeof(double)));
     CK(cudaMalloc(&h->d_partial, std::max<int64_t>(nch, 1) * sizeof(double)));
@@ -206,8 +206,9 @@ int enqueue_solve(glu_handle *h, const double *db, double *dx, int32_t nrhs, cud
         d.abort = h->d_abort;
         d.err = h->d_serr;
         d.spin_limit_cycles = h->spin_cycles;
-        CKL(d.nitems > 0, launch_solve_df<double>(a, d, y, nrhs, h->num_sms, st));
-        CKL(1, launch_permute_out<double>(dx, y, h->d_perm, n, nrhs, st));
+        double *z = y + (int64_t)n * nrhs;
+        CKL(d.nitems > 0, launch_solve_df<double>(a, d, y, z, nrhs, h->num_sms, st));
+        CKL(1, launch_permute_out<double>(dx, z, h->d_perm, n, nrhs, st));
         return GLU_OK;
     }
     int launched = 0;
@@ -683,7 +684,7 @@ int glu_get_stats(const glu_handle *h, glu_stats *s) {
     s->solve_levels_fwd = (int32_t)P.fwd_ptr.size() - 1;
     s->solve_levels_bwd = (int32_t)P.bwd_ptr.size() - 1;
     s->max_level_width = P.max_level_width;
-    s->device_bytes = (int64_t)(h->arena_bytes + h->map_total + 3 * h->work_elems * sizeof(double) +
+    s->device_bytes = (int64_t)(h->arena_bytes + h->map_total + 4 * h->work_elems * sizeof(double) +
                                 (int64_t)std::max(P.fwd_chunks.size(), P.bwd_chunks.size()) * h->work_nrhs *
                                     sizeof(double));
     s->analyze_ms = h->analyze_ms;

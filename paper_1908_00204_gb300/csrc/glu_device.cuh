@@ -101,7 +101,7 @@ template <typename T>
 cudaError_t launch_permute_out(double *x, const T *y, const int32_t *perm, int32_t n, int32_t nrhs,
                                cudaStream_t s);
 template <typename T>
-cudaError_t launch_solve_df(const SolveArgs<T> &s, const DFSolveArgs &a, T *y, int32_t nrhs, int num_sms,
+cudaError_t launch_solve_df(const SolveArgs<T> &s, const DFSolveArgs &a, T *y, T *z, int32_t nrhs, int num_sms,
                             cudaStream_t st);
 template <typename T>
 cudaError_t launch_solve_level(const SolveArgs<T> &a, bool backward, T *y, int32_t nrhs, const SolveRow *items,

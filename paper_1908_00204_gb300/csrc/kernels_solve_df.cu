@@ -10,6 +10,9 @@
 // so they need no reset between calls.  Every wait is bounded: past the limit
 // the kernel records GLU_ERR_TIMEOUT, raises an abort flag that ends all other
 // waits, publishes its own result and carries on, so the launch always ends.
+// The backward sweep writes its own vector z: with an unsymmetric pattern a
+// backward row can be ready while a forward row still reads the forward value
+// of that row, so the two sweeps must not share storage.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -59,7 +62,7 @@ __device__ __forceinline__ bool wait_flag(const int32_t *flag, int epoch, const 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(128) k_solve_df(const SolveArgs<T> s, const DFSolveArgs a, T *y, int32_t nrhs) {
+__global__ void __launch_bounds__(128) k_solve_df(const SolveArgs<T> s, const DFSolveArgs a, T *y, T *z, int32_t nrhs) {
     const int lane = threadIdx.x & 31;
     const int n = s.n;
     while (true) {
@@ -78,7 +81,7 @@ __global__ void __launch_bounds__(128) k_solve_df(const SolveArgs<T> s, const DF
             const SolveChunk ch = (bwd ? a.bchunks : a.fchunks)[it.chunk];
             T *partial = static_cast<T *>(bwd ? a.bpartial_v : a.fpartial_v);
             for (int32_t r = 0; r < nrhs; r++) {
-                const T *yr = y + (int64_t)r * n;
+                const T *yr = (bwd ? z : y) + (int64_t)r * n;
                 T acc = (T)0;
                 for (int64_t p = ch.p0 + lane; p < ch.p1; p += 32) {
                     const int32_t j = col[p];
@@ -103,7 +106,8 @@ __global__ void __launch_bounds__(128) k_solve_df(const SolveArgs<T> s, const DF
             for (int32_t c = it.cb; c < it.ce; c++) wait_flag(chunk_ready + c, a.epoch, a);
         const int64_t b = rptr[i], e = rptr[i + 1];
         for (int32_t r = 0; r < nrhs; r++) {
-            T *yr = y + (int64_t)r * n;
+            const T *yr = (bwd ? z : y) + (int64_t)r * n;   // values the row reads
+            T *out = (bwd ? z : y) + (int64_t)r * n;
             T acc = (T)0;
             if (it.ce > it.cb) {
                 if (lane == 0)
@@ -117,8 +121,8 @@ __global__ void __launch_bounds__(128) k_solve_df(const SolveArgs<T> s, const DF
                 acc = warp_sum_df(acc);
             }
             if (lane == 0) {
-                const T v = ld_cg(yr + i);
-                yr[i] = bwd ? (v - acc) / d : v - acc;
+                const T v = ld_cg(y + (int64_t)r * n + i);   // c(i) forward, y(i) backward
+                out[i] = bwd ? (v - acc) / d : v - acc;
             }
         }
         __syncwarp();
@@ -129,7 +133,7 @@ __global__ void __launch_bounds__(128) k_solve_df(const SolveArgs<T> s, const DF
 }  // namespace
 
 template <typename T>
-cudaError_t launch_solve_df(const SolveArgs<T> &s, const DFSolveArgs &a, T *y, int32_t nrhs, int num_sms,
+cudaError_t launch_solve_df(const SolveArgs<T> &s, const DFSolveArgs &a, T *y, T *z, int32_t nrhs, int num_sms,
                             cudaStream_t st) {
     if (a.nitems == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(a.ticket, 0, sizeof(unsigned), st);
@@ -139,13 +143,13 @@ cudaError_t launch_solve_df(const SolveArgs<T> &s, const DFSolveArgs &a, T *y, i
     int64_t blocks = ((int64_t)a.nitems * 32 + 127) / 128;
     const int64_t cap = (int64_t)num_sms * 8;
     if (blocks > cap) blocks = cap;
-    k_solve_df<T><<<(unsigned)blocks, 128, 0, st>>>(s, a, y, nrhs);
+    k_solve_df<T><<<(unsigned)blocks, 128, 0, st>>>(s, a, y, z, nrhs);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_solve_df<double>(const SolveArgs<double> &, const DFSolveArgs &, double *, int32_t, int,
-                                             cudaStream_t);
-template cudaError_t launch_solve_df<float>(const SolveArgs<float> &, const DFSolveArgs &, float *, int32_t, int,
-                                            cudaStream_t);
+template cudaError_t launch_solve_df<double>(const SolveArgs<double> &, const DFSolveArgs &, double *, double *,
+                                             int32_t, int, cudaStream_t);
+template cudaError_t launch_solve_df<float>(const SolveArgs<float> &, const DFSolveArgs &, float *, float *, int32_t,
+                                            int, cudaStream_t);
 
 }  // namespace glu

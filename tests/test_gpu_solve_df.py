@@ -70,3 +70,18 @@ def test_wait_timeout_is_reported_and_context_survives(glu):
     xg = glu.glu_solve(good, b).cpu().numpy()
     glu.glu_sync(good)
     assert backward_error(m.n, m.colptr, m.rowidx, v, b.cpu().numpy(), xg) <= BERR_TOL
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_dataflow_unsymmetric_patterns(glu, seed):
+    """Unsymmetric patterns: a backward row can be ready while forward rows
+    still read the forward value of that row."""
+    n = 20 + 23 * seed
+    cp, ri, v = synth.random_pattern_matrix(n, 0.12, 900 + seed)
+    perm = np.random.default_rng(seed).permutation(n).astype(np.int32)
+    f = oracle.Factorization(n, cp, ri, perm, v)
+    b = synth.rhs(n, 2, seed)
+    h = glu.glu_analyze(n, cp, ri, perm)
+    glu.glu_factor(h, v)
+    x = glu.glu_solve(h, b)
+    np.testing.assert_allclose(x, f.solve(b), rtol=1e-9, atol=1e-12)
