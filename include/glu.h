@@ -113,6 +113,15 @@ typedef struct glu_stats {
     int64_t kernel_launches;  /* CUDA kernels this handle has launched so far */
 } glu_stats;
 
+/* Outcome of glu_solve_refine. */
+typedef struct glu_refine_info {
+    int32_t iterations;       /* corrections applied (FP32 solves after the first) */
+    int32_t converged;        /* 1 if every right-hand side reached tol */
+    double berr;              /* final normwise backward error, max over the sides:
+                                 ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf) */
+    double berr_first;        /* the same after the first FP32 solve */
+} glu_refine_info;
+
 /* Fill every field of *opts with its default. */
 void glu_default_options(glu_options *opts);
 
@@ -151,6 +160,23 @@ int glu_sync(glu_handle *h);
  * vectors of length n each; b and x must not overlap.
  * Errors: GLU_ERR_NOT_FACTORED, GLU_ERR_INVALID, pending factor errors. */
 int glu_solve(glu_handle *h, const double *b, double *x, int32_t nrhs);
+
+/* FP32 numeric refactorization: the same level-scheduled right-looking
+ * update as glu_factor, on FP32 values with FP32 accumulation (the paper's
+ * own precision, Section IV).  The FP64 values are kept for the residuals of
+ * glu_solve_refine.  values: nnz_a doubles, host or device, A's CSC order.
+ * Errors as glu_factor. */
+int glu_factor_f32(glu_handle *h, const double *values);
+
+/* Mixed-precision solve: FP32 triangular solves with the glu_factor_f32
+ * factors, FP64 iterative refinement on the GPU (r = b - A x with the FP64
+ * values, x += d in FP64), until the normwise backward error of every side is
+ * <= tol or maxit corrections were applied.  b, x: nrhs vectors of length n,
+ * host or device.  info may be NULL.  Not converging is not an error: check
+ * info->converged.  Errors: GLU_ERR_NOT_FACTORED (no FP32 factorization),
+ * GLU_ERR_INVALID, pending device errors. */
+int glu_solve_refine(glu_handle *h, const double *b, double *x, int32_t nrhs, double tol, int32_t maxit,
+                     glu_refine_info *info);
 
 /* Pattern of the fill (Section II-A): lu_colptr[n+1], lu_rowidx[nnz]
  * (rows ascending per column), host memory owned by the handle. */

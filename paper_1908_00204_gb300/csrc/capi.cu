@@ -53,6 +53,20 @@ struct glu_handle {
     unsigned *d_abort = nullptr;
     unsigned long long *d_serr = nullptr;
     long long spin_cycles = 0;
+    // FP32 factors and the refinement path
+    float *d_lu32 = nullptr;
+    cudaGraphExec_t fgraph32 = nullptr;
+    int64_t fgraph32_launches = 0;
+    bool factored32 = false;
+    double *d_aval_csr = nullptr;        // FP64 values in compressed-row order
+    int64_t *d_acsr_ptr = nullptr;
+    int32_t *d_acsr_col = nullptr;
+    int64_t *d_acsr_src = nullptr;
+    double *d_ir = nullptr;              // r and d, n * nrhs each
+    unsigned long long *d_irnorm = nullptr;  // anorm, then rmax, xmax, bmax (nrhs each)
+    int32_t *d_done = nullptr;           // nrhs flags, then the count
+    double *d_berr = nullptr;
+    int32_t ir_nrhs = 0;
     // solve scratch (grown on demand): permuted vector, staging, partials
     double *d_work = nullptr;
     double *d_bstage = nullptr;
@@ -228,6 +242,111 @@ int enqueue_solve(glu_handle *h, const double *db, double *dx, int32_t nrhs, cud
     return GLU_OK;
 }
 
+template <typename T>
+FactorArgs<T> fargs_t(glu_handle *h, T *lu) {
+    FactorArgs<T> a;
+    a.lu = lu;
+    a.diag_pos = h->d_diag;
+    a.map = h->map;
+    a.segs = h->d_segs;
+    a.tasks = h->d_tasks;
+    a.norms = h->d_norms;
+    a.err = h->d_err;
+    return a;
+}
+
+template <typename T>
+SolveArgs<T> sargs_t(glu_handle *h, const T *lu) {
+    SolveArgs<T> a;
+    a.lu = lu;
+    a.diag_pos = h->d_diag;
+    a.lrow_ptr = h->d_lrow_ptr;
+    a.lrow_col = h->d_lrow_col;
+    a.lrow_pos = h->d_lrow_pos;
+    a.urow_ptr = h->d_urow_ptr;
+    a.urow_col = h->d_urow_col;
+    a.urow_pos = h->d_urow_pos;
+    a.n = h->P.n;
+    return a;
+}
+
+// The FP32 factor sequence (same schedule as the FP64 one).
+int enqueue_factor_f32(glu_handle *h, cudaStream_t st) {
+    HostPlan &P = h->P;
+    CKL(1, launch_reset_err(h->d_err, st));
+    CKL(P.lu_colptr[P.n] > 0, launch_gather<float>(h->d_lu32, h->d_aval, h->d_gsrc, P.lu_colptr[P.n], st));
+    FactorArgs<float> a = fargs_t<float>(h, h->d_lu32);
+    const int32_t nl = (int32_t)P.level_ptr.size() - 1;
+    for (int32_t l = 0; l <= nl; l++) {
+        LevelRange r;
+        r.t_begin = l < nl ? P.lvl_task_ptr[l] : 0;
+        r.row_begin = l < nl ? P.lvl_row_ptr[l] : 0;
+        r.lane_begin = l < nl ? P.lvl_lane_ptr[l] : 0;
+        r.t_end = l < nl ? P.lvl_task_ptr[l + 1] : 0;
+        r.n_begin = P.lvl_norm_ptr[l];
+        r.n_end = P.lvl_norm_ptr[l + 1];
+        CKL((r.t_end - r.t_begin) + (r.n_end - r.n_begin) > 0, launch_level<float>(a, h->map_bytes, r, h->num_sms, st));
+    }
+    CKL(P.n > 0, launch_pivot_check<float>(h->d_lu32, h->d_diag, P.n, h->d_err, st));
+    // FP64 values in row order for the residuals
+    CKL(P.nnz_a > 0, launch_csr_values(h->d_aval_csr, h->d_aval, h->d_acsr_src, P.nnz_a, st));
+    return GLU_OK;
+}
+
+// FP32 dataflow solve of db (FP64) into dx (FP64): rounding to FP32 on the
+// way in, FP32 sweeps, widening on the way out.
+int enqueue_solve_f32(glu_handle *h, const double *db, double *dx, int32_t nrhs, cudaStream_t st) {
+    HostPlan &P = h->P;
+    const int32_t n = P.n;
+    float *y = reinterpret_cast<float *>(h->d_work);
+    float *z = y + (int64_t)n * nrhs;
+    CKL(1, launch_permute_in<float>(y, db, h->d_perm, n, nrhs, st));
+    SolveArgs<float> a = sargs_t<float>(h, h->d_lu32);
+    CK(cudaMemsetAsync(h->d_flags, 0, h->n_flags * sizeof(int32_t), st));
+    CK(cudaMemsetAsync(h->d_serr, 0xff, sizeof(unsigned long long), st));
+    DFSolveArgs d;
+    d.items = h->d_df_items;
+    d.nitems = (int32_t)(P.df_items.size() / 8);
+    d.epoch = 1;
+    d.fault_row = h->opt.fault_row;
+    d.fchunks = h->d_fwd_chunks;
+    d.bchunks = h->d_bwd_chunks;
+    float *part = reinterpret_cast<float *>(h->d_partial);
+    d.fpartial_v = part;
+    d.bpartial_v = part + (int64_t)P.fwd_chunks.size() * nrhs;
+    d.fready = h->d_flags;
+    d.bready = h->d_flags + n;
+    d.fchunk_ready = h->d_flags + 2 * (int64_t)n;
+    d.bchunk_ready = d.fchunk_ready + P.fwd_chunks.size();
+    d.ticket = h->d_ticket;
+    d.abort = h->d_abort;
+    d.err = h->d_serr;
+    d.spin_limit_cycles = h->spin_cycles;
+    CKL(d.nitems > 0, launch_solve_df<float>(a, d, y, z, nrhs, h->num_sms, st));
+    CKL(1, launch_permute_out<float>(dx, z, h->d_perm, n, nrhs, st));
+    return GLU_OK;
+}
+
+int ensure_ir(glu_handle *h, int32_t nrhs) {
+    if (nrhs <= h->ir_nrhs) return GLU_OK;
+    cudaFree(h->d_ir);
+    cudaFree(h->d_irnorm);
+    cudaFree(h->d_done);
+    cudaFree(h->d_berr);
+    h->d_ir = nullptr;
+    h->d_irnorm = nullptr;
+    h->d_done = nullptr;
+    h->d_berr = nullptr;
+    h->ir_nrhs = 0;
+    const int64_t elems = (int64_t)h->P.n * nrhs;
+    CK(cudaMalloc(&h->d_ir, 2 * std::max<int64_t>(elems, 1) * sizeof(double)));
+    CK(cudaMalloc(&h->d_irnorm, (1 + 3 * (size_t)nrhs) * sizeof(unsigned long long)));
+    CK(cudaMalloc(&h->d_done, (1 + (size_t)nrhs) * sizeof(int32_t)));
+    CK(cudaMalloc(&h->d_berr, (size_t)nrhs * sizeof(double)));
+    h->ir_nrhs = nrhs;
+    return GLU_OK;
+}
+
 // Capture `fn` (which enqueues on the given stream) into an executable graph.
 template <typename F>
 int capture(glu_handle *h, F &&fn, cudaGraphExec_t *exec, int64_t *launches) {
@@ -315,7 +434,9 @@ int upload_plan(glu_handle *h) {
            o_fc = c.take<SolveChunk>(P.fwd_chunks.size()), o_bc = c.take<SolveChunk>(P.bwd_chunks.size()),
            o_dfi = c.take<int32_t>(P.df_items.size()),
            o_flags = c.take<int32_t>(2 * (size_t)n + P.fwd_chunks.size() + P.bwd_chunks.size()),
-           o_ticket = c.take<unsigned>(1), o_abort = c.take<unsigned>(1), o_serr = c.take<unsigned long long>(1);
+           o_ticket = c.take<unsigned>(1), o_abort = c.take<unsigned>(1), o_serr = c.take<unsigned long long>(1),
+           o_acp = c.take<int64_t>(n + 1), o_acc = c.take<int32_t>(P.acsr_col.size()),
+           o_acs = c.take<int64_t>(P.acsr_src.size()), o_acv = c.take<double>(P.acsr_src.size());
     h->arena_bytes = c.off + 256;
     CK(cudaMalloc(&h->arena, h->arena_bytes));
     char *A = h->arena;
@@ -349,6 +470,10 @@ int upload_plan(glu_handle *h) {
     h->d_ticket = at<unsigned>(A, o_ticket);
     h->d_abort = at<unsigned>(A, o_abort);
     h->d_serr = at<unsigned long long>(A, o_serr);
+    h->d_acsr_ptr = at<int64_t>(A, o_acp);
+    h->d_acsr_col = at<int32_t>(A, o_acc);
+    h->d_acsr_src = at<int64_t>(A, o_acs);
+    h->d_aval_csr = at<double>(A, o_acv);
     int32_t *d_pair_k = at<int32_t>(A, o_pk);
     int64_t *d_lcp = at<int64_t>(A, o_lcp);
     int32_t *d_lri = at<int32_t>(A, o_lri);
@@ -375,6 +500,9 @@ int upload_plan(glu_handle *h) {
     CK(upload(h->d_fwd_chunks, P.fwd_chunks));
     CK(upload(h->d_bwd_chunks, P.bwd_chunks));
     CK(upload(reinterpret_cast<int32_t *>(h->d_df_items), P.df_items));
+    CK(upload(h->d_acsr_ptr, P.acsr_ptr));
+    CK(upload(h->d_acsr_col, P.acsr_col));
+    CK(upload(h->d_acsr_src, P.acsr_src));
     CK(cudaMemset(h->d_flags, 0, std::max<int64_t>(h->n_flags, 1) * sizeof(int32_t)));
     CK(cudaMemset(h->d_serr, 0xff, sizeof(unsigned long long)));
     {
@@ -581,7 +709,7 @@ int glu_sync(glu_handle *h) {
     if (h->opt.host_only) return GLU_OK;
     CK(cudaSetDevice(h->device));
     int rc = read_err(h);
-    if (rc == GLU_ERR_ZERO_PIVOT || rc == GLU_ERR_NONFINITE) h->factored = false;
+    if (rc == GLU_ERR_ZERO_PIVOT || rc == GLU_ERR_NONFINITE) h->factored = h->factored32 = false;
     return rc;
 }
 
@@ -631,6 +759,103 @@ int glu_solve(glu_handle *h, const double *b, double *x, int32_t nrhs) {
         return glu_sync(h);
     }
     return GLU_OK;
+}
+
+int glu_factor_f32(glu_handle *h, const double *values) {
+    if (!h || h->opt.host_only) return GLU_ERR_INVALID;
+    HostPlan &P = h->P;
+    if (P.nnz_a > 0 && !values) return GLU_ERR_INVALID;
+    CK(cudaSetDevice(h->device));
+    if (!h->d_lu32) CK(cudaMalloc(&h->d_lu32, std::max<int64_t>(P.lu_colptr[P.n], 1) * sizeof(float)));
+    h->err_col = -1;
+    const bool dev = P.nnz_a > 0 && is_device_ptr(values);
+    // the FP64 values stay in the handle: the residuals of the refinement use them
+    if (P.nnz_a > 0)
+        CK(cudaMemcpyAsync(h->d_aval, values, P.nnz_a * sizeof(double),
+                           dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+    if (h->opt.use_graph) {
+        if (!h->fgraph32) {
+            int rc = capture(h, [&](cudaStream_t st) { return enqueue_factor_f32(h, st); }, &h->fgraph32,
+                             &h->fgraph32_launches);
+            if (rc != GLU_OK) return rc;
+        }
+        CK(cudaGraphLaunch(h->fgraph32, h->stream));
+        h->launches += h->fgraph32_launches;
+    } else {
+        int rc = enqueue_factor_f32(h, h->stream);
+        if (rc != GLU_OK) return rc;
+    }
+    h->factored32 = true;
+    if (P.nnz_a > 0 && !dev) return glu_sync(h);
+    return GLU_OK;
+}
+
+int glu_solve_refine(glu_handle *h, const double *b, double *x, int32_t nrhs, double tol, int32_t maxit,
+                     glu_refine_info *info) {
+    if (!h || nrhs < 0 || maxit < 0 || !(tol >= 0.0) || h->opt.host_only) return GLU_ERR_INVALID;
+    if (!h->factored32) return GLU_ERR_NOT_FACTORED;
+    glu_refine_info inf{0, 1, 0.0, 0.0};
+    HostPlan &P = h->P;
+    const int32_t n = P.n;
+    const int64_t elems = (int64_t)n * nrhs;
+    if (elems == 0) {
+        if (info) *info = inf;
+        return GLU_OK;
+    }
+    if (!b || !x) return GLU_ERR_INVALID;
+    CK(cudaSetDevice(h->device));
+    int rc = ensure_work(h, nrhs);
+    if (rc != GLU_OK) return rc;
+    rc = ensure_ir(h, nrhs);
+    if (rc != GLU_OK) return rc;
+    cudaStream_t st = h->stream;
+    const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
+    const double *db = b;
+    if (!bdev) {
+        CK(cudaMemcpyAsync(h->d_bstage, b, elems * sizeof(double), cudaMemcpyHostToDevice, st));
+        db = h->d_bstage;
+    }
+    double *dx = xdev ? x : h->d_xstage;
+    double *r = h->d_ir, *d = h->d_ir + elems;
+    unsigned long long *anorm = h->d_irnorm, *rmax = anorm + 1, *xmax = rmax + nrhs, *bmax = xmax + nrhs;
+    int32_t *done = h->d_done, *ndone = h->d_done + nrhs;
+    CK(cudaMemsetAsync(h->d_irnorm, 0, (1 + 3 * (size_t)nrhs) * sizeof(unsigned long long), st));
+    CKL(1, launch_anorm(h->d_acsr_ptr, h->d_aval_csr, n, anorm, st));
+    CKL(1, launch_absmax(db, n, nrhs, bmax, st));
+    CK(cudaMemsetAsync(dx, 0, elems * sizeof(double), st));
+    std::vector<double> berr((size_t)nrhs);
+    int32_t solves = 0;
+    while (true) {
+        CK(cudaMemsetAsync(rmax, 0, 2 * (size_t)nrhs * sizeof(unsigned long long), st));
+        CK(cudaMemsetAsync(ndone, 0, sizeof(int32_t), st));
+        CKL(1, launch_residual(h->d_acsr_ptr, h->d_acsr_col, h->d_aval_csr, db, dx, r, n, nrhs, rmax, xmax, st));
+        CKL(1, launch_check(rmax, xmax, bmax, anorm, nrhs, tol, done, h->d_berr, ndone, st));
+        int32_t nd = 0;
+        CK(cudaMemcpyAsync(&nd, ndone, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(berr.data(), h->d_berr, (size_t)nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        double mx = 0.0;
+        for (double e : berr) mx = std::max(mx, e);
+        inf.berr = mx;
+        if (solves == 1) inf.berr_first = mx;
+        if (nd == nrhs) {
+            inf.converged = 1;
+            break;
+        }
+        if (solves >= 1 + maxit) {
+            inf.converged = 0;
+            break;
+        }
+        rc = enqueue_solve_f32(h, r, d, nrhs, st);
+        if (rc != GLU_OK) return rc;
+        CKL(1, launch_update(dx, d, done, n, nrhs, st));
+        solves++;
+    }
+    inf.iterations = std::max(0, solves - 1);
+    if (solves == 0) inf.berr_first = inf.berr;
+    if (info) *info = inf;
+    if (!xdev) CK(cudaMemcpyAsync(x, dx, elems * sizeof(double), cudaMemcpyDeviceToHost, st));
+    return glu_sync(h);
 }
 
 int glu_get_fill(const glu_handle *h, const int64_t **cp, const int32_t **ri, int64_t *nnz) {
@@ -708,6 +933,12 @@ void glu_destroy(glu_handle *h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
     if (h->fgraph) cudaGraphExecDestroy(h->fgraph);
+    if (h->fgraph32) cudaGraphExecDestroy(h->fgraph32);
+    cudaFree(h->d_lu32);
+    cudaFree(h->d_ir);
+    cudaFree(h->d_irnorm);
+    cudaFree(h->d_done);
+    cudaFree(h->d_berr);
     for (auto &g : h->sgraphs) cudaGraphExecDestroy(g.second);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     cudaFree(h->arena);

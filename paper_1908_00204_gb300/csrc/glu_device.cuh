@@ -108,4 +108,16 @@ cudaError_t launch_solve_level(const SolveArgs<T> &a, bool backward, T *y, int32
                                int32_t nitems, const SolveChunk *chunks, int32_t c0, int32_t c1, T *partial,
                                cudaStream_t s, int *launched);
 
+// launchers (kernels_refine.cu): FP64 residual side of iterative refinement
+cudaError_t launch_csr_values(double *out, const double *aval, const int64_t *src, int64_t nnz, cudaStream_t s);
+cudaError_t launch_anorm(const int64_t *rp, const double *av, int32_t n, unsigned long long *anorm, cudaStream_t s);
+cudaError_t launch_residual(const int64_t *rp, const int32_t *ci, const double *av, const double *b, const double *x,
+                            double *r, int32_t n, int32_t nrhs, unsigned long long *rmax, unsigned long long *xmax,
+                            cudaStream_t s);
+cudaError_t launch_absmax(const double *v, int32_t n, int32_t nrhs, unsigned long long *out, cudaStream_t s);
+cudaError_t launch_check(const unsigned long long *rmax, const unsigned long long *xmax,
+                         const unsigned long long *bmax, const unsigned long long *anorm, int32_t nrhs, double tol,
+                         int32_t *done, double *berr, int32_t *ndone, cudaStream_t s);
+cudaError_t launch_update(double *x, const double *d, const int32_t *done, int32_t n, int32_t nrhs, cudaStream_t s);
+
 }  // namespace glu

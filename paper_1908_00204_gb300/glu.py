@@ -48,6 +48,11 @@ class glu_stats(C.Structure):
                 ("kernel_launches", C.c_int64)]
 
 
+class glu_refine_info(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("converged", C.c_int32), ("berr", C.c_double),
+                ("berr_first", C.c_double)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -72,6 +77,8 @@ def load_library(path: Optional[str] = None):
             "glu_sync": (C.c_int, [P]),
             "glu_solve": (C.c_int, [P, P, P, i32]),
             "glu_solve_noalloc": (C.c_int, [P, P, P, i32]),
+            "glu_factor_f32": (C.c_int, [P, P]),
+            "glu_solve_refine": (C.c_int, [P, P, P, i32, C.c_double, i32, C.POINTER(glu_refine_info)]),
             "glu_get_fill": (C.c_int, [P, C.POINTER(P), C.POINTER(P), C.POINTER(i64)]),
             "glu_get_deps": (C.c_int, [P, C.POINTER(P), C.POINTER(P)]),
             "glu_get_levels": (C.c_int, [P, C.POINTER(i32), C.POINTER(P), C.POINTER(P)]),
@@ -187,6 +194,23 @@ def glu_factor(h: Handle, values) -> None:
     if values is not None and len(values) != h.nnz_a:
         raise ValueError(f"values must have nnz(A) = {h.nnz_a} entries")
     _check(load_library().glu_factor(h._ptr, _ptr(values, np.float64)), "glu_factor", h)
+
+
+def glu_factor_f32(h: Handle, values) -> None:
+    if values is not None and len(values) != h.nnz_a:
+        raise ValueError(f"values must have nnz(A) = {h.nnz_a} entries")
+    _check(load_library().glu_factor_f32(h._ptr, _ptr(values, np.float64)), "glu_factor_f32", h)
+
+
+def glu_solve_refine(h: Handle, b, x=None, tol: float = 1e-12, maxit: int = 10, nrhs: Optional[int] = None):
+    """FP32-factor solve with FP64 refinement; returns (x, info dict)."""
+    k = _nrhs(b, h.n) if nrhs is None else nrhs
+    if x is None:
+        x = np.empty_like(b) if isinstance(b, np.ndarray) else b.new_empty(b.shape)
+    info = glu_refine_info()
+    _check(load_library().glu_solve_refine(h._ptr, _ptr(b, np.float64), _ptr(x, np.float64), int(k),
+                                           float(tol), int(maxit), C.byref(info)), "glu_solve_refine", h)
+    return x, {name: getattr(info, name) for name, _ in glu_refine_info._fields_}
 
 
 def glu_sync(h: Handle) -> None:
