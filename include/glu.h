@@ -178,6 +178,35 @@ int glu_factor_f32(glu_handle *h, const double *values);
 int glu_solve_refine(glu_handle *h, const double *b, double *x, int32_t nrhs, double tol, int32_t maxit,
                      glu_refine_info *info);
 
+/* Batched refactorization: `batch` value sets of the same pattern (Newton
+ * iterations, transient steps, Monte-Carlo corners), value p of set b at
+ * values[b * ld + p], ld >= nnz_a, host or device.  The level schedule of the
+ * single factorization runs once for all sets, with the sets interleaved in
+ * memory (lanes of a warp over the sets); the whole sequence is one
+ * captured CUDA graph launch.  FP64 arithmetic.  The handle keeps one batch:
+ * a later call replaces it.  A zero or non-finite pivot in any set raises
+ * GLU_ERR_ZERO_PIVOT / GLU_ERR_NONFINITE with the smallest such column. */
+int glu_factor_batched(glu_handle *h, const double *values, int32_t batch, int64_t ld);
+
+/* As glu_factor_batched with FP32 values and FP32 accumulation; the FP64
+ * values are kept for glu_solve_batched_refine. */
+int glu_factor_batched_f32(glu_handle *h, const double *values, int32_t batch, int64_t ld);
+
+/* Solves with the last glu_factor_batched factors: right-hand side r of set
+ * b at b[(b * nrhs + r) * n ...], x likewise; host or device.  `batch` must
+ * equal the factorized batch. */
+int glu_solve_batched(glu_handle *h, const double *b, double *x, int32_t nrhs, int32_t batch);
+
+/* FP32 solves with the glu_factor_batched_f32 factors and FP64 iterative
+ * refinement per set and side, until every side of every set reaches tol or
+ * maxit corrections; info summarizes over all sets (berr = the largest). */
+int glu_solve_batched_refine(glu_handle *h, const double *b, double *x, int32_t nrhs, int32_t batch, double tol,
+                             int32_t maxit, glu_refine_info *info);
+
+/* Copy the FP64 factors of one set of the last glu_factor_batched to host
+ * memory (pattern order, nnz_lu doubles); synchronizes. */
+int glu_get_factors_batched(glu_handle *h, int32_t set, double *lu_val_host);
+
 /* Pattern of the fill (Section II-A): lu_colptr[n+1], lu_rowidx[nnz]
  * (rows ascending per column), host memory owned by the handle. */
 int glu_get_fill(const glu_handle *h, const int64_t **lu_colptr,

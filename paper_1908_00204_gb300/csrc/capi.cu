@@ -67,6 +67,26 @@ struct glu_handle {
     int32_t *d_done = nullptr;           // nrhs flags, then the count
     double *d_berr = nullptr;
     int32_t ir_nrhs = 0;
+    // batched value sets (interleaved, stride bS = batch rounded up to 32)
+    int32_t bB = 0, bS = 0;            // factorized batch and its stride
+    int32_t bcap = 0;                  // stride the buffers were sized for
+    int bprec = 0;                     // 64 or 32: which factors are valid (0: none)
+    double *d_vstage = nullptr;        // the caller's values, set-major, ld = nnz_a
+    double *d_aT = nullptr;            // values interleaved
+    double *d_avb = nullptr;           // values interleaved, compressed-row order
+    double *d_lub = nullptr;           // FP64 factors
+    float *d_lub32 = nullptr;          // FP32 factors
+    int32_t *d_bflags = nullptr;
+    int64_t n_bflags = 0;
+    std::vector<std::pair<int, cudaGraphExec_t>> bgraphs;   // key: prec
+    std::vector<int64_t> bgraph_launches;
+    // batched solve buffers
+    int32_t bwork_nrhs = 0;
+    double *d_bwork = nullptr;         // y, z (as T), in, out, r, d, x: n*nrhs*bS each
+    double *d_bpartial = nullptr;
+    unsigned long long *d_bnorm = nullptr;
+    int32_t *d_bdone = nullptr;
+    double *d_bberr = nullptr;
     // solve scratch (grown on demand): permuted vector, staging, partials
     double *d_work = nullptr;
     double *d_bstage = nullptr;
@@ -709,7 +729,10 @@ int glu_sync(glu_handle *h) {
     if (h->opt.host_only) return GLU_OK;
     CK(cudaSetDevice(h->device));
     int rc = read_err(h);
-    if (rc == GLU_ERR_ZERO_PIVOT || rc == GLU_ERR_NONFINITE) h->factored = h->factored32 = false;
+    if (rc == GLU_ERR_ZERO_PIVOT || rc == GLU_ERR_NONFINITE) {
+        h->factored = h->factored32 = false;
+        h->bprec = 0;
+    }
     return rc;
 }
 
@@ -934,6 +957,18 @@ void glu_destroy(glu_handle *h) {
     else cudaDeviceSynchronize();
     if (h->fgraph) cudaGraphExecDestroy(h->fgraph);
     if (h->fgraph32) cudaGraphExecDestroy(h->fgraph32);
+    for (auto &g : h->bgraphs) cudaGraphExecDestroy(g.second);
+    cudaFree(h->d_vstage);
+    cudaFree(h->d_aT);
+    cudaFree(h->d_avb);
+    cudaFree(h->d_lub);
+    cudaFree(h->d_lub32);
+    cudaFree(h->d_bflags);
+    cudaFree(h->d_bwork);
+    cudaFree(h->d_bpartial);
+    cudaFree(h->d_bnorm);
+    cudaFree(h->d_bdone);
+    cudaFree(h->d_bberr);
     cudaFree(h->d_lu32);
     cudaFree(h->d_ir);
     cudaFree(h->d_irnorm);
@@ -1035,4 +1070,287 @@ extern "C" int glu_solve_noalloc(glu_handle *h, const double *b, double *x, int3
     }
     CKL(1, launch_permute_out<double>(x, y, h->d_perm, n, nrhs, st));
     return GLU_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched value sets.
+namespace {
+
+int ensure_batch(glu_handle *h, int32_t S, bool f32) {
+    HostPlan &P = h->P;
+    const int64_t nnz = P.lu_colptr[P.n];
+    if (S != h->bcap) {
+        for (auto &g : h->bgraphs) cudaGraphExecDestroy(g.second);
+        h->bgraphs.clear();
+        h->bgraph_launches.clear();
+        cudaFree(h->d_vstage);
+        cudaFree(h->d_aT);
+        cudaFree(h->d_avb);
+        cudaFree(h->d_lub);
+        cudaFree(h->d_lub32);
+        cudaFree(h->d_bflags);
+        h->d_vstage = h->d_aT = h->d_avb = h->d_lub = nullptr;
+        h->d_lub32 = nullptr;
+        h->d_bflags = nullptr;
+        h->bcap = 0;
+        h->bwork_nrhs = 0;   // solve buffers depend on the stride too
+        const int32_t G = S / 32;
+        const int64_t na = std::max<int64_t>(P.nnz_a, 1);
+        CK(cudaMalloc(&h->d_vstage, na * S * sizeof(double)));
+        CK(cudaMalloc(&h->d_aT, na * S * sizeof(double)));
+        CK(cudaMalloc(&h->d_avb, na * S * sizeof(double)));
+        h->n_bflags = (2 * (int64_t)P.n + (int64_t)P.fwd_chunks.size() + (int64_t)P.bwd_chunks.size()) * G;
+        CK(cudaMalloc(&h->d_bflags, std::max<int64_t>(h->n_bflags, 1) * sizeof(int32_t)));
+        h->bcap = S;
+    }
+    if (f32 && !h->d_lub32) CK(cudaMalloc(&h->d_lub32, std::max<int64_t>(nnz, 1) * S * sizeof(float)));
+    if (!f32 && !h->d_lub) CK(cudaMalloc(&h->d_lub, std::max<int64_t>(nnz, 1) * S * sizeof(double)));
+    return GLU_OK;
+}
+
+template <typename T>
+int enqueue_factor_b(glu_handle *h, T *lu, int32_t B, int32_t S, cudaStream_t st) {
+    HostPlan &P = h->P;
+    CKL(1, launch_reset_err(h->d_err, st));
+    CKL(P.nnz_a > 0, launch_values_in(h->d_aT, h->d_vstage, P.nnz_a, B, P.nnz_a, S, st));
+    CKL(P.lu_colptr[P.n] > 0, launch_gather_b<T>(lu, h->d_aT, h->d_gsrc, P.lu_colptr[P.n], S, st));
+    FactorArgs<T> a = fargs_t<T>(h, lu);
+    const int32_t nl = (int32_t)P.level_ptr.size() - 1;
+    for (int32_t l = 0; l <= nl; l++) {
+        LevelRange r;
+        r.t_begin = l < nl ? P.lvl_task_ptr[l] : 0;
+        r.row_begin = l < nl ? P.lvl_row_ptr[l] : 0;
+        r.lane_begin = l < nl ? P.lvl_lane_ptr[l] : 0;
+        r.t_end = l < nl ? P.lvl_task_ptr[l + 1] : 0;
+        r.n_begin = P.lvl_norm_ptr[l];
+        r.n_end = P.lvl_norm_ptr[l + 1];
+        CKL((r.t_end - r.t_begin) + (r.n_end - r.n_begin) > 0, launch_level_b<T>(a, h->map_bytes, r, S, h->num_sms, st));
+    }
+    CKL(P.n > 0, launch_pivot_b<T>(lu, h->d_diag, P.n, B, S, h->d_err, st));
+    return GLU_OK;
+}
+
+int factor_batched(glu_handle *h, const double *values, int32_t batch, int64_t ld, bool f32) {
+    if (!h || h->opt.host_only || batch <= 0) return GLU_ERR_INVALID;
+    HostPlan &P = h->P;
+    if (P.nnz_a > 0 && (!values || ld < P.nnz_a)) return GLU_ERR_INVALID;
+    CK(cudaSetDevice(h->device));
+    const int32_t S = (batch + 31) / 32 * 32;
+    h->bprec = 0;
+    int rc = ensure_batch(h, S, f32);
+    if (rc != GLU_OK) return rc;
+    h->err_col = -1;
+    cudaStream_t st = h->stream;
+    const bool dev = P.nnz_a > 0 && is_device_ptr(values);
+    if (P.nnz_a > 0)
+        CK(cudaMemcpy2DAsync(h->d_vstage, P.nnz_a * sizeof(double), values, ld * sizeof(double),
+                             P.nnz_a * sizeof(double), batch, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                             st));
+    // the graph depends on the batch through the padding lanes: key on both
+    const int key = (f32 ? 1 : 0) | (batch << 1);
+    size_t gi = 0;
+    while (gi < h->bgraphs.size() && h->bgraphs[gi].first != key) gi++;
+    if (gi == h->bgraphs.size()) {
+        cudaGraphExec_t ex = nullptr;
+        int64_t nlaunch = 0;
+        if (f32)
+            rc = capture(h, [&](cudaStream_t cs) { return enqueue_factor_b<float>(h, h->d_lub32, batch, S, cs); }, &ex,
+                         &nlaunch);
+        else
+            rc = capture(h, [&](cudaStream_t cs) { return enqueue_factor_b<double>(h, h->d_lub, batch, S, cs); }, &ex,
+                         &nlaunch);
+        if (rc != GLU_OK) return rc;
+        h->bgraphs.emplace_back(key, ex);
+        h->bgraph_launches.push_back(nlaunch);
+    }
+    CK(cudaGraphLaunch(h->bgraphs[gi].second, st));
+    h->launches += h->bgraph_launches[gi];
+    h->bB = batch;
+    h->bS = S;
+    h->bprec = f32 ? 32 : 64;
+    if (P.nnz_a > 0 && !dev) return glu_sync(h);
+    return GLU_OK;
+}
+
+int ensure_bwork(glu_handle *h, int32_t nrhs) {
+    if (nrhs <= h->bwork_nrhs) return GLU_OK;
+    cudaFree(h->d_bwork);
+    cudaFree(h->d_bpartial);
+    cudaFree(h->d_bnorm);
+    cudaFree(h->d_bdone);
+    cudaFree(h->d_bberr);
+    h->d_bwork = h->d_bpartial = h->d_bberr = nullptr;
+    h->d_bnorm = nullptr;
+    h->d_bdone = nullptr;
+    h->bwork_nrhs = 0;
+    const int64_t S = h->bcap;
+    const int64_t e = std::max<int64_t>((int64_t)h->P.n * nrhs * S, 1);
+    const int64_t nch = std::max<int64_t>((int64_t)(h->P.fwd_chunks.size() + h->P.bwd_chunks.size()) * nrhs * S, 1);
+    CK(cudaMalloc(&h->d_bwork, 7 * e * sizeof(double)));
+    CK(cudaMalloc(&h->d_bpartial, nch * sizeof(double)));
+    CK(cudaMalloc(&h->d_bnorm, (S + 3 * (size_t)nrhs * S) * sizeof(unsigned long long)));
+    CK(cudaMalloc(&h->d_bdone, (1 + (size_t)nrhs * S) * sizeof(int32_t)));
+    CK(cudaMalloc(&h->d_bberr, (size_t)nrhs * S * sizeof(double)));
+    h->bwork_nrhs = nrhs;
+    return GLU_OK;
+}
+
+template <typename T>
+int enqueue_solve_b(glu_handle *h, const T *lu, const double *in, double *out, int32_t nrhs, cudaStream_t st) {
+    HostPlan &P = h->P;
+    const int32_t n = P.n, S = h->bS, G = S / 32;
+    const int64_t e = (int64_t)n * nrhs * S;
+    T *y = reinterpret_cast<T *>(h->d_bwork);
+    T *z = y + e;
+    CK(cudaMemsetAsync(h->d_bflags, 0, h->n_bflags * sizeof(int32_t), st));
+    CK(cudaMemsetAsync(h->d_serr, 0xff, sizeof(unsigned long long), st));
+    SolveArgs<T> sa = sargs_t<T>(h, lu);
+    DFSolveArgs d;
+    d.items = h->d_df_items;
+    d.nitems = (int32_t)(P.df_items.size() / 8);
+    d.epoch = 1;
+    d.fault_row = -1;
+    d.fchunks = h->d_fwd_chunks;
+    d.bchunks = h->d_bwd_chunks;
+    T *part = reinterpret_cast<T *>(h->d_bpartial);
+    d.fpartial_v = part;
+    d.bpartial_v = part + (int64_t)P.fwd_chunks.size() * nrhs * S;
+    d.fready = h->d_bflags;
+    d.bready = h->d_bflags + (int64_t)n * G;
+    d.fchunk_ready = h->d_bflags + 2 * (int64_t)n * G;
+    d.bchunk_ready = d.fchunk_ready + (int64_t)P.fwd_chunks.size() * G;
+    d.ticket = h->d_ticket;
+    d.abort = h->d_abort;
+    d.err = h->d_serr;
+    d.spin_limit_cycles = h->spin_cycles;
+    CKL(3, launch_solve_b<T>(sa, d, in, out, y, z, h->d_perm, nrhs, S, h->num_sms, st));
+    return GLU_OK;
+}
+
+}  // namespace
+
+extern "C" int glu_factor_batched(glu_handle *h, const double *values, int32_t batch, int64_t ld) {
+    return factor_batched(h, values, batch, ld, false);
+}
+
+extern "C" int glu_factor_batched_f32(glu_handle *h, const double *values, int32_t batch, int64_t ld) {
+    return factor_batched(h, values, batch, ld, true);
+}
+
+extern "C" int glu_solve_batched(glu_handle *h, const double *b, double *x, int32_t nrhs, int32_t batch) {
+    if (!h || h->opt.host_only || nrhs < 0 || batch <= 0) return GLU_ERR_INVALID;
+    if (h->bprec != 64) return GLU_ERR_NOT_FACTORED;
+    if (batch != h->bB) return GLU_ERR_INVALID;
+    HostPlan &P = h->P;
+    const int32_t n = P.n, S = h->bS;
+    const int64_t elems = (int64_t)n * nrhs * batch;
+    if (elems == 0) return GLU_OK;
+    if (!b || !x) return GLU_ERR_INVALID;
+    CK(cudaSetDevice(h->device));
+    int rc = ensure_bwork(h, nrhs);
+    if (rc != GLU_OK) return rc;
+    cudaStream_t st = h->stream;
+    const int64_t e = (int64_t)n * nrhs * S;
+    double *bin = h->d_bwork + 2 * e, *bout = h->d_bwork + 3 * e, *stage = h->d_bwork + 4 * e;
+    const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
+    const double *src = b;
+    if (!bdev) {
+        CK(cudaMemcpyAsync(stage, b, elems * sizeof(double), cudaMemcpyHostToDevice, st));
+        src = stage;
+    }
+    CKL(1, launch_rhs_in(bin, src, n, nrhs, batch, S, st));
+    rc = enqueue_solve_b<double>(h, h->d_lub, bin, bout, nrhs, st);
+    if (rc != GLU_OK) return rc;
+    double *dst = xdev ? x : stage;
+    CKL(1, launch_rhs_out(dst, bout, n, nrhs, batch, S, st));
+    if (!xdev) {
+        CK(cudaMemcpyAsync(x, stage, elems * sizeof(double), cudaMemcpyDeviceToHost, st));
+        return glu_sync(h);
+    }
+    return GLU_OK;
+}
+
+extern "C" int glu_solve_batched_refine(glu_handle *h, const double *b, double *x, int32_t nrhs, int32_t batch,
+                                        double tol, int32_t maxit, glu_refine_info *info) {
+    if (!h || h->opt.host_only || nrhs < 0 || batch <= 0 || maxit < 0 || !(tol >= 0.0)) return GLU_ERR_INVALID;
+    if (h->bprec != 32) return GLU_ERR_NOT_FACTORED;
+    if (batch != h->bB) return GLU_ERR_INVALID;
+    glu_refine_info inf{0, 1, 0.0, 0.0};
+    HostPlan &P = h->P;
+    const int32_t n = P.n, S = h->bS;
+    const int64_t elems = (int64_t)n * nrhs * batch;
+    if (elems == 0) {
+        if (info) *info = inf;
+        return GLU_OK;
+    }
+    if (!b || !x) return GLU_ERR_INVALID;
+    CK(cudaSetDevice(h->device));
+    int rc = ensure_bwork(h, nrhs);
+    if (rc != GLU_OK) return rc;
+    cudaStream_t st = h->stream;
+    const int64_t e = (int64_t)n * nrhs * S;
+    double *bin = h->d_bwork + 2 * e, *stage = h->d_bwork + 3 * e, *r = h->d_bwork + 4 * e, *d = h->d_bwork + 5 * e,
+           *xi = h->d_bwork + 6 * e;
+    unsigned long long *anorm = h->d_bnorm, *rmax = anorm + S, *xmax = rmax + (int64_t)nrhs * S,
+                       *bmax = xmax + (int64_t)nrhs * S;
+    int32_t *done = h->d_bdone, *ndone = h->d_bdone + (int64_t)nrhs * S;
+    const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
+    const double *src = b;
+    if (!bdev) {
+        CK(cudaMemcpyAsync(stage, b, elems * sizeof(double), cudaMemcpyHostToDevice, st));
+        src = stage;
+    }
+    CKL(1, launch_rhs_in(bin, src, n, nrhs, batch, S, st));
+    CK(cudaMemsetAsync(h->d_bnorm, 0, (S + 3 * (size_t)nrhs * S) * sizeof(unsigned long long), st));
+    CKL(3, launch_ir_b(0, h->d_acsr_ptr, h->d_acsr_col, h->d_avb, h->d_aT, h->d_acsr_src, P.nnz_a, bin, xi, r, d, n,
+                       nrhs, batch, S, anorm, rmax, xmax, bmax, tol, done, h->d_bberr, ndone, st));
+    CK(cudaMemsetAsync(xi, 0, e * sizeof(double), st));
+    std::vector<double> berr((size_t)nrhs * S);
+    int32_t solves = 0;
+    while (true) {
+        CK(cudaMemsetAsync(rmax, 0, 2 * (size_t)nrhs * S * sizeof(unsigned long long), st));
+        CK(cudaMemsetAsync(ndone, 0, sizeof(int32_t), st));
+        CKL(2, launch_ir_b(1, h->d_acsr_ptr, h->d_acsr_col, h->d_avb, h->d_aT, h->d_acsr_src, P.nnz_a, bin, xi, r, d,
+                           n, nrhs, batch, S, anorm, rmax, xmax, bmax, tol, done, h->d_bberr, ndone, st));
+        int32_t nd = 0;
+        CK(cudaMemcpyAsync(&nd, ndone, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(berr.data(), h->d_bberr, berr.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        double mx = 0.0;
+        for (double v : berr) mx = std::max(mx, v);
+        inf.berr = mx;
+        if (solves == 1) inf.berr_first = mx;
+        if (nd == nrhs * batch) {
+            inf.converged = 1;
+            break;
+        }
+        if (solves >= 1 + maxit) {
+            inf.converged = 0;
+            break;
+        }
+        rc = enqueue_solve_b<float>(h, h->d_lub32, r, d, nrhs, st);
+        if (rc != GLU_OK) return rc;
+        CKL(1, launch_ir_b(2, h->d_acsr_ptr, h->d_acsr_col, h->d_avb, h->d_aT, h->d_acsr_src, P.nnz_a, bin, xi, r, d, n,
+                           nrhs, batch, S, anorm, rmax, xmax, bmax, tol, done, h->d_bberr, ndone, st));
+        solves++;
+    }
+    inf.iterations = std::max(0, solves - 1);
+    if (solves == 0) inf.berr_first = inf.berr;
+    if (info) *info = inf;
+    double *dst = xdev ? x : stage;
+    CKL(1, launch_rhs_out(dst, xi, n, nrhs, batch, S, st));
+    if (!xdev) CK(cudaMemcpyAsync(x, stage, elems * sizeof(double), cudaMemcpyDeviceToHost, st));
+    return glu_sync(h);
+}
+
+extern "C" int glu_get_factors_batched(glu_handle *h, int32_t set, double *out) {
+    if (!h || !out || h->opt.host_only) return GLU_ERR_INVALID;
+    if (h->bprec != 64) return GLU_ERR_NOT_FACTORED;
+    if (set < 0 || set >= h->bB) return GLU_ERR_INVALID;
+    const int64_t nnz = h->P.lu_colptr[h->P.n];
+    if (nnz == 0) return GLU_OK;
+    CK(cudaSetDevice(h->device));
+    CK(cudaMemcpy2DAsync(out, sizeof(double), h->d_lub + set, (size_t)h->bS * sizeof(double), sizeof(double), nnz,
+                         cudaMemcpyDeviceToHost, h->stream));
+    return glu_sync(h);
 }

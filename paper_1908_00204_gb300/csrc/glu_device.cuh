@@ -120,4 +120,28 @@ cudaError_t launch_check(const unsigned long long *rmax, const unsigned long lon
                          int32_t *done, double *berr, int32_t *ndone, cudaStream_t s);
 cudaError_t launch_update(double *x, const double *d, const int32_t *done, int32_t n, int32_t nrhs, cudaStream_t s);
 
+// launchers (kernels_batched.cu): interleaved value sets, S lanes per entry
+cudaError_t launch_values_in(double *aT, const double *v, int64_t nnz, int32_t B, int64_t ld, int32_t S,
+                             cudaStream_t s);
+template <typename T>
+cudaError_t launch_gather_b(T *lu, const double *aT, const int32_t *gsrc, int64_t nnz, int32_t S, cudaStream_t s);
+template <typename T>
+cudaError_t launch_level_b(const FactorArgs<T> &a, int map_bytes, const LevelRange &r, int32_t S, int num_sms,
+                           cudaStream_t s);
+template <typename T>
+cudaError_t launch_pivot_b(const T *lu, const int64_t *diag_pos, int32_t n, int32_t B, int32_t S,
+                           unsigned long long *err, cudaStream_t s);
+cudaError_t launch_rhs_in(double *out, const double *in, int32_t n, int32_t nrhs, int32_t B, int32_t S,
+                          cudaStream_t s);
+cudaError_t launch_rhs_out(double *out, const double *in, int32_t n, int32_t nrhs, int32_t B, int32_t S,
+                           cudaStream_t s);
+template <typename T>
+cudaError_t launch_solve_b(const SolveArgs<T> &sa, const DFSolveArgs &a, const double *in, double *out, T *y, T *z,
+                           const int32_t *perm, int32_t nrhs, int32_t S, int num_sms, cudaStream_t s);
+cudaError_t launch_ir_b(int op, const int64_t *rp, const int32_t *ci, const double *av, const double *aT,
+                        const int64_t *src, int64_t nnz, const double *bb, double *x, double *r, const double *d,
+                        int32_t n, int32_t nrhs, int32_t B, int32_t S, unsigned long long *anorm,
+                        unsigned long long *rmax, unsigned long long *xmax, unsigned long long *bmax, double tol,
+                        int32_t *done, double *berr, int32_t *ndone, cudaStream_t s);
+
 }  // namespace glu

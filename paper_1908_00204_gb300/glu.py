@@ -78,6 +78,12 @@ def load_library(path: Optional[str] = None):
             "glu_solve": (C.c_int, [P, P, P, i32]),
             "glu_solve_noalloc": (C.c_int, [P, P, P, i32]),
             "glu_factor_f32": (C.c_int, [P, P]),
+            "glu_factor_batched": (C.c_int, [P, P, i32, i64]),
+            "glu_get_factors_batched": (C.c_int, [P, i32, P]),
+            "glu_factor_batched_f32": (C.c_int, [P, P, i32, i64]),
+            "glu_solve_batched": (C.c_int, [P, P, P, i32, i32]),
+            "glu_solve_batched_refine": (C.c_int, [P, P, P, i32, i32, C.c_double, i32,
+                                                   C.POINTER(glu_refine_info)]),
             "glu_solve_refine": (C.c_int, [P, P, P, i32, C.c_double, i32, C.POINTER(glu_refine_info)]),
             "glu_get_fill": (C.c_int, [P, C.POINTER(P), C.POINTER(P), C.POINTER(i64)]),
             "glu_get_deps": (C.c_int, [P, C.POINTER(P), C.POINTER(P)]),
@@ -213,6 +219,52 @@ def glu_solve_refine(h: Handle, b, x=None, tol: float = 1e-12, maxit: int = 10, 
     return x, {name: getattr(info, name) for name, _ in glu_refine_info._fields_}
 
 
+def _batch_values(h, values):
+    """(batch, nnz_a) values -> (pointer, batch, ld)."""
+    shape = tuple(values.shape)
+    if len(shape) != 2 or shape[1] < h.nnz_a:
+        raise ValueError("batched values must be (batch, >= nnz(A))")
+    return _ptr(values, np.float64), shape[0], shape[1]
+
+
+def glu_factor_batched(h: Handle, values) -> None:
+    """FP64 refactorization of every row of ``values`` (batch, nnz(A))."""
+    p, B, ld = _batch_values(h, values)
+    _check(load_library().glu_factor_batched(h._ptr, p, B, ld), "glu_factor_batched", h)
+
+
+def glu_factor_batched_f32(h: Handle, values) -> None:
+    p, B, ld = _batch_values(h, values)
+    _check(load_library().glu_factor_batched_f32(h._ptr, p, B, ld), "glu_factor_batched_f32", h)
+
+
+def _batch_rhs(h, b):
+    shape = tuple(b.shape)
+    if len(shape) != 3 or shape[2] != h.n:
+        raise ValueError("batched right-hand sides must be (batch, nrhs, n)")
+    return shape[0], shape[1]
+
+
+def glu_solve_batched(h: Handle, b, x=None):
+    B, k = _batch_rhs(h, b)
+    if x is None:
+        x = np.empty_like(b) if isinstance(b, np.ndarray) else b.new_empty(b.shape)
+    _check(load_library().glu_solve_batched(h._ptr, _ptr(b, np.float64), _ptr(x, np.float64), k, B),
+           "glu_solve_batched", h)
+    return x
+
+
+def glu_solve_batched_refine(h: Handle, b, x=None, tol: float = 1e-12, maxit: int = 10):
+    B, k = _batch_rhs(h, b)
+    if x is None:
+        x = np.empty_like(b) if isinstance(b, np.ndarray) else b.new_empty(b.shape)
+    info = glu_refine_info()
+    _check(load_library().glu_solve_batched_refine(h._ptr, _ptr(b, np.float64), _ptr(x, np.float64), k, B,
+                                                   float(tol), int(maxit), C.byref(info)),
+           "glu_solve_batched_refine", h)
+    return x, {name: getattr(info, name) for name, _ in glu_refine_info._fields_}
+
+
 def glu_sync(h: Handle) -> None:
     _check(load_library().glu_sync(h._ptr), "glu_sync", h)
 
@@ -278,6 +330,14 @@ def glu_get_factors(h: Handle) -> np.ndarray:
     st = glu_get_stats(h)
     out = np.empty(max(st["nnz_lu"], 1), np.float64)
     _check(load_library().glu_get_factors(h._ptr, out.ctypes.data), "glu_get_factors", h)
+    return out[:st["nnz_lu"]]
+
+
+def glu_get_factors_batched(h: Handle, set_index: int) -> np.ndarray:
+    st = glu_get_stats(h)
+    out = np.empty(max(st["nnz_lu"], 1), np.float64)
+    _check(load_library().glu_get_factors_batched(h._ptr, int(set_index), out.ctypes.data),
+           "glu_get_factors_batched", h)
     return out[:st["nnz_lu"]]
 
 
