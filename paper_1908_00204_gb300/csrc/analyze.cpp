@@ -511,11 +511,11 @@ void solve_levels(HostPlan &P) {
     };
     group(lf, nf, P.fwd_ptr, P.fwd_rows);
     group(lb, nb, P.bwd_ptr, P.bwd_rows);
-    // rows with more than SOLVE_CHUNK entries: their dot products are split
+    // rows with more than `chunk` entries: their dot products are split
     // into chunks, summed later in chunk order
     auto items = [](const std::vector<int32_t> &ptr, const std::vector<int32_t> &rows,
-                    const std::vector<int64_t> &rptr, std::vector<SolveRow> &it, std::vector<SolveChunk> &ch,
-                    std::vector<int32_t> &chp) {
+                    const std::vector<int64_t> &rptr, int64_t chunk, std::vector<SolveRow> &it,
+                    std::vector<SolveChunk> &ch, std::vector<int32_t> &chp) {
         const size_t nlev = ptr.size() - 1;
         it.clear();
         ch.clear();
@@ -525,8 +525,8 @@ void solve_levels(HostPlan &P) {
                 const int32_t i = rows[q];
                 const int64_t b = rptr[i], e = rptr[i + 1];
                 SolveRow r{i, (int32_t)ch.size(), (int32_t)ch.size(), 0};
-                if (e - b > SOLVE_CHUNK) {
-                    for (int64_t p = b; p < e; p += SOLVE_CHUNK) ch.push_back(SolveChunk{p, std::min(e, p + SOLVE_CHUNK)});
+                if (e - b > chunk) {
+                    for (int64_t p = b; p < e; p += chunk) ch.push_back(SolveChunk{p, std::min(e, p + chunk)});
                     r.ce = (int32_t)ch.size();
                 }
                 it.push_back(r);
@@ -534,16 +534,12 @@ void solve_levels(HostPlan &P) {
             chp[l + 1] = (int32_t)ch.size();
         }
     };
-    items(P.fwd_ptr, P.fwd_rows, P.lrow_ptr, P.fwd_items, P.fwd_chunks, P.fwd_chunk_ptr);
-    items(P.bwd_ptr, P.bwd_rows, P.urow_ptr, P.bwd_items, P.bwd_chunks, P.bwd_chunk_ptr);
-
     // Dataflow order: a chunk of a long row only reads rows of lower levels,
     // so it goes at level 1 + (highest level it reads), before the rows of
     // that level; far ahead of its row when it covers early columns.
-    P.df_items.clear();
-    auto emit = [&](bool bwd, const std::vector<int32_t> &lv, int32_t nlev, const std::vector<SolveRow> &it,
-                    const std::vector<SolveChunk> &ch, const std::vector<int32_t> &colv,
-                    const std::vector<int32_t> &ptr) {
+    auto emit = [](std::vector<int32_t> &out, bool bwd, const std::vector<int32_t> &lv, int32_t nlev,
+                   const std::vector<SolveRow> &it, const std::vector<SolveChunk> &ch,
+                   const std::vector<int32_t> &colv, const std::vector<int32_t> &ptr) {
         std::vector<int32_t> chlev(ch.size(), 0), chrow(ch.size(), 0);
         for (const SolveRow &r : it)
             for (int32_t c = r.cb; c < r.ce; c++) chrow[c] = r.row;
@@ -565,17 +561,25 @@ void solve_levels(HostPlan &P) {
             for (int32_t q = cnt[l]; q < cnt[l + 1]; q++) {
                 const int32_t c = byl[q];
                 const int32_t rec[8] = {chrow[c], 0, 0, c, fl | 2, 0, 0, 0};
-                P.df_items.insert(P.df_items.end(), rec, rec + 8);
+                out.insert(out.end(), rec, rec + 8);
             }
             for (int32_t q = ptr[l]; q < ptr[l + 1]; q++) {
                 const SolveRow &r = it[q];
                 const int32_t rec[8] = {r.row, r.cb, r.ce, -1, fl, 0, 0, 0};
-                P.df_items.insert(P.df_items.end(), rec, rec + 8);
+                out.insert(out.end(), rec, rec + 8);
             }
         }
     };
-    emit(false, lf, nf, P.fwd_items, P.fwd_chunks, P.lrow_col, P.fwd_ptr);
-    emit(true, lb, nb, P.bwd_items, P.bwd_chunks, P.urow_col, P.bwd_ptr);
+    items(P.fwd_ptr, P.fwd_rows, P.lrow_ptr, SOLVE_CHUNK, P.fwd_items, P.fwd_chunks, P.fwd_chunk_ptr);
+    items(P.bwd_ptr, P.bwd_rows, P.urow_ptr, SOLVE_CHUNK, P.bwd_items, P.bwd_chunks, P.bwd_chunk_ptr);
+    P.df_items.clear();
+    emit(P.df_items, false, lf, nf, P.fwd_items, P.fwd_chunks, P.lrow_col, P.fwd_ptr);
+    emit(P.df_items, true, lb, nb, P.bwd_items, P.bwd_chunks, P.urow_col, P.bwd_ptr);
+    items(P.fwd_ptr, P.fwd_rows, P.lrow_ptr, SOLVE_CHUNK_B, P.bfwd_items, P.bfwd_chunks, P.bfwd_chunk_ptr);
+    items(P.bwd_ptr, P.bwd_rows, P.urow_ptr, SOLVE_CHUNK_B, P.bbwd_items, P.bbwd_chunks, P.bbwd_chunk_ptr);
+    P.df_items_b.clear();
+    emit(P.df_items_b, false, lf, nf, P.bfwd_items, P.bfwd_chunks, P.lrow_col, P.fwd_ptr);
+    emit(P.df_items_b, true, lb, nb, P.bbwd_items, P.bbwd_chunks, P.urow_col, P.bwd_ptr);
 }
 
 }  // namespace

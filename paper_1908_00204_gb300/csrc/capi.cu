@@ -87,6 +87,8 @@ struct glu_handle {
     unsigned long long *d_bnorm = nullptr;
     int32_t *d_bdone = nullptr;
     double *d_bberr = nullptr;
+    DFItem *d_bdf_items = nullptr;     // batched solve schedule (shorter chunks)
+    SolveChunk *d_bfwd_chunks = nullptr, *d_bbwd_chunks = nullptr;
     // solve scratch (grown on demand): permuted vector, staging, partials
     double *d_work = nullptr;
     double *d_bstage = nullptr;
@@ -456,7 +458,9 @@ int upload_plan(glu_handle *h) {
            o_flags = c.take<int32_t>(2 * (size_t)n + P.fwd_chunks.size() + P.bwd_chunks.size()),
            o_ticket = c.take<unsigned>(1), o_abort = c.take<unsigned>(1), o_serr = c.take<unsigned long long>(1),
            o_acp = c.take<int64_t>(n + 1), o_acc = c.take<int32_t>(P.acsr_col.size()),
-           o_acs = c.take<int64_t>(P.acsr_src.size()), o_acv = c.take<double>(P.acsr_src.size());
+           o_acs = c.take<int64_t>(P.acsr_src.size()), o_acv = c.take<double>(P.acsr_src.size()),
+           o_bdfi = c.take<int32_t>(P.df_items_b.size()), o_bfc = c.take<SolveChunk>(P.bfwd_chunks.size()),
+           o_bbc = c.take<SolveChunk>(P.bbwd_chunks.size());
     h->arena_bytes = c.off + 256;
     CK(cudaMalloc(&h->arena, h->arena_bytes));
     char *A = h->arena;
@@ -494,6 +498,9 @@ int upload_plan(glu_handle *h) {
     h->d_acsr_col = at<int32_t>(A, o_acc);
     h->d_acsr_src = at<int64_t>(A, o_acs);
     h->d_aval_csr = at<double>(A, o_acv);
+    h->d_bdf_items = at<DFItem>(A, o_bdfi);
+    h->d_bfwd_chunks = at<SolveChunk>(A, o_bfc);
+    h->d_bbwd_chunks = at<SolveChunk>(A, o_bbc);
     int32_t *d_pair_k = at<int32_t>(A, o_pk);
     int64_t *d_lcp = at<int64_t>(A, o_lcp);
     int32_t *d_lri = at<int32_t>(A, o_lri);
@@ -523,6 +530,9 @@ int upload_plan(glu_handle *h) {
     CK(upload(h->d_acsr_ptr, P.acsr_ptr));
     CK(upload(h->d_acsr_col, P.acsr_col));
     CK(upload(h->d_acsr_src, P.acsr_src));
+    CK(upload(reinterpret_cast<int32_t *>(h->d_bdf_items), P.df_items_b));
+    CK(upload(h->d_bfwd_chunks, P.bfwd_chunks));
+    CK(upload(h->d_bbwd_chunks, P.bbwd_chunks));
     CK(cudaMemset(h->d_flags, 0, std::max<int64_t>(h->n_flags, 1) * sizeof(int32_t)));
     CK(cudaMemset(h->d_serr, 0xff, sizeof(unsigned long long)));
     {
@@ -1099,7 +1109,7 @@ int ensure_batch(glu_handle *h, int32_t S, bool f32) {
         CK(cudaMalloc(&h->d_vstage, na * S * sizeof(double)));
         CK(cudaMalloc(&h->d_aT, na * S * sizeof(double)));
         CK(cudaMalloc(&h->d_avb, na * S * sizeof(double)));
-        h->n_bflags = (2 * (int64_t)P.n + (int64_t)P.fwd_chunks.size() + (int64_t)P.bwd_chunks.size()) * G;
+        h->n_bflags = (2 * (int64_t)P.n + (int64_t)P.bfwd_chunks.size() + (int64_t)P.bbwd_chunks.size()) * G;
         CK(cudaMalloc(&h->d_bflags, std::max<int64_t>(h->n_bflags, 1) * sizeof(int32_t)));
         h->bcap = S;
     }
@@ -1185,7 +1195,7 @@ int ensure_bwork(glu_handle *h, int32_t nrhs) {
     h->bwork_nrhs = 0;
     const int64_t S = h->bcap;
     const int64_t e = std::max<int64_t>((int64_t)h->P.n * nrhs * S, 1);
-    const int64_t nch = std::max<int64_t>((int64_t)(h->P.fwd_chunks.size() + h->P.bwd_chunks.size()) * nrhs * S, 1);
+    const int64_t nch = std::max<int64_t>((int64_t)(h->P.bfwd_chunks.size() + h->P.bbwd_chunks.size()) * nrhs * S, 1);
     CK(cudaMalloc(&h->d_bwork, 7 * e * sizeof(double)));
     CK(cudaMalloc(&h->d_bpartial, nch * sizeof(double)));
     CK(cudaMalloc(&h->d_bnorm, (S + 3 * (size_t)nrhs * S) * sizeof(unsigned long long)));
@@ -1206,19 +1216,19 @@ int enqueue_solve_b(glu_handle *h, const T *lu, const double *in, double *out, i
     CK(cudaMemsetAsync(h->d_serr, 0xff, sizeof(unsigned long long), st));
     SolveArgs<T> sa = sargs_t<T>(h, lu);
     DFSolveArgs d;
-    d.items = h->d_df_items;
-    d.nitems = (int32_t)(P.df_items.size() / 8);
+    d.items = h->d_bdf_items;
+    d.nitems = (int32_t)(P.df_items_b.size() / 8);
     d.epoch = 1;
     d.fault_row = -1;
-    d.fchunks = h->d_fwd_chunks;
-    d.bchunks = h->d_bwd_chunks;
+    d.fchunks = h->d_bfwd_chunks;
+    d.bchunks = h->d_bbwd_chunks;
     T *part = reinterpret_cast<T *>(h->d_bpartial);
     d.fpartial_v = part;
-    d.bpartial_v = part + (int64_t)P.fwd_chunks.size() * nrhs * S;
+    d.bpartial_v = part + (int64_t)P.bfwd_chunks.size() * nrhs * S;
     d.fready = h->d_bflags;
     d.bready = h->d_bflags + (int64_t)n * G;
     d.fchunk_ready = h->d_bflags + 2 * (int64_t)n * G;
-    d.bchunk_ready = d.fchunk_ready + (int64_t)P.fwd_chunks.size() * G;
+    d.bchunk_ready = d.fchunk_ready + (int64_t)P.bfwd_chunks.size() * G;
     d.ticket = h->d_ticket;
     d.abort = h->d_abort;
     d.err = h->d_serr;

@@ -74,7 +74,8 @@ struct SolveChunk {
     int64_t p0;
     int64_t p1;
 };
-constexpr int64_t SOLVE_CHUNK = 512;
+constexpr int64_t SOLVE_CHUNK = 128;    // single matrix: lanes over a row's entries
+constexpr int64_t SOLVE_CHUNK_B = 32;   // batched: lanes over the sets, entries in sequence
 
 // Everything glu_analyze computes on the host.
 struct HostPlan {
@@ -117,6 +118,11 @@ struct HostPlan {
     // dataflow solve: items in topological order, packed as int32 x 8
     // {row, cb, ce, chunk, flags, 0, 0, 0}
     std::vector<int32_t> df_items;
+    // the same for the batched solve, with shorter chunks
+    std::vector<SolveRow> bfwd_items, bbwd_items;
+    std::vector<SolveChunk> bfwd_chunks, bbwd_chunks;
+    std::vector<int32_t> bfwd_chunk_ptr, bbwd_chunk_ptr;
+    std::vector<int32_t> df_items_b;
     // A in compressed rows (original numbering) for residuals
     std::vector<int64_t> acsr_ptr;
     std::vector<int32_t> acsr_col;

@@ -212,8 +212,31 @@ __device__ __forceinline__ void wait_b(const int32_t *flag, const DFSolveArgs &a
     }
 }
 
+// sum over entries p0..p1-1 of M[pos[p]] * v[col[p]] for this lane's set;
+// entries in sequence, BU independent loads in flight
+template <typename T>
+__device__ __forceinline__ T dot_b(const T *__restrict__ lu, const int64_t *__restrict__ pos,
+                                   const int32_t *__restrict__ col, const T *v, int64_t p0, int64_t p1, int32_t S) {
+    T acc = (T)0;
+    for (int64_t pb = p0; pb < p1; pb += BU) {
+        T lv[BU], yv[BU];
+#pragma unroll
+        for (int u = 0; u < BU; u++)
+            if (pb + u < p1) {
+                lv[u] = lu[pos[pb + u] * S];
+                yv[u] = __ldcg(v + (int64_t)col[pb + u] * S);
+            }
+#pragma unroll
+        for (int u = 0; u < BU; u++)
+            if (pb + u < p1) acc += lv[u] * yv[u];
+    }
+    return acc;
+}
+
 // Dataflow solve for all sets: work item (DF item, lane group).  Flags are per
-// (row, group) and per (chunk, group).  Forward writes y, backward z.
+// (row, group) and per (chunk, group).  Forward writes y, backward z.  The
+// lanes of a warp acquire the flags of an item's entries together, then each
+// lane runs the entries in sequence for its own set.
 template <typename T>
 __global__ void __launch_bounds__(128) k_solve_df_b(const SolveArgs<T> s, const DFSolveArgs a, T *y, T *z,
                                                     int32_t nrhs, int32_t S) {
@@ -236,29 +259,27 @@ __global__ void __launch_bounds__(128) k_solve_df_b(const SolveArgs<T> s, const 
         const int32_t *col = bwd ? s.urow_col : s.lrow_col;
         int32_t *ready = bwd ? a.bready : a.fready;
         const T *src = bwd ? z : y;
+        const T *lub = s.lu + b;
         if (it.flags & DF_CHUNK) {
             const SolveChunk ch = (bwd ? a.bchunks : a.fchunks)[it.chunk];
             T *partial = static_cast<T *>(bwd ? a.bpartial_v : a.fpartial_v);
-            if (lane == 0)
-                for (int64_t p = ch.p0; p < ch.p1; p++) wait_b(ready + (int64_t)col[p] * G + g, a);
+            for (int64_t p = ch.p0 + lane; p < ch.p1; p += 32) wait_b(ready + (int64_t)col[p] * G + g, a);
             __syncwarp();
-            for (int32_t r = 0; r < nrhs; r++) {
-                T acc = (T)0;
-                for (int64_t p = ch.p0; p < ch.p1; p++)
-                    acc += s.lu[pos[p] * S + b] * __ldcg(src + ((int64_t)r * n + col[p]) * S + b);
-                partial[(((int64_t)it.chunk * nrhs) + r) * S + b] = acc;
-            }
+            for (int32_t r = 0; r < nrhs; r++)
+                partial[(((int64_t)it.chunk * nrhs) + r) * S + b] =
+                    dot_b<T>(lub, pos, col, src + (int64_t)r * n * S + b, ch.p0, ch.p1, S);
             __syncwarp();
             if (lane == 0) st_release_b((bwd ? a.bchunk_ready : a.fchunk_ready) + (int64_t)it.chunk * G + g, a.epoch);
             continue;
         }
         const int32_t i = it.row;
-        if (lane == 0) {
-            if (bwd) wait_b(a.fready + (int64_t)i * G + g, a);
-            const int32_t *crd = bwd ? a.bchunk_ready : a.fchunk_ready;
-            for (int32_t c = it.cb; c < it.ce; c++) wait_b(crd + (int64_t)c * G + g, a);
-            if (it.ce == it.cb)
-                for (int64_t p = rptr[i]; p < rptr[i + 1]; p++) wait_b(ready + (int64_t)col[p] * G + g, a);
+        const int64_t p0 = rptr[i], p1 = rptr[i + 1];
+        const int32_t *crd = bwd ? a.bchunk_ready : a.fchunk_ready;
+        if (lane == 0 && bwd) wait_b(a.fready + (int64_t)i * G + g, a);
+        if (it.ce > it.cb) {
+            for (int32_t c = it.cb + lane; c < it.ce; c += 32) wait_b(crd + (int64_t)c * G + g, a);
+        } else {
+            for (int64_t p = p0 + lane; p < p1; p += 32) wait_b(ready + (int64_t)col[p] * G + g, a);
         }
         __syncwarp();
         const T d = bwd ? s.lu[s.diag_pos[i] * S + b] : (T)1;
@@ -268,8 +289,7 @@ __global__ void __launch_bounds__(128) k_solve_df_b(const SolveArgs<T> s, const 
             if (it.ce > it.cb) {
                 for (int32_t c = it.cb; c < it.ce; c++) acc += __ldcg(partial + (((int64_t)c * nrhs) + r) * S + b);
             } else {
-                for (int64_t p = rptr[i]; p < rptr[i + 1]; p++)
-                    acc += s.lu[pos[p] * S + b] * __ldcg(src + ((int64_t)r * n + col[p]) * S + b);
+                acc = dot_b<T>(lub, pos, col, src + (int64_t)r * n * S + b, p0, p1, S);
             }
             const T v = __ldcg(y + ((int64_t)r * n + i) * S + b);
             (bwd ? z : y)[((int64_t)r * n + i) * S + b] = bwd ? (v - acc) / d : v - acc;
