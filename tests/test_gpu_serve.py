@@ -1,0 +1,76 @@
+"""Serving loop: requests for several patterns with new values and 1-4
+right-hand sides, submitted while others run.  Every result equals, within
+the factor tolerance, the result of the same request served alone, and meets
+the FP64 backward-error bound."""
+import numpy as np
+import pytest
+
+import synth
+from parity import BERR_TOL, backward_error
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def glu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1908_00204_gb300 as g
+    g.build.build()
+    g.load_library()
+    return g
+
+
+def mixed_requests(n_req=60, seed=0):
+    from paper_1908_00204_gb300.serve import Request
+    mats = {f"p{k}": synth.CircuitMatrix(synth.CircuitSpec(r, c, 8, nf, 0.02, 0.05, "nd"), 10 + k)
+            for k, (r, c, nf) in enumerate([(20, 25, 10), (30, 40, 20), (40, 50, 30)])}
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(n_req):
+        key = f"p{rng.integers(3)}"
+        m = mats[key]
+        k = int(rng.integers(1, 5))
+        reqs.append(Request(i, key, m.values(5000 + i, sigma=0.1, base_seed=3), synth.rhs(m.n, k, 9000 + i)))
+    return mats, reqs
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_mix_equals_alone(glu, precision):
+    from paper_1908_00204_gb300.serve import Request, Server
+    mats, reqs = mixed_requests()
+    srv = Server(device_budget_bytes=8e9, max_batch=16, slots=3, precision=precision)
+    for key, m in mats.items():
+        srv.register(key, m.n, m.colptr, m.rowidx, m.perm)
+    arrivals = np.cumsum(np.random.default_rng(1).exponential(1 / 2000.0, len(reqs)))
+    srv.run(list(arrivals), lambda i: reqs[i])
+    assert len(srv.done) == len(reqs) and srv.batches < len(reqs)   # some batching happened
+    alone = Server(device_budget_bytes=8e9, max_batch=1, slots=1, precision=precision)
+    for key, m in mats.items():
+        alone.register(key, m.n, m.colptr, m.rowidx, m.perm)
+    for r in reqs:
+        m = mats[r.key]
+        assert backward_error(m.n, m.colptr, m.rowidx, r.values, r.b, r.x) <= BERR_TOL
+        single = Request(r.rid, r.key, r.values, r.b)
+        alone.submit(single)
+        alone.drain()
+        np.testing.assert_allclose(r.x, single.x, rtol=1e-10, atol=1e-13)
+    lat = srv.latencies()
+    assert lat.size == len(reqs) and np.all(lat > 0)
+
+
+def test_budget_evicts_idle_patterns(glu):
+    from paper_1908_00204_gb300.serve import Server
+    mats, reqs = mixed_requests(12, seed=4)
+    # a budget that holds roughly one pattern forces evictions between patterns
+    one = max(glu.glu_get_stats(glu.glu_analyze(m.n, m.colptr, m.rowidx, m.perm))["device_bytes"]
+              for m in mats.values())
+    srv = Server(device_budget_bytes=1.5 * one + 64e6, max_batch=1, slots=1)
+    for key, m in mats.items():
+        srv.register(key, m.n, m.colptr, m.rowidx, m.perm)
+    for r in reqs:
+        srv.submit(r)
+    srv.drain()
+    assert len(srv.done) == len(reqs)
+    assert srv.evictions > 0 and srv._bytes_in_use() <= srv.budget
