@@ -1,7 +1,10 @@
 """Serving loop: requests for several patterns with new values and 1-4
-right-hand sides, submitted while others run.  Every result equals, within
-the factor tolerance, the result of the same request served alone, and meets
-the FP64 backward-error bound."""
+right-hand sides, submitted while others run.  Every result meets the FP64
+backward-error bound and equals the result of the same request served alone:
+FP64 within 1e-10 relative (the batched and single kernels differ only in
+rounding order); FP32 + refinement, refined to a backward error of 1e-14 in
+both runs, within 1e-8 relative (two solutions with backward error <= 1e-14
+differ by at most about cond(A) * 1e-14, and cond(A) < 1e5 here)."""
 import numpy as np
 import pytest
 
@@ -40,13 +43,15 @@ def mixed_requests(n_req=60, seed=0):
 def test_mix_equals_alone(glu, precision):
     from paper_1908_00204_gb300.serve import Request, Server
     mats, reqs = mixed_requests()
-    srv = Server(device_budget_bytes=8e9, max_batch=16, slots=3, precision=precision)
+    tol = 1e-14 if precision == "fp32" else 1e-12
+    rtol = 1e-8 if precision == "fp32" else 1e-10
+    srv = Server(device_budget_bytes=8e9, max_batch=16, slots=3, precision=precision, tol=tol, maxit=20)
     for key, m in mats.items():
         srv.register(key, m.n, m.colptr, m.rowidx, m.perm)
     arrivals = np.cumsum(np.random.default_rng(1).exponential(1 / 2000.0, len(reqs)))
     srv.run(list(arrivals), lambda i: reqs[i])
     assert len(srv.done) == len(reqs) and srv.batches < len(reqs)   # some batching happened
-    alone = Server(device_budget_bytes=8e9, max_batch=1, slots=1, precision=precision)
+    alone = Server(device_budget_bytes=8e9, max_batch=1, slots=1, precision=precision, tol=tol, maxit=20)
     for key, m in mats.items():
         alone.register(key, m.n, m.colptr, m.rowidx, m.perm)
     for r in reqs:
@@ -55,7 +60,7 @@ def test_mix_equals_alone(glu, precision):
         single = Request(r.rid, r.key, r.values, r.b)
         alone.submit(single)
         alone.drain()
-        np.testing.assert_allclose(r.x, single.x, rtol=1e-10, atol=1e-13)
+        np.testing.assert_allclose(r.x, single.x, rtol=rtol, atol=1e-13)
     lat = srv.latencies()
     assert lat.size == len(reqs) and np.all(lat > 0)
 
