@@ -71,7 +71,7 @@ def test_budget_evicts_idle_patterns(glu):
     # a budget that holds roughly one pattern forces evictions between patterns
     one = max(glu.glu_get_stats(glu.glu_analyze(m.n, m.colptr, m.rowidx, m.perm))["device_bytes"]
               for m in mats.values())
-    srv = Server(device_budget_bytes=1.5 * one + 64e6, max_batch=1, slots=1)
+    srv = Server(device_budget_bytes=1.2 * one, max_batch=1, slots=1)
     for key, m in mats.items():
         srv.register(key, m.n, m.colptr, m.rowidx, m.perm)
     for r in reqs:
