@@ -110,7 +110,7 @@ class Server:
     def _batch_bytes(self, res: _Resident, batch: int, nrhs: int) -> int:
         s = (batch + 31) // 32 * 32
         per_value = 8 if self.precision == "fp64" else 4
-        a = res.pat.colptr[-1]
+        a = int(res.pat.colptr[-1])
         return int(res.nnz_lu * s * per_value + 3 * a * s * 8 + 8 * res.pat.n * nrhs * s * 8)
 
     def _make_room(self, need: int, keep: str) -> bool:
