@@ -156,8 +156,10 @@ class Server:
             return False
         take = min(len(q), self.max_batch)
         nrhs = max(r.b.shape[0] for r in list(q)[:take])
-        # shrink the batch until its buffers fit the budget
-        while take > 1 and not self._make_room(self._batch_bytes(res, take, nrhs) - res.batch_bytes, best):
+        # a batch never evicts other patterns: it shrinks to what the budget
+        # leaves (batch buffers stay with the pattern until it is evicted)
+        free = self.budget - self._bytes_in_use()
+        while take > 1 and self._batch_bytes(res, take, nrhs) - res.batch_bytes > free:
             take //= 2
         reqs = [q.popleft() for _ in range(take)]
         nrhs = max(r.b.shape[0] for r in reqs)
