@@ -234,7 +234,7 @@ void levelize(HostPlan &P) {
 // becomes KIND_ROW tasks (split by row ranges when large), a group with many
 // sources becomes one KIND_SRC task per touched 32-position chunk of column
 // k.  Each level's kernel also normalizes the previous level's L columns.
-void schedule(HostPlan &P, const glu_options &opt) {
+void schedule(HostPlan &P, const glu_options &opt, int num_sms) {
     const int32_t n = P.n;
     const int32_t nl = (int32_t)P.level_ptr.size() - 1;
     const int64_t piece = opt.piece_updates > 0 ? opt.piece_updates : 1024;
@@ -290,17 +290,25 @@ void schedule(HostPlan &P, const glu_options &opt) {
     std::vector<std::vector<PSeg>> chunk_segs;
     std::vector<int32_t> touched;
 
+    // A level's time is set by its slowest work item.  Large single-target
+    // work is cut into row pieces so that a level has about two tasks per
+    // resident warp (16 per SM), but no piece below 128 updates: one batch of
+    // loads per lane.
+    const int64_t resident_warps = (int64_t)(num_sms > 0 ? num_sms : 152) * 16;
     for (int32_t l = 0; l < nl; l++) {
         lvl_tasks.clear();
         int64_t g = lvl_pair_ptr[l];
         const int64_t ge_l = lvl_pair_ptr[l + 1];
+        int64_t lvl_work = 0;
+        for (int64_t q = g; q < ge_l; q++) lvl_work += lcount(P.pair_j[q]);
+        const int64_t piece_l = std::max<int64_t>(128, std::min<int64_t>(piece, lvl_work / (2 * resident_warps)));
         while (g < ge_l) {
             const int32_t k = P.pair_k[g];
             int64_t ge = g;
             int64_t work = 0;
             while (ge < ge_l && P.pair_k[ge] == k) { work += lcount(P.pair_j[ge]); ge++; }
             const int64_t nsrc = ge - g;
-            if (nsrc < src_min && work <= piece) {
+            if (nsrc < src_min && work <= piece_l) {
                 Task t{(int32_t)0, 0, KIND_ROW, 0, 0, work};
                 t.seg_begin = (int32_t)psegs.size();
                 for (int64_t q = g; q < ge; q++)
@@ -350,7 +358,7 @@ void schedule(HostPlan &P, const glu_options &opt) {
                 // tasks.  A chunk reached by one segment holds rows that no
                 // other source of this group updates: those segments need no
                 // ordering, so consecutive ones of a source merge and are
-                // packed into KIND_ROW tasks of about `piece` updates.
+                // packed into small tasks.
                 std::vector<PSeg> priv;
                 for (int32_t ch : touched) {
                     std::vector<PSeg> &cs = chunk_segs[ch];
@@ -387,14 +395,14 @@ void schedule(HostPlan &P, const glu_options &opt) {
                     lvl_tasks.push_back(t);
                 }
             } else {                // few sources, much work: consecutive chunks merged into
-                // KIND_ROW pieces of about `piece` updates; inside a piece
+                // KIND_ROW pieces of about `piece_l` updates; inside a piece
                 // the segments of one source are contiguous in t, so they
                 // merge into one, kept in ascending source order.
                 size_t a = 0;
                 while (a < touched.size()) {
                     size_t b = a;
                     int64_t w = 0;
-                    while (b < touched.size() && (b == a || w + chunk_work[touched[b]] <= piece)) {
+                    while (b < touched.size() && (b == a || w + chunk_work[touched[b]] <= piece_l)) {
                         w += chunk_work[touched[b]];
                         b++;
                     }
@@ -585,7 +593,7 @@ void solve_levels(HostPlan &P) {
 }  // namespace
 
 int analyze_host(int32_t n, const int32_t *colptr, const int32_t *rowidx, const int32_t *perm,
-                 const glu_options &opt, HostPlan &P, std::string &why) {
+                 const glu_options &opt, int num_sms, HostPlan &P, std::string &why) {
     if (n < 0 || (n > 0 && (!colptr || !rowidx))) { why = "bad arguments"; return GLU_ERR_INVALID; }
     P.n = n;
     if (n == 0) {
@@ -649,7 +657,7 @@ int analyze_host(int32_t n, const int32_t *colptr, const int32_t *rowidx, const 
     double t2 = now_ms();
     levelize(P);
     double t3 = now_ms();
-    schedule(P, opt);
+    schedule(P, opt, num_sms);
     solve_levels(P);
     // A in compressed rows (original numbering), for residuals
     P.acsr_ptr.assign((size_t)n + 1, 0);

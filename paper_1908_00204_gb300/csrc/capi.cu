@@ -600,8 +600,14 @@ int glu_analyze_opts(int32_t n, const int32_t *colptr, const int32_t *rowidx, co
         h->opt = *opts;
     }
     int rc;
+    int sms = 152;
+    if (!h->opt.host_only) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaGetLastError();
+    }
     try {
-        rc = analyze_host(n, colptr, rowidx, perm, h->opt, h->P, h->why);
+        rc = analyze_host(n, colptr, rowidx, perm, h->opt, sms, h->P, h->why);
     } catch (const std::bad_alloc &) {
         rc = GLU_ERR_OOM;
     }

@@ -137,6 +137,6 @@ struct HostPlan {
 
 // Runs every host step of glu_analyze.  Returns a GLU_ code.
 int analyze_host(int32_t n, const int32_t *colptr, const int32_t *rowidx, const int32_t *perm,
-                 const glu_options &opt, HostPlan &P, std::string &why);
+                 const glu_options &opt, int num_sms, HostPlan &P, std::string &why);
 
 }  // namespace glu
