@@ -290,18 +290,12 @@ void schedule(HostPlan &P, const glu_options &opt, int num_sms) {
     std::vector<std::vector<PSeg>> chunk_segs;
     std::vector<int32_t> touched;
 
-    // A level's time is set by its slowest work item.  Large single-target
-    // work is cut into row pieces so that a level has about two tasks per
-    // resident warp (16 per SM), but no piece below 128 updates: one batch of
-    // loads per lane.
-    const int64_t resident_warps = (int64_t)(num_sms > 0 ? num_sms : 152) * 16;
+    (void)num_sms;
     for (int32_t l = 0; l < nl; l++) {
         lvl_tasks.clear();
         int64_t g = lvl_pair_ptr[l];
         const int64_t ge_l = lvl_pair_ptr[l + 1];
-        int64_t lvl_work = 0;
-        for (int64_t q = g; q < ge_l; q++) lvl_work += lcount(P.pair_j[q]);
-        const int64_t piece_l = std::max<int64_t>(128, std::min<int64_t>(piece, lvl_work / (2 * resident_warps)));
+        const int64_t piece_l = piece;
         while (g < ge_l) {
             const int32_t k = P.pair_k[g];
             int64_t ge = g;

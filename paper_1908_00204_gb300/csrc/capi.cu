@@ -53,6 +53,10 @@ struct glu_handle {
     unsigned *d_abort = nullptr;
     unsigned long long *d_serr = nullptr;
     long long spin_cycles = 0;
+    // level ranges on the device (persistent multi-level launches) and the
+    // grid-barrier words
+    LevelRange *d_ranges = nullptr;
+    unsigned *d_gbar = nullptr;          // count, abort
     // FP32 factors and the refinement path
     float *d_lu32 = nullptr;
     cudaGraphExec_t fgraph32 = nullptr;
@@ -167,6 +171,50 @@ cudaError_t upload(T *dst, const std::vector<T> &src) {
 FactorArgs<double> fargs(glu_handle *h);
 SolveArgs<double> sargs(glu_handle *h);
 
+// Work list of level l (l == nlevels: the final normalization pass).
+LevelRange level_range(const HostPlan &P, int32_t l) {
+    const int32_t nl = (int32_t)P.level_ptr.size() - 1;
+    LevelRange r;
+    r.t_begin = l < nl ? P.lvl_task_ptr[l] : 0;
+    r.row_begin = l < nl ? P.lvl_row_ptr[l] : 0;
+    r.lane_begin = l < nl ? P.lvl_lane_ptr[l] : 0;
+    r.t_end = l < nl ? P.lvl_task_ptr[l + 1] : 0;
+    r.n_begin = P.lvl_norm_ptr[l];
+    r.n_end = P.lvl_norm_ptr[l + 1];
+    return r;
+}
+
+// Launch the levels of one factorization: a run of consecutive pipelined
+// (mode 2) levels, and the final normalization pass after them, goes into
+// one persistent launch; every other level is one launch.
+template <typename T>
+int enqueue_levels(glu_handle *h, const FactorArgs<T> &a, cudaStream_t st) {
+    HostPlan &P = h->P;
+    const int32_t nl = (int32_t)P.level_ptr.size() - 1;
+    GridBarrier bar{h->d_gbar, h->d_gbar + 1, h->d_err, h->spin_cycles};
+    int32_t l = 0;
+    while (l <= nl) {
+        const bool pipelined = l == nl ? (nl > 0 && P.level_mode[nl - 1] == 2) : P.level_mode[l] == 2;
+        if (!pipelined) {
+            const LevelRange r = level_range(P, l);
+            CKL((r.t_end - r.t_begin) + (r.n_end - r.n_begin) > 0, launch_level<T>(a, h->map_bytes, r, h->num_sms, st));
+            l++;
+            continue;
+        }
+        int32_t e = l;
+        while (e < nl && P.level_mode[e] == 2) e++;
+        if (e == nl) e = nl + 1;   // include the final pass
+        if (e - l == 1) {
+            const LevelRange r = level_range(P, l);
+            CKL((r.t_end - r.t_begin) + (r.n_end - r.n_begin) > 0, launch_level<T>(a, h->map_bytes, r, h->num_sms, st));
+        } else {
+            CKL(1, launch_levels_persistent<T>(a, h->map_bytes, h->d_ranges + l, e - l, bar, h->num_sms, st));
+        }
+        l = e;
+    }
+    return GLU_OK;
+}
+
 int ensure_work(glu_handle *h, int32_t nrhs) {
     if (nrhs <= h->work_nrhs) return GLU_OK;
     const int64_t elems = (int64_t)h->P.n * nrhs;
@@ -199,17 +247,18 @@ int enqueue_factor(glu_handle *h, const double *av, cudaStream_t st, std::vector
     CKL(P.lu_colptr[P.n] > 0, launch_gather<double>(h->d_lu, av, h->d_gsrc, P.lu_colptr[P.n], st));
     FactorArgs<double> a = fargs(h);
     const int32_t nl = (int32_t)P.level_ptr.size() - 1;
-    if (lev_events) CK(cudaEventRecord((*lev_events)[0], st));
-    for (int32_t l = 0; l <= nl; l++) {
-        LevelRange r;
-        r.t_begin = l < nl ? P.lvl_task_ptr[l] : 0;
-        r.row_begin = l < nl ? P.lvl_row_ptr[l] : 0;
-        r.lane_begin = l < nl ? P.lvl_lane_ptr[l] : 0;
-        r.t_end = l < nl ? P.lvl_task_ptr[l + 1] : 0;
-        r.n_begin = P.lvl_norm_ptr[l];
-        r.n_end = P.lvl_norm_ptr[l + 1];
-        CKL((r.t_end - r.t_begin) + (r.n_end - r.n_begin) > 0, launch_level<double>(a, h->map_bytes, r, h->num_sms, st));
-        if (lev_events) CK(cudaEventRecord((*lev_events)[l + 1], st));
+    if (lev_events) {
+        // per-level timing diagnostic: one launch per level
+        CK(cudaEventRecord((*lev_events)[0], st));
+        for (int32_t l = 0; l <= nl; l++) {
+            const LevelRange r = level_range(P, l);
+            CKL((r.t_end - r.t_begin) + (r.n_end - r.n_begin) > 0,
+                launch_level<double>(a, h->map_bytes, r, h->num_sms, st));
+            CK(cudaEventRecord((*lev_events)[l + 1], st));
+        }
+    } else {
+        int rc = enqueue_levels<double>(h, a, st);
+        if (rc != GLU_OK) return rc;
     }
     CKL(P.n > 0, launch_pivot_check<double>(h->d_lu, h->d_diag, P.n, h->d_err, st));
     return GLU_OK;
@@ -298,17 +347,8 @@ int enqueue_factor_f32(glu_handle *h, cudaStream_t st) {
     CKL(1, launch_reset_err(h->d_err, st));
     CKL(P.lu_colptr[P.n] > 0, launch_gather<float>(h->d_lu32, h->d_aval, h->d_gsrc, P.lu_colptr[P.n], st));
     FactorArgs<float> a = fargs_t<float>(h, h->d_lu32);
-    const int32_t nl = (int32_t)P.level_ptr.size() - 1;
-    for (int32_t l = 0; l <= nl; l++) {
-        LevelRange r;
-        r.t_begin = l < nl ? P.lvl_task_ptr[l] : 0;
-        r.row_begin = l < nl ? P.lvl_row_ptr[l] : 0;
-        r.lane_begin = l < nl ? P.lvl_lane_ptr[l] : 0;
-        r.t_end = l < nl ? P.lvl_task_ptr[l + 1] : 0;
-        r.n_begin = P.lvl_norm_ptr[l];
-        r.n_end = P.lvl_norm_ptr[l + 1];
-        CKL((r.t_end - r.t_begin) + (r.n_end - r.n_begin) > 0, launch_level<float>(a, h->map_bytes, r, h->num_sms, st));
-    }
+    int rc = enqueue_levels<float>(h, a, st);
+    if (rc != GLU_OK) return rc;
     CKL(P.n > 0, launch_pivot_check<float>(h->d_lu32, h->d_diag, P.n, h->d_err, st));
     // FP64 values in row order for the residuals
     CKL(P.nnz_a > 0, launch_csr_values(h->d_aval_csr, h->d_aval, h->d_acsr_src, P.nnz_a, st));
@@ -460,7 +500,8 @@ int upload_plan(glu_handle *h) {
            o_acp = c.take<int64_t>(n + 1), o_acc = c.take<int32_t>(P.acsr_col.size()),
            o_acs = c.take<int64_t>(P.acsr_src.size()), o_acv = c.take<double>(P.acsr_src.size()),
            o_bdfi = c.take<int32_t>(P.df_items_b.size()), o_bfc = c.take<SolveChunk>(P.bfwd_chunks.size()),
-           o_bbc = c.take<SolveChunk>(P.bbwd_chunks.size());
+           o_bbc = c.take<SolveChunk>(P.bbwd_chunks.size()),
+           o_rng = c.take<LevelRange>(P.level_ptr.size()), o_gbar = c.take<unsigned>(2);
     h->arena_bytes = c.off + 256;
     CK(cudaMalloc(&h->arena, h->arena_bytes));
     char *A = h->arena;
@@ -501,6 +542,8 @@ int upload_plan(glu_handle *h) {
     h->d_bdf_items = at<DFItem>(A, o_bdfi);
     h->d_bfwd_chunks = at<SolveChunk>(A, o_bfc);
     h->d_bbwd_chunks = at<SolveChunk>(A, o_bbc);
+    h->d_ranges = at<LevelRange>(A, o_rng);
+    h->d_gbar = at<unsigned>(A, o_gbar);
     int32_t *d_pair_k = at<int32_t>(A, o_pk);
     int64_t *d_lcp = at<int64_t>(A, o_lcp);
     int32_t *d_lri = at<int32_t>(A, o_lri);
@@ -533,6 +576,11 @@ int upload_plan(glu_handle *h) {
     CK(upload(reinterpret_cast<int32_t *>(h->d_bdf_items), P.df_items_b));
     CK(upload(h->d_bfwd_chunks, P.bfwd_chunks));
     CK(upload(h->d_bbwd_chunks, P.bbwd_chunks));
+    {
+        std::vector<LevelRange> rg(P.level_ptr.size());
+        for (size_t l = 0; l < rg.size(); l++) rg[l] = level_range(P, (int32_t)l);
+        CK(upload(h->d_ranges, rg));
+    }
     CK(cudaMemset(h->d_flags, 0, std::max<int64_t>(h->n_flags, 1) * sizeof(int32_t)));
     CK(cudaMemset(h->d_serr, 0xff, sizeof(unsigned long long)));
     {

@@ -19,6 +19,14 @@ struct LevelRange {
     int32_t n_begin, n_end;
 };
 
+// Grid barrier state of the persistent multi-level kernel.
+struct GridBarrier {
+    unsigned *count;
+    unsigned *abort;
+    unsigned long long *err;
+    long long spin_limit_cycles;
+};
+
 template <typename T>
 struct FactorArgs {
     T *lu;                       // values over the filled pattern
@@ -87,6 +95,9 @@ template <typename T>
 cudaError_t launch_gather(T *lu, const double *aval, const int32_t *gsrc, int64_t nnz, cudaStream_t s);
 template <typename T>
 cudaError_t launch_level(const FactorArgs<T> &a, int map_bytes, const LevelRange &r, int num_sms, cudaStream_t s);
+template <typename T>
+cudaError_t launch_levels_persistent(const FactorArgs<T> &a, int map_bytes, const LevelRange *ranges, int32_t nlev,
+                                     const GridBarrier &bar, int num_sms, cudaStream_t s);
 template <typename T>
 cudaError_t launch_pivot_check(const T *lu, const int64_t *diag_pos, int32_t n,
                                unsigned long long *err, cudaStream_t s);

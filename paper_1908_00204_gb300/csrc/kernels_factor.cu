@@ -229,20 +229,17 @@ constexpr int LEVEL_WARPS = 4;
 
 // One level.  Work items, in order: normalization items, KIND_SRC tasks and
 // KIND_ROW tasks (one warp each), then KIND_LANE tasks, 32 per warp.
+// The work items of one level: normalization items, KIND_SRC and KIND_ROW
+// tasks (one warp each), KIND_LANE tasks (32 per warp); warps stride over them.
 template <typename T, typename M>
-__global__ void __launch_bounds__(LEVEL_WARPS * 32, 4)
-k_level(const FactorArgs<T> a, LevelRange r) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    T *acc = reinterpret_cast<T *>(smem_raw) + wib * (32 * (SRC_SLOTS + 1));
-    const int64_t nw = (int64_t)gridDim.x * LEVEL_WARPS;
+__device__ __forceinline__ void run_level(const FactorArgs<T> &a, const LevelRange &r, int lane, int64_t warp,
+                                          int64_t nw, T *acc) {
     const int64_t nn = r.n_end - r.n_begin;
     const int64_t nsrc = r.row_begin - r.t_begin;
     const int64_t nrow = r.lane_begin - r.row_begin;
     const int64_t nlane = r.t_end - r.lane_begin;
     const int64_t total = nn + nsrc + nrow + (nlane + 31) / 32;
-    for (int64_t it = (int64_t)blockIdx.x * LEVEL_WARPS + wib; it < total; it += nw) {
+    for (int64_t it = warp; it < total; it += nw) {
         int64_t k = it;
         if (k < nn) {
             norm_item<T>(a, a.norms[r.n_begin + k], lane);
@@ -262,6 +259,72 @@ k_level(const FactorArgs<T> a, LevelRange r) {
         const int64_t q = r.lane_begin + k * 32 + lane;
         if (q < r.t_end) lane_task<T, M>(a, a.tasks[q]);
         __syncwarp();
+    }
+}
+
+// One level per launch.
+template <typename T, typename M>
+__global__ void __launch_bounds__(LEVEL_WARPS * 32, 4)
+k_level(const FactorArgs<T> a, LevelRange r) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    T *acc = reinterpret_cast<T *>(smem_raw) + wib * (32 * (SRC_SLOTS + 1));
+    run_level<T, M>(a, r, lane, (int64_t)blockIdx.x * LEVEL_WARPS + wib, (int64_t)gridDim.x * LEVEL_WARPS, acc);
+}
+
+// Consecutive levels in one launch (the pipelined tail mode): all blocks are
+// resident (cooperative launch) and meet at a grid barrier between levels, a
+// monotone arrival counter.  Every wait is bounded: past the limit the block records GLU_ERR_TIMEOUT,
+// raises the abort word and returns; the other blocks see the abort word and
+// return too, so the launch always ends.
+template <typename T, typename M>
+__global__ void __launch_bounds__(LEVEL_WARPS * 32, 4)
+k_levels_persistent(const FactorArgs<T> a, const LevelRange *__restrict__ ranges, int32_t nlev,
+                    GridBarrier bar) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    T *acc = reinterpret_cast<T *>(smem_raw) + wib * (32 * (SRC_SLOTS + 1));
+    const int64_t warp = (int64_t)blockIdx.x * LEVEL_WARPS + wib;
+    const int64_t nw = (int64_t)gridDim.x * LEVEL_WARPS;
+    __shared__ int s_stop;
+    for (int32_t li = 0; li < nlev; li++) {
+        const LevelRange r = ranges[li];
+        run_level<T, M>(a, r, lane, warp, nw, acc);
+        if (li + 1 == nlev) break;
+        // grid barrier: the block's first thread fences, arrives and waits,
+        // then fences again; the block barriers on both sides order the other
+        // threads' accesses (the scheme of a cooperative-groups grid sync)
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_stop = 0;
+            __threadfence();
+            atomicAdd(bar.count, 1u);
+            const unsigned target = (unsigned)(li + 1) * gridDim.x;
+            if (*(volatile const unsigned *)bar.count < target) {
+                const long long t0 = clock64();
+                int spins = 0;
+                while (*(volatile const unsigned *)bar.count < target) {
+                    __nanosleep(20);
+                    if ((++spins & 63) == 0) {
+                        if (*(volatile const unsigned *)bar.abort) {
+                            s_stop = 1;
+                            break;
+                        }
+                        if (clock64() - t0 > bar.spin_limit_cycles) {
+                            atomicOr(bar.abort, 1u);
+                            raise_err(bar.err, 0xffffff, DEVERR_TIMEOUT);
+                            s_stop = 1;
+                            break;
+                        }
+                    }
+                }
+            }
+            __threadfence();
+        }
+        __syncthreads();
+        if (s_stop) return;
     }
 }
 
@@ -343,6 +406,34 @@ cudaError_t launch_level(const FactorArgs<T> &a, int map_bytes, const LevelRange
 }
 
 template <typename T>
+cudaError_t launch_levels_persistent(const FactorArgs<T> &a, int map_bytes, const LevelRange *ranges, int32_t nlev,
+                                     const GridBarrier &bar, int num_sms, cudaStream_t s) {
+    if (nlev <= 0) return cudaSuccess;
+    const size_t smem = sizeof(T) * LEVEL_WARPS * 32 * (SRC_SLOTS + 1);
+    const void *fn = map_bytes == 2 ? (const void *)k_levels_persistent<T, uint16_t>
+                                    : (const void *)k_levels_persistent<T, uint32_t>;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, LEVEL_WARPS * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorLaunchOutOfResources;
+    e = cudaMemsetAsync(bar.count, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bar.abort, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(num_sms * per_sm));
+    cfg.blockDim = dim3(LEVEL_WARPS * 32);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (map_bytes == 2) return cudaLaunchKernelEx(&cfg, k_levels_persistent<T, uint16_t>, a, ranges, nlev, bar);
+    return cudaLaunchKernelEx(&cfg, k_levels_persistent<T, uint32_t>, a, ranges, nlev, bar);
+}
+
+template <typename T>
 cudaError_t launch_pivot_check(const T *lu, const int64_t *diag_pos, int32_t n, unsigned long long *err,
                                cudaStream_t s) {
     if (n == 0) return cudaSuccess;
@@ -368,6 +459,10 @@ template cudaError_t launch_gather<double>(double *, const double *, const int32
 template cudaError_t launch_gather<float>(float *, const double *, const int32_t *, int64_t, cudaStream_t);
 template cudaError_t launch_level<double>(const FactorArgs<double> &, int, const LevelRange &, int, cudaStream_t);
 template cudaError_t launch_level<float>(const FactorArgs<float> &, int, const LevelRange &, int, cudaStream_t);
+template cudaError_t launch_levels_persistent<double>(const FactorArgs<double> &, int, const LevelRange *, int32_t,
+                                                     const GridBarrier &, int, cudaStream_t);
+template cudaError_t launch_levels_persistent<float>(const FactorArgs<float> &, int, const LevelRange *, int32_t,
+                                                    const GridBarrier &, int, cudaStream_t);
 template cudaError_t launch_pivot_check<double>(const double *, const int64_t *, int32_t, unsigned long long *,
                                                 cudaStream_t);
 template cudaError_t launch_pivot_check<float>(const float *, const int64_t *, int32_t, unsigned long long *,
