@@ -262,6 +262,42 @@ __device__ __forceinline__ void run_level(const FactorArgs<T> &a, const LevelRan
     }
 }
 
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// Pull into L2 the schedule records and position-map lines that this warp
+// will read in level r (its items are warp, warp + nw, ...): they are static,
+// and otherwise each is a first-touch DRAM read on the level's critical path.
+template <typename T, typename M>
+__device__ __forceinline__ void prefetch_level(const FactorArgs<T> &a, const LevelRange &r, int lane, int64_t warp,
+                                               int64_t nw) {
+    const M *map = static_cast<const M *>(a.map);
+    const int64_t nn = r.n_end - r.n_begin;
+    const int64_t nsrc = r.row_begin - r.t_begin;
+    const int64_t nrow = r.lane_begin - r.row_begin;
+    const int64_t nlane = r.t_end - r.lane_begin;
+    const int64_t total = nn + nsrc + nrow + (nlane + 31) / 32;
+    for (int64_t it = warp; it < total; it += nw) {
+        int64_t k = it - nn;
+        if (k < 0) continue;
+        int64_t tq;
+        if (k < nsrc + nrow) {
+            tq = r.t_begin + k;
+        } else {
+            tq = r.lane_begin + (k - nsrc - nrow) * 32 + lane;
+            if (tq >= r.t_end) continue;
+        }
+        const Task tk = a.tasks[tq];
+        const bool mine = k >= nsrc + nrow || lane == 0;
+        if (!mine) continue;
+        for (int32_t s = tk.seg_begin; s < tk.seg_end; s++) {
+            const Seg sg = a.segs[s];
+            for (int32_t t = sg.t0; t < sg.t1; t += 128 / (int)sizeof(M)) prefetch_l2(map + sg.mb + t);
+        }
+    }
+}
+
 // One level per launch.
 template <typename T, typename M>
 __global__ void __launch_bounds__(LEVEL_WARPS * 32, 4)
@@ -293,6 +329,7 @@ k_levels_persistent(const FactorArgs<T> a, const LevelRange *__restrict__ ranges
         const LevelRange r = ranges[li];
         run_level<T, M>(a, r, lane, warp, nw, acc);
         if (li + 1 == nlev) break;
+        prefetch_level<T, M>(a, ranges[li + 1], lane, warp, nw);
         // grid barrier: the block's first thread fences, arrives and waits,
         // then fences again; the block barriers on both sides order the other
         // threads' accesses (the scheme of a cooperative-groups grid sync)
