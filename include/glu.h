@@ -73,8 +73,10 @@ typedef struct glu_options {
     int32_t mode_force;       /* -1 per-level choice; 0 warp-per-column,
                                  1 block-per-column, 2 pipelined tail, for every level */
     int32_t tail_threshold;   /* levels with at most this many columns run in the
-                                 pipelined tail mode (the paper's stream-mode
-                                 threshold, 16, Section III-B.2 item 3) */
+                                 pipelined mode: consecutive such levels share one
+                                 persistent launch with a grid barrier between
+                                 levels (the paper's stream-mode threshold is 16,
+                                 Section III-B.2 item 3); 0 (default): off */
     int32_t piece_updates;    /* target-column updates per warp task (work split size) */
     int32_t wide_threshold;   /* levels with more columns than this run warp-per-column */
     int32_t use_graph;        /* 1: capture the level sequence in a CUDA graph */

@@ -446,7 +446,7 @@ void schedule(HostPlan &P, const glu_options &opt, int num_sms) {
         P.lvl_row_ptr[l] = r;
         P.lvl_lane_ptr[l] = ln;
         const int32_t width = P.level_ptr[l + 1] - P.level_ptr[l];
-        const int32_t tail = opt.tail_threshold > 0 ? opt.tail_threshold : 16;
+        const int32_t tail = opt.tail_threshold > 0 ? opt.tail_threshold : 0;
         const int32_t wide = opt.wide_threshold > 0 ? opt.wide_threshold : 256;
         int8_t mode = width <= tail ? 2 : (width > wide ? 0 : 1);
         if (opt.mode_force >= 0 && opt.mode_force <= 2) mode = (int8_t)opt.mode_force;

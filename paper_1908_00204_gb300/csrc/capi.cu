@@ -625,7 +625,7 @@ void glu_default_options(glu_options *o) {
     std::memset(o, 0, sizeof(*o));
     o->struct_size = (int32_t)sizeof(glu_options);
     o->mode_force = -1;
-    o->tail_threshold = 16;
+    o->tail_threshold = 0;
     o->piece_updates = 2048;
     o->wide_threshold = 256;
     o->use_graph = 1;

@@ -298,7 +298,11 @@ __device__ __forceinline__ void prefetch_level(const FactorArgs<T> &a, const Lev
     }
 }
 
-// One level per launch.
+// One level per launch, chained to the previous level's launch by a
+// programmatic dependency: the prologue pulls this warp's (static) schedule
+// records and map lines into L2 while the previous level still runs, then
+// waits for it to finish (griddepcontrol.wait makes its writes visible);
+// each block lets the next level start once its own items are done.
 template <typename T, typename M>
 __global__ void __launch_bounds__(LEVEL_WARPS * 32, 4)
 k_level(const FactorArgs<T> a, LevelRange r) {
@@ -306,7 +310,13 @@ k_level(const FactorArgs<T> a, LevelRange r) {
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     T *acc = reinterpret_cast<T *>(smem_raw) + wib * (32 * (SRC_SLOTS + 1));
-    run_level<T, M>(a, r, lane, (int64_t)blockIdx.x * LEVEL_WARPS + wib, (int64_t)gridDim.x * LEVEL_WARPS, acc);
+    const int64_t warp = (int64_t)blockIdx.x * LEVEL_WARPS + wib;
+    const int64_t nw = (int64_t)gridDim.x * LEVEL_WARPS;
+    prefetch_level<T, M>(a, r, lane, warp, nw);
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    run_level<T, M>(a, r, lane, warp, nw, acc);
+    __syncthreads();
+    asm volatile("griddepcontrol.launch_dependents;");
 }
 
 // Consecutive levels in one launch (the pipelined tail mode): all blocks are
@@ -435,11 +445,18 @@ cudaError_t launch_level(const FactorArgs<T> &a, int map_bytes, const LevelRange
     const int64_t cap = (int64_t)num_sms * 8;
     if (blocks > cap) blocks = cap;
     const size_t smem = sizeof(T) * LEVEL_WARPS * 32 * (SRC_SLOTS + 1);
-    if (map_bytes == 2)
-        k_level<T, uint16_t><<<(unsigned)blocks, LEVEL_WARPS * 32, smem, s>>>(a, r);
-    else
-        k_level<T, uint32_t><<<(unsigned)blocks, LEVEL_WARPS * 32, smem, s>>>(a, r);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(LEVEL_WARPS * 32);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (map_bytes == 2) return cudaLaunchKernelEx(&cfg, k_level<T, uint16_t>, a, r);
+    return cudaLaunchKernelEx(&cfg, k_level<T, uint32_t>, a, r);
 }
 
 template <typename T>

@@ -43,7 +43,7 @@ def test_strerror_and_options(glu):
     assert glu.glu_strerror(0) == "ok"
     assert "pivot" in glu.glu_strerror(-3)
     o = glu.default_options()
-    assert o.tail_threshold == 16 and o.mode_force == -1
+    assert o.tail_threshold == 0 and o.mode_force == -1
 
 
 def host(glu, n, cp, ri, perm=None):
