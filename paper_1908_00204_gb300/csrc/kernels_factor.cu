@@ -312,7 +312,10 @@ k_level(const FactorArgs<T> a, LevelRange r) {
     T *acc = reinterpret_cast<T *>(smem_raw) + wib * (32 * (SRC_SLOTS + 1));
     const int64_t warp = (int64_t)blockIdx.x * LEVEL_WARPS + wib;
     const int64_t nw = (int64_t)gridDim.x * LEVEL_WARPS;
-    prefetch_level<T, M>(a, r, lane, warp, nw);
+    // only a narrow level, a couple of items per warp, has a latency-bound
+    // chain worth shortening; a wide level is throughput-bound
+    const int64_t items = (r.n_end - r.n_begin) + (r.lane_begin - r.t_begin) + (r.t_end - r.lane_begin + 31) / 32;
+    if (items <= 2 * nw) prefetch_level<T, M>(a, r, lane, warp, nw);
     asm volatile("griddepcontrol.wait;" ::: "memory");
     run_level<T, M>(a, r, lane, warp, nw, acc);
     __syncthreads();
@@ -442,7 +445,9 @@ cudaError_t launch_level(const FactorArgs<T> &a, int map_bytes, const LevelRange
                           (r.n_end - r.n_begin);
     if (items <= 0) return cudaSuccess;
     int64_t blocks = (items + LEVEL_WARPS - 1) / LEVEL_WARPS;
-    const int64_t cap = (int64_t)num_sms * 8;
+    // at most the resident capacity (4 blocks per SM): the next level's early
+    // blocks then take only slots this level no longer needs
+    const int64_t cap = (int64_t)num_sms * 4;
     if (blocks > cap) blocks = cap;
     const size_t smem = sizeof(T) * LEVEL_WARPS * 32 * (SRC_SLOTS + 1);
     cudaLaunchConfig_t cfg = {};
