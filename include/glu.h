@@ -91,7 +91,9 @@ typedef struct glu_options {
     int32_t fault_row;        /* testing only: in the dataflow solve this row never
                                  publishes its result, so waits on it time out
                                  (-1: off) */
-    int32_t reserved[5];
+    int32_t solve_tail;       /* 1 (default): a trailing fully dense block of 32..1024
+                                 rows is solved by one block in shared memory; 0: off */
+    int32_t reserved[4];
 } glu_options;
 
 /* Analysis statistics (glu_get_stats). */
@@ -113,6 +115,8 @@ typedef struct glu_stats {
     int64_t device_bytes;     /* device memory held by the handle */
     double analyze_ms;        /* host wall time of glu_analyze */
     int64_t kernel_launches;  /* CUDA kernels this handle has launched so far */
+    int32_t tail_rows;        /* rows of the dense tail solved by one block (0: none) */
+    int32_t spare;
 } glu_stats;
 
 /* Outcome of glu_solve_refine. */

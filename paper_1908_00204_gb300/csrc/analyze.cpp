@@ -9,6 +9,7 @@
 // target columns, the warp tasks); the row views and levels of the two
 // triangular solves.
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cstring>
 #include <numeric>
@@ -486,7 +487,7 @@ void schedule(HostPlan &P, const glu_options &opt, int num_sms) {
 
 // Solve levels: forward lf(i) = 1 + max lf(j) over L(i,j) != 0 (0 if none);
 // backward lb(i) = 1 + max lb(k) over U(i,k) != 0, k > i (0 if none).
-void solve_levels(HostPlan &P) {
+void solve_levels(HostPlan &P, const glu_options &opt) {
     const int32_t n = P.n;
     std::vector<int32_t> lf((size_t)n, 0), lb((size_t)n, 0);
     int32_t nf = n ? 1 : 0, nb = n ? 1 : 0;
@@ -574,9 +575,77 @@ void solve_levels(HostPlan &P) {
     };
     items(P.fwd_ptr, P.fwd_rows, P.lrow_ptr, SOLVE_CHUNK, P.fwd_items, P.fwd_chunks, P.fwd_chunk_ptr);
     items(P.bwd_ptr, P.bwd_rows, P.urow_ptr, SOLVE_CHUNK, P.bwd_items, P.bwd_chunks, P.bwd_chunk_ptr);
+    // Dense tail: the largest trailing block [t0, n), TAIL_MIN <= n - t0 <=
+    // TAIL_MAX, in which every entry of L+U is present.
+    P.tail_t0 = n;
+    if (opt.solve_tail != 0) {
+        const int32_t tmax = std::min<int32_t>(n, TAIL_MAX);
+        int32_t best = n;
+        for (int32_t T = 1; T <= tmax; T++) {
+            const int32_t t0 = n - T;
+            // adding row/column t0: column t0 needs rows t0..n-1, row t0 needs
+            // columns t0..n-1 (the columns > t0 hold row t0 iff their count of
+            // rows >= t0 reaches n - t0)
+            bool ok = P.lu_colptr[t0 + 1] - P.diag_pos[t0] == T;
+            for (int32_t j = t0 + 1; ok && j < n; j++) {
+                const int64_t q = P.lu_colptr[j + 1] - T;
+                ok = q >= P.lu_colptr[j] && P.lu_rowidx[q] == t0;
+            }
+            if (!ok) break;
+            best = t0;
+        }
+        if (n - best >= TAIL_MIN) P.tail_t0 = best;
+    }
+    const int32_t t0 = P.tail_t0;
+    // dataflow schedule: forward rows before the tail, plus the tail rows'
+    // partial sums over the columns before the tail; backward rows before the
+    // tail (the tail rows' U entries all lie inside the tail)
+    P.df_fchunks = P.fwd_chunks;
+    P.df_bchunks = P.bwd_chunks;
+    P.tail_cb.assign((size_t)(n - t0), 0);
+    P.tail_ce.assign((size_t)(n - t0), 0);
+    struct Rec { int32_t level, type, seq; std::array<int32_t, 8> item; };
+    auto build = [&](bool bwd, const std::vector<int32_t> &lv, const std::vector<SolveRow> &it,
+                     const std::vector<SolveChunk> &ch, const std::vector<int32_t> &colv, std::vector<Rec> &recs) {
+        std::vector<int32_t> chrow(ch.size(), -1);
+        for (const SolveRow &r : it)
+            for (int32_t c = r.cb; c < r.ce; c++) chrow[c] = r.row;
+        for (size_t c = 0; c < ch.size(); c++) {
+            if (chrow[c] < 0) continue;                    // a chunk no kept row uses
+            int32_t m = 0;
+            for (int64_t p = ch[c].p0; p < ch[c].p1; p++) m = std::max(m, lv[colv[p]] + 1);
+            recs.push_back(Rec{m, 0, (int32_t)recs.size(), {chrow[c], 0, 0, (int32_t)c, (bwd ? 1 : 0) | 2, 0, 0, 0}});
+        }
+        for (const SolveRow &r : it)
+            recs.push_back(Rec{lv[r.row], 1, (int32_t)recs.size(), {r.row, r.cb, r.ce, -1, bwd ? 1 : 0, 0, 0, 0}});
+        std::stable_sort(recs.begin(), recs.end(), [](const Rec &a, const Rec &b) {
+            return a.level != b.level ? a.level < b.level : a.type < b.type;
+        });
+    };
+    std::vector<SolveRow> fkeep, bkeep;
+    for (const SolveRow &r : P.fwd_items)
+        if (r.row < t0) fkeep.push_back(r);
+    for (int32_t i = t0; i < n; i++) {
+        // entries of row i in columns < t0 form a prefix (columns ascend)
+        const int64_t b = P.lrow_ptr[i];
+        int64_t e = b;
+        while (e < P.lrow_ptr[i + 1] && P.lrow_col[e] < t0) e++;
+        const int32_t cb = (int32_t)P.df_fchunks.size();
+        for (int64_t p = b; p < e; p += SOLVE_CHUNK) P.df_fchunks.push_back(SolveChunk{p, std::min(e, p + SOLVE_CHUNK)});
+        P.tail_cb[i - t0] = cb;
+        P.tail_ce[i - t0] = (int32_t)P.df_fchunks.size();
+        if (P.tail_ce[i - t0] > cb) fkeep.push_back(SolveRow{i, cb, P.tail_ce[i - t0], 1});   // chunks only
+    }
+    for (const SolveRow &r : P.bwd_items)
+        if (r.row < t0) bkeep.push_back(r);
+    std::vector<Rec> frec, brec;
+    build(false, lf, fkeep, P.df_fchunks, P.lrow_col, frec);
+    build(true, lb, bkeep, P.df_bchunks, P.urow_col, brec);
     P.df_items.clear();
-    emit(P.df_items, false, lf, nf, P.fwd_items, P.fwd_chunks, P.lrow_col, P.fwd_ptr);
-    emit(P.df_items, true, lb, nb, P.bwd_items, P.bwd_chunks, P.urow_col, P.bwd_ptr);
+    for (const Rec &r : frec)
+        if (!(r.type == 1 && r.item[0] >= t0)) P.df_items.insert(P.df_items.end(), r.item.begin(), r.item.end());
+    P.df_nfwd = (int32_t)(P.df_items.size() / 8);
+    for (const Rec &r : brec) P.df_items.insert(P.df_items.end(), r.item.begin(), r.item.end());
     items(P.fwd_ptr, P.fwd_rows, P.lrow_ptr, SOLVE_CHUNK_B, P.bfwd_items, P.bfwd_chunks, P.bfwd_chunk_ptr);
     items(P.bwd_ptr, P.bwd_rows, P.urow_ptr, SOLVE_CHUNK_B, P.bbwd_items, P.bbwd_chunks, P.bbwd_chunk_ptr);
     P.df_items_b.clear();
@@ -603,6 +672,9 @@ int analyze_host(int32_t n, const int32_t *colptr, const int32_t *rowidx, const 
         P.bwd_ptr.assign(1, 0);
         P.fwd_chunk_ptr.assign(1, 0);
         P.bwd_chunk_ptr.assign(1, 0);
+        P.bfwd_chunk_ptr.assign(1, 0);
+        P.bbwd_chunk_ptr.assign(1, 0);
+        P.tail_t0 = 0;
         P.acsr_ptr.assign(1, 0);
         return GLU_OK;
     }
@@ -652,7 +724,7 @@ int analyze_host(int32_t n, const int32_t *colptr, const int32_t *rowidx, const 
     levelize(P);
     double t3 = now_ms();
     schedule(P, opt, num_sms);
-    solve_levels(P);
+    solve_levels(P, opt);
     // A in compressed rows (original numbering), for residuals
     P.acsr_ptr.assign((size_t)n + 1, 0);
     for (int64_t p = 0; p < P.nnz_a; p++) P.acsr_ptr[P.a_rowidx[p] + 1]++;

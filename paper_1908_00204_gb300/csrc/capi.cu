@@ -47,6 +47,9 @@ struct glu_handle {
     // dataflow solve: items, ready flags (forward rows, backward rows, forward
     // chunks, backward chunks, contiguous), ticket, abort word, error word
     DFItem *d_df_items = nullptr;
+    int64_t *d_lu_colptr = nullptr;
+    SolveChunk *d_df_fchunks = nullptr, *d_df_bchunks = nullptr;
+    int32_t *d_tail_cb = nullptr, *d_tail_ce = nullptr;
     int32_t *d_flags = nullptr;
     int64_t n_flags = 0;
     unsigned *d_ticket = nullptr;
@@ -218,7 +221,8 @@ int enqueue_levels(glu_handle *h, const FactorArgs<T> &a, cudaStream_t st) {
 int ensure_work(glu_handle *h, int32_t nrhs) {
     if (nrhs <= h->work_nrhs) return GLU_OK;
     const int64_t elems = (int64_t)h->P.n * nrhs;
-    const int64_t nch = (int64_t)(h->P.fwd_chunks.size() + h->P.bwd_chunks.size()) * nrhs;
+    const int64_t nch = (int64_t)std::max(h->P.fwd_chunks.size() + h->P.bwd_chunks.size(),
+                                          h->P.df_fchunks.size() + h->P.df_bchunks.size()) * nrhs;
     // graphs captured with the old buffers are stale
     for (auto &g : h->sgraphs) cudaGraphExecDestroy(g.second);
     h->sgraphs.clear();
@@ -264,6 +268,43 @@ int enqueue_factor(glu_handle *h, const double *av, cudaStream_t st, std::vector
     return GLU_OK;
 }
 
+// The dataflow solve of y (already permuted) into z: forward items, the dense
+// tail on one block, backward items.
+template <typename T>
+int enqueue_df(glu_handle *h, const SolveArgs<T> &a, T *y, T *z, T *partial, int32_t nrhs, cudaStream_t st) {
+    HostPlan &P = h->P;
+    const int32_t n = P.n;
+    CK(cudaMemsetAsync(h->d_flags, 0, h->n_flags * sizeof(int32_t), st));
+    CK(cudaMemsetAsync(h->d_serr, 0xff, sizeof(unsigned long long), st));
+    DFSolveArgs d;
+    d.epoch = 1;
+    d.fault_row = h->opt.fault_row;
+    d.fchunks = h->d_df_fchunks;
+    d.bchunks = h->d_df_bchunks;
+    d.fpartial_v = partial;
+    d.bpartial_v = partial + (int64_t)P.df_fchunks.size() * nrhs;
+    d.fready = h->d_flags;
+    d.bready = h->d_flags + n;
+    d.fchunk_ready = h->d_flags + 2 * (int64_t)n;
+    d.bchunk_ready = d.fchunk_ready + P.df_fchunks.size();
+    d.ticket = h->d_ticket;
+    d.abort = h->d_abort;
+    d.err = h->d_serr;
+    d.spin_limit_cycles = h->spin_cycles;
+    const int32_t nall = (int32_t)(P.df_items.size() / 8);
+    d.items = h->d_df_items;
+    d.nitems = P.df_nfwd;
+    CKL(d.nitems > 0, launch_solve_df<T>(a, d, y, z, nrhs, h->num_sms, st));
+    if (P.tail_t0 < n) {
+        TailArgs ta{P.tail_t0, h->d_tail_cb, h->d_tail_ce, d.bready, d.epoch};
+        CKL(1, launch_solve_tail<T>(a, h->d_lu_colptr, ta, partial, y, z, nrhs, st));
+    }
+    d.items = h->d_df_items + P.df_nfwd;
+    d.nitems = nall - P.df_nfwd;
+    CKL(d.nitems > 0, launch_solve_df<T>(a, d, y, z, nrhs, h->num_sms, st));
+    return GLU_OK;
+}
+
 // The solve sequence from device b to device x.
 int enqueue_solve(glu_handle *h, const double *db, double *dx, int32_t nrhs, cudaStream_t st) {
     HostPlan &P = h->P;
@@ -272,27 +313,9 @@ int enqueue_solve(glu_handle *h, const double *db, double *dx, int32_t nrhs, cud
     CKL(1, launch_permute_in<double>(y, db, h->d_perm, n, nrhs, st));
     SolveArgs<double> a = sargs(h);
     if (h->opt.solve_mode == 1) {
-        CK(cudaMemsetAsync(h->d_flags, 0, h->n_flags * sizeof(int32_t), st));
-        CK(cudaMemsetAsync(h->d_serr, 0xff, sizeof(unsigned long long), st));
-        DFSolveArgs d;
-        d.items = h->d_df_items;
-        d.nitems = (int32_t)(P.df_items.size() / 8);
-        d.epoch = 1;
-        d.fault_row = h->opt.fault_row;
-        d.fchunks = h->d_fwd_chunks;
-        d.bchunks = h->d_bwd_chunks;
-        d.fpartial_v = h->d_partial;
-        d.bpartial_v = h->d_partial + (int64_t)P.fwd_chunks.size() * nrhs;
-        d.fready = h->d_flags;
-        d.bready = h->d_flags + n;
-        d.fchunk_ready = h->d_flags + 2 * (int64_t)n;
-        d.bchunk_ready = d.fchunk_ready + P.fwd_chunks.size();
-        d.ticket = h->d_ticket;
-        d.abort = h->d_abort;
-        d.err = h->d_serr;
-        d.spin_limit_cycles = h->spin_cycles;
         double *z = y + (int64_t)n * nrhs;
-        CKL(d.nitems > 0, launch_solve_df<double>(a, d, y, z, nrhs, h->num_sms, st));
+        int rc = enqueue_df<double>(h, a, y, z, h->d_partial, nrhs, st);
+        if (rc != GLU_OK) return rc;
         CKL(1, launch_permute_out<double>(dx, z, h->d_perm, n, nrhs, st));
         return GLU_OK;
     }
@@ -364,27 +387,8 @@ int enqueue_solve_f32(glu_handle *h, const double *db, double *dx, int32_t nrhs,
     float *z = y + (int64_t)n * nrhs;
     CKL(1, launch_permute_in<float>(y, db, h->d_perm, n, nrhs, st));
     SolveArgs<float> a = sargs_t<float>(h, h->d_lu32);
-    CK(cudaMemsetAsync(h->d_flags, 0, h->n_flags * sizeof(int32_t), st));
-    CK(cudaMemsetAsync(h->d_serr, 0xff, sizeof(unsigned long long), st));
-    DFSolveArgs d;
-    d.items = h->d_df_items;
-    d.nitems = (int32_t)(P.df_items.size() / 8);
-    d.epoch = 1;
-    d.fault_row = h->opt.fault_row;
-    d.fchunks = h->d_fwd_chunks;
-    d.bchunks = h->d_bwd_chunks;
-    float *part = reinterpret_cast<float *>(h->d_partial);
-    d.fpartial_v = part;
-    d.bpartial_v = part + (int64_t)P.fwd_chunks.size() * nrhs;
-    d.fready = h->d_flags;
-    d.bready = h->d_flags + n;
-    d.fchunk_ready = h->d_flags + 2 * (int64_t)n;
-    d.bchunk_ready = d.fchunk_ready + P.fwd_chunks.size();
-    d.ticket = h->d_ticket;
-    d.abort = h->d_abort;
-    d.err = h->d_serr;
-    d.spin_limit_cycles = h->spin_cycles;
-    CKL(d.nitems > 0, launch_solve_df<float>(a, d, y, z, nrhs, h->num_sms, st));
+    int rc = enqueue_df<float>(h, a, y, z, reinterpret_cast<float *>(h->d_partial), nrhs, st);
+    if (rc != GLU_OK) return rc;
     CKL(1, launch_permute_out<float>(dx, z, h->d_perm, n, nrhs, st));
     return GLU_OK;
 }
@@ -495,7 +499,9 @@ int upload_plan(glu_handle *h) {
            o_fi = c.take<SolveRow>(P.fwd_items.size()), o_bi = c.take<SolveRow>(P.bwd_items.size()),
            o_fc = c.take<SolveChunk>(P.fwd_chunks.size()), o_bc = c.take<SolveChunk>(P.bwd_chunks.size()),
            o_dfi = c.take<int32_t>(P.df_items.size()),
-           o_flags = c.take<int32_t>(2 * (size_t)n + P.fwd_chunks.size() + P.bwd_chunks.size()),
+           o_flags = c.take<int32_t>(2 * (size_t)n + P.df_fchunks.size() + P.df_bchunks.size()),
+           o_dffc = c.take<SolveChunk>(P.df_fchunks.size()), o_dfbc = c.take<SolveChunk>(P.df_bchunks.size()),
+           o_tcb = c.take<int32_t>(P.tail_cb.size()), o_tce = c.take<int32_t>(P.tail_ce.size()),
            o_ticket = c.take<unsigned>(1), o_abort = c.take<unsigned>(1), o_serr = c.take<unsigned long long>(1),
            o_acp = c.take<int64_t>(n + 1), o_acc = c.take<int32_t>(P.acsr_col.size()),
            o_acs = c.take<int64_t>(P.acsr_src.size()), o_acv = c.take<double>(P.acsr_src.size()),
@@ -531,7 +537,11 @@ int upload_plan(glu_handle *h) {
     h->d_bwd_chunks = at<SolveChunk>(A, o_bc);
     h->d_df_items = at<DFItem>(A, o_dfi);
     h->d_flags = at<int32_t>(A, o_flags);
-    h->n_flags = 2 * (int64_t)n + (int64_t)P.fwd_chunks.size() + (int64_t)P.bwd_chunks.size();
+    h->n_flags = 2 * (int64_t)n + (int64_t)P.df_fchunks.size() + (int64_t)P.df_bchunks.size();
+    h->d_df_fchunks = at<SolveChunk>(A, o_dffc);
+    h->d_df_bchunks = at<SolveChunk>(A, o_dfbc);
+    h->d_tail_cb = at<int32_t>(A, o_tcb);
+    h->d_tail_ce = at<int32_t>(A, o_tce);
     h->d_ticket = at<unsigned>(A, o_ticket);
     h->d_abort = at<unsigned>(A, o_abort);
     h->d_serr = at<unsigned long long>(A, o_serr);
@@ -546,6 +556,7 @@ int upload_plan(glu_handle *h) {
     h->d_gbar = at<unsigned>(A, o_gbar);
     int32_t *d_pair_k = at<int32_t>(A, o_pk);
     int64_t *d_lcp = at<int64_t>(A, o_lcp);
+    h->d_lu_colptr = d_lcp;
     int32_t *d_lri = at<int32_t>(A, o_lri);
     CK(upload(h->d_gsrc, P.gsrc));
     CK(upload(h->d_diag, P.diag_pos));
@@ -633,6 +644,7 @@ void glu_default_options(glu_options *o) {
     o->solve_mode = 1;
     o->spin_limit_us = 2000000;
     o->fault_row = -1;
+    o->solve_tail = 1;
 }
 
 int glu_analyze_opts(int32_t n, const int32_t *colptr, const int32_t *rowidx, const int32_t *perm,
@@ -1001,6 +1013,7 @@ int glu_get_stats(const glu_handle *h, glu_stats *s) {
                                     sizeof(double));
     s->analyze_ms = h->analyze_ms;
     s->kernel_launches = h->launches;
+    s->tail_rows = P.n - P.tail_t0;
     return GLU_OK;
 }
 

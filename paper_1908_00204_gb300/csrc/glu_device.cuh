@@ -77,7 +77,7 @@ struct DFItem {
 };
 
 struct DFSolveArgs {
-    const DFItem *items;
+    const DFItem *items;      // this launch's items (a sub-range of the list)
     int32_t nitems;
     int32_t epoch;
     int32_t fault_row;            // test hook: this row never publishes (-1: none)
@@ -114,6 +114,17 @@ cudaError_t launch_permute_out(double *x, const T *y, const int32_t *perm, int32
 template <typename T>
 cudaError_t launch_solve_df(const SolveArgs<T> &s, const DFSolveArgs &a, T *y, T *z, int32_t nrhs, int num_sms,
                             cudaStream_t st);
+// One-block solve of the dense tail [t0, n): forward rows start from the
+// partial sums over columns < t0, then both column sweeps in shared memory.
+struct TailArgs {
+    int32_t t0;
+    const int32_t *cb, *ce;       // forward partial chunks of each tail row
+    int32_t *bready;              // backward ready flags, set for the tail rows
+    int32_t epoch;
+};
+template <typename T>
+cudaError_t launch_solve_tail(const SolveArgs<T> &s, const int64_t *lu_colptr, const TailArgs &t, const T *fpartial,
+                              T *y, T *z, int32_t nrhs, cudaStream_t st);
 template <typename T>
 cudaError_t launch_solve_level(const SolveArgs<T> &a, bool backward, T *y, int32_t nrhs, const SolveRow *items,
                                int32_t nitems, const SolveChunk *chunks, int32_t c0, int32_t c1, T *partial,

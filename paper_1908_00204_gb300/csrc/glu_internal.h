@@ -76,6 +76,7 @@ struct SolveChunk {
 };
 constexpr int64_t SOLVE_CHUNK = 128;    // single matrix: lanes over a row's entries
 constexpr int64_t SOLVE_CHUNK_B = 32;   // batched: lanes over the sets, entries in sequence
+constexpr int32_t TAIL_MIN = 32, TAIL_MAX = 1024;   // dense-tail solve size range
 
 // Everything glu_analyze computes on the host.
 struct HostPlan {
@@ -116,8 +117,15 @@ struct HostPlan {
     std::vector<SolveChunk> fwd_chunks, bwd_chunks;
     std::vector<int32_t> fwd_chunk_ptr, bwd_chunk_ptr;   // nlevels + 1
     // dataflow solve: items in topological order, packed as int32 x 8
-    // {row, cb, ce, chunk, flags, 0, 0, 0}
+    // {row, cb, ce, chunk, flags, 0, 0, 0}; forward items first
     std::vector<int32_t> df_items;
+    int32_t df_nfwd = 0;                       // number of forward items
+    std::vector<SolveChunk> df_fchunks, df_bchunks;
+    // dense tail [tail_t0, n) solved by one block (tail_t0 == n: none); the
+    // partial sums of each tail row over the columns before the tail are
+    // forward chunks tail_cb[i]..tail_ce[i]-1
+    int32_t tail_t0 = 0;
+    std::vector<int32_t> tail_cb, tail_ce;
     // the same for the batched solve, with shorter chunks
     std::vector<SolveRow> bfwd_items, bbwd_items;
     std::vector<SolveChunk> bfwd_chunks, bbwd_chunks;

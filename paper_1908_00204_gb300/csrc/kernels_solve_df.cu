@@ -130,7 +130,62 @@ __global__ void __launch_bounds__(128) k_solve_df(const SolveArgs<T> s, const DF
     }
 }
 
+// The dense tail, one block.  Tail column j's rows below (and, in U, above
+// from t0) are contiguous in the CSC values, so a column sweep reads them
+// coalesced; the tail's values stay in shared memory; one barrier per column
+// forward, two backward (the pivot division is done once).
+template <typename T>
+__global__ void __launch_bounds__(1024) k_solve_tail(const SolveArgs<T> s, const int64_t *__restrict__ lu_colptr,
+                                                     const TailArgs ta, const T *__restrict__ fpartial, T *y, T *z,
+                                                     int32_t nrhs) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int32_t n = s.n, t0 = ta.t0, NT = n - t0;
+    T *yt = reinterpret_cast<T *>(smem_raw);
+    T *zt = yt + NT;
+    for (int32_t r = 0; r < nrhs; r++) {
+        const T *yr = y + (int64_t)r * n;
+        T *zr = z + (int64_t)r * n;
+        for (int32_t ii = threadIdx.x; ii < NT; ii += blockDim.x) {
+            T v = __ldcg(yr + t0 + ii);
+            for (int32_t c = ta.cb[ii]; c < ta.ce[ii]; c++) v -= __ldcg(fpartial + (int64_t)c * nrhs + r);
+            yt[ii] = v;
+        }
+        __syncthreads();
+        // forward: y(i) -= L(i,j) y(j) for the rows i > j of the tail
+        for (int32_t jj = 0; jj < NT; jj++) {
+            const int64_t lb = s.diag_pos[t0 + jj] + 1 - (jj + 1);   // L(t0+ii, t0+jj) at lb + ii
+            const T vj = yt[jj];
+            for (int32_t ii = jj + 1 + threadIdx.x; ii < NT; ii += blockDim.x)
+                yt[ii] = yt[ii] - s.lu[lb + ii] * vj;
+            __syncthreads();
+        }
+        // backward: z(j) = y(j) / U(j,j); y(i) -= U(i,j) z(j) for the rows t0 <= i < j
+        for (int32_t jj = NT - 1; jj >= 0; jj--) {
+            const int32_t j = t0 + jj;
+            if (threadIdx.x == 0) zt[jj] = yt[jj] / s.lu[s.diag_pos[j]];
+            __syncthreads();
+            const int64_t ub = lu_colptr[j + 1] - NT;                 // U(t0+ii, j) at ub + ii
+            const T zj = zt[jj];
+            for (int32_t ii = threadIdx.x; ii < jj; ii += blockDim.x) yt[ii] = yt[ii] - s.lu[ub + ii] * zj;
+            __syncthreads();
+        }
+        for (int32_t ii = threadIdx.x; ii < NT; ii += blockDim.x) zr[t0 + ii] = zt[ii];
+        __syncthreads();
+    }
+    for (int32_t ii = threadIdx.x; ii < NT; ii += blockDim.x) ta.bready[t0 + ii] = ta.epoch;
+}
+
 }  // namespace
+
+template <typename T>
+cudaError_t launch_solve_tail(const SolveArgs<T> &s, const int64_t *lu_colptr, const TailArgs &t, const T *fpartial,
+                              T *y, T *z, int32_t nrhs, cudaStream_t st) {
+    const int32_t NT = s.n - t.t0;
+    if (NT <= 0) return cudaSuccess;
+    const size_t smem = 2 * (size_t)NT * sizeof(T);
+    k_solve_tail<T><<<1, 1024, smem, st>>>(s, lu_colptr, t, fpartial, y, z, nrhs);
+    return cudaGetLastError();
+}
 
 template <typename T>
 cudaError_t launch_solve_df(const SolveArgs<T> &s, const DFSolveArgs &a, T *y, T *z, int32_t nrhs, int num_sms,
@@ -147,6 +202,10 @@ cudaError_t launch_solve_df(const SolveArgs<T> &s, const DFSolveArgs &a, T *y, T
     return cudaGetLastError();
 }
 
+template cudaError_t launch_solve_tail<double>(const SolveArgs<double> &, const int64_t *, const TailArgs &,
+                                               const double *, double *, double *, int32_t, cudaStream_t);
+template cudaError_t launch_solve_tail<float>(const SolveArgs<float> &, const int64_t *, const TailArgs &,
+                                              const float *, float *, float *, int32_t, cudaStream_t);
 template cudaError_t launch_solve_df<double>(const SolveArgs<double> &, const DFSolveArgs &, double *, double *,
                                              int32_t, int, cudaStream_t);
 template cudaError_t launch_solve_df<float>(const SolveArgs<float> &, const DFSolveArgs &, float *, float *, int32_t,
