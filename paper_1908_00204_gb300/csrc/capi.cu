@@ -581,6 +581,10 @@ int upload_plan(glu_handle *h) {
     CK(upload(h->d_fwd_chunks, P.fwd_chunks));
     CK(upload(h->d_bwd_chunks, P.bwd_chunks));
     CK(upload(reinterpret_cast<int32_t *>(h->d_df_items), P.df_items));
+    CK(upload(h->d_df_fchunks, P.df_fchunks));
+    CK(upload(h->d_df_bchunks, P.df_bchunks));
+    CK(upload(h->d_tail_cb, P.tail_cb));
+    CK(upload(h->d_tail_ce, P.tail_ce));
     CK(upload(h->d_acsr_ptr, P.acsr_ptr));
     CK(upload(h->d_acsr_col, P.acsr_col));
     CK(upload(h->d_acsr_src, P.acsr_src));
@@ -714,6 +718,14 @@ int glu_analyze_opts(int32_t n, const int32_t *colptr, const int32_t *rowidx, co
                              (long long)sg[2], (long long)wk[2], (long long)mw, (long long)ms, (long long)mseg[0],
                              (long long)mseg[1], (long long)mseg[2]);
             }
+            std::fclose(fp);
+        }
+    }
+    if (const char *dump = std::getenv("GLU_DUMP_DF")) {
+        // dataflow solve items (8 int32 each), then the forward item count
+        if (FILE *fp = std::fopen(dump, "wb")) {
+            const HostPlan &P = h->P;
+            std::fwrite(P.df_items.data(), sizeof(int32_t), P.df_items.size(), fp);
             std::fclose(fp);
         }
     }
