@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP32+refinement and batched lines")
     return ap.parse_args()
 
 
@@ -174,6 +175,67 @@ def run_reference(args):
     return 0
 
 
+def extras(g, torch, dev, m, vals_host, b_host, h):
+    """FP32 + FP64 refinement on the bench matrix, and batched refactorization
+    of 256 Monte-Carlo value sets of the 20k-unknown matrix (FP64 and FP32 +
+    refinement, 4 right-hand sides each) against one-at-a-time FP64."""
+    out = {}
+
+    def timed(fn, reps=3):
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            ts.append((time.perf_counter() - t0) * 1e3)
+        return float(np.median(ts))
+
+    v = torch.from_numpy(vals_host[0]).to(dev)
+    b = torch.from_numpy(b_host).to(dev)
+    x = torch.empty_like(b)
+    info = {}
+
+    def ir():
+        _, i = g.glu_solve_refine(h, b, x, tol=1e-12, maxit=20)
+        info.update(i)
+    g.glu_factor_f32(h, v)
+    ir()
+    f32 = timed(lambda: g.glu_factor_f32(h, v))
+    s32 = timed(ir)
+    out["fp32_refine"] = {"workload": m.stats()["rows"] and WORKLOAD, "factor_ms": f32,
+                          "refine_solve_ms": s32, "refactor_solve_per_s": 1e3 / (f32 + s32),
+                          "iterations": info.get("iterations"), "berr": info.get("berr")}
+    mb = synth.make("mesh100x200_nets64", 1)
+    B, K = 256, 4
+    V = torch.from_numpy(np.stack([mb.values(100 + i, sigma=0.1, base_seed=5) for i in range(B)])).to(dev)
+    R = torch.from_numpy(np.stack([synth.rhs(mb.n, K, 300 + i) for i in range(B)])).to(dev)
+    hb = g.glu_analyze(mb.n, mb.colptr, mb.rowidx, mb.perm)
+    g.glu_set_stream(hb, torch.cuda.current_stream(dev))
+    v0, r0 = V[0].contiguous(), R[0].contiguous()
+    g.glu_factor(hb, v0)
+    g.glu_solve(hb, r0)
+    single = timed(lambda: (g.glu_factor(hb, v0), g.glu_solve(hb, r0)))
+    g.glu_factor_batched(hb, V)
+    g.glu_solve_batched(hb, R)
+    b64 = timed(lambda: (g.glu_factor_batched(hb, V), g.glu_solve_batched(hb, R)))
+    binfo = {}
+
+    def bir():
+        g.glu_factor_batched_f32(hb, V)
+        _, i = g.glu_solve_batched_refine(hb, R, tol=1e-12, maxit=20)
+        binfo.update(i)
+    bir()
+    b32 = timed(bir)
+    out["batched"] = {"workload": "mesh100x200_nets64", "n": mb.n, "sets": B, "nrhs": K,
+                      "one_at_a_time_fp64_per_s": 1e3 / single, "fp64_batched_per_s": B * 1e3 / b64,
+                      "fp32_refine_batched_per_s": B * 1e3 / b32, "fp64_batched_ms": b64, "fp32_refine_batched_ms": b32,
+                      "refine_iterations": binfo.get("iterations"), "refine_berr": binfo.get("berr"),
+                      "graph_launches_per_batched_factor": 1}
+    g.glu_destroy(hb)
+    return out
+
+
 def run_ours(args):
     import torch
     import paper_1908_00204_gb300 as g
@@ -261,6 +323,10 @@ def run_ours(args):
                "h2d_bytes_per_step": int(m.nnz * 8 + b_host.size * 8),
                "d2h_bytes_per_step": int(b_host.size * 8 + 2 * 8)}
 
+    extra = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        extra = extras(g, torch, dev, m, vals_host, b_host, h)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, reps, el = cpu_oracle_steps(m, vals_host, b_host)
@@ -284,6 +350,7 @@ def run_ours(args):
                          "kernel": "k_level (FP64 level sweep of one refactorization)",
                          "peak_source": "nominal GB300 FP64 rate (the measured peaks cover HBM and bf16 only)"},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
+            "extras": extra,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
