@@ -485,6 +485,66 @@ void schedule(HostPlan &P, const glu_options &opt, int num_sms) {
     }
 }
 
+// Dataflow schedule of the solve for a chunk size and a dense tail [t0, n):
+// forward rows before the tail, the tail rows' partial sums over the columns
+// before the tail (forward chunks tail_cb[i]..tail_ce[i]-1), backward rows
+// before the tail (the tail rows' U entries all lie inside the tail).  Items
+// are ordered by level, a chunk at 1 + the highest level it reads and before
+// the rows of its level; forward items first (nfwd of them).
+void build_df(const HostPlan &P, const std::vector<int32_t> &lf, const std::vector<int32_t> &lb, int64_t chunk,
+              int32_t t0, const std::vector<SolveRow> &fitems, const std::vector<SolveChunk> &fchunks,
+              const std::vector<SolveRow> &bitems, const std::vector<SolveChunk> &bchunks, std::vector<int32_t> &out,
+              std::vector<SolveChunk> &dff, std::vector<SolveChunk> &dfb, std::vector<int32_t> &tcb,
+              std::vector<int32_t> &tce, int32_t &nfwd) {
+    const int32_t n = P.n;
+    dff = fchunks;
+    dfb = bchunks;
+    tcb.assign((size_t)(n - t0), 0);
+    tce.assign((size_t)(n - t0), 0);
+    struct Rec { int32_t level, type, seq; std::array<int32_t, 8> item; };
+    auto build = [&](bool bwd, const std::vector<int32_t> &lv, const std::vector<SolveRow> &it,
+                     const std::vector<SolveChunk> &ch, const std::vector<int32_t> &colv, std::vector<Rec> &recs) {
+        std::vector<int32_t> chrow(ch.size(), -1);
+        for (const SolveRow &r : it)
+            for (int32_t c = r.cb; c < r.ce; c++) chrow[c] = r.row;
+        for (size_t c = 0; c < ch.size(); c++) {
+            if (chrow[c] < 0) continue;                    // a chunk no kept row uses
+            int32_t m = 0;
+            for (int64_t p = ch[c].p0; p < ch[c].p1; p++) m = std::max(m, lv[colv[p]] + 1);
+            recs.push_back(Rec{m, 0, (int32_t)recs.size(), {chrow[c], 0, 0, (int32_t)c, (bwd ? 1 : 0) | 2, 0, 0, 0}});
+        }
+        for (const SolveRow &r : it)
+            recs.push_back(Rec{lv[r.row], 1, (int32_t)recs.size(), {r.row, r.cb, r.ce, -1, bwd ? 1 : 0, 0, 0, 0}});
+        std::stable_sort(recs.begin(), recs.end(), [](const Rec &a, const Rec &b) {
+            return a.level != b.level ? a.level < b.level : a.type < b.type;
+        });
+    };
+    std::vector<SolveRow> fkeep, bkeep;
+    for (const SolveRow &r : fitems)
+        if (r.row < t0) fkeep.push_back(r);
+    for (int32_t i = t0; i < n; i++) {
+        // entries of row i in columns < t0 form a prefix (columns ascend)
+        const int64_t b = P.lrow_ptr[i];
+        int64_t e = b;
+        while (e < P.lrow_ptr[i + 1] && P.lrow_col[e] < t0) e++;
+        const int32_t cb = (int32_t)dff.size();
+        for (int64_t p = b; p < e; p += chunk) dff.push_back(SolveChunk{p, std::min(e, p + chunk)});
+        tcb[i - t0] = cb;
+        tce[i - t0] = (int32_t)dff.size();
+        if (tce[i - t0] > cb) fkeep.push_back(SolveRow{i, cb, tce[i - t0], 1});   // chunks only
+    }
+    for (const SolveRow &r : bitems)
+        if (r.row < t0) bkeep.push_back(r);
+    std::vector<Rec> frec, brec;
+    build(false, lf, fkeep, dff, P.lrow_col, frec);
+    build(true, lb, bkeep, dfb, P.urow_col, brec);
+    out.clear();
+    for (const Rec &r : frec)
+        if (!(r.type == 1 && r.item[0] >= t0)) out.insert(out.end(), r.item.begin(), r.item.end());
+    nfwd = (int32_t)(out.size() / 8);
+    for (const Rec &r : brec) out.insert(out.end(), r.item.begin(), r.item.end());
+}
+
 // Solve levels: forward lf(i) = 1 + max lf(j) over L(i,j) != 0 (0 if none);
 // backward lb(i) = 1 + max lb(k) over U(i,k) != 0, k > i (0 if none).
 void solve_levels(HostPlan &P, const glu_options &opt) {
@@ -596,61 +656,18 @@ void solve_levels(HostPlan &P, const glu_options &opt) {
         }
         if (n - best >= TAIL_MIN) P.tail_t0 = best;
     }
-    const int32_t t0 = P.tail_t0;
-    // dataflow schedule: forward rows before the tail, plus the tail rows'
-    // partial sums over the columns before the tail; backward rows before the
-    // tail (the tail rows' U entries all lie inside the tail)
-    P.df_fchunks = P.fwd_chunks;
-    P.df_bchunks = P.bwd_chunks;
-    P.tail_cb.assign((size_t)(n - t0), 0);
-    P.tail_ce.assign((size_t)(n - t0), 0);
-    struct Rec { int32_t level, type, seq; std::array<int32_t, 8> item; };
-    auto build = [&](bool bwd, const std::vector<int32_t> &lv, const std::vector<SolveRow> &it,
-                     const std::vector<SolveChunk> &ch, const std::vector<int32_t> &colv, std::vector<Rec> &recs) {
-        std::vector<int32_t> chrow(ch.size(), -1);
-        for (const SolveRow &r : it)
-            for (int32_t c = r.cb; c < r.ce; c++) chrow[c] = r.row;
-        for (size_t c = 0; c < ch.size(); c++) {
-            if (chrow[c] < 0) continue;                    // a chunk no kept row uses
-            int32_t m = 0;
-            for (int64_t p = ch[c].p0; p < ch[c].p1; p++) m = std::max(m, lv[colv[p]] + 1);
-            recs.push_back(Rec{m, 0, (int32_t)recs.size(), {chrow[c], 0, 0, (int32_t)c, (bwd ? 1 : 0) | 2, 0, 0, 0}});
-        }
-        for (const SolveRow &r : it)
-            recs.push_back(Rec{lv[r.row], 1, (int32_t)recs.size(), {r.row, r.cb, r.ce, -1, bwd ? 1 : 0, 0, 0, 0}});
-        std::stable_sort(recs.begin(), recs.end(), [](const Rec &a, const Rec &b) {
-            return a.level != b.level ? a.level < b.level : a.type < b.type;
-        });
-    };
-    std::vector<SolveRow> fkeep, bkeep;
-    for (const SolveRow &r : P.fwd_items)
-        if (r.row < t0) fkeep.push_back(r);
-    for (int32_t i = t0; i < n; i++) {
-        // entries of row i in columns < t0 form a prefix (columns ascend)
-        const int64_t b = P.lrow_ptr[i];
-        int64_t e = b;
-        while (e < P.lrow_ptr[i + 1] && P.lrow_col[e] < t0) e++;
-        const int32_t cb = (int32_t)P.df_fchunks.size();
-        for (int64_t p = b; p < e; p += SOLVE_CHUNK) P.df_fchunks.push_back(SolveChunk{p, std::min(e, p + SOLVE_CHUNK)});
-        P.tail_cb[i - t0] = cb;
-        P.tail_ce[i - t0] = (int32_t)P.df_fchunks.size();
-        if (P.tail_ce[i - t0] > cb) fkeep.push_back(SolveRow{i, cb, P.tail_ce[i - t0], 1});   // chunks only
-    }
-    for (const SolveRow &r : P.bwd_items)
-        if (r.row < t0) bkeep.push_back(r);
-    std::vector<Rec> frec, brec;
-    build(false, lf, fkeep, P.df_fchunks, P.lrow_col, frec);
-    build(true, lb, bkeep, P.df_bchunks, P.urow_col, brec);
-    P.df_items.clear();
-    for (const Rec &r : frec)
-        if (!(r.type == 1 && r.item[0] >= t0)) P.df_items.insert(P.df_items.end(), r.item.begin(), r.item.end());
-    P.df_nfwd = (int32_t)(P.df_items.size() / 8);
-    for (const Rec &r : brec) P.df_items.insert(P.df_items.end(), r.item.begin(), r.item.end());
+    build_df(P, lf, lb, SOLVE_CHUNK, P.tail_t0, P.fwd_items, P.fwd_chunks, P.bwd_items, P.bwd_chunks, P.df_items,
+             P.df_fchunks, P.df_bchunks, P.tail_cb, P.tail_ce, P.df_nfwd);
     items(P.fwd_ptr, P.fwd_rows, P.lrow_ptr, SOLVE_CHUNK_B, P.bfwd_items, P.bfwd_chunks, P.bfwd_chunk_ptr);
     items(P.bwd_ptr, P.bwd_rows, P.urow_ptr, SOLVE_CHUNK_B, P.bbwd_items, P.bbwd_chunks, P.bbwd_chunk_ptr);
-    P.df_items_b.clear();
-    emit(P.df_items_b, false, lf, nf, P.bfwd_items, P.bfwd_chunks, P.lrow_col, P.fwd_ptr);
-    emit(P.df_items_b, true, lb, nb, P.bbwd_items, P.bbwd_chunks, P.urow_col, P.bwd_ptr);
+    // batched: the tail's values for 32 sets sit in shared memory, so at most
+    // TAIL_MAX_B rows of the dense block (a trailing part of it is dense too)
+    P.btail_t0 = (P.tail_t0 < n) ? std::max<int32_t>(P.tail_t0, n - TAIL_MAX_B) : n;
+    build_df(P, lf, lb, SOLVE_CHUNK_B, P.btail_t0, P.bfwd_items, P.bfwd_chunks, P.bbwd_items, P.bbwd_chunks,
+             P.df_items_b, P.bdf_fchunks, P.bdf_bchunks, P.btail_cb, P.btail_ce, P.bdf_nfwd);
+    (void)emit;
+    (void)nf;
+    (void)nb;
 }
 
 }  // namespace

@@ -94,8 +94,9 @@ struct glu_handle {
     unsigned long long *d_bnorm = nullptr;
     int32_t *d_bdone = nullptr;
     double *d_bberr = nullptr;
-    DFItem *d_bdf_items = nullptr;     // batched solve schedule (shorter chunks)
+    DFItem *d_bdf_items = nullptr;     // batched solve schedule (shorter chunks, smaller tail)
     SolveChunk *d_bfwd_chunks = nullptr, *d_bbwd_chunks = nullptr;
+    int32_t *d_btail_cb = nullptr, *d_btail_ce = nullptr;
     // solve scratch (grown on demand): permuted vector, staging, partials
     double *d_work = nullptr;
     double *d_bstage = nullptr;
@@ -505,8 +506,9 @@ int upload_plan(glu_handle *h) {
            o_ticket = c.take<unsigned>(1), o_abort = c.take<unsigned>(1), o_serr = c.take<unsigned long long>(1),
            o_acp = c.take<int64_t>(n + 1), o_acc = c.take<int32_t>(P.acsr_col.size()),
            o_acs = c.take<int64_t>(P.acsr_src.size()), o_acv = c.take<double>(P.acsr_src.size()),
-           o_bdfi = c.take<int32_t>(P.df_items_b.size()), o_bfc = c.take<SolveChunk>(P.bfwd_chunks.size()),
-           o_bbc = c.take<SolveChunk>(P.bbwd_chunks.size()),
+           o_bdfi = c.take<int32_t>(P.df_items_b.size()), o_bfc = c.take<SolveChunk>(P.bdf_fchunks.size()),
+           o_bbc = c.take<SolveChunk>(P.bdf_bchunks.size()), o_btcb = c.take<int32_t>(P.btail_cb.size()),
+           o_btce = c.take<int32_t>(P.btail_ce.size()),
            o_rng = c.take<LevelRange>(P.level_ptr.size()), o_gbar = c.take<unsigned>(2);
     h->arena_bytes = c.off + 256;
     CK(cudaMalloc(&h->arena, h->arena_bytes));
@@ -552,6 +554,8 @@ int upload_plan(glu_handle *h) {
     h->d_bdf_items = at<DFItem>(A, o_bdfi);
     h->d_bfwd_chunks = at<SolveChunk>(A, o_bfc);
     h->d_bbwd_chunks = at<SolveChunk>(A, o_bbc);
+    h->d_btail_cb = at<int32_t>(A, o_btcb);
+    h->d_btail_ce = at<int32_t>(A, o_btce);
     h->d_ranges = at<LevelRange>(A, o_rng);
     h->d_gbar = at<unsigned>(A, o_gbar);
     int32_t *d_pair_k = at<int32_t>(A, o_pk);
@@ -589,8 +593,10 @@ int upload_plan(glu_handle *h) {
     CK(upload(h->d_acsr_col, P.acsr_col));
     CK(upload(h->d_acsr_src, P.acsr_src));
     CK(upload(reinterpret_cast<int32_t *>(h->d_bdf_items), P.df_items_b));
-    CK(upload(h->d_bfwd_chunks, P.bfwd_chunks));
-    CK(upload(h->d_bbwd_chunks, P.bbwd_chunks));
+    CK(upload(h->d_bfwd_chunks, P.bdf_fchunks));
+    CK(upload(h->d_bbwd_chunks, P.bdf_bchunks));
+    CK(upload(h->d_btail_cb, P.btail_cb));
+    CK(upload(h->d_btail_ce, P.btail_ce));
     {
         std::vector<LevelRange> rg(P.level_ptr.size());
         for (size_t l = 0; l < rg.size(); l++) rg[l] = level_range(P, (int32_t)l);
@@ -1188,7 +1194,7 @@ int ensure_batch(glu_handle *h, int32_t S, bool f32) {
         CK(cudaMalloc(&h->d_vstage, na * S * sizeof(double)));
         CK(cudaMalloc(&h->d_aT, na * S * sizeof(double)));
         CK(cudaMalloc(&h->d_avb, na * S * sizeof(double)));
-        h->n_bflags = (2 * (int64_t)P.n + (int64_t)P.bfwd_chunks.size() + (int64_t)P.bbwd_chunks.size()) * G;
+        h->n_bflags = (2 * (int64_t)P.n + (int64_t)P.bdf_fchunks.size() + (int64_t)P.bdf_bchunks.size()) * G;
         CK(cudaMalloc(&h->d_bflags, std::max<int64_t>(h->n_bflags, 1) * sizeof(int32_t)));
         h->bcap = S;
     }
@@ -1274,7 +1280,7 @@ int ensure_bwork(glu_handle *h, int32_t nrhs) {
     h->bwork_nrhs = 0;
     const int64_t S = h->bcap;
     const int64_t e = std::max<int64_t>((int64_t)h->P.n * nrhs * S, 1);
-    const int64_t nch = std::max<int64_t>((int64_t)(h->P.bfwd_chunks.size() + h->P.bbwd_chunks.size()) * nrhs * S, 1);
+    const int64_t nch = std::max<int64_t>((int64_t)(h->P.bdf_fchunks.size() + h->P.bdf_bchunks.size()) * nrhs * S, 1);
     CK(cudaMalloc(&h->d_bwork, 7 * e * sizeof(double)));
     CK(cudaMalloc(&h->d_bpartial, nch * sizeof(double)));
     CK(cudaMalloc(&h->d_bnorm, (S + 3 * (size_t)nrhs * S) * sizeof(unsigned long long)));
@@ -1303,16 +1309,18 @@ int enqueue_solve_b(glu_handle *h, const T *lu, const double *in, double *out, i
     d.bchunks = h->d_bbwd_chunks;
     T *part = reinterpret_cast<T *>(h->d_bpartial);
     d.fpartial_v = part;
-    d.bpartial_v = part + (int64_t)P.bfwd_chunks.size() * nrhs * S;
+    d.bpartial_v = part + (int64_t)P.bdf_fchunks.size() * nrhs * S;
     d.fready = h->d_bflags;
     d.bready = h->d_bflags + (int64_t)n * G;
     d.fchunk_ready = h->d_bflags + 2 * (int64_t)n * G;
-    d.bchunk_ready = d.fchunk_ready + (int64_t)P.bfwd_chunks.size() * G;
+    d.bchunk_ready = d.fchunk_ready + (int64_t)P.bdf_fchunks.size() * G;
     d.ticket = h->d_ticket;
     d.abort = h->d_abort;
     d.err = h->d_serr;
     d.spin_limit_cycles = h->spin_cycles;
-    CKL(3, launch_solve_b<T>(sa, d, in, out, y, z, h->d_perm, nrhs, S, h->num_sms, st));
+    TailArgs ta{P.btail_t0, h->d_btail_cb, h->d_btail_ce, d.bready, d.epoch};
+    CKL(4 + (P.btail_t0 < n), launch_solve_b<T>(sa, d, P.bdf_nfwd, h->d_lu_colptr, ta, in, out, y, z, h->d_perm, nrhs, S,
+                                                h->num_sms, st));
     return GLU_OK;
 }
 

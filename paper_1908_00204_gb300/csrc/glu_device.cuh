@@ -158,8 +158,9 @@ cudaError_t launch_rhs_in(double *out, const double *in, int32_t n, int32_t nrhs
 cudaError_t launch_rhs_out(double *out, const double *in, int32_t n, int32_t nrhs, int32_t B, int32_t S,
                            cudaStream_t s);
 template <typename T>
-cudaError_t launch_solve_b(const SolveArgs<T> &sa, const DFSolveArgs &a, const double *in, double *out, T *y, T *z,
-                           const int32_t *perm, int32_t nrhs, int32_t S, int num_sms, cudaStream_t s);
+cudaError_t launch_solve_b(const SolveArgs<T> &sa, const DFSolveArgs &a, int32_t nfwd, const int64_t *lu_colptr,
+                           const TailArgs &ta, const double *in, double *out, T *y, T *z, const int32_t *perm,
+                           int32_t nrhs, int32_t S, int num_sms, cudaStream_t s);
 cudaError_t launch_ir_b(int op, const int64_t *rp, const int32_t *ci, const double *av, const double *aT,
                         const int64_t *src, int64_t nnz, const double *bb, double *x, double *r, const double *d,
                         int32_t n, int32_t nrhs, int32_t B, int32_t S, unsigned long long *anorm,

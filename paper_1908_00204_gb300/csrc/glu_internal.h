@@ -77,6 +77,7 @@ struct SolveChunk {
 constexpr int64_t SOLVE_CHUNK = 128;    // single matrix: lanes over a row's entries
 constexpr int64_t SOLVE_CHUNK_B = 32;   // batched: lanes over the sets, entries in sequence
 constexpr int32_t TAIL_MIN = 32, TAIL_MAX = 1024;   // dense-tail solve size range
+constexpr int32_t TAIL_MAX_B = 768;                 // batched: tail rows x 32 sets in shared memory
 
 // Everything glu_analyze computes on the host.
 struct HostPlan {
@@ -131,6 +132,9 @@ struct HostPlan {
     std::vector<SolveChunk> bfwd_chunks, bbwd_chunks;
     std::vector<int32_t> bfwd_chunk_ptr, bbwd_chunk_ptr;
     std::vector<int32_t> df_items_b;
+    int32_t bdf_nfwd = 0, btail_t0 = 0;
+    std::vector<SolveChunk> bdf_fchunks, bdf_bchunks;
+    std::vector<int32_t> btail_cb, btail_ce;
     // A in compressed rows (original numbering) for residuals
     std::vector<int64_t> acsr_ptr;
     std::vector<int32_t> acsr_col;

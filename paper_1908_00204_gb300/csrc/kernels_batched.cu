@@ -299,6 +299,53 @@ __global__ void __launch_bounds__(128) k_solve_df_b(const SolveArgs<T> s, const 
     }
 }
 
+// The dense tail [t0, n) for one group of 32 sets per block: warp w takes
+// rows w, w+32, ...; lane = set.  The tail's values of the group stay in
+// shared memory; one barrier per column forward, two backward.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_solve_tail_b(const SolveArgs<T> s, const int64_t *__restrict__ lu_colptr,
+                                                       const TailArgs ta, const T *__restrict__ fpartial, const T *y,
+                                                       T *z, int32_t nrhs, int32_t S) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int32_t n = s.n, t0 = ta.t0, NT = n - t0, G = S / 32;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int32_t g = blockIdx.x;
+    const int32_t b = g * 32 + lane;
+    T *yt = reinterpret_cast<T *>(smem_raw);      // [NT][32]
+    T *zc = yt + (int64_t)NT * 32;                 // [32]: z of the current column
+    for (int32_t r = 0; r < nrhs; r++) {
+        for (int32_t ii = w; ii < NT; ii += nwarp) {
+            T v = __ldcg(y + ((int64_t)r * n + t0 + ii) * S + b);
+            for (int32_t c = ta.cb[ii]; c < ta.ce[ii]; c++) v -= __ldcg(fpartial + (((int64_t)c * nrhs) + r) * S + b);
+            yt[ii * 32 + lane] = v;
+        }
+        __syncthreads();
+        for (int32_t jj = 0; jj < NT; jj++) {
+            const int64_t lb = s.diag_pos[t0 + jj] - jj;
+            const T vj = yt[jj * 32 + lane];
+            for (int32_t ii = jj + 1 + w; ii < NT; ii += nwarp)
+                yt[ii * 32 + lane] = yt[ii * 32 + lane] - s.lu[(lb + ii) * S + b] * vj;
+            __syncthreads();
+        }
+        T *zr = z + (int64_t)r * n * S;
+        for (int32_t jj = NT - 1; jj >= 0; jj--) {
+            const int32_t j = t0 + jj;
+            if (w == 0) {
+                const T zj = yt[jj * 32 + lane] / s.lu[s.diag_pos[j] * S + b];
+                zc[lane] = zj;
+                zr[(int64_t)j * S + b] = zj;
+            }
+            __syncthreads();
+            const int64_t ub = lu_colptr[j + 1] - NT;
+            const T zj = zc[lane];
+            for (int32_t ii = w; ii < jj; ii += nwarp)
+                yt[ii * 32 + lane] = yt[ii * 32 + lane] - s.lu[(ub + ii) * S + b] * zj;
+            __syncthreads();
+        }
+    }
+    for (int32_t ii = threadIdx.x; ii < NT; ii += blockDim.x) ta.bready[(int64_t)(t0 + ii) * G + g] = ta.epoch;
+}
+
 // ------------------------------------------------------------ refinement
 __device__ __forceinline__ void max_abs_b(unsigned long long *slot, double v) {
     atomicMax(slot, (unsigned long long)__double_as_longlong(fabs(v)));
@@ -438,16 +485,37 @@ cudaError_t launch_rhs_out(double *out, const double *in, int32_t n, int32_t nrh
 }
 
 template <typename T>
-cudaError_t launch_solve_b(const SolveArgs<T> &sa, const DFSolveArgs &a, const double *in, double *out, T *y, T *z,
-                           const int32_t *perm, int32_t nrhs, int32_t S, int num_sms, cudaStream_t s) {
+cudaError_t launch_solve_b(const SolveArgs<T> &sa, const DFSolveArgs &a, int32_t nfwd, const int64_t *lu_colptr,
+                           const TailArgs &ta, const double *in, double *out, T *y, T *z, const int32_t *perm,
+                           int32_t nrhs, int32_t S, int num_sms, cudaStream_t s) {
     const int32_t n = sa.n;
     k_perm_in_b<T><<<grid_b((int64_t)n * nrhs * S), 256, 0, s>>>(y, in, perm, n, nrhs, S);
-    cudaError_t e = cudaMemsetAsync(a.ticket, 0, sizeof(unsigned), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(a.abort, 0, sizeof(unsigned), s);
-    if (e != cudaSuccess) return e;
-    int64_t blocks = ((int64_t)a.nitems * (S / 32) * 32 + 127) / 128;
-    if (blocks > (int64_t)num_sms * 8) blocks = (int64_t)num_sms * 8;
-    if (blocks > 0) k_solve_df_b<T><<<(unsigned)blocks, 128, 0, s>>>(sa, a, y, z, nrhs, S);
+    // forward items, the tail, backward items
+    for (int part = 0; part < 2; part++) {
+        DFSolveArgs d = a;
+        if (part == 0) d.nitems = nfwd;
+        else {
+            d.items = a.items + nfwd;
+            d.nitems = a.nitems - nfwd;
+        }
+        if (d.nitems > 0) {
+            cudaError_t e = cudaMemsetAsync(a.ticket, 0, sizeof(unsigned), s);
+            if (e == cudaSuccess) e = cudaMemsetAsync(a.abort, 0, sizeof(unsigned), s);
+            if (e != cudaSuccess) return e;
+            int64_t blocks = ((int64_t)d.nitems * (S / 32) * 32 + 127) / 128;
+            if (blocks > (int64_t)num_sms * 8) blocks = (int64_t)num_sms * 8;
+            k_solve_df_b<T><<<(unsigned)blocks, 128, 0, s>>>(sa, d, y, z, nrhs, S);
+        }
+        if (part == 0 && ta.t0 < n) {
+            const size_t smem = ((size_t)(n - ta.t0) * 32 + 32) * sizeof(T);
+            cudaError_t e = cudaFuncSetAttribute(k_solve_tail_b<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+            if (e != cudaSuccess) return e;
+            k_solve_tail_b<T><<<(unsigned)(S / 32), 1024, smem, s>>>(sa, lu_colptr, ta,
+                                                                     static_cast<const T *>(a.fpartial_v), y, z,
+                                                                     nrhs, S);
+        }
+    }
     k_perm_out_b<T><<<grid_b((int64_t)n * nrhs * S), 256, 0, s>>>(out, z, perm, n, nrhs, S);
     return cudaGetLastError();
 }
@@ -486,9 +554,11 @@ template cudaError_t launch_pivot_b<double>(const double *, const int64_t *, int
                                             unsigned long long *, cudaStream_t);
 template cudaError_t launch_pivot_b<float>(const float *, const int64_t *, int32_t, int32_t, int32_t,
                                            unsigned long long *, cudaStream_t);
-template cudaError_t launch_solve_b<double>(const SolveArgs<double> &, const DFSolveArgs &, const double *, double *,
-                                            double *, double *, const int32_t *, int32_t, int32_t, int, cudaStream_t);
-template cudaError_t launch_solve_b<float>(const SolveArgs<float> &, const DFSolveArgs &, const double *, double *,
-                                           float *, float *, const int32_t *, int32_t, int32_t, int, cudaStream_t);
+template cudaError_t launch_solve_b<double>(const SolveArgs<double> &, const DFSolveArgs &, int32_t, const int64_t *,
+                                            const TailArgs &, const double *, double *, double *, double *,
+                                            const int32_t *, int32_t, int32_t, int, cudaStream_t);
+template cudaError_t launch_solve_b<float>(const SolveArgs<float> &, const DFSolveArgs &, int32_t, const int64_t *,
+                                           const TailArgs &, const double *, double *, float *, float *,
+                                           const int32_t *, int32_t, int32_t, int, cudaStream_t);
 
 }  // namespace glu
