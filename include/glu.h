@@ -93,7 +93,11 @@ typedef struct glu_options {
                                  (-1: off) */
     int32_t solve_tail;       /* 1 (default): a trailing fully dense block of 32..1024
                                  rows is solved by one block in shared memory; 0: off */
-    int32_t reserved[4];
+    int32_t factor_tail;      /* 1 (default): a trailing fully dense block of 64..3200
+                                 columns that forms the last levels (one column each)
+                                 is factored as a dense matrix by one cooperative
+                                 launch instead of one launch per level; 0: off */
+    int32_t reserved[3];
 } glu_options;
 
 /* Analysis statistics (glu_get_stats). */
@@ -116,7 +120,7 @@ typedef struct glu_stats {
     double analyze_ms;        /* host wall time of glu_analyze */
     int64_t kernel_launches;  /* CUDA kernels this handle has launched so far */
     int32_t tail_rows;        /* rows of the dense tail solved by one block (0: none) */
-    int32_t spare;
+    int32_t factor_tail_cols; /* columns of the dense block factored densely (0: none) */
 } glu_stats;
 
 /* Outcome of glu_solve_refine. */

@@ -547,6 +547,54 @@ void build_df(const HostPlan &P, const std::vector<int32_t> &lf, const std::vect
 
 // Solve levels: forward lf(i) = 1 + max lf(j) over L(i,j) != 0 (0 if none);
 // backward lb(i) = 1 + max lb(k) over U(i,k) != 0, k > i (0 if none).
+// Start of the largest trailing block [t0, n), n - t0 <= tmax, in which every
+// entry of L+U is present (n: none).
+int32_t dense_trailing_block(const HostPlan &P, int32_t tmax) {
+    const int32_t n = P.n;
+    tmax = std::min(n, tmax);
+    int32_t best = n;
+    for (int32_t T = 1; T <= tmax; T++) {
+        const int32_t t0 = n - T;
+        // adding row/column t0: column t0 needs rows t0..n-1, row t0 needs
+        // columns t0..n-1 (the columns > t0 hold row t0 iff their count of
+        // rows >= t0 reaches n - t0)
+        bool ok = P.lu_colptr[t0 + 1] - P.diag_pos[t0] == T;
+        for (int32_t j = t0 + 1; ok && j < n; j++) {
+            const int64_t q = P.lu_colptr[j + 1] - T;
+            ok = q >= P.lu_colptr[j] && P.lu_rowidx[q] == t0;
+        }
+        if (!ok) break;
+        best = t0;
+    }
+    return best;
+}
+
+// Dense trailing block of the factorization: the largest dense [t0, n),
+// FTAIL_MIN <= n - t0 <= FTAIL_MAX, whose columns are the last levels, one
+// column per level, with every column before t0 in an earlier level.  The
+// level sweep then stops before level(t0): by then every update from
+// outside the block has been applied, and the block is factored as a dense
+// matrix (no pivoting) instead of one level per column.
+void factor_tail(HostPlan &P, const glu_options &opt) {
+    const int32_t n = P.n, nl = (int32_t)P.level_ptr.size() - 1;
+    P.ftail_t0 = n;
+    P.ftail_level = nl;
+    if (opt.factor_tail == 0 || n < FTAIL_MIN) return;
+    const int32_t d0 = dense_trailing_block(P, FTAIL_MAX);
+    if (n - d0 < FTAIL_MIN) return;
+    std::vector<int32_t> pm(n + 1, -1);   // pm[t] = max level of the columns before t
+    for (int32_t j = 0; j < n; j++) pm[j + 1] = std::max(pm[j], P.level_of[j]);
+    int32_t best = n;
+    for (int32_t t = n - 1; t >= d0; t--) {
+        if (P.level_of[t] != nl - (n - t) || pm[t] >= P.level_of[t]) break;
+        best = t;
+    }
+    if (n - best >= FTAIL_MIN) {
+        P.ftail_t0 = best;
+        P.ftail_level = P.level_of[best];
+    }
+}
+
 void solve_levels(HostPlan &P, const glu_options &opt) {
     const int32_t n = P.n;
     std::vector<int32_t> lf((size_t)n, 0), lb((size_t)n, 0);
@@ -597,63 +645,13 @@ void solve_levels(HostPlan &P, const glu_options &opt) {
             chp[l + 1] = (int32_t)ch.size();
         }
     };
-    // Dataflow order: a chunk of a long row only reads rows of lower levels,
-    // so it goes at level 1 + (highest level it reads), before the rows of
-    // that level; far ahead of its row when it covers early columns.
-    auto emit = [](std::vector<int32_t> &out, bool bwd, const std::vector<int32_t> &lv, int32_t nlev,
-                   const std::vector<SolveRow> &it, const std::vector<SolveChunk> &ch,
-                   const std::vector<int32_t> &colv, const std::vector<int32_t> &ptr) {
-        std::vector<int32_t> chlev(ch.size(), 0), chrow(ch.size(), 0);
-        for (const SolveRow &r : it)
-            for (int32_t c = r.cb; c < r.ce; c++) chrow[c] = r.row;
-        for (size_t c = 0; c < ch.size(); c++) {
-            int32_t m = 0;
-            for (int64_t p = ch[c].p0; p < ch[c].p1; p++) m = std::max(m, lv[colv[p]] + 1);
-            chlev[c] = m;
-        }
-        std::vector<int32_t> cnt((size_t)nlev + 2, 0);
-        for (size_t c = 0; c < ch.size(); c++) cnt[chlev[c] + 1]++;
-        for (int32_t l = 0; l <= nlev; l++) cnt[l + 1] += cnt[l];
-        std::vector<int32_t> byl(ch.size());
-        {
-            std::vector<int32_t> f(cnt.begin(), cnt.end() - 1);
-            for (size_t c = 0; c < ch.size(); c++) byl[f[chlev[c]]++] = (int32_t)c;
-        }
-        const int32_t fl = bwd ? 1 : 0;
-        for (int32_t l = 0; l < nlev; l++) {
-            for (int32_t q = cnt[l]; q < cnt[l + 1]; q++) {
-                const int32_t c = byl[q];
-                const int32_t rec[8] = {chrow[c], 0, 0, c, fl | 2, 0, 0, 0};
-                out.insert(out.end(), rec, rec + 8);
-            }
-            for (int32_t q = ptr[l]; q < ptr[l + 1]; q++) {
-                const SolveRow &r = it[q];
-                const int32_t rec[8] = {r.row, r.cb, r.ce, -1, fl, 0, 0, 0};
-                out.insert(out.end(), rec, rec + 8);
-            }
-        }
-    };
     items(P.fwd_ptr, P.fwd_rows, P.lrow_ptr, SOLVE_CHUNK, P.fwd_items, P.fwd_chunks, P.fwd_chunk_ptr);
     items(P.bwd_ptr, P.bwd_rows, P.urow_ptr, SOLVE_CHUNK, P.bwd_items, P.bwd_chunks, P.bwd_chunk_ptr);
     // Dense tail: the largest trailing block [t0, n), TAIL_MIN <= n - t0 <=
     // TAIL_MAX, in which every entry of L+U is present.
     P.tail_t0 = n;
     if (opt.solve_tail != 0) {
-        const int32_t tmax = std::min<int32_t>(n, TAIL_MAX);
-        int32_t best = n;
-        for (int32_t T = 1; T <= tmax; T++) {
-            const int32_t t0 = n - T;
-            // adding row/column t0: column t0 needs rows t0..n-1, row t0 needs
-            // columns t0..n-1 (the columns > t0 hold row t0 iff their count of
-            // rows >= t0 reaches n - t0)
-            bool ok = P.lu_colptr[t0 + 1] - P.diag_pos[t0] == T;
-            for (int32_t j = t0 + 1; ok && j < n; j++) {
-                const int64_t q = P.lu_colptr[j + 1] - T;
-                ok = q >= P.lu_colptr[j] && P.lu_rowidx[q] == t0;
-            }
-            if (!ok) break;
-            best = t0;
-        }
+        const int32_t best = dense_trailing_block(P, TAIL_MAX);
         if (n - best >= TAIL_MIN) P.tail_t0 = best;
     }
     build_df(P, lf, lb, SOLVE_CHUNK, P.tail_t0, P.fwd_items, P.fwd_chunks, P.bwd_items, P.bwd_chunks, P.df_items,
@@ -665,9 +663,6 @@ void solve_levels(HostPlan &P, const glu_options &opt) {
     P.btail_t0 = (P.tail_t0 < n) ? std::max<int32_t>(P.tail_t0, n - TAIL_MAX_B) : n;
     build_df(P, lf, lb, SOLVE_CHUNK_B, P.btail_t0, P.bfwd_items, P.bfwd_chunks, P.bbwd_items, P.bbwd_chunks,
              P.df_items_b, P.bdf_fchunks, P.bdf_bchunks, P.btail_cb, P.btail_ce, P.bdf_nfwd);
-    (void)emit;
-    (void)nf;
-    (void)nb;
 }
 
 }  // namespace
@@ -741,6 +736,7 @@ int analyze_host(int32_t n, const int32_t *colptr, const int32_t *rowidx, const 
     levelize(P);
     double t3 = now_ms();
     schedule(P, opt, num_sms);
+    factor_tail(P, opt);
     solve_levels(P, opt);
     // A in compressed rows (original numbering), for residuals
     P.acsr_ptr.assign((size_t)n + 1, 0);

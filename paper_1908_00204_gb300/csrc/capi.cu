@@ -190,14 +190,18 @@ LevelRange level_range(const HostPlan &P, int32_t l) {
 
 // Launch the levels of one factorization: a run of consecutive pipelined
 // (mode 2) levels, and the final normalization pass after them, goes into
-// one persistent launch; every other level is one launch.
+// one persistent launch; every other level is one launch.  With a dense
+// trailing block the sweep stops before the block's first level: that
+// level's normalizations run alone, then the block is factored densely.
 template <typename T>
 int enqueue_levels(glu_handle *h, const FactorArgs<T> &a, cudaStream_t st) {
     HostPlan &P = h->P;
     const int32_t nl = (int32_t)P.level_ptr.size() - 1;
+    const bool dense = P.ftail_t0 < P.n;
+    const int32_t lend = dense ? P.ftail_level : nl;   // levels [0, lend) run here
     GridBarrier bar{h->d_gbar, h->d_gbar + 1, h->d_err, h->spin_cycles};
     int32_t l = 0;
-    while (l <= nl) {
+    while (l < lend || (!dense && l == nl)) {
         const bool pipelined = l == nl ? (nl > 0 && P.level_mode[nl - 1] == 2) : P.level_mode[l] == 2;
         if (!pipelined) {
             const LevelRange r = level_range(P, l);
@@ -206,8 +210,8 @@ int enqueue_levels(glu_handle *h, const FactorArgs<T> &a, cudaStream_t st) {
             continue;
         }
         int32_t e = l;
-        while (e < nl && P.level_mode[e] == 2) e++;
-        if (e == nl) e = nl + 1;   // include the final pass
+        while (e < lend && P.level_mode[e] == 2) e++;
+        if (!dense && e == nl) e = nl + 1;   // include the final pass
         if (e - l == 1) {
             const LevelRange r = level_range(P, l);
             CKL((r.t_end - r.t_begin) + (r.n_end - r.n_begin) > 0, launch_level<T>(a, h->map_bytes, r, h->num_sms, st));
@@ -215,6 +219,13 @@ int enqueue_levels(glu_handle *h, const FactorArgs<T> &a, cudaStream_t st) {
             CKL(1, launch_levels_persistent<T>(a, h->map_bytes, h->d_ranges + l, e - l, bar, h->num_sms, st));
         }
         l = e;
+    }
+    if (dense) {
+        LevelRange r = level_range(P, lend);
+        r.t_begin = r.row_begin = r.lane_begin = r.t_end = 0;   // normalizations only
+        CKL(r.n_end > r.n_begin, launch_level<T>(a, h->map_bytes, r, h->num_sms, st));
+        DenseTailArgs d{P.ftail_t0, P.n - P.ftail_t0, h->d_lu_colptr};
+        CKL(1, launch_dense_tail<T>(a.lu, d, bar, h->num_sms, st));
     }
     return GLU_OK;
 }
@@ -655,6 +666,7 @@ void glu_default_options(glu_options *o) {
     o->spin_limit_us = 2000000;
     o->fault_row = -1;
     o->solve_tail = 1;
+    o->factor_tail = 1;
 }
 
 int glu_analyze_opts(int32_t n, const int32_t *colptr, const int32_t *rowidx, const int32_t *perm,
@@ -1032,6 +1044,7 @@ int glu_get_stats(const glu_handle *h, glu_stats *s) {
     s->analyze_ms = h->analyze_ms;
     s->kernel_launches = h->launches;
     s->tail_rows = P.n - P.tail_t0;
+    s->factor_tail_cols = P.n - P.ftail_t0;
     return GLU_OK;
 }
 

@@ -19,12 +19,60 @@ struct LevelRange {
     int32_t n_begin, n_end;
 };
 
-// Grid barrier state of the persistent multi-level kernel.
+// Grid barrier state of the cooperative kernels (a monotone arrival count
+// and an abort word, both zeroed before the launch).
 struct GridBarrier {
     unsigned *count;
     unsigned *abort;
     unsigned long long *err;
     long long spin_limit_cycles;
+};
+
+#ifdef __CUDACC__
+// Grid barrier of a cooperative launch: the block's first thread fences,
+// arrives and waits until `target` blocks have arrived, then fences again;
+// the block barriers on both sides order the other threads' accesses (the
+// scheme of a cooperative-groups grid sync).  The wait is bounded: past the
+// limit the block records GLU_ERR_TIMEOUT and raises the abort word; a block
+// that sees the abort word stops waiting.  Returns false (in every thread of
+// the block) when the launch must end.
+__device__ __forceinline__ bool grid_sync(const GridBarrier &bar, unsigned target, int *s_stop) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *s_stop = 0;
+        __threadfence();
+        atomicAdd(bar.count, 1u);
+        if (*(volatile const unsigned *)bar.count < target) {
+            const long long t0 = clock64();
+            int spins = 0;
+            while (*(volatile const unsigned *)bar.count < target) {
+                __nanosleep(20);
+                if ((++spins & 63) == 0) {
+                    if (*(volatile const unsigned *)bar.abort) {
+                        *s_stop = 1;
+                        break;
+                    }
+                    if (clock64() - t0 > bar.spin_limit_cycles) {
+                        atomicOr(bar.abort, 1u);
+                        atomicMin(bar.err, (0xffffffull << 8) | DEVERR_TIMEOUT);
+                        *s_stop = 1;
+                        break;
+                    }
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *(volatile int *)s_stop == 0;
+}
+#endif
+
+// The dense trailing block [t0, t0 + nt) of the factorization: column t0 + k
+// keeps rows t0 .. t0+nt-1 as its last nt entries.
+struct DenseTailArgs {
+    int32_t t0, nt;
+    const int64_t *colptr;       // lu_colptr
 };
 
 template <typename T>
@@ -98,6 +146,11 @@ cudaError_t launch_level(const FactorArgs<T> &a, int map_bytes, const LevelRange
 template <typename T>
 cudaError_t launch_levels_persistent(const FactorArgs<T> &a, int map_bytes, const LevelRange *ranges, int32_t nlev,
                                      const GridBarrier &bar, int num_sms, cudaStream_t s);
+// Dense LU of the trailing block (one cooperative launch, grid barriers).
+template <typename T>
+int32_t dense_tail_panel(int32_t nt);
+template <typename T>
+cudaError_t launch_dense_tail(T *lu, const DenseTailArgs &d, const GridBarrier &bar, int num_sms, cudaStream_t s);
 template <typename T>
 cudaError_t launch_pivot_check(const T *lu, const int64_t *diag_pos, int32_t n,
                                unsigned long long *err, cudaStream_t s);

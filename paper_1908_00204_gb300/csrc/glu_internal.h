@@ -78,6 +78,7 @@ constexpr int64_t SOLVE_CHUNK = 128;    // single matrix: lanes over a row's ent
 constexpr int64_t SOLVE_CHUNK_B = 32;   // batched: lanes over the sets, entries in sequence
 constexpr int32_t TAIL_MIN = 32, TAIL_MAX = 1024;   // dense-tail solve size range
 constexpr int32_t TAIL_MAX_B = 768;                 // batched: tail rows x 32 sets in shared memory
+constexpr int32_t FTAIL_MIN = 64, FTAIL_MAX = 3200;  // dense-tail factorization size range
 
 // Everything glu_analyze computes on the host.
 struct HostPlan {
@@ -135,6 +136,10 @@ struct HostPlan {
     int32_t bdf_nfwd = 0, btail_t0 = 0;
     std::vector<SolveChunk> bdf_fchunks, bdf_bchunks;
     std::vector<int32_t> btail_cb, btail_ce;
+    // dense trailing block of the factorization [ftail_t0, n) (ftail_t0 == n:
+    // none); the level sweep runs levels [0, ftail_level) and the
+    // normalizations of level ftail_level, then the block is factored dense
+    int32_t ftail_t0 = 0, ftail_level = 0;
     // A in compressed rows (original numbering) for residuals
     std::vector<int64_t> acsr_ptr;
     std::vector<int32_t> acsr_col;

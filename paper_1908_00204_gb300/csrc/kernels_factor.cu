@@ -343,38 +343,7 @@ k_levels_persistent(const FactorArgs<T> a, const LevelRange *__restrict__ ranges
         run_level<T, M>(a, r, lane, warp, nw, acc);
         if (li + 1 == nlev) break;
         prefetch_level<T, M>(a, ranges[li + 1], lane, warp, nw);
-        // grid barrier: the block's first thread fences, arrives and waits,
-        // then fences again; the block barriers on both sides order the other
-        // threads' accesses (the scheme of a cooperative-groups grid sync)
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            s_stop = 0;
-            __threadfence();
-            atomicAdd(bar.count, 1u);
-            const unsigned target = (unsigned)(li + 1) * gridDim.x;
-            if (*(volatile const unsigned *)bar.count < target) {
-                const long long t0 = clock64();
-                int spins = 0;
-                while (*(volatile const unsigned *)bar.count < target) {
-                    __nanosleep(20);
-                    if ((++spins & 63) == 0) {
-                        if (*(volatile const unsigned *)bar.abort) {
-                            s_stop = 1;
-                            break;
-                        }
-                        if (clock64() - t0 > bar.spin_limit_cycles) {
-                            atomicOr(bar.abort, 1u);
-                            raise_err(bar.err, 0xffffff, DEVERR_TIMEOUT);
-                            s_stop = 1;
-                            break;
-                        }
-                    }
-                }
-            }
-            __threadfence();
-        }
-        __syncthreads();
-        if (s_stop) return;
+        if (!grid_sync(bar, (unsigned)(li + 1) * gridDim.x, &s_stop)) return;
     }
 }
 

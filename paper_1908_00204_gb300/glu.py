@@ -37,7 +37,7 @@ class glu_options(C.Structure):
                 ("piece_updates", C.c_int32), ("wide_threshold", C.c_int32), ("use_graph", C.c_int32),
                 ("verbose", C.c_int32), ("host_only", C.c_int32), ("solve_mode", C.c_int32),
                 ("spin_limit_us", C.c_int32), ("fault_row", C.c_int32), ("solve_tail", C.c_int32),
-                ("reserved", C.c_int32 * 4)]
+                ("factor_tail", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 class glu_stats(C.Structure):
@@ -46,7 +46,8 @@ class glu_stats(C.Structure):
                 ("n_updates", C.c_int64), ("flops", C.c_double), ("levels_by_mode", C.c_int32 * 3),
                 ("solve_levels_fwd", C.c_int32), ("solve_levels_bwd", C.c_int32),
                 ("max_level_width", C.c_int32), ("device_bytes", C.c_int64), ("analyze_ms", C.c_double),
-                ("kernel_launches", C.c_int64), ("tail_rows", C.c_int32), ("spare", C.c_int32)]
+                ("kernel_launches", C.c_int64), ("tail_rows", C.c_int32),
+                ("factor_tail_cols", C.c_int32)]
 
 
 class glu_refine_info(C.Structure):

@@ -6,7 +6,9 @@ Knobs (all fields of ``glu_options``):
   pipelined mode (one persistent launch with grid barriers) instead of one
   launch per level (the paper's stream-mode threshold, Section III-B.2);
 * ``piece_updates`` -- target updates per row task (work split size);
-* ``solve_tail`` -- dense trailing block solved by one block, or not.
+* ``solve_tail`` -- dense trailing block solved by one block, or not;
+* ``factor_tail`` -- dense trailing block factored by the dense kernel, or
+  one level per column.
 
 Each candidate is analysed, factorized and solved on the current GPU with
 new values; the fastest refactor + solve (median of a few runs, CUDA events)
@@ -32,6 +34,7 @@ DEFAULT_CANDIDATES: List[Dict[str, int]] = [
     {"tail_threshold": 0, "piece_updates": 512, "solve_tail": 1},
     {"tail_threshold": 4, "piece_updates": 1024, "solve_tail": 1},
     {"tail_threshold": 0, "piece_updates": 1024, "solve_tail": 0},
+    {"tail_threshold": 0, "piece_updates": 1024, "factor_tail": 0},
 ]
 
 

@@ -166,3 +166,61 @@ def test_multiple_rhs_device(glu):
     f = oracle.Factorization(m.n, m.colptr, m.rowidx, m.perm, v)
     np.testing.assert_allclose(x, f.solve(b), rtol=1e-9, atol=1e-12)
     assert backward_error(m.n, m.colptr, m.rowidx, v, b, x) <= BERR_TOL
+
+
+@pytest.mark.parametrize("spec", [(16, 20, 900, 15), (16, 20, 1700, 10)])
+def test_dense_tail_factor(glu, spec):
+    """A trailing dense block of ~900 / ~1700 columns (panel widths 16 and 8)
+    factored by the dense kernel: factors against the oracle, and against the
+    level sweep run over the same block (factor_tail=0)."""
+    m = synth.CircuitMatrix(synth.CircuitSpec(spec[0], spec[1], spec[2], spec[3], 0.02, 0.05, "nd"), 3)
+    v = m.values(8)
+    h, got, _ = run_case(glu, m.n, m.colptr, m.rowidx, m.perm, v, synth.rhs(m.n, 2, 8))
+    assert glu.glu_get_stats(h)["factor_tail_cols"] >= 800
+    h0 = glu.glu_analyze(m.n, m.colptr, m.rowidx, m.perm, glu.default_options(factor_tail=0))
+    assert glu.glu_get_stats(h0)["factor_tail_cols"] == 0
+    glu.glu_factor(h0, v)
+    ref = glu.glu_get_factors(h0)
+    np.testing.assert_allclose(got, ref, rtol=1e-11, atol=1e-14 * np.abs(ref).max())
+
+
+def test_dense_tail_factor_mesh100x200(glu):
+    m = synth.make("mesh100x200_nets64", 1)
+    h = glu.glu_analyze(m.n, m.colptr, m.rowidx, m.perm)
+    assert glu.glu_get_stats(h)["factor_tail_cols"] >= 64
+    f = oracle.Factorization(m.n, m.colptr, m.rowidx, m.perm)
+    v = m.values(31)
+    glu.glu_factor(h, v)
+    got = glu.glu_get_factors(h)
+    bad, _ = factor_mismatches(f.lu_colptr, f.lu_rowidx, got, f.factor(v))
+    assert bad.size == 0
+    # the pipelined (persistent) mode before the block, and the FP32 path
+    hp = glu.glu_analyze(m.n, m.colptr, m.rowidx, m.perm, glu.default_options(tail_threshold=4))
+    glu.glu_factor(hp, v)
+    assert np.array_equal(glu.glu_get_factors(hp), got)
+    glu.glu_factor_f32(h, v)
+    b = synth.rhs(m.n, 2, 5)
+    x, info = glu.glu_solve_refine(h, b, tol=1e-12, maxit=10)
+    assert info["converged"] == 1 and backward_error(m.n, m.colptr, m.rowidx, v, b, x) <= BERR_TOL
+
+
+def test_dense_tail_nonfinite_pivot_reported(glu):
+    """A non-finite pivot inside the dense block is reported with its column
+    (the numbering of P A P^T), and a good refactorization works afterwards."""
+    m = synth.CircuitMatrix(synth.CircuitSpec(16, 20, 900, 15, 0.02, 0.05, "nd"), 3)
+    h = glu.glu_analyze(m.n, m.colptr, m.rowidx, m.perm)
+    t = glu.glu_get_stats(h)["factor_tail_cols"]
+    assert t >= 800
+    c = m.n - t // 2                          # a column inside the block
+    old = int(m.perm[c])                      # B(c, c) = A(old, old)
+    q = m.colptr[old] + int(np.searchsorted(m.rowidx[m.colptr[old]:m.colptr[old + 1]], old))
+    assert m.rowidx[q] == old
+    v = m.values(8)
+    v2 = v.copy()
+    v2[q] = np.nan
+    with pytest.raises(glu.GluError) as e:
+        glu.glu_factor(h, v2)
+    assert e.value.code == glu.glu.GLU_ERR_NONFINITE and e.value.column == c
+    glu.glu_factor(h, v)
+    b = synth.rhs(m.n, 1, 3)
+    assert backward_error(m.n, m.colptr, m.rowidx, v, b, glu.glu_solve(h, b)) <= BERR_TOL
