@@ -352,24 +352,70 @@ void schedule(HostPlan &P, const glu_options &opt, int num_sms) {
                 // Chunks reached by two or more segments become KIND_SRC
                 // tasks.  A chunk reached by one segment holds rows that no
                 // other source of this group updates: those segments need no
-                // ordering, so consecutive ones of a source merge and are
-                // packed into small tasks.
+                // ordering, so consecutive ones of a source merge (up to
+                // piece_l rows) and are packed into small tasks.
                 std::vector<PSeg> priv;
+                auto add_priv = [&](const PSeg &sg) {
+                    if (!priv.empty() && priv.back().pair == sg.pair && priv.back().t1 == sg.t0 &&
+                        priv.back().t1 - priv.back().t0 + (sg.t1 - sg.t0) <= piece_l)
+                        priv.back().t1 = sg.t1;
+                    else
+                        priv.push_back(sg);
+                };
                 for (int32_t ch : touched) {
                     std::vector<PSeg> &cs = chunk_segs[ch];
-                    if (cs.size() >= 2) {
-                        Task t{(int32_t)psegs.size(), 0, KIND_SRC,
-                               (int32_t)std::min<int64_t>(SRC_SLOTS, clen - (int64_t)ch * SRC_SLOTS),
-                               c0 + (int64_t)ch * SRC_SLOTS, chunk_work[ch]};
+                    const int64_t cb = (int64_t)ch * SRC_SLOTS;
+                    const int64_t cl = std::min<int64_t>(SRC_SLOTS, clen - cb);
+                    if (cs.size() < 2) {
+                        add_priv(cs[0]);
+                    } else if (chunk_work[ch] <= piece_l) {
+                        Task t{(int32_t)psegs.size(), 0, KIND_SRC, (int32_t)cl, c0 + cb, chunk_work[ch]};
                         psegs.insert(psegs.end(), cs.begin(), cs.end());
                         t.seg_end = (int32_t)psegs.size();
                         lvl_tasks.push_back(t);
                     } else {
-                        const PSeg &sg = cs[0];
-                        if (!priv.empty() && priv.back().pair == sg.pair && priv.back().t1 == sg.t0)
-                            priv.back().t1 = sg.t1;
-                        else
-                            priv.push_back(sg);
+                        // A heavily shared chunk: a task's time is its lanes'
+                        // serial work, so split the chunk's positions into
+                        // equal parts (16, 8, ... positions) until each part
+                        // holds at most piece_l updates.  A segment's rows
+                        // split at the parts' first rows.
+                        auto clip = [&](const PSeg &sg, int64_t p0, int64_t p1) {
+                            const int32_t *L = P.lu_rowidx.data() + lstart(P.pair_j[sg.pair]);
+                            const int32_t a0 = p0 <= cb ? sg.t0
+                                : (int32_t)(std::lower_bound(L + sg.t0, L + sg.t1, krows[p0]) - L);
+                            const int32_t a1 = p1 >= cb + cl ? sg.t1
+                                : (int32_t)(std::lower_bound(L + sg.t0, L + sg.t1, krows[p1]) - L);
+                            return PSeg{sg.pair, a0, a1, 0};
+                        };
+                        int64_t part = SRC_SLOTS;
+                        while (part > 1) {
+                            int64_t worst = 0;
+                            for (int64_t p0 = cb; p0 < cb + cl; p0 += part) {
+                                int64_t w = 0;
+                                for (const PSeg &sg : cs) {
+                                    const PSeg c = clip(sg, p0, std::min(p0 + part, cb + cl));
+                                    w += c.t1 - c.t0;
+                                }
+                                worst = std::max(worst, w);
+                            }
+                            if (worst <= piece_l) break;
+                            part /= 2;
+                        }
+                        for (int64_t p0 = cb; p0 < cb + cl; p0 += part) {
+                            const int64_t p1 = std::min(p0 + part, cb + cl);
+                            std::vector<PSeg> sub;
+                            int64_t w = 0;
+                            for (const PSeg &sg : cs) {
+                                const PSeg c = clip(sg, p0, p1);
+                                if (c.t1 > c.t0) { sub.push_back(c); w += c.t1 - c.t0; }
+                            }
+                            if (sub.empty()) continue;
+                            if (sub.size() == 1) { add_priv(sub[0]); continue; }
+                            Task t{(int32_t)psegs.size(), 0, KIND_SRC, (int32_t)(p1 - p0), c0 + p0, w};
+                            psegs.insert(psegs.end(), sub.begin(), sub.end());
+                            t.seg_end = (int32_t)psegs.size();
+                            lvl_tasks.push_back(t);
+                        }
                     }
                     cs.clear();
                     chunk_work[ch] = 0;
@@ -469,7 +515,7 @@ void schedule(HostPlan &P, const glu_options &opt, int num_sms) {
 
     // normalization items: level l's columns run in level l+1's kernel; the
     // last level's columns in the final pass
-    const int32_t nchunk = 1024;
+    const int32_t nchunk = 256;   // rows per item: 8 divisions per lane
     P.norms.clear();
     P.lvl_norm_ptr.assign((size_t)nl + 2, 0);
     for (int32_t l = 0; l <= nl; l++) {

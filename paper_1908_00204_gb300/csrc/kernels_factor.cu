@@ -50,7 +50,17 @@ __device__ __forceinline__ void norm_item(const FactorArgs<T> &a, const NormItem
     const int64_t dj = a.diag_pos[it.col];
     const T d = a.lu[dj];
     T *L = a.lu + dj + 1;
-    for (int32_t t = it.t0 + lane; t < it.t1; t += 32) L[t] = L[t] / d;
+    // all loads of the item first (at most 8 per lane), then the divisions
+    constexpr int NU = 8;
+    for (int32_t tb = it.t0 + lane; tb < it.t1; tb += 32 * NU) {
+        T v[NU];
+#pragma unroll
+        for (int u = 0; u < NU; u++)
+            if (tb + 32 * u < it.t1) v[u] = L[tb + 32 * u];
+#pragma unroll
+        for (int u = 0; u < NU; u++)
+            if (tb + 32 * u < it.t1) L[tb + 32 * u] = v[u] / d;
+    }
 }
 
 // Everything a segment needs, gathered once: the position of U(j,k), the
@@ -92,8 +102,17 @@ __device__ __forceinline__ SegMeta<T> shfl_meta(const SegMeta<T> &m, int src) {
     return o;
 }
 
-constexpr int ROW_UNROLL = 4;   // rows per lane batch, lanes over rows
-constexpr int LANE_UNROLL = 4;  // rows per batch when one lane walks a segment
+#ifndef GLU_ROW_UNROLL
+#define GLU_ROW_UNROLL 4            // rows per lane batch, lanes over rows
+#endif
+#ifndef GLU_LANE_UNROLL
+#define GLU_LANE_UNROLL 4           // rows per batch when one lane walks a segment
+#endif
+#ifndef GLU_SRC_UNROLL
+#define GLU_SRC_UNROLL 8            // the same inside KIND_SRC tasks
+#endif
+constexpr int ROW_UNROLL = GLU_ROW_UNROLL;
+constexpr int LANE_UNROLL = GLU_LANE_UNROLL;
 
 // Rows t0..t1-1 of one segment, lanes over rows.  Within a segment every row
 // hits a different target entry, so all loads of a batch go out before any
@@ -124,33 +143,79 @@ __device__ __forceinline__ void row_segment(T *__restrict__ lu, const M *__restr
     }
 }
 
-// KIND_ROW: lanes fetch the metadata of up to 32 segments at once, then the
-// warp applies the segments in order (ascending source), lanes over rows.
+// KIND_ROW tasks of one warp, tq0, tq0 + stride, ... (cnt of them), applied one
+// after the other as row_task would, but with the metadata of up to 32
+// segments -- spanning several tasks -- fetched at once, one per lane, so the
+// multiplier divisions of a warp's many short tasks share instructions.
 template <typename T, typename M>
-__device__ __forceinline__ void row_task(const FactorArgs<T> &a, const Task &tk, int lane) {
+__device__ __forceinline__ void row_tasks(const FactorArgs<T> &a, int64_t tq0, int64_t stride, int64_t cnt,
+                                          int lane) {
     const M *__restrict__ map = static_cast<const M *>(a.map);
-    for (int32_t base = tk.seg_begin; base < tk.seg_end; base += 32) {
-        const int cnt = min(32, tk.seg_end - base);
+    int64_t i = 0;      // next task of the list
+    int32_t skip = 0;   // segments of task i already applied
+    while (i < cnt) {
+        const bool valid = i + lane < cnt;
+        int32_t sb = 0, ns = 0;
+        if (valid) {
+            const Task tk = a.tasks[tq0 + (i + lane) * stride];
+            sb = tk.seg_begin;
+            ns = tk.seg_end - tk.seg_begin;
+            if (lane == 0) {
+                sb += skip;
+                ns -= skip;
+            }
+        }
+        int32_t incl = ns;   // inclusive prefix sum of the segment counts
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+        const int32_t take = min(tot, 32);
+        // slot `lane` belongs to the first task whose prefix sum exceeds it
+        int t = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1)
+            if (__shfl_sync(0xffffffffu, incl, t + step - 1) <= lane) t += step;
+        t = min(t, 31);
+        const int32_t t_incl = __shfl_sync(0xffffffffu, incl, t);
+        const int32_t t_ns = __shfl_sync(0xffffffffu, ns, t);
+        const int32_t t_sb = __shfl_sync(0xffffffffu, sb, t);
         SegMeta<T> mine;
-        if (lane < cnt) load_meta<T>(a, base + lane, mine);
-        for (int q = 0; q < cnt; q++) {
+        if (lane < take) load_meta<T>(a, t_sb + (lane - (t_incl - t_ns)), mine);
+        for (int q = 0; q < take; q++) {
             const SegMeta<T> m = shfl_meta<T>(mine, q);
             row_segment<T, M>(a.lu, map, m, lane);
             __syncwarp();
+        }
+        if (tot <= 32) {
+            i += (cnt - i < 32) ? cnt - i : 32;
+            skip = 0;
+        } else {
+            // tasks wholly applied, then the one cut at slot 32
+            const int tp = __popc(__ballot_sync(0xffffffffu, valid && incl <= 32));
+            const int32_t p_incl = __shfl_sync(0xffffffffu, incl, tp);
+            const int32_t p_ns = __shfl_sync(0xffffffffu, ns, tp);
+            skip = (tp == 0 ? skip : 0) + (32 - (p_incl - p_ns));
+            i += tp;
         }
     }
 }
 
 // KIND_SRC: lanes over segments; lane l accumulates its products into row l
 // of a 32 x 33 shared-memory tile (slot = target position - base); then lane
-// s sums column s over the 32 lanes in order and applies it.  The next
-// segment's metadata is fetched before the current one's rows.
+// s sums column s over the lanes that had segments, in order, and applies
+// it.  The next segment's metadata is fetched before the current one's rows.
 template <typename T, typename M>
 __device__ __forceinline__ void src_task(const FactorArgs<T> &a, const Task &tk, int lane, T *__restrict__ acc) {
     const M *__restrict__ map = static_cast<const M *>(a.map);
     T *__restrict__ row = acc + lane * (SRC_SLOTS + 1);
+    const int nl = min(32, tk.seg_end - tk.seg_begin);   // lanes with segments
+    if (lane < nl) {
 #pragma unroll
-    for (int s = 0; s < SRC_SLOTS; s++) row[s] = (T)0;
+        for (int s = 0; s < SRC_SLOTS; s++) row[s] = (T)0;
+    }
     int32_t s = tk.seg_begin + lane;
     SegMeta<T> cur;
     bool have = s < tk.seg_end;
@@ -163,17 +228,17 @@ __device__ __forceinline__ void src_task(const FactorArgs<T> &a, const Task &tk,
         const M *__restrict__ mp = map + cur.mb;
         const T *__restrict__ L = a.lu + cur.lstart;
         const int32_t rel = (int32_t)(cur.pos + 1 - tk.base);
-        for (int32_t tb = cur.t0; tb < cur.t1; tb += LANE_UNROLL) {
-            uint32_t off[LANE_UNROLL];
-            T lv[LANE_UNROLL];
+        for (int32_t tb = cur.t0; tb < cur.t1; tb += GLU_SRC_UNROLL) {
+            uint32_t off[GLU_SRC_UNROLL];
+            T lv[GLU_SRC_UNROLL];
 #pragma unroll
-            for (int u = 0; u < LANE_UNROLL; u++)
+            for (int u = 0; u < GLU_SRC_UNROLL; u++)
                 if (tb + u < cur.t1) {
                     off[u] = mp[tb + u];
                     lv[u] = L[tb + u];
                 }
 #pragma unroll
-            for (int u = 0; u < LANE_UNROLL; u++)
+            for (int u = 0; u < GLU_SRC_UNROLL; u++)
                 if (tb + u < cur.t1) {
                     const int32_t slot = rel + (int32_t)off[u];
                     row[slot] = fma_t<T>(lv[u], cur.f, row[slot]);
@@ -186,8 +251,7 @@ __device__ __forceinline__ void src_task(const FactorArgs<T> &a, const Task &tk,
     __syncwarp();
     if (lane < tk.nslots) {
         T sum = (T)0;
-#pragma unroll 8
-        for (int l = 0; l < 32; l++) sum += acc[l * (SRC_SLOTS + 1) + lane];
+        for (int l = 0; l < nl; l++) sum += acc[l * (SRC_SLOTS + 1) + lane];
         a.lu[tk.base + lane] -= sum;
     }
     __syncwarp();
@@ -226,6 +290,9 @@ __device__ __forceinline__ void lane_task(const FactorArgs<T> &a, const Task &tk
 }
 
 constexpr int LEVEL_WARPS = 4;
+#ifndef GLU_LEVEL_BLOCKS_PER_SM
+#define GLU_LEVEL_BLOCKS_PER_SM 4   // resident k_level blocks per SM the launch aims for
+#endif
 
 // One level.  Work items, in order: normalization items, KIND_SRC tasks and
 // KIND_ROW tasks (one warp each), then KIND_LANE tasks, 32 per warp.
@@ -239,24 +306,20 @@ __device__ __forceinline__ void run_level(const FactorArgs<T> &a, const LevelRan
     const int64_t nrow = r.lane_begin - r.row_begin;
     const int64_t nlane = r.t_end - r.lane_begin;
     const int64_t total = nn + nsrc + nrow + (nlane + 31) / 32;
-    for (int64_t it = warp; it < total; it += nw) {
-        int64_t k = it;
-        if (k < nn) {
-            norm_item<T>(a, a.norms[r.n_begin + k], lane);
-            continue;
-        }
-        k -= nn;
-        if (k < nsrc) {
-            src_task<T, M>(a, a.tasks[r.t_begin + k], lane, acc);
-            continue;
-        }
-        k -= nsrc;
-        if (k < nrow) {
-            row_task<T, M>(a, a.tasks[r.row_begin + k], lane);
-            continue;
-        }
-        k -= nrow;
-        const int64_t q = r.lane_begin + k * 32 + lane;
+    int64_t it = warp;
+    for (; it < nn + nsrc; it += nw) {
+        if (it < nn) norm_item<T>(a, a.norms[r.n_begin + it], lane);
+        else src_task<T, M>(a, a.tasks[r.t_begin + (it - nn)], lane, acc);
+    }
+    if (it < nn + nsrc + nrow) {
+        // this warp's KIND_ROW tasks: every nw-th from k0
+        const int64_t k0 = it - nn - nsrc;
+        const int64_t cnt = (nrow - k0 + nw - 1) / nw;
+        row_tasks<T, M>(a, r.row_begin + k0, nw, cnt, lane);
+        it += cnt * nw;
+    }
+    for (; it < total; it += nw) {
+        const int64_t q = r.lane_begin + (it - nn - nsrc - nrow) * 32 + lane;
         if (q < r.t_end) lane_task<T, M>(a, a.tasks[q]);
         __syncwarp();
     }
@@ -304,7 +367,7 @@ __device__ __forceinline__ void prefetch_level(const FactorArgs<T> &a, const Lev
 // waits for it to finish (griddepcontrol.wait makes its writes visible);
 // each block lets the next level start once its own items are done.
 template <typename T, typename M>
-__global__ void __launch_bounds__(LEVEL_WARPS * 32, 4)
+__global__ void __launch_bounds__(LEVEL_WARPS * 32, GLU_LEVEL_BLOCKS_PER_SM)
 k_level(const FactorArgs<T> a, LevelRange r) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -414,9 +477,10 @@ cudaError_t launch_level(const FactorArgs<T> &a, int map_bytes, const LevelRange
                           (r.n_end - r.n_begin);
     if (items <= 0) return cudaSuccess;
     int64_t blocks = (items + LEVEL_WARPS - 1) / LEVEL_WARPS;
-    // at most the resident capacity (4 blocks per SM): the next level's early
-    // blocks then take only slots this level no longer needs
-    const int64_t cap = (int64_t)num_sms * 4;
+    // at most the resident capacity (GLU_LEVEL_BLOCKS_PER_SM blocks per SM):
+    // the next level's early blocks then take only slots this level no
+    // longer needs
+    const int64_t cap = (int64_t)num_sms * GLU_LEVEL_BLOCKS_PER_SM;
     if (blocks > cap) blocks = cap;
     const size_t smem = sizeof(T) * LEVEL_WARPS * 32 * (SRC_SLOTS + 1);
     cudaLaunchConfig_t cfg = {};
