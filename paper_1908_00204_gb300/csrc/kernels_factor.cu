@@ -103,10 +103,10 @@ __device__ __forceinline__ SegMeta<T> shfl_meta(const SegMeta<T> &m, int src) {
 }
 
 #ifndef GLU_ROW_UNROLL
-#define GLU_ROW_UNROLL 4            // rows per lane batch, lanes over rows
+#define GLU_ROW_UNROLL 8            // rows per lane batch, lanes over rows
 #endif
 #ifndef GLU_LANE_UNROLL
-#define GLU_LANE_UNROLL 4           // rows per batch when one lane walks a segment
+#define GLU_LANE_UNROLL 16          // rows per batch when one lane walks a segment
 #endif
 #ifndef GLU_SRC_UNROLL
 #define GLU_SRC_UNROLL 8            // the same inside KIND_SRC tasks
