@@ -97,7 +97,10 @@ typedef struct glu_options {
                                  columns that forms the last levels (one column each)
                                  is factored as a dense matrix by one cooperative
                                  launch instead of one launch per level; 0: off */
-    int32_t reserved[3];
+    int32_t solve_blocks;     /* 1 (default): in the dataflow solve, dense diagonal blocks of
+                                 4..128 rows are solved by one warp each (their rows'
+                                 entries outside the block as parallel partial sums); 0: off */
+    int32_t reserved[2];
 } glu_options;
 
 /* Analysis statistics (glu_get_stats). */

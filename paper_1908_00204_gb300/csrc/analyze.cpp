@@ -531,68 +531,174 @@ void schedule(HostPlan &P, const glu_options &opt, int num_sms) {
     }
 }
 
-// Dataflow schedule of the solve for a chunk size and a dense tail [t0, n):
-// forward rows before the tail, the tail rows' partial sums over the columns
-// before the tail (forward chunks tail_cb[i]..tail_ce[i]-1), backward rows
-// before the tail (the tail rows' U entries all lie inside the tail).  Items
-// are ordered by level, a chunk at 1 + the highest level it reads and before
-// the rows of its level; forward items first (nfwd of them).
-void build_df(const HostPlan &P, const std::vector<int32_t> &lf, const std::vector<int32_t> &lb, int64_t chunk,
-              int32_t t0, const std::vector<SolveRow> &fitems, const std::vector<SolveChunk> &fchunks,
-              const std::vector<SolveRow> &bitems, const std::vector<SolveChunk> &bchunks, std::vector<int32_t> &out,
+// Dense diagonal blocks ("supernodes") of the solve among the rows [0, t0):
+// maximal runs [c0, c1) in which L(B, B) is dense lower and U(B, B) dense
+// upper, cut into pieces of at most SN_MAX rows; pieces of at least SN_MIN
+// rows are kept.
+std::vector<std::pair<int32_t, int32_t>> solve_blocks(const HostPlan &P, int32_t t0) {
+    std::vector<std::pair<int32_t, int32_t>> out;
+    auto flush = [&](int32_t c0, int32_t c1) {
+        for (int32_t a = c0; a < c1; a += SN_MAX) {
+            const int32_t b = std::min(c1, a + SN_MAX);
+            if (b - a >= SN_MIN) out.emplace_back(a, b);
+        }
+    };
+    int32_t c0 = 0;
+    for (int32_t i = 1; i <= t0; i++) {
+        bool ext = i < t0;
+        if (ext) {
+            // L row i holds columns c0..i-1 iff i - c0 of its entries are >= c0
+            const int32_t *lc = P.lrow_col.data();
+            const int64_t lb = P.lrow_ptr[i], le = P.lrow_ptr[i + 1];
+            const int64_t nl = le - (std::lower_bound(lc + lb, lc + le, c0) - lc);
+            // U column i holds rows c0..i-1 iff i - c0 of its rows above the diagonal are >= c0
+            const int32_t *ur = P.lu_rowidx.data();
+            const int64_t ub = P.lu_colptr[i], ue = P.diag_pos[i];
+            const int64_t nu = ue - (std::lower_bound(ur + ub, ur + ue, c0) - ur);
+            ext = nl == i - c0 && nu == i - c0;
+        }
+        if (!ext) {
+            flush(c0, i);
+            c0 = i;
+        }
+    }
+    return out;
+}
+
+// Dataflow schedule of the solve for a chunk size and a dense tail [t0, n).
+// Items: a row (its dot product, or the sum of its chunks' partials when it
+// has more than `chunk` entries), a chunk (a partial dot product of at most
+// `chunk` entries), and -- when `blocks` is set -- a dense diagonal block of
+// the solve, whose rows' entries outside the block are always chunks and whose
+// own triangle one warp sweeps.  Forward items cover the rows before the tail
+// and the tail rows' partial sums over the columns before it (forward chunks
+// tail_cb[i]..tail_ce[i]-1); backward items the rows before the tail.  Each
+// item comes after everything it reads: levels are longest paths with every
+// block contracted to one node, a chunk sits at 1 + the highest level it
+// reads and before the rows of its level.  snx lists, per block, the first
+// chunk of each of its rows and the end (offset in the item's third field).
+void build_df(const HostPlan &P, int64_t chunk, int32_t t0, bool blocks, std::vector<int32_t> &out,
               std::vector<SolveChunk> &dff, std::vector<SolveChunk> &dfb, std::vector<int32_t> &tcb,
-              std::vector<int32_t> &tce, int32_t &nfwd) {
+              std::vector<int32_t> &tce, int32_t &nfwd, std::vector<int32_t> &snx_f, std::vector<int32_t> &snx_b) {
     const int32_t n = P.n;
-    dff = fchunks;
-    dfb = bchunks;
+    const auto bl = blocks ? solve_blocks(P, t0) : std::vector<std::pair<int32_t, int32_t>>();
+    std::vector<int32_t> bof((size_t)n, -1);
+    for (size_t q = 0; q < bl.size(); q++)
+        for (int32_t i = bl[q].first; i < bl[q].second; i++) bof[i] = (int32_t)q;
+    dff.clear();
+    dfb.clear();
+    snx_f.clear();
+    snx_b.clear();
     tcb.assign((size_t)(n - t0), 0);
     tce.assign((size_t)(n - t0), 0);
     struct Rec { int32_t level, type, seq; std::array<int32_t, 8> item; };
-    auto build = [&](bool bwd, const std::vector<int32_t> &lv, const std::vector<SolveRow> &it,
-                     const std::vector<SolveChunk> &ch, const std::vector<int32_t> &colv, std::vector<Rec> &recs) {
-        std::vector<int32_t> chrow(ch.size(), -1);
-        for (const SolveRow &r : it)
-            for (int32_t c = r.cb; c < r.ce; c++) chrow[c] = r.row;
-        for (size_t c = 0; c < ch.size(); c++) {
-            if (chrow[c] < 0) continue;                    // a chunk no kept row uses
+    auto add_chunks = [&](std::vector<SolveChunk> &ch, int64_t b, int64_t e) {
+        for (int64_t p = b; p < e; p += chunk) ch.push_back(SolveChunk{p, std::min(e, p + chunk)});
+    };
+    auto chunk_recs = [&](bool bwd, const std::vector<SolveChunk> &ch, int32_t c_begin, const std::vector<int32_t> &lv,
+                          const std::vector<int32_t> &colv, int32_t row, std::vector<Rec> &recs) {
+        for (int32_t c = c_begin; c < (int32_t)ch.size(); c++) {
             int32_t m = 0;
             for (int64_t p = ch[c].p0; p < ch[c].p1; p++) m = std::max(m, lv[colv[p]] + 1);
-            recs.push_back(Rec{m, 0, (int32_t)recs.size(), {chrow[c], 0, 0, (int32_t)c, (bwd ? 1 : 0) | 2, 0, 0, 0}});
+            recs.push_back(Rec{m, 0, (int32_t)recs.size(), {row, 0, 0, c, (bwd ? 1 : 0) | 2, 0, 0, 0}});
         }
-        for (const SolveRow &r : it)
-            recs.push_back(Rec{lv[r.row], 1, (int32_t)recs.size(), {r.row, r.cb, r.ce, -1, bwd ? 1 : 0, 0, 0, 0}});
+    };
+    auto finish = [](std::vector<Rec> &recs) {
         std::stable_sort(recs.begin(), recs.end(), [](const Rec &a, const Rec &b) {
             return a.level != b.level ? a.level < b.level : a.type < b.type;
         });
     };
-    std::vector<SolveRow> fkeep, bkeep;
-    for (const SolveRow &r : fitems)
-        if (r.row < t0) fkeep.push_back(r);
+    // ---- forward (unit L), rows ascending
+    std::vector<int32_t> lf((size_t)n, 0);
+    std::vector<Rec> frec;
+    for (int32_t i = 0; i < t0;) {
+        if (bof[i] >= 0) {
+            const int32_t c0 = bl[bof[i]].first, c1 = bl[bof[i]].second;
+            int32_t lev = 0;
+            const int32_t off = (int32_t)snx_f.size();
+            for (int32_t r = c0; r < c1; r++) {
+                // entries before the block: all but the last r - c0
+                const int64_t b = P.lrow_ptr[r], e = P.lrow_ptr[r + 1] - (r - c0);
+                for (int64_t p = b; p < e; p++) lev = std::max(lev, lf[P.lrow_col[p]] + 1);
+                const int32_t cb = (int32_t)dff.size();
+                snx_f.push_back(cb);
+                add_chunks(dff, b, e);
+                chunk_recs(false, dff, cb, lf, P.lrow_col, r, frec);
+            }
+            snx_f.push_back((int32_t)dff.size());
+            for (int32_t r = c0; r < c1; r++) lf[r] = lev;
+            frec.push_back(Rec{lev, 1, (int32_t)frec.size(), {c0, c1, off, -1, 4, 0, 0, 0}});
+            i = c1;
+            continue;
+        }
+        const int64_t b = P.lrow_ptr[i], e = P.lrow_ptr[i + 1];
+        int32_t lev = 0;
+        for (int64_t p = b; p < e; p++) lev = std::max(lev, lf[P.lrow_col[p]] + 1);
+        lf[i] = lev;
+        int32_t cb = (int32_t)dff.size(), ce = cb;
+        if (e - b > chunk) {
+            add_chunks(dff, b, e);
+            ce = (int32_t)dff.size();
+            chunk_recs(false, dff, cb, lf, P.lrow_col, i, frec);
+        }
+        frec.push_back(Rec{lev, 1, (int32_t)frec.size(), {i, cb, ce, -1, 0, 0, 0, 0}});
+        i++;
+    }
     for (int32_t i = t0; i < n; i++) {
-        // entries of row i in columns < t0 form a prefix (columns ascend)
+        // entries of tail row i in columns < t0 form a prefix (columns ascend)
         const int64_t b = P.lrow_ptr[i];
         int64_t e = b;
         while (e < P.lrow_ptr[i + 1] && P.lrow_col[e] < t0) e++;
         const int32_t cb = (int32_t)dff.size();
-        for (int64_t p = b; p < e; p += chunk) dff.push_back(SolveChunk{p, std::min(e, p + chunk)});
+        add_chunks(dff, b, e);
         tcb[i - t0] = cb;
         tce[i - t0] = (int32_t)dff.size();
-        if (tce[i - t0] > cb) fkeep.push_back(SolveRow{i, cb, tce[i - t0], 1});   // chunks only
+        chunk_recs(false, dff, cb, lf, P.lrow_col, i, frec);
     }
-    for (const SolveRow &r : bitems)
-        if (r.row < t0) bkeep.push_back(r);
-    std::vector<Rec> frec, brec;
-    build(false, lf, fkeep, dff, P.lrow_col, frec);
-    build(true, lb, bkeep, dfb, P.urow_col, brec);
+    finish(frec);
+    // ---- backward (U), rows descending; the tail is solved before
+    std::vector<int32_t> lb((size_t)n, -1);
+    std::vector<Rec> brec;
+    for (int32_t i = t0 - 1; i >= 0;) {
+        if (bof[i] >= 0) {
+            const int32_t c0 = bl[bof[i]].first, c1 = bl[bof[i]].second;
+            int32_t lev = 0;
+            const int32_t off = (int32_t)snx_b.size();
+            for (int32_t r = c0; r < c1; r++) {
+                // U row r's entries after the block: all but the first c1 - 1 - r
+                const int64_t b = P.urow_ptr[r] + (c1 - 1 - r), e = P.urow_ptr[r + 1];
+                for (int64_t p = b; p < e; p++) lev = std::max(lev, lb[P.urow_col[p]] + 1);
+                const int32_t cb = (int32_t)dfb.size();
+                snx_b.push_back(cb);
+                add_chunks(dfb, b, e);
+                chunk_recs(true, dfb, cb, lb, P.urow_col, r, brec);
+            }
+            snx_b.push_back((int32_t)dfb.size());
+            for (int32_t r = c0; r < c1; r++) lb[r] = lev;
+            brec.push_back(Rec{lev, 1, (int32_t)brec.size(), {c0, c1, off, -1, 1 | 4, 0, 0, 0}});
+            i = c0 - 1;
+            continue;
+        }
+        const int64_t b = P.urow_ptr[i], e = P.urow_ptr[i + 1];
+        int32_t lev = 0;
+        for (int64_t p = b; p < e; p++) lev = std::max(lev, lb[P.urow_col[p]] + 1);
+        lb[i] = lev;
+        int32_t cb = (int32_t)dfb.size(), ce = cb;
+        if (e - b > chunk) {
+            add_chunks(dfb, b, e);
+            ce = (int32_t)dfb.size();
+            chunk_recs(true, dfb, cb, lb, P.urow_col, i, brec);
+        }
+        brec.push_back(Rec{lev, 1, (int32_t)brec.size(), {i, cb, ce, -1, 1, 0, 0, 0}});
+        i--;
+    }
+    finish(brec);
     out.clear();
-    for (const Rec &r : frec)
-        if (!(r.type == 1 && r.item[0] >= t0)) out.insert(out.end(), r.item.begin(), r.item.end());
+    for (const Rec &r : frec) out.insert(out.end(), r.item.begin(), r.item.end());
     nfwd = (int32_t)(out.size() / 8);
     for (const Rec &r : brec) out.insert(out.end(), r.item.begin(), r.item.end());
 }
 
-// Solve levels: forward lf(i) = 1 + max lf(j) over L(i,j) != 0 (0 if none);
-// backward lb(i) = 1 + max lb(k) over U(i,k) != 0, k > i (0 if none).
 // Start of the largest trailing block [t0, n), n - t0 <= tmax, in which every
 // entry of L+U is present (n: none).
 int32_t dense_trailing_block(const HostPlan &P, int32_t tmax) {
@@ -641,6 +747,8 @@ void factor_tail(HostPlan &P, const glu_options &opt) {
     }
 }
 
+// Solve levels: forward lf(i) = 1 + max lf(j) over L(i,j) != 0 (0 if none);
+// backward lb(i) = 1 + max lb(k) over U(i,k) != 0, k > i (0 if none).
 void solve_levels(HostPlan &P, const glu_options &opt) {
     const int32_t n = P.n;
     std::vector<int32_t> lf((size_t)n, 0), lb((size_t)n, 0);
@@ -700,15 +808,16 @@ void solve_levels(HostPlan &P, const glu_options &opt) {
         const int32_t best = dense_trailing_block(P, TAIL_MAX);
         if (n - best >= TAIL_MIN) P.tail_t0 = best;
     }
-    build_df(P, lf, lb, SOLVE_CHUNK, P.tail_t0, P.fwd_items, P.fwd_chunks, P.bwd_items, P.bwd_chunks, P.df_items,
-             P.df_fchunks, P.df_bchunks, P.tail_cb, P.tail_ce, P.df_nfwd);
+    build_df(P, SOLVE_CHUNK, P.tail_t0, opt.solve_blocks != 0, P.df_items, P.df_fchunks, P.df_bchunks, P.tail_cb,
+             P.tail_ce, P.df_nfwd, P.df_snx_f, P.df_snx_b);
     items(P.fwd_ptr, P.fwd_rows, P.lrow_ptr, SOLVE_CHUNK_B, P.bfwd_items, P.bfwd_chunks, P.bfwd_chunk_ptr);
     items(P.bwd_ptr, P.bwd_rows, P.urow_ptr, SOLVE_CHUNK_B, P.bbwd_items, P.bbwd_chunks, P.bbwd_chunk_ptr);
     // batched: the tail's values for 32 sets sit in shared memory, so at most
     // TAIL_MAX_B rows of the dense block (a trailing part of it is dense too)
     P.btail_t0 = (P.tail_t0 < n) ? std::max<int32_t>(P.tail_t0, n - TAIL_MAX_B) : n;
-    build_df(P, lf, lb, SOLVE_CHUNK_B, P.btail_t0, P.bfwd_items, P.bfwd_chunks, P.bbwd_items, P.bbwd_chunks,
-             P.df_items_b, P.bdf_fchunks, P.bdf_bchunks, P.btail_cb, P.btail_ce, P.bdf_nfwd);
+    std::vector<int32_t> snx_f_b, snx_b_b;   // (no blocks in the batched solve)
+    build_df(P, SOLVE_CHUNK_B, P.btail_t0, false, P.df_items_b, P.bdf_fchunks, P.bdf_bchunks, P.btail_cb, P.btail_ce,
+             P.bdf_nfwd, snx_f_b, snx_b_b);
 }
 
 }  // namespace

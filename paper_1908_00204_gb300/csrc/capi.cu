@@ -50,6 +50,7 @@ struct glu_handle {
     int64_t *d_lu_colptr = nullptr;
     SolveChunk *d_df_fchunks = nullptr, *d_df_bchunks = nullptr;
     int32_t *d_tail_cb = nullptr, *d_tail_ce = nullptr;
+    int32_t *d_snx_f = nullptr, *d_snx_b = nullptr;   // dense diagonal blocks of the solve
     int32_t *d_flags = nullptr;
     int64_t n_flags = 0;
     unsigned *d_ticket = nullptr;
@@ -303,6 +304,8 @@ int enqueue_df(glu_handle *h, const SolveArgs<T> &a, T *y, T *z, T *partial, int
     d.abort = h->d_abort;
     d.err = h->d_serr;
     d.spin_limit_cycles = h->spin_cycles;
+    d.fsnx = h->d_snx_f;
+    d.bsnx = h->d_snx_b;
     const int32_t nall = (int32_t)(P.df_items.size() / 8);
     d.items = h->d_df_items;
     d.nitems = P.df_nfwd;
@@ -514,6 +517,7 @@ int upload_plan(glu_handle *h) {
            o_flags = c.take<int32_t>(2 * (size_t)n + P.df_fchunks.size() + P.df_bchunks.size()),
            o_dffc = c.take<SolveChunk>(P.df_fchunks.size()), o_dfbc = c.take<SolveChunk>(P.df_bchunks.size()),
            o_tcb = c.take<int32_t>(P.tail_cb.size()), o_tce = c.take<int32_t>(P.tail_ce.size()),
+           o_snf = c.take<int32_t>(P.df_snx_f.size()), o_snb = c.take<int32_t>(P.df_snx_b.size()),
            o_ticket = c.take<unsigned>(1), o_abort = c.take<unsigned>(1), o_serr = c.take<unsigned long long>(1),
            o_acp = c.take<int64_t>(n + 1), o_acc = c.take<int32_t>(P.acsr_col.size()),
            o_acs = c.take<int64_t>(P.acsr_src.size()), o_acv = c.take<double>(P.acsr_src.size()),
@@ -555,6 +559,8 @@ int upload_plan(glu_handle *h) {
     h->d_df_bchunks = at<SolveChunk>(A, o_dfbc);
     h->d_tail_cb = at<int32_t>(A, o_tcb);
     h->d_tail_ce = at<int32_t>(A, o_tce);
+    h->d_snx_f = at<int32_t>(A, o_snf);
+    h->d_snx_b = at<int32_t>(A, o_snb);
     h->d_ticket = at<unsigned>(A, o_ticket);
     h->d_abort = at<unsigned>(A, o_abort);
     h->d_serr = at<unsigned long long>(A, o_serr);
@@ -599,6 +605,8 @@ int upload_plan(glu_handle *h) {
     CK(upload(h->d_df_fchunks, P.df_fchunks));
     CK(upload(h->d_df_bchunks, P.df_bchunks));
     CK(upload(h->d_tail_cb, P.tail_cb));
+    CK(upload(h->d_snx_f, P.df_snx_f));
+    CK(upload(h->d_snx_b, P.df_snx_b));
     CK(upload(h->d_tail_ce, P.tail_ce));
     CK(upload(h->d_acsr_ptr, P.acsr_ptr));
     CK(upload(h->d_acsr_col, P.acsr_col));
@@ -667,6 +675,7 @@ void glu_default_options(glu_options *o) {
     o->fault_row = -1;
     o->solve_tail = 1;
     o->factor_tail = 1;
+    o->solve_blocks = 1;
 }
 
 int glu_analyze_opts(int32_t n, const int32_t *colptr, const int32_t *rowidx, const int32_t *perm,
@@ -740,10 +749,20 @@ int glu_analyze_opts(int32_t n, const int32_t *colptr, const int32_t *rowidx, co
         }
     }
     if (const char *dump = std::getenv("GLU_DUMP_DF")) {
-        // dataflow solve items (8 int32 each), then the forward item count
+        // the dataflow solve schedule as int64 words: counts (items, forward
+        // items, forward chunks, backward chunks, block tables f / b, tail
+        // start), then items (8 each), chunks (p0, p1), block tables
         if (FILE *fp = std::fopen(dump, "wb")) {
             const HostPlan &P = h->P;
-            std::fwrite(P.df_items.data(), sizeof(int32_t), P.df_items.size(), fp);
+            std::vector<int64_t> w = {(int64_t)P.df_items.size() / 8, P.df_nfwd, (int64_t)P.df_fchunks.size(),
+                                      (int64_t)P.df_bchunks.size(), (int64_t)P.df_snx_f.size(),
+                                      (int64_t)P.df_snx_b.size(), P.tail_t0};
+            for (int32_t v : P.df_items) w.push_back(v);
+            for (const SolveChunk &c : P.df_fchunks) { w.push_back(c.p0); w.push_back(c.p1); }
+            for (const SolveChunk &c : P.df_bchunks) { w.push_back(c.p0); w.push_back(c.p1); }
+            for (int32_t v : P.df_snx_f) w.push_back(v);
+            for (int32_t v : P.df_snx_b) w.push_back(v);
+            std::fwrite(w.data(), sizeof(int64_t), w.size(), fp);
             std::fclose(fp);
         }
     }
@@ -1331,6 +1350,7 @@ int enqueue_solve_b(glu_handle *h, const T *lu, const double *in, double *out, i
     d.abort = h->d_abort;
     d.err = h->d_serr;
     d.spin_limit_cycles = h->spin_cycles;
+    d.fsnx = d.bsnx = nullptr;
     TailArgs ta{P.btail_t0, h->d_btail_cb, h->d_btail_ce, d.bready, d.epoch};
     CKL(4 + (P.btail_t0 < n), launch_solve_b<T>(sa, d, P.bdf_nfwd, h->d_lu_colptr, ta, in, out, y, z, h->d_perm, nrhs, S,
                                                 h->num_sms, st));

@@ -114,7 +114,7 @@ struct SolveArgs {
 
 // Dataflow solve: one work item per row or long-row chunk, in topological
 // order (forward items, then backward items).
-enum : int32_t { DF_BACKWARD = 1, DF_CHUNK = 2 };
+enum : int32_t { DF_BACKWARD = 1, DF_CHUNK = 2, DF_BLOCK = 4 };
 struct DFItem {
     int32_t row;
     int32_t cb;      // row item: its chunks cb..ce-1 (none if equal)
@@ -136,6 +136,7 @@ struct DFSolveArgs {
     unsigned *abort;
     unsigned long long *err;
     long long spin_limit_cycles;
+    const int32_t *fsnx, *bsnx;   // dense diagonal blocks: per row, its first outside chunk
 };
 
 // launchers (kernels_factor.cu)

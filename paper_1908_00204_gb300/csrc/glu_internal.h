@@ -79,6 +79,7 @@ constexpr int64_t SOLVE_CHUNK_B = 32;   // batched: lanes over the sets, entries
 constexpr int32_t TAIL_MIN = 32, TAIL_MAX = 1024;   // dense-tail solve size range
 constexpr int32_t TAIL_MAX_B = 768;                 // batched: tail rows x 32 sets in shared memory
 constexpr int32_t FTAIL_MIN = 64, FTAIL_MAX = 3200;  // dense-tail factorization size range
+constexpr int32_t SN_MIN = 4, SN_MAX = 128;          // dense diagonal blocks of the dataflow solve
 
 // Everything glu_analyze computes on the host.
 struct HostPlan {
@@ -128,6 +129,9 @@ struct HostPlan {
     // forward chunks tail_cb[i]..tail_ce[i]-1
     int32_t tail_t0 = 0;
     std::vector<int32_t> tail_cb, tail_ce;
+    // dense diagonal blocks of the dataflow solve: per block, the first chunk
+    // of each row's entries outside the block, then the end
+    std::vector<int32_t> df_snx_f, df_snx_b;
     // the same for the batched solve, with shorter chunks
     std::vector<SolveRow> bfwd_items, bbwd_items;
     std::vector<SolveChunk> bfwd_chunks, bbwd_chunks;

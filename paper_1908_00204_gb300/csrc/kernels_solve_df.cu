@@ -61,6 +61,212 @@ __device__ __forceinline__ bool wait_flag(const int32_t *flag, int epoch, const 
     }
 }
 
+__device__ __forceinline__ int ld_relaxed(const int32_t *p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+// Poll *flag (relaxed reads) until it holds epoch; false once the wait gave
+// up.  The caller fences afterwards.
+__device__ __forceinline__ bool spin_flag(const int32_t *flag, int epoch, const DFSolveArgs &a) {
+    const long long t0 = clock64();
+    int spins = 0;
+    while (true) {
+        __nanosleep(32);
+        if (ld_relaxed(flag) == epoch) return true;
+        if ((++spins & 63) == 0) {
+            if (*(volatile const unsigned *)a.abort) return false;
+            if (clock64() - t0 > a.spin_limit_cycles) {
+                atomicOr(a.abort, 1u);
+                atomicMin(a.err, ((unsigned long long)0xffffffu << 8) | DEVERR_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+// Rows without chunks and chunks hold at most SOLVE_CHUNK = 4 x 32 entries.
+constexpr int DF_PER_LANE = 4;
+
+// The entries p0..p1-1 of a row of L or U, up to DF_PER_LANE per lane: their
+// columns and values do not depend on other rows, so they are loaded before
+// any wait.  j = -1 marks an empty slot.
+template <typename T>
+__device__ __forceinline__ void load_entries(const SolveArgs<T> &s, const int32_t *col, const int64_t *pos,
+                                             int64_t p0, int64_t p1, int lane, int32_t (&j)[DF_PER_LANE],
+                                             T (&l)[DF_PER_LANE]) {
+#pragma unroll
+    for (int k = 0; k < DF_PER_LANE; k++) {
+        const int64_t p = p0 + lane + 32 * k;
+        j[k] = p < p1 ? col[p] : -1;
+    }
+#pragma unroll
+    for (int k = 0; k < DF_PER_LANE; k++) {
+        const int64_t p = p0 + lane + 32 * k;
+        l[k] = p < p1 ? s.lu[pos[p]] : (T)0;
+    }
+}
+
+// Wait for the ready flags of a lane's columns: all first reads go out at
+// once, then any flag not yet set is polled; one fence after the relaxed
+// reads completes the acquire, so the writers' values are visible.
+__device__ __forceinline__ void wait_cols(const int32_t *ready, const int32_t (&j)[DF_PER_LANE], int epoch,
+                                          const DFSolveArgs &a) {
+    int v[DF_PER_LANE];
+#pragma unroll
+    for (int k = 0; k < DF_PER_LANE; k++) v[k] = j[k] >= 0 ? ld_relaxed(ready + j[k]) : epoch;
+#pragma unroll
+    for (int k = 0; k < DF_PER_LANE; k++)
+        if (v[k] != epoch) spin_flag(ready + j[k], epoch, a);
+    fence_acq_rel();
+}
+
+template <typename T>
+__device__ __forceinline__ T dot_entries(const int32_t (&j)[DF_PER_LANE], const T (&l)[DF_PER_LANE], const T *yr) {
+    T acc = (T)0;
+#pragma unroll
+    for (int k = 0; k < DF_PER_LANE; k++)
+        if (j[k] >= 0) acc += l[k] * ld_cg(yr + j[k]);
+    return warp_sum_df(acc);
+}
+
+// A dense diagonal block [c0, c1) of at most SN_MAX rows, one warp: lane l
+// keeps rows l, l + 32, ... in registers.  After the partial sums of the
+// rows' entries outside the block (chunk items) are ready, the block's own
+// triangle is swept a column at a time: the owner of row jj holds its final
+// value, a shuffle broadcasts it, every other row of the block subtracts
+// L(i, jj) times it (forward), or, backward, z(jj) = y(jj) / U(jj, jj) and the
+// rows above subtract U(i, jj) z(jj).  The block being dense, column c0+jj's
+// entries in rows c0..c1-1 are contiguous in the CSC values, at
+// diag_pos[c0+jj] - jj + i; the coefficients of BLK_PF columns are loaded
+// together, ahead of their steps.
+constexpr int BLK_K = SN_MAX / 32;   // rows per lane
+#ifndef GLU_BLK_PF
+#define GLU_BLK_PF 4
+#endif
+constexpr int BLK_PF = GLU_BLK_PF;   // columns whose coefficients load together
+
+template <typename T>
+__device__ __forceinline__ void block_item(const SolveArgs<T> &s, const DFSolveArgs &a, const DFItem &it, T *y, T *z,
+                                           int32_t nrhs, int lane) {
+    const bool bwd = it.flags & DF_BACKWARD;
+    const int32_t c0 = it.row, ns = it.cb - it.row;
+    const int32_t *snx = (bwd ? a.bsnx : a.fsnx) + it.ce;
+    const int32_t *chunk_ready = bwd ? a.bchunk_ready : a.fchunk_ready;
+    const T *partial = static_cast<const T *>(bwd ? a.bpartial_v : a.fpartial_v);
+    int32_t *ready = bwd ? a.bready : a.fready;
+    const int n = s.n;
+    for (int32_t c = snx[0] + lane; c < snx[ns]; c += 32)
+        if (ld_relaxed(chunk_ready + c) != a.epoch) spin_flag(chunk_ready + c, a.epoch, a);
+    fence_acq_rel();
+    __syncwarp();
+    int32_t cb[BLK_K], ce[BLK_K];
+    int64_t bj[BLK_K];   // lane l, slot k: diag_pos of column c0 + 32k + l, minus its offset
+    T d[BLK_K];
+#pragma unroll
+    for (int k = 0; k < BLK_K; k++) {
+        const int32_t ii = k * 32 + lane;
+        cb[k] = ce[k] = 0;
+        bj[k] = 0;
+        d[k] = (T)1;
+        if (ii < ns) {
+            cb[k] = snx[ii];
+            ce[k] = snx[ii + 1];
+            const int64_t dp = s.diag_pos[c0 + ii];
+            bj[k] = dp - ii;
+            if (bwd) d[k] = s.lu[dp];
+        }
+    }
+    for (int32_t r = 0; r < nrhs; r++) {
+        T v[BLK_K];
+#pragma unroll
+        for (int k = 0; k < BLK_K; k++) {
+            const int32_t ii = k * 32 + lane;
+            T x = (T)0;
+            if (ii < ns) {
+                x = ld_cg(y + (int64_t)r * n + c0 + ii);
+                for (int32_t c = cb[k]; c < ce[k]; c++) x -= ld_cg(partial + (int64_t)c * nrhs + r);
+            }
+            v[k] = x;
+        }
+        if (!bwd) {
+#pragma unroll
+            for (int kj = 0; kj < BLK_K; kj++) {
+                for (int32_t tg = 0; tg < 32; tg += BLK_PF) {
+                    const int32_t jj0 = kj * 32 + tg;
+                    if (jj0 >= ns) break;
+                    T cf[BLK_PF][BLK_K];
+#pragma unroll
+                    for (int u = 0; u < BLK_PF; u++) {
+                        const int32_t jj = jj0 + u;
+                        const int64_t base = __shfl_sync(0xffffffffu, bj[kj], tg + u);
+#pragma unroll
+                        for (int kk = 0; kk < BLK_K; kk++) {
+                            const int32_t ii = kk * 32 + lane;
+                            cf[u][kk] = (kk >= kj && ii > jj && ii < ns) ? s.lu[base + ii] : (T)0;
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < BLK_PF; u++) {
+                        const int32_t jj = jj0 + u;
+                        const T vj = __shfl_sync(0xffffffffu, v[kj], tg + u);
+                        if (jj < ns) {
+#pragma unroll
+                            for (int kk = 0; kk < BLK_K; kk++)
+                                if (kk >= kj && kk * 32 + lane > jj) v[kk] = v[kk] - cf[u][kk] * vj;
+                        }
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int kj = BLK_K - 1; kj >= 0; kj--) {
+                for (int32_t tg = 32 - BLK_PF; tg >= 0; tg -= BLK_PF) {
+                    if (kj * 32 + tg >= ns) continue;
+                    T cf[BLK_PF][BLK_K];
+#pragma unroll
+                    for (int u = 0; u < BLK_PF; u++) {
+                        const int32_t t = tg + BLK_PF - 1 - u;   // columns descending
+                        const int32_t jj = kj * 32 + t;
+                        const int64_t base = __shfl_sync(0xffffffffu, bj[kj], t);
+#pragma unroll
+                        for (int kk = 0; kk < BLK_K; kk++) {
+                            const int32_t ii = kk * 32 + lane;
+                            cf[u][kk] = (kk <= kj && jj < ns && ii < jj) ? s.lu[base + ii] : (T)0;
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < BLK_PF; u++) {
+                        const int32_t t = tg + BLK_PF - 1 - u;
+                        const int32_t jj = kj * 32 + t;
+                        const T zo = v[kj] / d[kj];
+                        const T zj = __shfl_sync(0xffffffffu, zo, t);
+                        if (jj < ns) {
+                            if (lane == t) v[kj] = zj;
+#pragma unroll
+                            for (int kk = 0; kk < BLK_K; kk++)
+                                if (kk <= kj && kk * 32 + lane < jj) v[kk] = v[kk] - cf[u][kk] * zj;
+                        }
+                    }
+                }
+            }
+        }
+        T *out = (bwd ? z : y) + (int64_t)r * n + c0;
+#pragma unroll
+        for (int k = 0; k < BLK_K; k++)
+            if (k * 32 + lane < ns) out[k * 32 + lane] = v[k];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < BLK_K; k++) {
+        const int32_t i = c0 + k * 32 + lane;
+        if (k * 32 + lane < ns && i != a.fault_row) st_release(ready + i, a.epoch);
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(128) k_solve_df(const SolveArgs<T> s, const DFSolveArgs a, T *y, T *z, int32_t nrhs) {
     const int lane = threadIdx.x & 31;
@@ -76,19 +282,21 @@ __global__ void __launch_bounds__(128) k_solve_df(const SolveArgs<T> s, const DF
         const int64_t *pos = bwd ? s.urow_pos : s.lrow_pos;
         const int32_t *col = bwd ? s.urow_col : s.lrow_col;
         int32_t *ready = bwd ? a.bready : a.fready;
+        const T *src = bwd ? z : y;   // values the dot products read
+        if (it.flags & DF_BLOCK) {
+            block_item<T>(s, a, it, y, z, nrhs, lane);
+            continue;
+        }
+        int32_t j[DF_PER_LANE];
+        T l[DF_PER_LANE];
         if (it.flags & DF_CHUNK) {
             // partial dot product of entries p0..p1-1 of a long row
             const SolveChunk ch = (bwd ? a.bchunks : a.fchunks)[it.chunk];
             T *partial = static_cast<T *>(bwd ? a.bpartial_v : a.fpartial_v);
+            load_entries<T>(s, col, pos, ch.p0, ch.p1, lane, j, l);
+            wait_cols(ready, j, a.epoch, a);
             for (int32_t r = 0; r < nrhs; r++) {
-                const T *yr = (bwd ? z : y) + (int64_t)r * n;
-                T acc = (T)0;
-                for (int64_t p = ch.p0 + lane; p < ch.p1; p += 32) {
-                    const int32_t j = col[p];
-                    if (r == 0) wait_flag(ready + j, a.epoch, a);
-                    acc += s.lu[pos[p]] * ld_cg(yr + j);
-                }
-                acc = warp_sum_df(acc);
+                const T acc = dot_entries<T>(j, l, src + (int64_t)r * n);
                 if (lane == 0) partial[(int64_t)it.chunk * nrhs + r] = acc;
             }
             __syncwarp();
@@ -99,30 +307,37 @@ __global__ void __launch_bounds__(128) k_solve_df(const SolveArgs<T> s, const DF
         // the backward row needs the forward result of its own row
         if (bwd && lane == 0) wait_flag(a.fready + i, a.epoch, a);
         __syncwarp();
-        const T d = bwd ? s.lu[s.diag_pos[i]] : (T)1;
-        const T *partial = static_cast<const T *>(bwd ? a.bpartial_v : a.fpartial_v);
-        const int32_t *chunk_ready = bwd ? a.bchunk_ready : a.fchunk_ready;
-        if (it.ce > it.cb && lane == 0)
-            for (int32_t c = it.cb; c < it.ce; c++) wait_flag(chunk_ready + c, a.epoch, a);
-        const int64_t b = rptr[i], e = rptr[i + 1];
-        for (int32_t r = 0; r < nrhs; r++) {
-            const T *yr = (bwd ? z : y) + (int64_t)r * n;   // values the row reads
-            T *out = (bwd ? z : y) + (int64_t)r * n;
-            T acc = (T)0;
-            if (it.ce > it.cb) {
-                if (lane == 0)
-                    for (int32_t c = it.cb; c < it.ce; c++) acc += ld_cg(partial + (int64_t)c * nrhs + r);
-            } else {
-                for (int64_t p = b + lane; p < e; p += 32) {
-                    const int32_t j = col[p];
-                    if (r == 0) wait_flag(ready + j, a.epoch, a);
-                    acc += s.lu[pos[p]] * ld_cg(yr + j);
-                }
-                acc = warp_sum_df(acc);
-            }
+        T d = (T)1, v0 = (T)0;
+        if (lane == 0) {
+            if (bwd) d = s.lu[s.diag_pos[i]];
+            v0 = ld_cg(y + i);    // c(i) forward, y(i) backward, first side
+        }
+        if (it.ce > it.cb) {
+            // a long row: the sum of its chunks' partials, in chunk order
+            const T *partial = static_cast<const T *>(bwd ? a.bpartial_v : a.fpartial_v);
+            const int32_t *chunk_ready = bwd ? a.bchunk_ready : a.fchunk_ready;
+            for (int32_t c = it.cb + lane; c < it.ce; c += 32)
+                if (ld_relaxed(chunk_ready + c) != a.epoch) spin_flag(chunk_ready + c, a.epoch, a);
+            fence_acq_rel();
+            __syncwarp();
             if (lane == 0) {
-                const T v = ld_cg(y + (int64_t)r * n + i);   // c(i) forward, y(i) backward
-                out[i] = bwd ? (v - acc) / d : v - acc;
+                for (int32_t r = 0; r < nrhs; r++) {
+                    T acc = (T)0;
+                    for (int32_t c = it.cb; c < it.ce; c++) acc += ld_cg(partial + (int64_t)c * nrhs + r);
+                    const T v = r == 0 ? v0 : ld_cg(y + (int64_t)r * n + i);
+                    (bwd ? z : y)[(int64_t)r * n + i] = bwd ? (v - acc) / d : v - acc;
+                }
+            }
+        } else {
+            const int64_t b = rptr[i], e = rptr[i + 1];
+            load_entries<T>(s, col, pos, b, e, lane, j, l);
+            wait_cols(ready, j, a.epoch, a);
+            for (int32_t r = 0; r < nrhs; r++) {
+                const T acc = dot_entries<T>(j, l, src + (int64_t)r * n);
+                if (lane == 0) {
+                    const T v = r == 0 ? v0 : ld_cg(y + (int64_t)r * n + i);
+                    (bwd ? z : y)[(int64_t)r * n + i] = bwd ? (v - acc) / d : v - acc;
+                }
             }
         }
         __syncwarp();
@@ -130,49 +345,98 @@ __global__ void __launch_bounds__(128) k_solve_df(const SolveArgs<T> s, const DF
     }
 }
 
-// The dense tail, one block.  Tail column j's rows below (and, in U, above
-// from t0) are contiguous in the CSC values, so a column sweep reads them
-// coalesced; the tail's values stay in shared memory; one barrier per column
-// forward, two backward (the pivot division is done once).
+// The dense tail, one block, one tail row per thread (at most 1024 rows),
+// its running value in a register.  Step jj of the forward sweep: the owner
+// of row jj publishes its final value in shared memory, one barrier, and
+// every row below subtracts L(i, jj) times it; the backward sweep does the
+// same with z(jj) = y(jj) / U(jj, jj) and the rows above.  The tail column
+// jj's entries are contiguous in the CSC values; each thread's coefficients
+// of the next TAIL_PF steps are loaded ahead into registers.
+constexpr int TAIL_PF = 8;
+
 template <typename T>
 __global__ void __launch_bounds__(1024) k_solve_tail(const SolveArgs<T> s, const int64_t *__restrict__ lu_colptr,
                                                      const TailArgs ta, const T *__restrict__ fpartial, T *y, T *z,
                                                      int32_t nrhs) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int32_t n = s.n, t0 = ta.t0, NT = n - t0;
-    T *yt = reinterpret_cast<T *>(smem_raw);
-    T *zt = yt + NT;
+    int64_t *lcol = reinterpret_cast<int64_t *>(smem_raw);   // L(t0+ii, t0+jj) at lcol[jj] + ii
+    int64_t *ucol = lcol + NT;                                // U(t0+ii, t0+jj) at ucol[jj] + ii
+    T *bc = reinterpret_cast<T *>(ucol + NT);                 // published values
+    const int32_t ii = threadIdx.x;
+    const bool own = ii < NT;
+    for (int32_t q = ii; q < NT; q += blockDim.x) {
+        lcol[q] = s.diag_pos[t0 + q] - q;
+        ucol[q] = lu_colptr[t0 + q + 1] - NT;
+    }
+    __syncthreads();
+    const T d = own ? s.lu[lcol[ii] + ii] : (T)1;
     for (int32_t r = 0; r < nrhs; r++) {
-        const T *yr = y + (int64_t)r * n;
-        T *zr = z + (int64_t)r * n;
-        for (int32_t ii = threadIdx.x; ii < NT; ii += blockDim.x) {
-            T v = __ldcg(yr + t0 + ii);
+        T v = (T)0;
+        if (own) {
+            v = __ldcg(y + (int64_t)r * n + t0 + ii);
             for (int32_t c = ta.cb[ii]; c < ta.ce[ii]; c++) v -= __ldcg(fpartial + (int64_t)c * nrhs + r);
-            yt[ii] = v;
+        }
+        // forward
+        T cur[TAIL_PF], nxt[TAIL_PF];
+#pragma unroll
+        for (int u = 0; u < TAIL_PF; u++) {
+            const int32_t jj = u;
+            cur[u] = (own && ii > jj && jj < NT) ? s.lu[lcol[jj] + ii] : (T)0;
+        }
+        for (int32_t jb = 0; jb < NT; jb += TAIL_PF) {
+#pragma unroll
+            for (int u = 0; u < TAIL_PF; u++) {
+                const int32_t jj = jb + TAIL_PF + u;
+                nxt[u] = (own && ii > jj && jj < NT) ? s.lu[lcol[jj] + ii] : (T)0;
+            }
+#pragma unroll
+            for (int u = 0; u < TAIL_PF; u++) {
+                const int32_t jj = jb + u;
+                if (jj < NT) {
+                    if (ii == jj) bc[jj] = v;
+                    __syncthreads();
+                    if (own && ii > jj) v = v - cur[u] * bc[jj];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < TAIL_PF; u++) cur[u] = nxt[u];
         }
         __syncthreads();
-        // forward: y(i) -= L(i,j) y(j) for the rows i > j of the tail
-        for (int32_t jj = 0; jj < NT; jj++) {
-            const int64_t lb = s.diag_pos[t0 + jj] + 1 - (jj + 1);   // L(t0+ii, t0+jj) at lb + ii
-            const T vj = yt[jj];
-            for (int32_t ii = jj + 1 + threadIdx.x; ii < NT; ii += blockDim.x)
-                yt[ii] = yt[ii] - s.lu[lb + ii] * vj;
-            __syncthreads();
+        // backward (the published slots are reused: every forward read is
+        // behind the barrier above)
+        T *zr = z + (int64_t)r * n;
+        const int32_t top = NT - 1;
+#pragma unroll
+        for (int u = 0; u < TAIL_PF; u++) {
+            const int32_t jj = top - u;
+            cur[u] = (own && ii < jj && jj >= 0) ? s.lu[ucol[jj] + ii] : (T)0;
         }
-        // backward: z(j) = y(j) / U(j,j); y(i) -= U(i,j) z(j) for the rows t0 <= i < j
-        for (int32_t jj = NT - 1; jj >= 0; jj--) {
-            const int32_t j = t0 + jj;
-            if (threadIdx.x == 0) zt[jj] = yt[jj] / s.lu[s.diag_pos[j]];
-            __syncthreads();
-            const int64_t ub = lu_colptr[j + 1] - NT;                 // U(t0+ii, j) at ub + ii
-            const T zj = zt[jj];
-            for (int32_t ii = threadIdx.x; ii < jj; ii += blockDim.x) yt[ii] = yt[ii] - s.lu[ub + ii] * zj;
-            __syncthreads();
+        for (int32_t jb = top; jb >= 0; jb -= TAIL_PF) {
+#pragma unroll
+            for (int u = 0; u < TAIL_PF; u++) {
+                const int32_t jj = jb - TAIL_PF - u;
+                nxt[u] = (own && ii < jj && jj >= 0) ? s.lu[ucol[jj] + ii] : (T)0;
+            }
+#pragma unroll
+            for (int u = 0; u < TAIL_PF; u++) {
+                const int32_t jj = jb - u;
+                if (jj >= 0) {
+                    if (ii == jj) {
+                        v = v / d;
+                        bc[jj] = v;
+                        zr[t0 + jj] = v;
+                    }
+                    __syncthreads();
+                    if (own && ii < jj) v = v - cur[u] * bc[jj];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < TAIL_PF; u++) cur[u] = nxt[u];
         }
-        for (int32_t ii = threadIdx.x; ii < NT; ii += blockDim.x) zr[t0 + ii] = zt[ii];
         __syncthreads();
     }
-    for (int32_t ii = threadIdx.x; ii < NT; ii += blockDim.x) ta.bready[t0 + ii] = ta.epoch;
+    if (own) ta.bready[t0 + ii] = ta.epoch;
 }
 
 }  // namespace
@@ -182,7 +446,8 @@ cudaError_t launch_solve_tail(const SolveArgs<T> &s, const int64_t *lu_colptr, c
                               T *y, T *z, int32_t nrhs, cudaStream_t st) {
     const int32_t NT = s.n - t.t0;
     if (NT <= 0) return cudaSuccess;
-    const size_t smem = 2 * (size_t)NT * sizeof(T);
+    if (NT > 1024) return cudaErrorInvalidValue;
+    const size_t smem = 2 * (size_t)NT * sizeof(int64_t) + (size_t)NT * sizeof(T);
     k_solve_tail<T><<<1, 1024, smem, st>>>(s, lu_colptr, t, fpartial, y, z, nrhs);
     return cudaGetLastError();
 }

@@ -37,7 +37,8 @@ class glu_options(C.Structure):
                 ("piece_updates", C.c_int32), ("wide_threshold", C.c_int32), ("use_graph", C.c_int32),
                 ("verbose", C.c_int32), ("host_only", C.c_int32), ("solve_mode", C.c_int32),
                 ("spin_limit_us", C.c_int32), ("fault_row", C.c_int32), ("solve_tail", C.c_int32),
-                ("factor_tail", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("factor_tail", C.c_int32), ("solve_blocks", C.c_int32),
+                ("reserved", C.c_int32 * 2)]
 
 
 class glu_stats(C.Structure):

@@ -1,5 +1,6 @@
-"""Dataflow solve (with and without the one-block dense tail): the same
-results as the level-by-level solve up to rounding order, and a bounded wait
+"""Dataflow solve (with and without the one-block dense tail and the
+one-warp dense diagonal blocks): the same results as the level-by-level
+solve up to rounding order, and a bounded wait
 that runs out (a row flag that nothing sets) returns GLU_ERR_TIMEOUT with the
 context still usable.  No GPU fault is involved: the missing flag is
 a host-chosen test hook and every device wait has a time limit."""
@@ -31,8 +32,9 @@ def test_dataflow_equals_level_solve(glu, name, nrhs):
     v = m.values(9)
     b = synth.rhs(m.n, nrhs, 9)
     hs = {}
-    for key, opts in (("levels", dict(solve_mode=0)), ("df", dict(solve_mode=1, solve_tail=0)),
-                      ("df+tail", dict(solve_mode=1, solve_tail=1))):
+    for key, opts in (("levels", dict(solve_mode=0)), ("df", dict(solve_mode=1, solve_tail=0, solve_blocks=0)),
+                      ("df+tail", dict(solve_mode=1, solve_tail=1, solve_blocks=0)),
+                      ("df+blocks+tail", dict(solve_mode=1, solve_tail=1, solve_blocks=1))):
         h = glu.glu_analyze(m.n, m.colptr, m.rowidx, m.perm, glu.default_options(**opts))
         glu.glu_factor(h, torch.from_numpy(v).cuda())
         hs[key] = glu.glu_solve(h, torch.from_numpy(b).cuda()).cpu().numpy()
@@ -41,6 +43,7 @@ def test_dataflow_equals_level_solve(glu, name, nrhs):
             assert glu.glu_get_stats(h)["tail_rows"] >= 32
     assert np.array_equal(hs["levels"], hs["df"])          # same per-row summation order
     np.testing.assert_allclose(hs["df+tail"], hs["df"], rtol=1e-10, atol=1e-14)
+    np.testing.assert_allclose(hs["df+blocks+tail"], hs["df"], rtol=1e-10, atol=1e-14)
     for x in hs.values():
         assert backward_error(m.n, m.colptr, m.rowidx, v, b, x) <= BERR_TOL
 
