@@ -100,7 +100,12 @@ typedef struct glu_options {
     int32_t solve_blocks;     /* 1 (default): in the dataflow solve, dense diagonal blocks of
                                  4..128 rows are solved by one warp each (their rows'
                                  entries outside the block as parallel partial sums); 0: off */
-    int32_t reserved[2];
+    int32_t factor_blocks;    /* 1: supernodal factorization -- runs of up to 32 columns with a
+                                 dense diagonal block and equal structure below are factored
+                                 as dense panels and update their targets once per run
+                                 (levels of the contracted Algorithm 4 graph); 0 (default):
+                                 one level per Algorithm 4 level */
+    int32_t reserved[1];
 } glu_options;
 
 /* Analysis statistics (glu_get_stats). */

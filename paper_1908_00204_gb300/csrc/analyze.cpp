@@ -699,6 +699,158 @@ void build_df(const HostPlan &P, int64_t chunk, int32_t t0, bool blocks, std::ve
     for (const Rec &r : brec) out.insert(out.end(), r.item.begin(), r.item.end());
 }
 
+// ---------------------------------------------------------------------------
+// The supernodal schedule.  Supernodes: maximal runs of at most BSN_MAX
+// columns whose diagonal block is dense and whose columns have the same rows
+// below the run.  Block levels: longest paths of the dependency graph
+// (Algorithm 4) with each supernode contracted to one node.  Pairs: for each
+// supernode B, every column k past B with U(j, k) != 0 for some j in B; by
+// the fill theorem the rows of B present in column k form a suffix of B and
+// column k holds every row of R_B.
+void block_schedule(HostPlan &P) {
+    const int32_t n = P.n;
+    std::vector<int32_t> &c0v = P.sn_c0;
+    c0v.assign(1, 0);
+    auto below = [&](int32_t j) { return P.lu_colptr[j + 1] - P.diag_pos[j] - 1; };
+    for (int32_t i = 1; i <= n; i++) {
+        const int32_t c0 = c0v.back();
+        bool ext = i < n && i - c0 < BSN_MAX;
+        if (ext) {
+            // U part of column i holds rows c0..i-1 (they are its last i - c0 rows above the diagonal)
+            const int64_t ub = P.lu_colptr[i], ue = P.diag_pos[i];
+            ext = ue - ub >= i - c0 && (i == c0 || (P.lu_rowidx[ue - (i - c0)] == c0));
+            // column i-1 continues with row i right below its diagonal, then exactly the rows
+            // column i has below its diagonal
+            if (ext) ext = below(i - 1) == below(i) + 1 && P.lu_rowidx[P.diag_pos[i - 1] + 1] == i;
+            if (ext) {
+                const int32_t *a = P.lu_rowidx.data() + P.diag_pos[i - 1] + 2;
+                const int32_t *b = P.lu_rowidx.data() + P.diag_pos[i] + 1;
+                ext = std::equal(a, a + below(i), b);
+            }
+        }
+        if (!ext) c0v.push_back(i);
+    }
+    if (n == 0) c0v.assign(1, 0);
+    const int32_t nsn = (int32_t)c0v.size() - 1;
+    std::vector<int32_t> sof((size_t)n);
+    P.sn_r.assign((size_t)nsn, 0);
+    for (int32_t q = 0; q < nsn; q++) {
+        for (int32_t j = c0v[q]; j < c0v[q + 1]; j++) sof[j] = q;
+        P.sn_r[q] = (int32_t)below(c0v[q + 1] - 1);
+    }
+    // block levels
+    std::vector<int32_t> blev((size_t)nsn, 0);
+    int32_t nbl = nsn > 0 ? 1 : 0;
+    for (int32_t q = 0; q < nsn; q++) {
+        int32_t lv = 0;
+        for (int32_t j = c0v[q]; j < c0v[q + 1]; j++)
+            for (int64_t p = P.dep_ptr[j]; p < P.dep_ptr[j + 1]; p++) {
+                const int32_t d = P.dep_idx[p];
+                if (d < c0v[q]) lv = std::max(lv, blev[sof[d]] + 1);
+            }
+        blev[q] = lv;
+        nbl = std::max(nbl, lv + 1);
+    }
+    P.nblev = nbl;
+    // pairs, bucketed by level, each bucket sorted by (k, sn): scanning
+    // columns k ascending and their U rows ascending gives that order
+    std::vector<int64_t> lcount((size_t)nbl + 1, 0);
+    std::vector<int32_t> last_sn((size_t)nsn, -1);   // last column k that recorded a pair for sn
+    for (int32_t k = 0; k < n; k++)
+        for (int64_t p = P.lu_colptr[k]; p < P.diag_pos[k]; p++) {
+            const int32_t q = sof[P.lu_rowidx[p]];
+            if (c0v[q + 1] > k || last_sn[q] == k) continue;
+            last_sn[q] = k;
+            lcount[blev[q] + 1]++;
+        }
+    for (int32_t l = 0; l < nbl; l++) lcount[l + 1] += lcount[l];
+    P.bpairs.assign((size_t)lcount[nbl], BPair{});
+    {
+        std::vector<int64_t> f(lcount.begin(), lcount.end() - 1);
+        std::fill(last_sn.begin(), last_sn.end(), -1);
+        for (int32_t k = 0; k < n; k++)
+            for (int64_t p = P.lu_colptr[k]; p < P.diag_pos[k]; p++) {
+                const int32_t j = P.lu_rowidx[p];
+                const int32_t q = sof[j];
+                if (c0v[q + 1] > k || last_sn[q] == k) continue;
+                last_sn[q] = k;
+                BPair &bp = P.bpairs[f[blev[q]]++];
+                bp.sn = q;
+                bp.k = k;
+                bp.f = j - c0v[q];
+                bp.upos = p;
+            }
+    }
+    int64_t mb = 0;
+    for (BPair &bp : P.bpairs) {
+        bp.mb = mb;
+        mb += P.sn_r[bp.sn];
+    }
+    P.bmap_size = mb;
+    // per level: diagonal blocks, panel items, update tasks
+    P.bdiag.clear();
+    P.bdiag_ptr.assign((size_t)nbl + 1, 0);
+    P.bitems.clear();
+    P.bitem_ptr.assign((size_t)nbl + 1, 0);
+    P.bsegs.clear();
+    P.btasks.clear();
+    P.btask_ptr.assign((size_t)nbl + 1, 0);
+    std::vector<std::vector<int32_t>> by_level((size_t)nbl);
+    for (int32_t q = 0; q < nsn; q++) by_level[blev[q]].push_back(q);
+    std::vector<int32_t> krows;
+    for (int32_t l = 0; l < nbl; l++) {
+        for (int32_t q : by_level[l])
+            if (c0v[q + 1] - c0v[q] >= 2) P.bdiag.push_back(q);
+        P.bdiag_ptr[l + 1] = (int32_t)P.bdiag.size();
+        for (int32_t q : by_level[l])
+            for (int32_t t = 0; t < P.sn_r[q]; t += 32)
+                P.bitems.push_back(BItem{q, 0, t, std::min(P.sn_r[q], t + 32)});
+        for (int64_t p = lcount[l]; p < lcount[l + 1]; p++) {
+            const BPair &bp = P.bpairs[p];
+            if (c0v[bp.sn + 1] - c0v[bp.sn] - bp.f >= 2) P.bitems.push_back(BItem{bp.sn, 1, (int32_t)p, 0});
+        }
+        P.bitem_ptr[l + 1] = (int32_t)P.bitems.size();
+        // update tasks: the level's pairs grouped by target column; each
+        // BCHUNK-position chunk of the column touched by some R_B is a task,
+        // its segments the pairs' rows inside the chunk, in supernode order
+        int64_t g = lcount[l];
+        while (g < lcount[l + 1]) {
+            const int32_t k = P.bpairs[g].k;
+            int64_t ge = g;
+            while (ge < lcount[l + 1] && P.bpairs[ge].k == k) ge++;
+            const int64_t cb = P.lu_colptr[k], clen = P.lu_colptr[k + 1] - cb;
+            const int32_t *kr = P.lu_rowidx.data() + cb;
+            int64_t qlo = clen, qhi = 0;
+            for (int64_t p = g; p < ge; p++) {
+                const int32_t q = P.bpairs[p].sn;
+                const int32_t r = P.sn_r[q];
+                if (r == 0) continue;
+                const int32_t *R = P.lu_rowidx.data() + P.lu_colptr[c0v[q + 1]] - r;
+                qlo = std::min<int64_t>(qlo, std::lower_bound(kr, kr + clen, R[0]) - kr);
+                qhi = std::max<int64_t>(qhi, (std::lower_bound(kr, kr + clen, R[r - 1]) - kr) + 1);
+            }
+            for (int64_t c = (qlo / BCHUNK) * BCHUNK; c < qhi; c += BCHUNK) {
+                const int32_t rlo = kr[c];
+                const int32_t rhi = c + BCHUNK < clen ? kr[c + BCHUNK] : INT32_MAX;
+                BTask t{(int32_t)P.bsegs.size(), 0};
+                for (int64_t p = g; p < ge; p++) {
+                    const int32_t q = P.bpairs[p].sn;
+                    const int32_t r = P.sn_r[q];
+                    const int32_t *R = P.lu_rowidx.data() + P.lu_colptr[c0v[q + 1]] - r;
+                    const int32_t t0 = (int32_t)(std::lower_bound(R, R + r, rlo) - R);
+                    const int32_t t1 = (int32_t)(std::lower_bound(R, R + r, rhi) - R);
+                    if (t1 > t0) P.bsegs.push_back(BSeg{(int32_t)p, t0, t1, 0});
+                }
+                t.seg_end = (int32_t)P.bsegs.size();
+                if (t.seg_end > t.seg_begin) P.btasks.push_back(t);
+            }
+            g = ge;
+        }
+        P.btask_ptr[l + 1] = (int32_t)P.btasks.size();
+    }
+    (void)krows;
+}
+
 // Start of the largest trailing block [t0, n), n - t0 <= tmax, in which every
 // entry of L+U is present (n: none).
 int32_t dense_trailing_block(const HostPlan &P, int32_t tmax) {
@@ -892,6 +1044,7 @@ int analyze_host(int32_t n, const int32_t *colptr, const int32_t *rowidx, const 
     double t3 = now_ms();
     schedule(P, opt, num_sms);
     factor_tail(P, opt);
+    if (opt.factor_blocks != 0) block_schedule(P);
     solve_levels(P, opt);
     // A in compressed rows (original numbering), for residuals
     P.acsr_ptr.assign((size_t)n + 1, 0);

@@ -27,6 +27,15 @@ struct glu_handle {
     size_t arena_bytes = 0;
     void *map = nullptr;
     size_t map_total = 0;
+    // supernodal factorization tables and map
+    int32_t *d_lu_rowidx = nullptr;
+    int32_t *d_sn_c0 = nullptr, *d_sn_r = nullptr, *d_bdiag = nullptr;
+    BItem *d_bitems = nullptr;
+    BPair *d_bpairs = nullptr;
+    BSeg *d_bsegs = nullptr;
+    BTask *d_btasks = nullptr;
+    void *bmap = nullptr;
+    size_t bmap_total = 0;
     int map_bytes = 2;
     double *d_lu = nullptr;
     double *d_aval = nullptr;
@@ -195,8 +204,23 @@ LevelRange level_range(const HostPlan &P, int32_t l) {
 // trailing block the sweep stops before the block's first level: that
 // level's normalizations run alone, then the block is factored densely.
 template <typename T>
+BlockArgs<T> bargs_t(glu_handle *h, T *lu);
+
+template <typename T>
 int enqueue_levels(glu_handle *h, const FactorArgs<T> &a, cudaStream_t st) {
     HostPlan &P = h->P;
+    if (h->opt.factor_blocks != 0) {
+        // the supernodal sweep: per block level, diagonal blocks, panels, updates
+        const BlockArgs<T> ba = bargs_t<T>(h, a.lu);
+        for (int32_t l = 0; l < P.nblev; l++) {
+            int launched = 0;
+            CK(launch_block_level<T>(ba, h->map_bytes, P.bdiag_ptr[l], P.bdiag_ptr[l + 1], P.bitem_ptr[l],
+                                     P.bitem_ptr[l + 1], P.btask_ptr[l], P.btask_ptr[l + 1], h->num_sms, st,
+                                     &launched));
+            h->launches += launched;
+        }
+        return GLU_OK;
+    }
     const int32_t nl = (int32_t)P.level_ptr.size() - 1;
     const bool dense = P.ftail_t0 < P.n;
     const int32_t lend = dense ? P.ftail_level : nl;   // levels [0, lend) run here
@@ -349,6 +373,25 @@ int enqueue_solve(glu_handle *h, const double *db, double *dx, int32_t nrhs, cud
     }
     CKL(1, launch_permute_out<double>(dx, y, h->d_perm, n, nrhs, st));
     return GLU_OK;
+}
+
+template <typename T>
+BlockArgs<T> bargs_t(glu_handle *h, T *lu) {
+    BlockArgs<T> a;
+    a.lu = lu;
+    a.colptr = h->d_lu_colptr;
+    a.rowidx = h->d_lu_rowidx;
+    a.diag_pos = h->d_diag;
+    a.sn_c0 = h->d_sn_c0;
+    a.sn_r = h->d_sn_r;
+    a.bdiag = h->d_bdiag;
+    a.bitems = h->d_bitems;
+    a.bpairs = h->d_bpairs;
+    a.bsegs = h->d_bsegs;
+    a.btasks = h->d_btasks;
+    a.map = h->bmap;
+    a.err = h->d_err;
+    return a;
 }
 
 template <typename T>
@@ -524,7 +567,11 @@ int upload_plan(glu_handle *h) {
            o_bdfi = c.take<int32_t>(P.df_items_b.size()), o_bfc = c.take<SolveChunk>(P.bdf_fchunks.size()),
            o_bbc = c.take<SolveChunk>(P.bdf_bchunks.size()), o_btcb = c.take<int32_t>(P.btail_cb.size()),
            o_btce = c.take<int32_t>(P.btail_ce.size()),
-           o_rng = c.take<LevelRange>(P.level_ptr.size()), o_gbar = c.take<unsigned>(2);
+           o_rng = c.take<LevelRange>(P.level_ptr.size()), o_gbar = c.take<unsigned>(2),
+           o_snc0 = c.take<int32_t>(P.sn_c0.size()), o_snr = c.take<int32_t>(P.sn_r.size()),
+           o_bdg = c.take<int32_t>(P.bdiag.size()), o_bit = c.take<BItem>(P.bitems.size()),
+           o_bpr = c.take<BPair>(P.bpairs.size()), o_bsg = c.take<BSeg>(P.bsegs.size()),
+           o_btk = c.take<BTask>(P.btasks.size());
     h->arena_bytes = c.off + 256;
     CK(cudaMalloc(&h->arena, h->arena_bytes));
     char *A = h->arena;
@@ -579,6 +626,14 @@ int upload_plan(glu_handle *h) {
     int64_t *d_lcp = at<int64_t>(A, o_lcp);
     h->d_lu_colptr = d_lcp;
     int32_t *d_lri = at<int32_t>(A, o_lri);
+    h->d_lu_rowidx = d_lri;
+    h->d_sn_c0 = at<int32_t>(A, o_snc0);
+    h->d_sn_r = at<int32_t>(A, o_snr);
+    h->d_bdiag = at<int32_t>(A, o_bdg);
+    h->d_bitems = at<BItem>(A, o_bit);
+    h->d_bpairs = at<BPair>(A, o_bpr);
+    h->d_bsegs = at<BSeg>(A, o_bsg);
+    h->d_btasks = at<BTask>(A, o_btk);
     CK(upload(h->d_gsrc, P.gsrc));
     CK(upload(h->d_diag, P.diag_pos));
     CK(upload(h->d_pair_j, P.pair_j));
@@ -631,6 +686,13 @@ int upload_plan(glu_handle *h) {
     }
     CK(upload(d_lcp, P.lu_colptr));
     CK(upload(d_lri, P.lu_rowidx));
+    CK(upload(h->d_sn_c0, P.sn_c0));
+    CK(upload(h->d_sn_r, P.sn_r));
+    CK(upload(h->d_bdiag, P.bdiag));
+    CK(upload(h->d_bitems, P.bitems));
+    CK(upload(h->d_bpairs, P.bpairs));
+    CK(upload(h->d_bsegs, P.bsegs));
+    CK(upload(h->d_btasks, P.btasks));
     // position map, built on the device
     h->map_bytes = (P.max_col_len <= 65536) ? 2 : 4;
     h->map_total = (size_t)std::max<int64_t>(P.n_updates, 1) * h->map_bytes;
@@ -648,6 +710,12 @@ int upload_plan(glu_handle *h) {
     mb.npairs = (int64_t)P.pair_j.size();
     mb.err = h->d_err;
     CK(launch_map_build(mb, h->map_bytes, h->stream));
+    if (h->opt.factor_blocks != 0) {
+        h->bmap_total = (size_t)std::max<int64_t>(P.bmap_size, 1) * h->map_bytes;
+        CK(cudaMalloc(&h->bmap, h->bmap_total));
+        BlockArgs<double> ba = bargs_t<double>(h, h->d_lu);
+        CK(launch_bmap_build(ba, h->map_bytes, (int64_t)P.bpairs.size(), h->num_sms, h->stream));
+    }
     int rc = read_err(h);
     if (rc != GLU_OK) {
         h->why = "position map build found a row outside its target column";
@@ -745,6 +813,31 @@ int glu_analyze_opts(int32_t n, const int32_t *colptr, const int32_t *rowidx, co
                              (long long)sg[2], (long long)wk[2], (long long)mw, (long long)ms, (long long)mseg[0],
                              (long long)mseg[1], (long long)mseg[2]);
             }
+            std::fclose(fp);
+        }
+    }
+    if (const char *dump = std::getenv("GLU_DUMP_BLOCKS")) {
+        // the supernodal schedule as int64 words: counts (supernodes, block
+        // levels, diagonal list, panel items, pairs, segments, tasks), then
+        // sn_c0, sn_r, bdiag_ptr, bdiag, bitem_ptr, bitems (4 each),
+        // bpairs (sn, k, f, upos, mb), bsegs (pair, t0, t1), btask_ptr,
+        // btasks (2 each)
+        if (FILE *fp = std::fopen(dump, "wb")) {
+            const HostPlan &P = h->P;
+            std::vector<int64_t> w = {(int64_t)P.sn_r.size(), P.nblev, (int64_t)P.bdiag.size(),
+                                      (int64_t)P.bitems.size(), (int64_t)P.bpairs.size(), (int64_t)P.bsegs.size(),
+                                      (int64_t)P.btasks.size()};
+            for (int32_t v : P.sn_c0) w.push_back(v);
+            for (int32_t v : P.sn_r) w.push_back(v);
+            for (int32_t v : P.bdiag_ptr) w.push_back(v);
+            for (int32_t v : P.bdiag) w.push_back(v);
+            for (int32_t v : P.bitem_ptr) w.push_back(v);
+            for (const BItem &b : P.bitems) w.insert(w.end(), {b.sn, b.kind, b.a, b.b});
+            for (const BPair &b : P.bpairs) w.insert(w.end(), {b.sn, b.k, b.f, b.upos, b.mb});
+            for (const BSeg &b : P.bsegs) w.insert(w.end(), {b.pair, b.t0, b.t1});
+            for (int32_t v : P.btask_ptr) w.push_back(v);
+            for (const BTask &b : P.btasks) w.insert(w.end(), {b.seg_begin, b.seg_end});
+            std::fwrite(w.data(), sizeof(int64_t), w.size(), fp);
             std::fclose(fp);
         }
     }
@@ -1057,7 +1150,7 @@ int glu_get_stats(const glu_handle *h, glu_stats *s) {
     s->solve_levels_fwd = (int32_t)P.fwd_ptr.size() - 1;
     s->solve_levels_bwd = (int32_t)P.bwd_ptr.size() - 1;
     s->max_level_width = P.max_level_width;
-    s->device_bytes = (int64_t)(h->arena_bytes + h->map_total + 4 * h->work_elems * sizeof(double) +
+    s->device_bytes = (int64_t)(h->arena_bytes + h->map_total + h->bmap_total + 4 * h->work_elems * sizeof(double) +
                                 (int64_t)std::max(P.fwd_chunks.size(), P.bwd_chunks.size()) * h->work_nrhs *
                                     sizeof(double));
     s->analyze_ms = h->analyze_ms;
@@ -1105,6 +1198,7 @@ void glu_destroy(glu_handle *h) {
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     cudaFree(h->arena);
     cudaFree(h->map);
+    cudaFree(h->bmap);
     cudaFree(h->d_work);
     cudaFree(h->d_bstage);
     cudaFree(h->d_xstage);

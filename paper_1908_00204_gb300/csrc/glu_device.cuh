@@ -68,6 +68,22 @@ __device__ __forceinline__ bool grid_sync(const GridBarrier &bar, unsigned targe
 }
 #endif
 
+// The supernodal factorization's tables (see kernels_blocks.cu).
+template <typename T>
+struct BlockArgs {
+    T *lu;
+    const int64_t *colptr;
+    const int32_t *rowidx;
+    const int64_t *diag_pos;
+    const int32_t *sn_c0, *sn_r, *bdiag;
+    const BItem *bitems;
+    const BPair *bpairs;
+    const BSeg *bsegs;
+    const BTask *btasks;
+    const void *map;             // per pair, offsets in column k of the rows R_B
+    unsigned long long *err;
+};
+
 // The dense trailing block [t0, t0 + nt) of the factorization: column t0 + k
 // keeps rows t0 .. t0+nt-1 as its last nt entries.
 struct DenseTailArgs {
@@ -147,6 +163,13 @@ cudaError_t launch_level(const FactorArgs<T> &a, int map_bytes, const LevelRange
 template <typename T>
 cudaError_t launch_levels_persistent(const FactorArgs<T> &a, int map_bytes, const LevelRange *ranges, int32_t nlev,
                                      const GridBarrier &bar, int num_sms, cudaStream_t s);
+// One level of the supernodal factorization: diagonal blocks d0..d1-1,
+// panel items i0..i1-1, update tasks k0..k1-1 (kernels_blocks.cu); *launched
+// counts the kernels launched.
+template <typename T>
+cudaError_t launch_block_level(const BlockArgs<T> &a, int map_bytes, int32_t d0, int32_t d1, int32_t i0,
+                               int32_t i1, int32_t k0, int32_t k1, int num_sms, cudaStream_t s, int *launched);
+cudaError_t launch_bmap_build(const BlockArgs<double> &a, int map_bytes, int64_t npairs, int num_sms, cudaStream_t s);
 // Dense LU of the trailing block (one cooperative launch, grid barriers).
 template <typename T>
 int32_t dense_tail_panel(int32_t nt);

@@ -62,6 +62,37 @@ struct Task {
 
 constexpr int SRC_SLOTS = 32;
 
+// Supernodal ("block") factorization.  A supernode B = columns [c0, c1),
+// at most BSN_MAX of them, has a dense diagonal block and the same rows R_B
+// below it in every column.  Per block level: the diagonal blocks are
+// factored (warp per supernode), then the panel rows L21 = A21 U11^-1 and the
+// target rows U12 = L11^-1 A12 (warp items), then every target column takes
+// A(R_B, k) -= L21 U12(:, k) from the level's supernodes (warp tasks owning
+// BCHUNK positions of the column).
+constexpr int32_t BSN_MAX = 32;
+constexpr int32_t BCHUNK = 128;
+
+struct BPair {          // supernode sn updates target column k
+    int32_t sn;
+    int32_t k;
+    int32_t f;          // first column offset in B with U(c0 + f, k) != 0 (a suffix of B)
+    int32_t spare;
+    int64_t upos;       // position of U(c0 + f, k) in the CSC values
+    int64_t mb;         // first map entry: offsets in column k of the rows R_B
+};
+
+struct BSeg {           // rows t0..t1-1 of R_B applied to the pair's target column
+    int32_t pair, t0, t1, spare;
+};
+
+struct BTask {
+    int32_t seg_begin, seg_end;
+};
+
+struct BItem {          // panel work: kind 0 rows [a, b) of R_B, kind 1 the pair a
+    int32_t sn, kind, a, b;
+};
+
 // Triangular-solve work: a row of a solve level; rows with many entries get
 // their dot product split into chunks computed first (partials cb..ce-1).
 struct SolveRow {
@@ -140,6 +171,18 @@ struct HostPlan {
     int32_t bdf_nfwd = 0, btail_t0 = 0;
     std::vector<SolveChunk> bdf_fchunks, bdf_bchunks;
     std::vector<int32_t> btail_cb, btail_ce;
+    // supernodal factorization (built when the block mode is selected)
+    std::vector<int32_t> sn_c0;          // nsn + 1 column boundaries
+    std::vector<int32_t> sn_r;           // |R_B|
+    std::vector<int32_t> bdiag, bdiag_ptr;   // supernodes of >= 2 columns, by block level
+    std::vector<BItem> bitems;
+    std::vector<int32_t> bitem_ptr;
+    std::vector<BPair> bpairs;
+    std::vector<BSeg> bsegs;
+    std::vector<BTask> btasks;
+    std::vector<int32_t> btask_ptr;
+    int64_t bmap_size = 0;
+    int32_t nblev = 0;
     // dense trailing block of the factorization [ftail_t0, n) (ftail_t0 == n:
     // none); the level sweep runs levels [0, ftail_level) and the
     // normalizations of level ftail_level, then the block is factored dense

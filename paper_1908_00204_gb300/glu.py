@@ -38,7 +38,7 @@ class glu_options(C.Structure):
                 ("verbose", C.c_int32), ("host_only", C.c_int32), ("solve_mode", C.c_int32),
                 ("spin_limit_us", C.c_int32), ("fault_row", C.c_int32), ("solve_tail", C.c_int32),
                 ("factor_tail", C.c_int32), ("solve_blocks", C.c_int32),
-                ("reserved", C.c_int32 * 2)]
+                ("factor_blocks", C.c_int32), ("reserved", C.c_int32 * 1)]
 
 
 class glu_stats(C.Structure):

@@ -224,3 +224,41 @@ def test_dense_tail_nonfinite_pivot_reported(glu):
     glu.glu_factor(h, v)
     b = synth.rhs(m.n, 1, 3)
     assert backward_error(m.n, m.colptr, m.rowidx, v, b, glu.glu_solve(h, b)) <= BERR_TOL
+
+
+@pytest.mark.parametrize("case", ["grid32", "random", "mesh_small", "mesh100x200", "dense900"])
+def test_block_factor_parity(glu, case):
+    """The supernodal factorization (factor_blocks=1) against the oracle."""
+    opts = glu.default_options(factor_blocks=1)
+    if case == "grid32":
+        m = synth.make("grid32_natural", 0)
+        args = (m.n, m.colptr, m.rowidx, m.perm, m.values(1), synth.rhs(m.n, 1, 2))
+    elif case == "random":
+        cp, ri, v = synth.random_pattern_matrix(150, 0.15, 45)
+        perm = np.random.default_rng(5).permutation(150).astype(np.int32)
+        args = (150, cp, ri, perm, v, synth.rhs(150, 3, 5))
+    elif case == "mesh_small":
+        m = synth.CircuitMatrix(synth.CircuitSpec(30, 40, 8, 60, 0.02, 0.05, "nd"), 3)
+        args = (m.n, m.colptr, m.rowidx, m.perm, m.values(5), synth.rhs(m.n, 2, 5))
+    elif case == "mesh100x200":
+        m = synth.make("mesh100x200_nets64", 1)
+        args = (m.n, m.colptr, m.rowidx, m.perm, m.values(2001), synth.rhs(m.n, 4, 2001))
+    else:
+        m = synth.CircuitMatrix(synth.CircuitSpec(16, 20, 900, 15, 0.02, 0.05, "nd"), 3)
+        args = (m.n, m.colptr, m.rowidx, m.perm, m.values(8), synth.rhs(m.n, 2, 8))
+    h, got, f = run_case(glu, *args, opts=opts)
+    # deterministic: the same factors again
+    glu.glu_factor(h, args[4])
+    assert np.array_equal(glu.glu_get_factors(h), got)
+    # the FP32 path through the same schedule, refined to 1e-12
+    glu.glu_factor_f32(h, args[4])
+    x, info = glu.glu_solve_refine(h, args[5], tol=1e-12, maxit=10)
+    assert info["converged"] == 1
+    assert backward_error(args[0], args[1], args[2], args[4], args[5], x) <= BERR_TOL
+
+
+def test_block_factor_mesh400x500_full(glu):
+    """The 200k-unknown workload through the supernodal factorization."""
+    m = synth.make("mesh400x500_nets64", 1)
+    run_case(glu, m.n, m.colptr, m.rowidx, m.perm, m.values(1001), synth.rhs(m.n, 1, 1001),
+             opts=glu.default_options(factor_blocks=1), device_inputs=True)
