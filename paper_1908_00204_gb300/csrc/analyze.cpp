@@ -236,6 +236,7 @@ void levelize(HostPlan &P) {
 // sources becomes one KIND_SRC task per touched 32-position chunk of column
 // k.  Each level's kernel also normalizes the previous level's L columns.
 void schedule(HostPlan &P, const glu_options &opt, int num_sms) {
+    P.has_schedule = true;
     const int32_t n = P.n;
     const int32_t nl = (int32_t)P.level_ptr.size() - 1;
     const int64_t piece = opt.piece_updates > 0 ? opt.piece_updates : 1024;
@@ -974,6 +975,10 @@ void solve_levels(HostPlan &P, const glu_options &opt) {
 
 }  // namespace
 
+void column_schedule(HostPlan &P, const glu_options &opt, int num_sms) {
+    if (!P.has_schedule) schedule(P, opt, num_sms);
+}
+
 int analyze_host(int32_t n, const int32_t *colptr, const int32_t *rowidx, const int32_t *perm,
                  const glu_options &opt, int num_sms, HostPlan &P, std::string &why) {
     if (n < 0 || (n > 0 && (!colptr || !rowidx))) { why = "bad arguments"; return GLU_ERR_INVALID; }
@@ -1042,7 +1047,10 @@ int analyze_host(int32_t n, const int32_t *colptr, const int32_t *rowidx, const 
     double t2 = now_ms();
     levelize(P);
     double t3 = now_ms();
-    schedule(P, opt, num_sms);
+    // the column schedule (and its position map) is only built here for the
+    // column-level factorization; the supernodal one builds it on demand
+    // (the batched path runs column levels)
+    if (opt.factor_blocks == 0) schedule(P, opt, num_sms);
     factor_tail(P, opt);
     if (opt.factor_blocks != 0) block_schedule(P);
     solve_levels(P, opt);
@@ -1063,11 +1071,18 @@ int analyze_host(int32_t n, const int32_t *colptr, const int32_t *rowidx, const 
     }
     double t4 = now_ms();
     P.flops = 0.0;
+    int64_t npairs = 0, nupd = 0;
     for (int32_t j = 0; j < n; j++) {
-        double lj = (double)(P.lu_colptr[j + 1] - P.diag_pos[j] - 1);
-        double uj = (double)(P.urow_ptr[j + 1] - P.urow_ptr[j]);
-        P.flops += lj + 2.0 * lj * uj;
+        const int64_t lj = P.lu_colptr[j + 1] - P.diag_pos[j] - 1;
+        const int64_t uj = P.urow_ptr[j + 1] - P.urow_ptr[j];
+        P.flops += (double)lj + 2.0 * (double)lj * (double)uj;
+        if (lj > 0) {
+            npairs += uj;
+            nupd += lj * uj;
+        }
     }
+    P.n_pairs = npairs;
+    P.n_updates = nupd;
     P.ms_symbolic = t1 - t0;
     P.ms_deps = t2 - t1;
     P.ms_levels = t3 - t2;

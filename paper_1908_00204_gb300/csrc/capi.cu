@@ -27,6 +27,9 @@ struct glu_handle {
     size_t arena_bytes = 0;
     void *map = nullptr;
     size_t map_total = 0;
+    char *carena = nullptr;      // the column-level schedule (built on first use in block mode)
+    size_t carena_bytes = 0;
+    bool col_ready = false;
     // supernodal factorization tables and map
     int32_t *d_lu_rowidx = nullptr;
     int32_t *d_sn_c0 = nullptr, *d_sn_r = nullptr, *d_bdiag = nullptr;
@@ -184,6 +187,7 @@ cudaError_t upload(T *dst, const std::vector<T> &src) {
 
 FactorArgs<double> fargs(glu_handle *h);
 SolveArgs<double> sargs(glu_handle *h);
+int setup_column_plan(glu_handle *h);
 
 // Work list of level l (l == nlevels: the final normalization pass).
 LevelRange level_range(const HostPlan &P, int32_t l) {
@@ -289,7 +293,10 @@ int enqueue_factor(glu_handle *h, const double *av, cudaStream_t st, std::vector
     FactorArgs<double> a = fargs(h);
     const int32_t nl = (int32_t)P.level_ptr.size() - 1;
     if (lev_events) {
-        // per-level timing diagnostic: one launch per level
+        // per-level timing diagnostic: one launch per level (column levels)
+        const int rc0 = setup_column_plan(h);
+        if (rc0 != GLU_OK) return rc0;
+        a = fargs(h);
         CK(cudaEventRecord((*lev_events)[0], st));
         for (int32_t l = 0; l <= nl; l++) {
             const LevelRange r = level_range(P, l);
@@ -538,22 +545,72 @@ SolveArgs<double> sargs(glu_handle *h) {
     return a;
 }
 
+// The column-level schedule on the device: pair tables, segments, tasks,
+// normalization items, per-level ranges and the position map (built by
+// k_map_build).  Run by glu_analyze for the column-level factorization and
+// on first use otherwise (the batched path runs column levels).
+int setup_column_plan(glu_handle *h) {
+    if (h->col_ready) return GLU_OK;
+    HostPlan &P = h->P;
+    column_schedule(P, h->opt, h->num_sms);
+    Carve c;
+    const size_t o_pj = c.take<int32_t>(P.pair_j.size()), o_ppos = c.take<int64_t>(P.pair_pos.size()),
+                 o_pmap = c.take<int64_t>(P.pair_map.size()), o_segs = c.take<Seg>(P.segs.size()),
+                 o_tasks = c.take<Task>(P.tasks.size()), o_norms = c.take<NormItem>(P.norms.size()),
+                 o_pk = c.take<int32_t>(P.pair_k.size()), o_rng = c.take<LevelRange>(P.level_ptr.size());
+    h->carena_bytes = c.off + 256;
+    CK(cudaMalloc(&h->carena, h->carena_bytes));
+    char *A = h->carena;
+    h->d_pair_j = at<int32_t>(A, o_pj);
+    h->d_pair_pos = at<int64_t>(A, o_ppos);
+    h->d_pair_map = at<int64_t>(A, o_pmap);
+    h->d_segs = at<Seg>(A, o_segs);
+    h->d_tasks = at<Task>(A, o_tasks);
+    h->d_norms = at<NormItem>(A, o_norms);
+    h->d_ranges = at<LevelRange>(A, o_rng);
+    int32_t *d_pair_k = at<int32_t>(A, o_pk);
+    CK(upload(h->d_pair_j, P.pair_j));
+    CK(upload(h->d_pair_pos, P.pair_pos));
+    CK(upload(h->d_pair_map, P.pair_map));
+    CK(upload(h->d_segs, P.segs));
+    CK(upload(h->d_tasks, P.tasks));
+    CK(upload(h->d_norms, P.norms));
+    CK(upload(d_pair_k, P.pair_k));
+    {
+        std::vector<LevelRange> rg(P.level_ptr.size());
+        for (size_t l = 0; l < rg.size(); l++) rg[l] = level_range(P, (int32_t)l);
+        CK(upload(h->d_ranges, rg));
+    }
+    h->map_total = (size_t)std::max<int64_t>(P.n_updates, 1) * h->map_bytes;
+    CK(cudaMalloc(&h->map, h->map_total));
+    MapBuildArgs mb;
+    mb.lu_colptr = h->d_lu_colptr;
+    mb.lu_rowidx = h->d_lu_rowidx;
+    mb.diag_pos = h->d_diag;
+    mb.pair_j = h->d_pair_j;
+    mb.pair_k = d_pair_k;
+    mb.pair_pos = h->d_pair_pos;
+    mb.pair_map = h->d_pair_map;
+    mb.map = h->map;
+    mb.npairs = (int64_t)P.pair_j.size();
+    mb.err = h->d_err;
+    CK(launch_map_build(mb, h->map_bytes, h->stream));
+    h->col_ready = true;
+    return GLU_OK;
+}
+
 int upload_plan(glu_handle *h) {
     HostPlan &P = h->P;
     const int32_t n = P.n;
     const int64_t nnz = P.lu_colptr[n];
     Carve c;
     size_t o_lu = c.take<double>(nnz), o_aval = c.take<double>(P.nnz_a), o_gsrc = c.take<int32_t>(nnz),
-           o_diag = c.take<int64_t>(n), o_pj = c.take<int32_t>(P.pair_j.size()),
-           o_ppos = c.take<int64_t>(P.pair_pos.size()), o_pmap = c.take<int64_t>(P.pair_map.size()),
-           o_segs = c.take<Seg>(P.segs.size()), o_tasks = c.take<Task>(P.tasks.size()),
-           o_norms = c.take<NormItem>(P.norms.size()), o_err = c.take<unsigned long long>(1),
+           o_diag = c.take<int64_t>(n), o_err = c.take<unsigned long long>(1),
            o_lrp = c.take<int64_t>(n + 1), o_lrc = c.take<int32_t>(P.lrow_col.size()),
            o_lrpos = c.take<int64_t>(P.lrow_pos.size()), o_urp = c.take<int64_t>(n + 1),
            o_urc = c.take<int32_t>(P.urow_col.size()), o_urpos = c.take<int64_t>(P.urow_pos.size()),
            o_fwd = c.take<int32_t>(P.fwd_rows.size()), o_bwd = c.take<int32_t>(P.bwd_rows.size()),
-           o_perm = c.take<int32_t>(n), o_pk = c.take<int32_t>(P.pair_k.size()),
-           o_lcp = c.take<int64_t>(n + 1), o_lri = c.take<int32_t>(nnz),
+           o_perm = c.take<int32_t>(n), o_lcp = c.take<int64_t>(n + 1), o_lri = c.take<int32_t>(nnz),
            o_fi = c.take<SolveRow>(P.fwd_items.size()), o_bi = c.take<SolveRow>(P.bwd_items.size()),
            o_fc = c.take<SolveChunk>(P.fwd_chunks.size()), o_bc = c.take<SolveChunk>(P.bwd_chunks.size()),
            o_dfi = c.take<int32_t>(P.df_items.size()),
@@ -567,7 +624,7 @@ int upload_plan(glu_handle *h) {
            o_bdfi = c.take<int32_t>(P.df_items_b.size()), o_bfc = c.take<SolveChunk>(P.bdf_fchunks.size()),
            o_bbc = c.take<SolveChunk>(P.bdf_bchunks.size()), o_btcb = c.take<int32_t>(P.btail_cb.size()),
            o_btce = c.take<int32_t>(P.btail_ce.size()),
-           o_rng = c.take<LevelRange>(P.level_ptr.size()), o_gbar = c.take<unsigned>(2),
+           o_gbar = c.take<unsigned>(2),
            o_snc0 = c.take<int32_t>(P.sn_c0.size()), o_snr = c.take<int32_t>(P.sn_r.size()),
            o_bdg = c.take<int32_t>(P.bdiag.size()), o_bit = c.take<BItem>(P.bitems.size()),
            o_bpr = c.take<BPair>(P.bpairs.size()), o_bsg = c.take<BSeg>(P.bsegs.size()),
@@ -579,12 +636,6 @@ int upload_plan(glu_handle *h) {
     h->d_aval = at<double>(A, o_aval);
     h->d_gsrc = at<int32_t>(A, o_gsrc);
     h->d_diag = at<int64_t>(A, o_diag);
-    h->d_pair_j = at<int32_t>(A, o_pj);
-    h->d_pair_pos = at<int64_t>(A, o_ppos);
-    h->d_pair_map = at<int64_t>(A, o_pmap);
-    h->d_segs = at<Seg>(A, o_segs);
-    h->d_tasks = at<Task>(A, o_tasks);
-    h->d_norms = at<NormItem>(A, o_norms);
     h->d_err = at<unsigned long long>(A, o_err);
     h->d_lrow_ptr = at<int64_t>(A, o_lrp);
     h->d_lrow_col = at<int32_t>(A, o_lrc);
@@ -620,9 +671,7 @@ int upload_plan(glu_handle *h) {
     h->d_bbwd_chunks = at<SolveChunk>(A, o_bbc);
     h->d_btail_cb = at<int32_t>(A, o_btcb);
     h->d_btail_ce = at<int32_t>(A, o_btce);
-    h->d_ranges = at<LevelRange>(A, o_rng);
     h->d_gbar = at<unsigned>(A, o_gbar);
-    int32_t *d_pair_k = at<int32_t>(A, o_pk);
     int64_t *d_lcp = at<int64_t>(A, o_lcp);
     h->d_lu_colptr = d_lcp;
     int32_t *d_lri = at<int32_t>(A, o_lri);
@@ -636,12 +685,6 @@ int upload_plan(glu_handle *h) {
     h->d_btasks = at<BTask>(A, o_btk);
     CK(upload(h->d_gsrc, P.gsrc));
     CK(upload(h->d_diag, P.diag_pos));
-    CK(upload(h->d_pair_j, P.pair_j));
-    CK(upload(h->d_pair_pos, P.pair_pos));
-    CK(upload(h->d_pair_map, P.pair_map));
-    CK(upload(h->d_segs, P.segs));
-    CK(upload(h->d_tasks, P.tasks));
-    CK(upload(h->d_norms, P.norms));
     CK(upload(h->d_lrow_ptr, P.lrow_ptr));
     CK(upload(h->d_lrow_col, P.lrow_col));
     CK(upload(h->d_lrow_pos, P.lrow_pos));
@@ -651,7 +694,6 @@ int upload_plan(glu_handle *h) {
     CK(upload(h->d_fwd_rows, P.fwd_rows));
     CK(upload(h->d_bwd_rows, P.bwd_rows));
     CK(upload(h->d_perm, P.perm));
-    CK(upload(d_pair_k, P.pair_k));
     CK(upload(h->d_fwd_items, P.fwd_items));
     CK(upload(h->d_bwd_items, P.bwd_items));
     CK(upload(h->d_fwd_chunks, P.fwd_chunks));
@@ -671,11 +713,6 @@ int upload_plan(glu_handle *h) {
     CK(upload(h->d_bbwd_chunks, P.bdf_bchunks));
     CK(upload(h->d_btail_cb, P.btail_cb));
     CK(upload(h->d_btail_ce, P.btail_ce));
-    {
-        std::vector<LevelRange> rg(P.level_ptr.size());
-        for (size_t l = 0; l < rg.size(); l++) rg[l] = level_range(P, (int32_t)l);
-        CK(upload(h->d_ranges, rg));
-    }
     CK(cudaMemset(h->d_flags, 0, std::max<int64_t>(h->n_flags, 1) * sizeof(int32_t)));
     CK(cudaMemset(h->d_serr, 0xff, sizeof(unsigned long long)));
     {
@@ -693,23 +730,12 @@ int upload_plan(glu_handle *h) {
     CK(upload(h->d_bpairs, P.bpairs));
     CK(upload(h->d_bsegs, P.bsegs));
     CK(upload(h->d_btasks, P.btasks));
-    // position map, built on the device
     h->map_bytes = (P.max_col_len <= 65536) ? 2 : 4;
-    h->map_total = (size_t)std::max<int64_t>(P.n_updates, 1) * h->map_bytes;
-    CK(cudaMalloc(&h->map, h->map_total));
     CK(launch_reset_err(h->d_err, h->stream));
-    MapBuildArgs mb;
-    mb.lu_colptr = d_lcp;
-    mb.lu_rowidx = d_lri;
-    mb.diag_pos = h->d_diag;
-    mb.pair_j = h->d_pair_j;
-    mb.pair_k = d_pair_k;
-    mb.pair_pos = h->d_pair_pos;
-    mb.pair_map = h->d_pair_map;
-    mb.map = h->map;
-    mb.npairs = (int64_t)P.pair_j.size();
-    mb.err = h->d_err;
-    CK(launch_map_build(mb, h->map_bytes, h->stream));
+    if (P.has_schedule) {
+        const int rc0 = setup_column_plan(h);
+        if (rc0 != GLU_OK) return rc0;
+    }
     if (h->opt.factor_blocks != 0) {
         h->bmap_total = (size_t)std::max<int64_t>(P.bmap_size, 1) * h->map_bytes;
         CK(cudaMalloc(&h->bmap, h->bmap_total));
@@ -1143,14 +1169,15 @@ int glu_get_stats(const glu_handle *h, glu_stats *s) {
     s->nnz_l = P.nnz_l;
     s->nnz_u = P.nnz_u;
     s->n_deps = P.dep_ptr[P.n];
-    s->n_pairs = (int64_t)P.pair_j.size();
+    s->n_pairs = P.n_pairs;
     s->n_updates = P.n_updates;
     s->flops = P.flops;
     for (int i = 0; i < 3; i++) s->levels_by_mode[i] = P.levels_by_mode[i];
     s->solve_levels_fwd = (int32_t)P.fwd_ptr.size() - 1;
     s->solve_levels_bwd = (int32_t)P.bwd_ptr.size() - 1;
     s->max_level_width = P.max_level_width;
-    s->device_bytes = (int64_t)(h->arena_bytes + h->map_total + h->bmap_total + 4 * h->work_elems * sizeof(double) +
+    s->device_bytes = (int64_t)(h->arena_bytes + h->carena_bytes + h->map_total + h->bmap_total +
+                                4 * h->work_elems * sizeof(double) +
                                 (int64_t)std::max(P.fwd_chunks.size(), P.bwd_chunks.size()) * h->work_nrhs *
                                     sizeof(double));
     s->analyze_ms = h->analyze_ms;
@@ -1199,6 +1226,7 @@ void glu_destroy(glu_handle *h) {
     cudaFree(h->arena);
     cudaFree(h->map);
     cudaFree(h->bmap);
+    cudaFree(h->carena);
     cudaFree(h->d_work);
     cudaFree(h->d_bstage);
     cudaFree(h->d_xstage);
@@ -1356,9 +1384,11 @@ int factor_batched(glu_handle *h, const double *values, int32_t batch, int64_t l
     HostPlan &P = h->P;
     if (P.nnz_a > 0 && (!values || ld < P.nnz_a)) return GLU_ERR_INVALID;
     CK(cudaSetDevice(h->device));
+    int rc = setup_column_plan(h);   // batches run the column-level schedule
+    if (rc != GLU_OK) return rc;
     const int32_t S = (batch + 31) / 32 * 32;
     h->bprec = 0;
-    int rc = ensure_batch(h, S, f32);
+    rc = ensure_batch(h, S, f32);
     if (rc != GLU_OK) return rc;
     h->err_col = -1;
     cudaStream_t st = h->stream;

@@ -131,7 +131,8 @@ struct HostPlan {
     // update schedule
     std::vector<int32_t> pair_j, pair_k;
     std::vector<int64_t> pair_pos, pair_map;
-    int64_t n_updates = 0;
+    int64_t n_updates = 0, n_pairs = 0;
+    bool has_schedule = false;           // the column-level schedule is built
     std::vector<Seg> segs;
     std::vector<Task> tasks;
     std::vector<int32_t> lvl_task_ptr;  // nlevels + 1
@@ -202,5 +203,9 @@ struct HostPlan {
 // Runs every host step of glu_analyze.  Returns a GLU_ code.
 int analyze_host(int32_t n, const int32_t *colptr, const int32_t *rowidx, const int32_t *perm,
                  const glu_options &opt, int num_sms, HostPlan &P, std::string &why);
+
+// The column-level update schedule (pairs, segments, tasks, normalization
+// items) if analyze_host skipped it.
+void column_schedule(HostPlan &P, const glu_options &opt, int num_sms);
 
 }  // namespace glu
