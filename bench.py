@@ -49,6 +49,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP32+refinement and batched lines")
+    ap.add_argument("--serve", action="store_true",
+                    help="instead of the refactor+solve step: the continuous-batching serving loop on mixed "
+                         "patterns with Poisson arrivals; prints p50/p99 latency")
+    ap.add_argument("--serve-patterns", default="serve5k,serve20k,serve50k,serve100k,serve200k,serve500k")
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="offered requests per second")
+    ap.add_argument("--serve-requests", type=int, default=3000, help="timed requests (after a tenth as warm-up)")
+    ap.add_argument("--serve-precision", default="fp64", choices=["fp64", "fp32"])
     return ap.parse_args()
 
 
@@ -358,10 +365,66 @@ def run_ours(args):
     return 0
 
 
+def run_serve(args):
+    """Requests (pattern uniform over the list, new values, 1-8 right-hand
+    sides) arrive as a Poisson process at the offered rate; the serving loop
+    batches same-pattern requests and overlaps patterns on streams.  Latency
+    is submit -> result on the host, the first tenth of the requests being
+    warm-up."""
+    import torch
+    import paper_1908_00204_gb300 as g
+    from paper_1908_00204_gb300.serve import Request, Server
+    names = args.serve_patterns.split(",")
+    mats = {k: synth.make(k, 1) for k in names}
+    pool = 16   # value sets per pattern, drawn in turn (consecutive requests of a pattern differ)
+    vals = {k: [m.values(100 + i, sigma=0.1, base_seed=7) for i in range(pool)] for k, m in mats.items()}
+    nwarm = max(args.serve_requests // 10, 1)
+    nreq = args.serve_requests + nwarm
+    rng = np.random.default_rng(2026)
+    keys = [names[i] for i in rng.integers(len(names), size=nreq)]
+    nrhs = rng.integers(1, 9, size=nreq)
+    rhs = {k: synth.rhs(m.n, 8, 11) for k, m in mats.items()}
+
+    def make(i):
+        k = keys[i]
+        return Request(i, k, vals[k][i % pool], rhs[k][: int(nrhs[i])])
+    srv = Server(device_budget_bytes=60e9, max_batch=64, slots=4, precision=args.serve_precision)
+    t0 = time.perf_counter()
+    for k, m in mats.items():
+        srv.register(k, m.n, m.colptr, m.rowidx, m.perm)
+        srv.submit(Request(-1, k, vals[k][0], rhs[k][:1]))   # analysis and first factorization
+    srv.drain()
+    setup_s = time.perf_counter() - t0
+    srv.done.clear()
+    arrivals = list(np.cumsum(rng.exponential(1.0 / args.serve_rate, nreq)))
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        t0 = time.perf_counter()
+        srv.run(arrivals, make)
+        wall = time.perf_counter() - t0
+    clock = clk.summary()
+    lat = srv.latencies(skip=nwarm) * 1e3
+    line = {"metric": "serving latency, submit to result (mixed patterns, Poisson arrivals)",
+            "value": float(np.percentile(lat, 99)), "unit": "ms (p99)", "higher_is_better": False,
+            "p50_ms": float(np.percentile(lat, 50)), "p90_ms": float(np.percentile(lat, 90)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+            "offered_rate_per_s": args.serve_rate, "achieved_rate_per_s": nreq / wall,
+            "requests": args.serve_requests, "warmup_requests": nwarm, "precision": args.serve_precision,
+            "patterns": {k: {"n": m.n, "nnz_a": m.nnz} for k, m in mats.items()},
+            "batches": srv.batches, "analyses": srv.analyses, "evictions": srv.evictions,
+            "setup_s": setup_s, "wall_s": wall, "n_gpus": 1, "data": "synthetic", "clocks": clock,
+            "config": {"workload": "serving " + ",".join(names), "nrhs": "uniform 1..8",
+                       "values": f"{pool} Monte-Carlo value sets per pattern, drawn in turn",
+                       "device_budget_gb": 60, "max_batch": 64, "streams": 4}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.serve:
+        return run_serve(args)
     return run_ours(args)
 
 
