@@ -243,6 +243,22 @@ def extras(g, torch, dev, m, vals_host, b_host, h):
     return out
 
 
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time, on every rank (ms itself without a process group)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(steps, world, max_ms):
+    """Whole-job throughput: each of the `world` replicas ran `steps` steps
+    (weak scaling), the job took as long as the slowest rank."""
+    return world * steps / (max_ms / 1e3)
+
+
 def run_ours(args):
     import torch
     import paper_1908_00204_gb300 as g
@@ -304,12 +320,8 @@ def run_ours(args):
     clocks = clk.summary()
     fac = [e0.elapsed_time(e1) for e0, e1, _ in ev]
     sol = [e1.elapsed_time(e2) for _, e1, e2 in ev]
-    total_ms = float(sum(f + s for f, s in zip(fac, sol)))
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(float(sum(f + s for f, s in zip(fac, sol))), dist, dev)
+    value = job_rate(args.steps, world, total_ms)
     fac_ms = float(np.mean(fac))
     flops = st["flops"]
     achieved = flops / (fac_ms * 1e-3) / 1e12
