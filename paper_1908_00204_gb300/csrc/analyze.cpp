@@ -534,13 +534,13 @@ void schedule(HostPlan &P, const glu_options &opt, int num_sms) {
 
 // Dense diagonal blocks ("supernodes") of the solve among the rows [0, t0):
 // maximal runs [c0, c1) in which L(B, B) is dense lower and U(B, B) dense
-// upper, cut into pieces of at most SN_MAX rows; pieces of at least SN_MIN
+// upper, cut into pieces of at most sn_max rows; pieces of at least SN_MIN
 // rows are kept.
-std::vector<std::pair<int32_t, int32_t>> solve_blocks(const HostPlan &P, int32_t t0) {
+std::vector<std::pair<int32_t, int32_t>> solve_blocks(const HostPlan &P, int32_t t0, int32_t sn_max) {
     std::vector<std::pair<int32_t, int32_t>> out;
     auto flush = [&](int32_t c0, int32_t c1) {
-        for (int32_t a = c0; a < c1; a += SN_MAX) {
-            const int32_t b = std::min(c1, a + SN_MAX);
+        for (int32_t a = c0; a < c1; a += sn_max) {
+            const int32_t b = std::min(c1, a + sn_max);
             if (b - a >= SN_MIN) out.emplace_back(a, b);
         }
     };
@@ -569,8 +569,8 @@ std::vector<std::pair<int32_t, int32_t>> solve_blocks(const HostPlan &P, int32_t
 // Dataflow schedule of the solve for a chunk size and a dense tail [t0, n).
 // Items: a row (its dot product, or the sum of its chunks' partials when it
 // has more than `chunk` entries), a chunk (a partial dot product of at most
-// `chunk` entries), and -- when `blocks` is set -- a dense diagonal block of
-// the solve, whose rows' entries outside the block are always chunks and whose
+// `chunk` entries), and -- when `blocks` > 0 -- a dense diagonal block of
+// the solve (at most `blocks` rows), whose rows' entries outside the block are always chunks and whose
 // own triangle one warp sweeps.  Forward items cover the rows before the tail
 // and the tail rows' partial sums over the columns before it (forward chunks
 // tail_cb[i]..tail_ce[i]-1); backward items the rows before the tail.  Each
@@ -578,11 +578,11 @@ std::vector<std::pair<int32_t, int32_t>> solve_blocks(const HostPlan &P, int32_t
 // block contracted to one node, a chunk sits at 1 + the highest level it
 // reads and before the rows of its level.  snx lists, per block, the first
 // chunk of each of its rows and the end (offset in the item's third field).
-void build_df(const HostPlan &P, int64_t chunk, int32_t t0, bool blocks, std::vector<int32_t> &out,
+void build_df(const HostPlan &P, int64_t chunk, int32_t t0, int32_t blocks, std::vector<int32_t> &out,
               std::vector<SolveChunk> &dff, std::vector<SolveChunk> &dfb, std::vector<int32_t> &tcb,
               std::vector<int32_t> &tce, int32_t &nfwd, std::vector<int32_t> &snx_f, std::vector<int32_t> &snx_b) {
     const int32_t n = P.n;
-    const auto bl = blocks ? solve_blocks(P, t0) : std::vector<std::pair<int32_t, int32_t>>();
+    const auto bl = blocks > 0 ? solve_blocks(P, t0, blocks) : std::vector<std::pair<int32_t, int32_t>>();
     std::vector<int32_t> bof((size_t)n, -1);
     for (size_t q = 0; q < bl.size(); q++)
         for (int32_t i = bl[q].first; i < bl[q].second; i++) bof[i] = (int32_t)q;
@@ -961,16 +961,15 @@ void solve_levels(HostPlan &P, const glu_options &opt) {
         const int32_t best = dense_trailing_block(P, TAIL_MAX);
         if (n - best >= TAIL_MIN) P.tail_t0 = best;
     }
-    build_df(P, SOLVE_CHUNK, P.tail_t0, opt.solve_blocks != 0, P.df_items, P.df_fchunks, P.df_bchunks, P.tail_cb,
-             P.tail_ce, P.df_nfwd, P.df_snx_f, P.df_snx_b);
+    build_df(P, SOLVE_CHUNK, P.tail_t0, opt.solve_blocks != 0 ? SN_MAX : 0, P.df_items, P.df_fchunks, P.df_bchunks,
+             P.tail_cb, P.tail_ce, P.df_nfwd, P.df_snx_f, P.df_snx_b);
     items(P.fwd_ptr, P.fwd_rows, P.lrow_ptr, SOLVE_CHUNK_B, P.bfwd_items, P.bfwd_chunks, P.bfwd_chunk_ptr);
     items(P.bwd_ptr, P.bwd_rows, P.urow_ptr, SOLVE_CHUNK_B, P.bbwd_items, P.bbwd_chunks, P.bbwd_chunk_ptr);
     // batched: the tail's values for 32 sets sit in shared memory, so at most
     // TAIL_MAX_B rows of the dense block (a trailing part of it is dense too)
     P.btail_t0 = (P.tail_t0 < n) ? std::max<int32_t>(P.tail_t0, n - TAIL_MAX_B) : n;
-    std::vector<int32_t> snx_f_b, snx_b_b;   // (no blocks in the batched solve)
-    build_df(P, SOLVE_CHUNK_B, P.btail_t0, false, P.df_items_b, P.bdf_fchunks, P.bdf_bchunks, P.btail_cb, P.btail_ce,
-             P.bdf_nfwd, snx_f_b, snx_b_b);
+    build_df(P, SOLVE_CHUNK_B, P.btail_t0, opt.solve_blocks != 0 ? SN_MAX_B : 0, P.df_items_b, P.bdf_fchunks,
+             P.bdf_bchunks, P.btail_cb, P.btail_ce, P.bdf_nfwd, P.bdf_snx_f, P.bdf_snx_b);
 }
 
 }  // namespace

@@ -110,6 +110,7 @@ struct glu_handle {
     DFItem *d_bdf_items = nullptr;     // batched solve schedule (shorter chunks, smaller tail)
     SolveChunk *d_bfwd_chunks = nullptr, *d_bbwd_chunks = nullptr;
     int32_t *d_btail_cb = nullptr, *d_btail_ce = nullptr;
+    int32_t *d_bsnx_f = nullptr, *d_bsnx_b = nullptr;
     // solve scratch (grown on demand): permuted vector, staging, partials
     double *d_work = nullptr;
     double *d_bstage = nullptr;
@@ -623,7 +624,8 @@ int upload_plan(glu_handle *h) {
            o_acs = c.take<int64_t>(P.acsr_src.size()), o_acv = c.take<double>(P.acsr_src.size()),
            o_bdfi = c.take<int32_t>(P.df_items_b.size()), o_bfc = c.take<SolveChunk>(P.bdf_fchunks.size()),
            o_bbc = c.take<SolveChunk>(P.bdf_bchunks.size()), o_btcb = c.take<int32_t>(P.btail_cb.size()),
-           o_btce = c.take<int32_t>(P.btail_ce.size()),
+           o_btce = c.take<int32_t>(P.btail_ce.size()), o_bsnf = c.take<int32_t>(P.bdf_snx_f.size()),
+           o_bsnb = c.take<int32_t>(P.bdf_snx_b.size()),
            o_gbar = c.take<unsigned>(2),
            o_snc0 = c.take<int32_t>(P.sn_c0.size()), o_snr = c.take<int32_t>(P.sn_r.size()),
            o_bdg = c.take<int32_t>(P.bdiag.size()), o_bit = c.take<BItem>(P.bitems.size()),
@@ -671,6 +673,8 @@ int upload_plan(glu_handle *h) {
     h->d_bbwd_chunks = at<SolveChunk>(A, o_bbc);
     h->d_btail_cb = at<int32_t>(A, o_btcb);
     h->d_btail_ce = at<int32_t>(A, o_btce);
+    h->d_bsnx_f = at<int32_t>(A, o_bsnf);
+    h->d_bsnx_b = at<int32_t>(A, o_bsnb);
     h->d_gbar = at<unsigned>(A, o_gbar);
     int64_t *d_lcp = at<int64_t>(A, o_lcp);
     h->d_lu_colptr = d_lcp;
@@ -713,6 +717,8 @@ int upload_plan(glu_handle *h) {
     CK(upload(h->d_bbwd_chunks, P.bdf_bchunks));
     CK(upload(h->d_btail_cb, P.btail_cb));
     CK(upload(h->d_btail_ce, P.btail_ce));
+    CK(upload(h->d_bsnx_f, P.bdf_snx_f));
+    CK(upload(h->d_bsnx_b, P.bdf_snx_b));
     CK(cudaMemset(h->d_flags, 0, std::max<int64_t>(h->n_flags, 1) * sizeof(int32_t)));
     CK(cudaMemset(h->d_serr, 0xff, sizeof(unsigned long long)));
     {
@@ -1371,7 +1377,7 @@ int enqueue_factor_b(glu_handle *h, T *lu, int32_t B, int32_t S, cudaStream_t st
         r.row_begin = l < nl ? P.lvl_row_ptr[l] : 0;
         r.lane_begin = l < nl ? P.lvl_lane_ptr[l] : 0;
         r.t_end = l < nl ? P.lvl_task_ptr[l + 1] : 0;
-        r.n_begin = P.lvl_norm_ptr[l];
+            r.n_begin = P.lvl_norm_ptr[l];
         r.n_end = P.lvl_norm_ptr[l + 1];
         CKL((r.t_end - r.t_begin) + (r.n_end - r.n_begin) > 0, launch_level_b<T>(a, h->map_bytes, r, S, h->num_sms, st));
     }
@@ -1474,7 +1480,8 @@ int enqueue_solve_b(glu_handle *h, const T *lu, const double *in, double *out, i
     d.abort = h->d_abort;
     d.err = h->d_serr;
     d.spin_limit_cycles = h->spin_cycles;
-    d.fsnx = d.bsnx = nullptr;
+    d.fsnx = h->d_bsnx_f;
+    d.bsnx = h->d_bsnx_b;
     TailArgs ta{P.btail_t0, h->d_btail_cb, h->d_btail_ce, d.bready, d.epoch};
     CKL(4 + (P.btail_t0 < n), launch_solve_b<T>(sa, d, P.bdf_nfwd, h->d_lu_colptr, ta, in, out, y, z, h->d_perm, nrhs, S,
                                                 h->num_sms, st));

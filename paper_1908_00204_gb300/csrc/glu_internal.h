@@ -111,6 +111,7 @@ constexpr int32_t TAIL_MIN = 32, TAIL_MAX = 1024;   // dense-tail solve size ran
 constexpr int32_t TAIL_MAX_B = 768;                 // batched: tail rows x 32 sets in shared memory
 constexpr int32_t FTAIL_MIN = 64, FTAIL_MAX = 3200;  // dense-tail factorization size range
 constexpr int32_t SN_MIN = 4, SN_MAX = 128;          // dense diagonal blocks of the dataflow solve
+constexpr int32_t SN_MAX_B = 32;                     // the same in the batched solve (rows in registers)
 
 // Everything glu_analyze computes on the host.
 struct HostPlan {
@@ -172,6 +173,7 @@ struct HostPlan {
     int32_t bdf_nfwd = 0, btail_t0 = 0;
     std::vector<SolveChunk> bdf_fchunks, bdf_bchunks;
     std::vector<int32_t> btail_cb, btail_ce;
+    std::vector<int32_t> bdf_snx_f, bdf_snx_b;
     // supernodal factorization (built when the block mode is selected)
     std::vector<int32_t> sn_c0;          // nsn + 1 column boundaries
     std::vector<int32_t> sn_r;           // |R_B|

@@ -260,6 +260,60 @@ __global__ void __launch_bounds__(128) k_solve_df_b(const SolveArgs<T> s, const 
         int32_t *ready = bwd ? a.bready : a.fready;
         const T *src = bwd ? z : y;
         const T *lub = s.lu + b;
+        if (it.flags & DF_BLOCK) {
+            // a dense diagonal block [c0, c1) of at most SN_MAX_B rows for this
+            // group: lane = set, the block's values of the set in registers,
+            // swept a column at a time (forward: rows below subtract L(i, jj)
+            // y(jj); backward: z(jj) = y(jj) / U(jj, jj), rows above subtract)
+            const int32_t c0 = it.row, ns = it.cb - it.row;
+            const int32_t *snx = (bwd ? a.bsnx : a.fsnx) + it.ce;
+            const int32_t *crd = bwd ? a.bchunk_ready : a.fchunk_ready;
+            for (int32_t c = snx[0] + lane; c < snx[ns]; c += 32) wait_b(crd + (int64_t)c * G + g, a);
+            __syncwarp();
+            const T *partial = static_cast<const T *>(bwd ? a.bpartial_v : a.fpartial_v);
+            for (int32_t r = 0; r < nrhs; r++) {
+                T v[SN_MAX_B];
+#pragma unroll
+                for (int kk = 0; kk < SN_MAX_B; kk++) {
+                    T x = (T)0;
+                    if (kk < ns) {
+                        x = __ldcg(y + ((int64_t)r * n + c0 + kk) * S + b);
+                        for (int32_t c = snx[kk]; c < snx[kk + 1]; c++)
+                            x -= __ldcg(partial + (((int64_t)c * nrhs) + r) * S + b);
+                    }
+                    v[kk] = x;
+                }
+                if (!bwd) {
+#pragma unroll
+                    for (int jj = 0; jj < SN_MAX_B; jj++) {
+                        if (jj + 1 < ns) {
+                            const int64_t base = s.diag_pos[c0 + jj] - jj;
+#pragma unroll
+                            for (int ii = jj + 1; ii < SN_MAX_B; ii++)
+                                if (ii < ns) v[ii] = v[ii] - lub[(base + ii) * S] * v[jj];
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int jj = SN_MAX_B - 1; jj >= 0; jj--) {
+                        if (jj < ns) {
+                            const int64_t dp = s.diag_pos[c0 + jj];
+                            v[jj] = v[jj] / lub[dp * S];
+                            const int64_t base = dp - jj;
+#pragma unroll
+                            for (int ii = 0; ii < jj; ii++) v[ii] = v[ii] - lub[(base + ii) * S] * v[jj];
+                        }
+                    }
+                }
+                T *out = (bwd ? z : y) + ((int64_t)r * n + c0) * S + b;
+#pragma unroll
+                for (int kk = 0; kk < SN_MAX_B; kk++)
+                    if (kk < ns) out[(int64_t)kk * S] = v[kk];
+            }
+            __syncwarp();
+            for (int32_t kk = lane; kk < ns; kk += 32) st_release_b(ready + (int64_t)(c0 + kk) * G + g, a.epoch);
+            continue;
+        }
         if (it.flags & DF_CHUNK) {
             const SolveChunk ch = (bwd ? a.bchunks : a.fchunks)[it.chunk];
             T *partial = static_cast<T *>(bwd ? a.bpartial_v : a.fpartial_v);

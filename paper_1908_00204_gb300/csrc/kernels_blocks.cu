@@ -114,9 +114,17 @@ __global__ void __launch_bounds__(BW * 32) k_bpanel(const BlockArgs<T> a, int32_
             const int32_t m = lane;
             const bool own = m >= bp.f && m < s;
             T x = own ? a.lu[bp.upos + (m - bp.f)] : (T)0;
-            for (int32_t jj = bp.f; jj + 1 < s; jj++) {
-                const T xj = __shfl_sync(0xffffffffu, x, jj);
-                if (own && m > jj) x = x - a.lu[a.diag_pos[c0 + jj] + (m - jj)] * xj;
+            // lane m's row of L11, loaded before the sweep
+            T l11[BSN_MAX];
+#pragma unroll
+            for (int jj = 0; jj < BSN_MAX; jj++)
+                l11[jj] = (own && jj >= bp.f && jj < m) ? a.lu[a.diag_pos[c0 + jj] + (m - jj)] : (T)0;
+#pragma unroll
+            for (int jj = 0; jj + 1 < BSN_MAX; jj++) {
+                if (jj >= bp.f && jj + 1 < s) {
+                    const T xj = __shfl_sync(0xffffffffu, x, jj);
+                    if (own && m > jj) x = x - l11[jj] * xj;
+                }
             }
             if (own) a.lu[bp.upos + (m - bp.f)] = x;
         }
