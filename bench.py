@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="offered requests per second")
     ap.add_argument("--serve-requests", type=int, default=3000, help="timed requests (after a tenth as warm-up)")
     ap.add_argument("--serve-precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", metavar="WORKLOAD", default=None,
+                    help="instead of the step: FP32 factor + FP64 refinement against FP64 and the CPU "
+                         "oracle on one workload (backward errors, differences, times)")
     return ap.parse_args()
 
 
@@ -450,12 +453,77 @@ def run_serve(args):
     return 0
 
 
+def run_precision(args):
+    """FP32 factorization + FP64 iterative refinement to 1e-12 against the
+    FP64 factorization and the CPU oracle on one workload: backward errors
+    (host FP64), max differences of the solutions, times."""
+    import scipy.sparse as sp
+    import torch
+    import oracle
+    import paper_1908_00204_gb300 as g
+    name = args.precision
+    m = synth.make(name, 1)
+    out = {"metric": "FP32 factor + FP64 refinement vs FP64 and the oracle", "workload": name,
+           "n": m.n, "nnz_a": m.nnz}
+    t0 = time.perf_counter()
+    h = g.glu_analyze(m.n, m.colptr, m.rowidx, m.perm)
+    out["analyze_s"] = time.perf_counter() - t0
+    st = g.glu_get_stats(h)
+    out.update({k: st[k] for k in ("nnz_lu", "nlevels", "n_updates", "flops", "device_bytes")})
+    v = m.values(4001)
+    b = synth.rhs(m.n, 1, 4001)
+    A = sp.csc_matrix((v, m.rowidx, m.colptr), shape=(m.n, m.n))
+    anorm = abs(A).sum(axis=1).max()
+
+    def berr(x):
+        x = np.asarray(x).reshape(-1)
+        bb = b.reshape(-1)
+        return float(np.abs(bb - A @ x).max() / (anorm * np.abs(x).max() + np.abs(bb).max()))
+    vd, bd = torch.from_numpy(v).cuda(), torch.from_numpy(b).cuda()
+    for _ in range(2):
+        g.glu_factor(h, vd)
+    torch.cuda.synchronize()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record()
+    g.glu_factor(h, vd)
+    e1.record()
+    x64 = g.glu_solve(h, bd)
+    e2.record()
+    torch.cuda.synchronize()
+    out["fp64_factor_ms"], out["fp64_solve_ms"] = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    x64h = x64.cpu().numpy().reshape(-1)
+    out["fp64_berr"] = berr(x64h)
+    g.glu_factor_f32(h, vd)
+    torch.cuda.synchronize()
+    e0.record()
+    g.glu_factor_f32(h, vd)
+    e1.record()
+    x32, info = g.glu_solve_refine(h, bd, tol=1e-12, maxit=30)
+    e2.record()
+    torch.cuda.synchronize()
+    out["fp32_factor_ms"], out["fp32_refine_solve_ms"] = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    out["refine"] = info
+    x32h = x32.cpu().numpy().reshape(-1)
+    out["fp32_refine_berr"] = berr(x32h)
+    out["max_rel_diff_refined_vs_fp64"] = float(np.abs(x32h - x64h).max() / np.abs(x64h).max())
+    t0 = time.perf_counter()
+    xo = np.asarray(oracle.Factorization(m.n, m.colptr, m.rowidx, m.perm, v).solve(b)).reshape(-1)
+    out["oracle_s"] = time.perf_counter() - t0
+    out["oracle_berr"] = berr(xo)
+    out["max_rel_diff_fp64_vs_oracle"] = float(np.abs(x64h - xo).max() / np.abs(xo).max())
+    out["max_rel_diff_refined_vs_oracle"] = float(np.abs(x32h - xo).max() / np.abs(xo).max())
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.serve:
         return run_serve(args)
+    if args.precision:
+        return run_precision(args)
     return run_ours(args)
 
 
