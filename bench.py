@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="offered requests per second")
     ap.add_argument("--serve-requests", type=int, default=3000, help="timed requests (after a tenth as warm-up)")
     ap.add_argument("--serve-precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--batched", action="store_true",
+                    help="instead of the step: the batched FP64 refactorization of 256 value sets of the "
+                         "20k-unknown matrix, timed per factorization, with its bandwidth roofline")
     ap.add_argument("--precision", metavar="WORKLOAD", default=None,
                     help="instead of the step: FP32 factor + FP64 refinement against FP64 and the CPU "
                          "oracle on one workload (backward errors, differences, times)")
@@ -453,6 +456,59 @@ def run_serve(args):
     return 0
 
 
+def run_batched(args):
+    """The batched refactorization alone: 256 Monte-Carlo value sets of the
+    20k-unknown matrix in one graph launch, CUDA events per factorization, L2
+    flushed between them.  Lanes run over value sets, so every update streams
+    the target (read + write) and L(i,j) of 32 sets at a time: the algorithmic
+    bytes per update and set are 16 (targets only, L from cache) to 24."""
+    import torch
+    import paper_1908_00204_gb300 as g
+    g.build.build()
+    g.load_library()
+    dev = torch.device("cuda", 0)
+    mb = synth.make("mesh100x200_nets64", 1)
+    B = 256
+    V = torch.from_numpy(np.stack([mb.values(100 + i, sigma=0.1, base_seed=5) for i in range(B)])).to(dev)
+    hb = g.glu_analyze(mb.n, mb.colptr, mb.rowidx, mb.perm)
+    stream = torch.cuda.current_stream(dev)
+    g.glu_set_stream(hb, stream)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(max(args.warmup, 3)):
+        g.glu_factor_batched(hb, V)
+    g.glu_sync(hb)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.glu_factor_batched(hb, V)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    g.glu_sync(hb)
+    st = g.glu_get_stats(hb)
+    ms = float(np.median(ts))
+    upd = float(st["n_updates"]) * B
+    hbm = measured_hbm_gbs()
+    lo, hi = 16.0 * upd / (ms * 1e-3) / 1e9, 24.0 * upd / (ms * 1e-3) / 1e9
+    line = {"metric": "batched FP64 refactorizations per second (256 value sets, n=20,064)",
+            "value": B * 1e3 / ms, "unit": "refactorizations/s", "higher_is_better": True,
+            "ms_per_batch": ms, "gflops": st["flops"] * B / (ms * 1e-3) / 1e9, "dtype": "f64",
+            "roofline": {"bound": "hbm", "achieved": lo, "achieved_upper": hi, "peak": hbm, "unit": "GB/s",
+                         "frac": lo / hbm if hbm else None, "frac_upper": hi / hbm if hbm else None,
+                         "traffic": None, "kernel": "k_level_b (one level of the batched sweep)",
+                         "algorithmic_bytes": "16-24 per update and value set (target read+write, L(i,j))",
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+            "config": {"workload": "mesh100x200_nets64", "sets": B, "updates_per_set": st["n_updates"],
+                       "l2": "flushed between factorizations"},
+            "steps": args.steps, "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    g.glu_destroy(hb)
+    return 0
+
+
 def run_precision(args):
     """FP32 factorization + FP64 iterative refinement to 1e-12 against the
     FP64 factorization and the CPU oracle on one workload: backward errors
@@ -524,6 +580,8 @@ def main():
         return run_serve(args)
     if args.precision:
         return run_precision(args)
+    if args.batched:
+        return run_batched(args)
     return run_ours(args)
 
 
