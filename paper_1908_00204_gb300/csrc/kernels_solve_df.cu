@@ -346,13 +346,16 @@ __global__ void __launch_bounds__(128) k_solve_df(const SolveArgs<T> s, const DF
 }
 
 // The dense tail, one block, one tail row per thread (at most 1024 rows),
-// its running value in a register.  Step jj of the forward sweep: the owner
-// of row jj publishes its final value in shared memory, one barrier, and
-// every row below subtracts L(i, jj) times it; the backward sweep does the
-// same with z(jj) = y(jj) / U(jj, jj) and the rows above.  The tail column
-// jj's entries are contiguous in the CSC values; each thread's coefficients
-// of the next TAIL_PF steps are loaded ahead into registers.
-constexpr int TAIL_PF = 8;
+// its running value in a register, columns taken TAIL_TB at a time.  For a
+// panel of columns j0..j0+TB-1 every thread loads its coefficients in them;
+// the warp owning the panel's rows solves the panel's triangle with shuffles
+// (row j0+u is final after the panel's columns before u), publishes the
+// values in shared memory, and after one barrier every row below subtracts
+// the panel's columns in order.  The backward sweep mirrors it (z(jj) =
+// y(jj) / U(jj, jj), rows above, columns descending).  Each row applies the
+// columns in the same order as a column-at-a-time sweep.  The tail column
+// jj's entries are contiguous in the CSC values.
+constexpr int TAIL_TB = 16;
 
 template <typename T>
 __global__ void __launch_bounds__(1024) k_solve_tail(const SolveArgs<T> s, const int64_t *__restrict__ lu_colptr,
@@ -364,6 +367,7 @@ __global__ void __launch_bounds__(1024) k_solve_tail(const SolveArgs<T> s, const
     int64_t *ucol = lcol + NT;                                // U(t0+ii, t0+jj) at ucol[jj] + ii
     T *bc = reinterpret_cast<T *>(ucol + NT);                 // published values
     const int32_t ii = threadIdx.x;
+    const int lane = ii & 31;
     const bool own = ii < NT;
     for (int32_t q = ii; q < NT; q += blockDim.x) {
         lcol[q] = s.diag_pos[t0 + q] - q;
@@ -377,62 +381,63 @@ __global__ void __launch_bounds__(1024) k_solve_tail(const SolveArgs<T> s, const
             v = __ldcg(y + (int64_t)r * n + t0 + ii);
             for (int32_t c = ta.cb[ii]; c < ta.ce[ii]; c++) v -= __ldcg(fpartial + (int64_t)c * nrhs + r);
         }
-        // forward
-        T cur[TAIL_PF], nxt[TAIL_PF];
+        // forward, panels j0 = 0, TB, 2TB, ... (a panel's rows lie in one warp)
+        for (int32_t j0 = 0; j0 < NT; j0 += TAIL_TB) {
+            const int32_t jn = min(TAIL_TB, NT - j0);
+            T lv[TAIL_TB];
 #pragma unroll
-        for (int u = 0; u < TAIL_PF; u++) {
-            const int32_t jj = u;
-            cur[u] = (own && ii > jj && jj < NT) ? s.lu[lcol[jj] + ii] : (T)0;
-        }
-        for (int32_t jb = 0; jb < NT; jb += TAIL_PF) {
+            for (int u = 0; u < TAIL_TB; u++)
+                lv[u] = (own && u < jn && ii > j0 + u) ? s.lu[lcol[j0 + u] + ii] : (T)0;
+            if ((ii >> 5) == (j0 >> 5)) {
+                const int base = j0 & 31;
+                const bool inside = own && ii >= j0 && ii < j0 + jn;
 #pragma unroll
-            for (int u = 0; u < TAIL_PF; u++) {
-                const int32_t jj = jb + TAIL_PF + u;
-                nxt[u] = (own && ii > jj && jj < NT) ? s.lu[lcol[jj] + ii] : (T)0;
-            }
-#pragma unroll
-            for (int u = 0; u < TAIL_PF; u++) {
-                const int32_t jj = jb + u;
-                if (jj < NT) {
-                    if (ii == jj) bc[jj] = v;
-                    __syncthreads();
-                    if (own && ii > jj) v = v - cur[u] * bc[jj];
+                for (int u = 0; u < TAIL_TB; u++) {
+                    if (u < jn) {
+                        const T vu = __shfl_sync(0xffffffffu, v, base + u);
+                        if (inside && ii > j0 + u) v = v - lv[u] * vu;
+                    }
                 }
+                if (inside) bc[ii] = v;
             }
+            __syncthreads();
+            if (own && ii >= j0 + jn) {
 #pragma unroll
-            for (int u = 0; u < TAIL_PF; u++) cur[u] = nxt[u];
+                for (int u = 0; u < TAIL_TB; u++)
+                    if (u < jn) v = v - lv[u] * bc[j0 + u];
+            }
         }
         __syncthreads();
-        // backward (the published slots are reused: every forward read is
-        // behind the barrier above)
+        // backward, panels from the last (aligned) one down
         T *zr = z + (int64_t)r * n;
-        const int32_t top = NT - 1;
+        for (int32_t j0 = ((NT - 1) / TAIL_TB) * TAIL_TB; j0 >= 0; j0 -= TAIL_TB) {
+            const int32_t jn = min(TAIL_TB, NT - j0);
+            T lv[TAIL_TB];
 #pragma unroll
-        for (int u = 0; u < TAIL_PF; u++) {
-            const int32_t jj = top - u;
-            cur[u] = (own && ii < jj && jj >= 0) ? s.lu[ucol[jj] + ii] : (T)0;
-        }
-        for (int32_t jb = top; jb >= 0; jb -= TAIL_PF) {
+            for (int u = 0; u < TAIL_TB; u++)
+                lv[u] = (own && u < jn && ii < j0 + u) ? s.lu[ucol[j0 + u] + ii] : (T)0;
+            if ((ii >> 5) == (j0 >> 5)) {
+                const int base = j0 & 31;
+                const bool inside = own && ii >= j0 && ii < j0 + jn;
 #pragma unroll
-            for (int u = 0; u < TAIL_PF; u++) {
-                const int32_t jj = jb - TAIL_PF - u;
-                nxt[u] = (own && ii < jj && jj >= 0) ? s.lu[ucol[jj] + ii] : (T)0;
-            }
-#pragma unroll
-            for (int u = 0; u < TAIL_PF; u++) {
-                const int32_t jj = jb - u;
-                if (jj >= 0) {
-                    if (ii == jj) {
-                        v = v / d;
-                        bc[jj] = v;
-                        zr[t0 + jj] = v;
+                for (int u = TAIL_TB - 1; u >= 0; u--) {
+                    if (u < jn) {
+                        if (inside && ii == j0 + u) v = v / d;
+                        const T zu = __shfl_sync(0xffffffffu, v, base + u);
+                        if (inside && ii < j0 + u) v = v - lv[u] * zu;
                     }
-                    __syncthreads();
-                    if (own && ii < jj) v = v - cur[u] * bc[jj];
+                }
+                if (inside) {
+                    bc[ii] = v;
+                    zr[t0 + ii] = v;
                 }
             }
+            __syncthreads();
+            if (own && ii < j0) {
 #pragma unroll
-            for (int u = 0; u < TAIL_PF; u++) cur[u] = nxt[u];
+                for (int u = TAIL_TB - 1; u >= 0; u--)
+                    if (u < jn) v = v - lv[u] * bc[j0 + u];
+            }
         }
         __syncthreads();
     }
