@@ -13,6 +13,7 @@
 #include <chrono>
 #include <cstring>
 #include <numeric>
+#include <thread>
 
 #include "glu_internal.h"
 
@@ -279,21 +280,31 @@ void schedule(HostPlan &P, const glu_options &opt, int num_sms) {
     P.pair_map[npairs] = acc;
     P.n_updates = acc;
 
-    std::vector<PSeg> psegs;
     P.tasks.clear();
     P.lvl_task_ptr.assign((size_t)nl + 1, 0);
     P.lvl_row_ptr.assign((size_t)nl, 0);
     P.lvl_lane_ptr.assign((size_t)nl, 0);
     const int64_t lane_max = 64;    // tasks up to this many updates run on one lane
     P.level_mode.assign((size_t)nl, 0);
+    (void)num_sms;
+    // Levels are scheduled independently: contiguous ranges of levels run on
+    // host threads, each into its own segment and task lists (task segment
+    // indices and level task offsets relative to them), concatenated in level
+    // order afterwards -- the result does not depend on the thread count.
+    struct Part {
+        std::vector<PSeg> psegs;
+        std::vector<Task> tasks;
+        std::vector<int32_t> tend, rowp, lanep;   // per level, relative to tasks
+        std::vector<int8_t> mode;
+    };
+    auto run_levels = [&](int32_t l0, int32_t l1, Part &pt) {
+    std::vector<PSeg> &psegs = pt.psegs;
     std::vector<Task> lvl_tasks;
     // per-chunk scratch for splitting one group
     std::vector<int64_t> chunk_work;
     std::vector<std::vector<PSeg>> chunk_segs;
     std::vector<int32_t> touched;
-
-    (void)num_sms;
-    for (int32_t l = 0; l < nl; l++) {
+    for (int32_t l = l0; l < l1; l++) {
         lvl_tasks.clear();
         int64_t g = lvl_pair_ptr[l];
         const int64_t ge_l = lvl_pair_ptr[l + 1];
@@ -483,36 +494,90 @@ void schedule(HostPlan &P, const glu_options &opt, int num_sms) {
             if (ka != kb) return ka < kb;
             return a.work > b.work;
         });
-        const int32_t tb = (int32_t)P.tasks.size();
-        P.tasks.insert(P.tasks.end(), lvl_tasks.begin(), lvl_tasks.end());
-        P.lvl_task_ptr[l + 1] = (int32_t)P.tasks.size();
+        const int32_t tb = (int32_t)pt.tasks.size();
+        pt.tasks.insert(pt.tasks.end(), lvl_tasks.begin(), lvl_tasks.end());
+        const int32_t te = (int32_t)pt.tasks.size();
         int32_t r = tb, ln = tb;
-        for (int32_t q = tb; q < P.lvl_task_ptr[l + 1]; q++) {
-            if (P.tasks[q].kind == KIND_SRC) { r = q + 1; ln = q + 1; }
-            else if (P.tasks[q].kind == KIND_ROW) ln = q + 1;
+        for (int32_t q = tb; q < te; q++) {
+            if (pt.tasks[q].kind == KIND_SRC) { r = q + 1; ln = q + 1; }
+            else if (pt.tasks[q].kind == KIND_ROW) ln = q + 1;
         }
-        P.lvl_row_ptr[l] = r;
-        P.lvl_lane_ptr[l] = ln;
+        pt.tend.push_back(te);
+        pt.rowp.push_back(r);
+        pt.lanep.push_back(ln);
         const int32_t width = P.level_ptr[l + 1] - P.level_ptr[l];
         const int32_t tail = opt.tail_threshold > 0 ? opt.tail_threshold : 0;
         const int32_t wide = opt.wide_threshold > 0 ? opt.wide_threshold : 256;
         int8_t mode = width <= tail ? 2 : (width > wide ? 0 : 1);
         if (opt.mode_force >= 0 && opt.mode_force <= 2) mode = (int8_t)opt.mode_force;
-        P.level_mode[l] = mode;
-        P.levels_by_mode[mode]++;
+        pt.mode.push_back(mode);
     }
-
-    // flatten the segments into self-contained records
-    P.segs.resize(psegs.size());
-    for (size_t q = 0; q < psegs.size(); q++) {
-        const PSeg &ps = psegs[q];
-        Seg &sg = P.segs[q];
-        sg.pos = P.pair_pos[ps.pair];
-        sg.dj = P.diag_pos[P.pair_j[ps.pair]];
-        sg.mb = P.pair_map[ps.pair];
-        sg.t0 = ps.t0;
-        sg.t1 = ps.t1;
+    };
+    // ranges of levels with about equal numbers of pairs
+    const int nth = std::max(1, std::min<int>(16, (int)std::thread::hardware_concurrency()));
+    std::vector<int32_t> cut(1, 0);
+    for (int t = 1; t < nth; t++) {
+        const int64_t want = npairs * t / nth;
+        const int32_t l = (int32_t)(std::lower_bound(lvl_pair_ptr.begin(), lvl_pair_ptr.end(), want) -
+                                    lvl_pair_ptr.begin());
+        cut.push_back(std::max(cut.back(), std::min(l, nl)));
     }
+    cut.push_back(nl);
+    std::vector<Part> parts(cut.size() - 1);
+    {
+        std::vector<std::thread> th;
+        for (size_t t = 1; t < parts.size(); t++)
+            if (cut[t + 1] > cut[t]) th.emplace_back(run_levels, cut[t], cut[t + 1], std::ref(parts[t]));
+        run_levels(cut[0], cut[1], parts[0]);
+        for (std::thread &x : th) x.join();
+    }
+    // concatenate: each part's tasks and segments go to their offsets (the
+    // segments flattened into self-contained records), in parallel
+    std::vector<int64_t> sbase(parts.size() + 1, 0), tbase(parts.size() + 1, 0);
+    for (size_t t = 0; t < parts.size(); t++) {
+        sbase[t + 1] = sbase[t] + (int64_t)parts[t].psegs.size();
+        tbase[t + 1] = tbase[t] + (int64_t)parts[t].tasks.size();
+    }
+    P.tasks.resize((size_t)tbase[parts.size()]);
+    P.segs.resize((size_t)sbase[parts.size()]);
+    auto place = [&](size_t t) {
+        const Part &pt = parts[t];
+        const int32_t sb = (int32_t)sbase[t];
+        for (size_t q = 0; q < pt.tasks.size(); q++) {
+            Task tk = pt.tasks[q];
+            tk.seg_begin += sb;
+            tk.seg_end += sb;
+            P.tasks[(size_t)tbase[t] + q] = tk;
+        }
+        for (size_t q = 0; q < pt.psegs.size(); q++) {
+            const PSeg &ps = pt.psegs[q];
+            Seg &sg = P.segs[(size_t)sbase[t] + q];
+            sg.pos = P.pair_pos[ps.pair];
+            sg.dj = P.diag_pos[P.pair_j[ps.pair]];
+            sg.mb = P.pair_map[ps.pair];
+            sg.t0 = ps.t0;
+            sg.t1 = ps.t1;
+        }
+    };
+    {
+        std::vector<std::thread> th;
+        for (size_t t = 1; t < parts.size(); t++) th.emplace_back(place, t);
+        place(0);
+        for (std::thread &x : th) x.join();
+    }
+    for (size_t t = 0; t < parts.size(); t++) {
+        const Part &pt = parts[t];
+        const int32_t tb = (int32_t)tbase[t];
+        for (int32_t q = 0; q < cut[t + 1] - cut[t]; q++) {
+            const int32_t l = cut[t] + q;
+            P.lvl_task_ptr[l + 1] = tb + pt.tend[q];
+            P.lvl_row_ptr[l] = tb + pt.rowp[q];
+            P.lvl_lane_ptr[l] = tb + pt.lanep[q];
+            P.level_mode[l] = pt.mode[q];
+            P.levels_by_mode[pt.mode[q]]++;
+        }
+    }
+    parts.clear();
 
     // normalization items: level l's columns run in level l+1's kernel; the
     // last level's columns in the final pass
@@ -1049,10 +1114,13 @@ int analyze_host(int32_t n, const int32_t *colptr, const int32_t *rowidx, const 
     // the column schedule (and its position map) is only built here for the
     // column-level factorization; the supernodal one builds it on demand
     // (the batched path runs column levels)
+    // the solve's schedule reads only the fill and its row views: it is built
+    // on its own thread while the factorization's schedule is built
+    std::thread solve_thread([&P, &opt] { solve_levels(P, opt); });
     if (opt.factor_blocks == 0) schedule(P, opt, num_sms);
     factor_tail(P, opt);
     if (opt.factor_blocks != 0) block_schedule(P);
-    solve_levels(P, opt);
+    solve_thread.join();
     // A in compressed rows (original numbering), for residuals
     P.acsr_ptr.assign((size_t)n + 1, 0);
     for (int64_t p = 0; p < P.nnz_a; p++) P.acsr_ptr[P.a_rowidx[p] + 1]++;

@@ -367,7 +367,6 @@ __global__ void __launch_bounds__(1024) k_solve_tail(const SolveArgs<T> s, const
     int64_t *ucol = lcol + NT;                                // U(t0+ii, t0+jj) at ucol[jj] + ii
     T *bc = reinterpret_cast<T *>(ucol + NT);                 // published values
     const int32_t ii = threadIdx.x;
-    const int lane = ii & 31;
     const bool own = ii < NT;
     for (int32_t q = ii; q < NT; q += blockDim.x) {
         lcol[q] = s.diag_pos[t0 + q] - q;
