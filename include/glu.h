@@ -278,6 +278,18 @@ int glu_last_error_info(const glu_handle *h, int32_t *column);
  * GLU_ERR_TOO_LARGE, GLU_ERR_CUDA. */
 int glu_solve_noalloc(glu_handle *h, const double *b, double *x, int32_t nrhs);
 
+/* A fill-reducing symmetric ordering of the pattern of A + A^T, for callers
+ * without one (the paper's flow takes a fill-reducing order before the
+ * symbolic analysis, Section II-C and Fig. 5; it names MC64 + AMD, which are
+ * not reproduced): graph nested dissection -- level structures from a
+ * pseudo-peripheral vertex, the smallest level near the middle as separator,
+ * ordered last, sides ordered recursively, leaves of at most 32 vertices by
+ * minimum degree.  Host only.  colptr[n+1], rowidx[nnz]: A's CSC pattern
+ * (0-based; rows need not be sorted; the diagonal may be absent); perm[n]
+ * receives new -> old, to pass to glu_analyze.  Deterministic.  Errors:
+ * GLU_ERR_INVALID (bad arguments or indices). */
+int glu_order_nd(int32_t n, const int32_t *colptr, const int32_t *rowidx, int32_t *perm);
+
 /* Free the handle and everything it owns.  NULL is ignored. */
 void glu_destroy(glu_handle *h);
 

@@ -1240,6 +1240,14 @@ void glu_destroy(glu_handle *h) {
     delete h;
 }
 
+int glu_order_nd(int32_t n, const int32_t *colptr, const int32_t *rowidx, int32_t *perm) {
+    try {
+        return order_nested_dissection(n, colptr, rowidx, perm);
+    } catch (const std::bad_alloc &) {
+        return GLU_ERR_OOM;
+    }
+}
+
 const char *glu_strerror(int code) {
     switch (code) {
         case GLU_OK: return "ok";

@@ -206,6 +206,10 @@ struct HostPlan {
 int analyze_host(int32_t n, const int32_t *colptr, const int32_t *rowidx, const int32_t *perm,
                  const glu_options &opt, int num_sms, HostPlan &P, std::string &why);
 
+// Nested-dissection ordering of the pattern of A + A^T (order.cpp): perm[new]
+// = old.  Returns a GLU_ code.
+int order_nested_dissection(int32_t n, const int32_t *colptr, const int32_t *rowidx, int32_t *perm);
+
 // The column-level update schedule (pairs, segments, tasks, normalization
 // items) if analyze_host skipped it.
 void column_schedule(HostPlan &P, const glu_options &opt, int num_sms);

@@ -95,6 +95,7 @@ def load_library(path: Optional[str] = None):
             "glu_get_stats": (C.c_int, [P, C.POINTER(glu_stats)]),
             "glu_last_error_info": (C.c_int, [P, C.POINTER(i32)]),
             "glu_destroy": (None, [P]),
+            "glu_order_nd": (C.c_int, [i32, P, P, P]),
             "glu_strerror": (C.c_char_p, [C.c_int]),
         }
         for name, (res, args) in sig.items():
@@ -362,6 +363,15 @@ def glu_destroy(h: Handle) -> None:
     if h._ptr:
         load_library().glu_destroy(h._ptr)
         h._ptr = None
+
+
+def glu_order_nd(n: int, colptr, rowidx) -> np.ndarray:
+    """Nested-dissection ordering of the pattern of A + A^T: perm[new] = old."""
+    cp = np.ascontiguousarray(colptr, np.int32)
+    ri = np.ascontiguousarray(rowidx, np.int32)
+    perm = np.empty(max(n, 1), np.int32)
+    _check(load_library().glu_order_nd(int(n), cp.ctypes.data, ri.ctypes.data, perm.ctypes.data), "glu_order_nd")
+    return perm[:n]
 
 
 def glu_strerror(code: int) -> str:
