@@ -8,7 +8,8 @@
 // levels) are set aside and ordered last, by degree.  Of the rest, a subgraph
 // larger than a leaf is split by a level structure rooted at a
 // pseudo-peripheral vertex -- the smallest level near the middle is the
-// separator, ordered last -- and each side is ordered recursively; a leaf is
+// separator, thinned of vertices with neighbours on one side only, and ordered
+// last -- and each side is ordered recursively; a leaf is
 // ordered by minimum degree on its own elimination graph.  Deterministic:
 // ties go to the smaller original index.
 #include <algorithm>
@@ -109,7 +110,23 @@ public:
         std::vector<int32_t> a, b;
         for (size_t l = 0; l < best; l++) a.insert(a.end(), levels[l].begin(), levels[l].end());
         for (size_t l = best + 1; l < levels.size(); l++) b.insert(b.end(), levels[l].begin(), levels[l].end());
-        std::vector<int32_t> sep = levels[best];
+        // thin the separator: a vertex with no neighbour beyond it joins the
+        // near side, one with no neighbour before it the far side
+        for (size_t l = 0; l < levels.size(); l++)
+            for (int32_t v : levels[l]) level_[v] = (int32_t)l;
+        std::vector<int32_t> sep;
+        for (int32_t v : levels[best]) {
+            bool before = false, after = false;
+            for (int64_t p = g_.ptr[v]; p < g_.ptr[v + 1]; p++) {
+                const int32_t w = g_.adj[p];
+                if (mark_[w] != tag) continue;
+                before |= level_[w] < (int32_t)best;
+                after |= level_[w] > (int32_t)best;
+            }
+            if (!after) a.push_back(v);
+            else if (!before) b.push_back(v);
+            else sep.push_back(v);
+        }
         order(a, out);
         order(b, out);
         std::sort(sep.begin(), sep.end());
