@@ -21,13 +21,6 @@ namespace {
 
 constexpr int BU = 4;   // rows per batch of independent loads
 
-template <typename T>
-__device__ __forceinline__ T fms(T l, T f, T t);   // t - l * f, one rounding
-template <>
-__device__ __forceinline__ double fms<double>(double l, double f, double t) { return fma(-l, f, t); }
-template <>
-__device__ __forceinline__ float fms<float>(float l, float f, float t) { return fmaf(-l, f, t); }
-
 __device__ __forceinline__ void raise_err_b(unsigned long long *err, int32_t col, unsigned code) {
     atomicMin(err, ((unsigned long long)(uint32_t)col << 8) | code);
 }
@@ -98,19 +91,19 @@ __global__ void __launch_bounds__(128) k_level_b(const FactorArgs<T> a, LevelRan
             T *tgt = lu + (sg.pos + 1) * S + b;
             for (int32_t tb = sg.t0; tb < sg.t1; tb += BU) {
                 int64_t off[BU];
-                T lv[BU], tv[BU];
+                T lv[BU];
 #pragma unroll
                 for (int u = 0; u < BU; u++)
                     if (tb + u < sg.t1) {
                         off[u] = (int64_t)mp[tb + u] * S;
                         lv[u] = L[(int64_t)(tb + u) * S];
                     }
+            // the targets take -L(i,j) f as reductions in L2; one lane (one
+            // value set) applies a task's segments in order, so each entry's
+            // additions come in a fixed order
 #pragma unroll
                 for (int u = 0; u < BU; u++)
-                    if (tb + u < sg.t1) tv[u] = tgt[off[u]];
-#pragma unroll
-                for (int u = 0; u < BU; u++)
-                    if (tb + u < sg.t1) tgt[off[u]] = fms<T>(lv[u], f, tv[u]);
+                    if (tb + u < sg.t1) atomicAdd(&tgt[off[u]], -lv[u] * f);
             }
         }
     }

@@ -115,8 +115,12 @@ constexpr int ROW_UNROLL = GLU_ROW_UNROLL;
 constexpr int LANE_UNROLL = GLU_LANE_UNROLL;
 
 // Rows t0..t1-1 of one segment, lanes over rows.  Within a segment every row
-// hits a different target entry, so all loads of a batch go out before any
-// store.
+// hits a different target entry, so all loads of a batch go out at once; the
+// target entries then take -L(i,j) f as reductions performed in L2
+// (red.global.add: no load of the target on the warp's path).  A level's
+// target entries have one owner warp, whose segments are separated by warp
+// barriers, so each entry's sequence of additions is fixed: the results are
+// the same from run to run.
 template <typename T, typename M>
 __device__ __forceinline__ void row_segment(T *__restrict__ lu, const M *__restrict__ map, const SegMeta<T> &m,
                                             int lane) {
@@ -125,7 +129,7 @@ __device__ __forceinline__ void row_segment(T *__restrict__ lu, const M *__restr
     T *tgt = lu + m.pos + 1;
     for (int32_t tb = m.t0 + lane; tb < m.t1; tb += 32 * ROW_UNROLL) {
         uint32_t off[ROW_UNROLL];
-        T lv[ROW_UNROLL], tv[ROW_UNROLL];
+        T lv[ROW_UNROLL];
 #pragma unroll
         for (int u = 0; u < ROW_UNROLL; u++) {
             const int32_t t = tb + 32 * u;
@@ -136,10 +140,7 @@ __device__ __forceinline__ void row_segment(T *__restrict__ lu, const M *__restr
         }
 #pragma unroll
         for (int u = 0; u < ROW_UNROLL; u++)
-            if (tb + 32 * u < m.t1) tv[u] = tgt[off[u]];
-#pragma unroll
-        for (int u = 0; u < ROW_UNROLL; u++)
-            if (tb + 32 * u < m.t1) tgt[off[u]] = fma_t<T>(-lv[u], m.f, tv[u]);
+            if (tb + 32 * u < m.t1) atomicAdd(&tgt[off[u]], -lv[u] * m.f);
     }
 }
 
@@ -272,7 +273,7 @@ __device__ __forceinline__ void lane_task(const FactorArgs<T> &a, const Task &tk
         T *tgt = a.lu + m.pos + 1;
         for (int32_t tb = m.t0; tb < m.t1; tb += LANE_UNROLL) {
             uint32_t off[LANE_UNROLL];
-            T lv[LANE_UNROLL], tv[LANE_UNROLL];
+            T lv[LANE_UNROLL];
 #pragma unroll
             for (int u = 0; u < LANE_UNROLL; u++)
                 if (tb + u < m.t1) {
@@ -281,10 +282,7 @@ __device__ __forceinline__ void lane_task(const FactorArgs<T> &a, const Task &tk
                 }
 #pragma unroll
             for (int u = 0; u < LANE_UNROLL; u++)
-                if (tb + u < m.t1) tv[u] = tgt[off[u]];
-#pragma unroll
-            for (int u = 0; u < LANE_UNROLL; u++)
-                if (tb + u < m.t1) tgt[off[u]] = fma_t<T>(-lv[u], m.f, tv[u]);
+                if (tb + u < m.t1) atomicAdd(&tgt[off[u]], -lv[u] * m.f);
         }
     }
 }
