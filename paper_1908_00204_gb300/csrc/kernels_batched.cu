@@ -7,8 +7,8 @@
 // every index (schedule, position map, pattern) is the same for all lanes and
 // every value access is 32 consecutive elements.  Each lane owns its own
 // matrix, so the right-looking update of a level (Algorithm 5 / Eq. 3) needs
-// no ordering between lanes and no atomics; a lane applies a task's segments
-// in order.  The dataflow solve and the FP64 refinement follow the single-
+// no ordering between lanes; a lane applies a task's segments in order, its
+// additions as L2 reductions.  The dataflow solve and the FP64 refinement follow the single-
 // matrix versions with lanes over the batch.
 #include <cuda_runtime.h>
 

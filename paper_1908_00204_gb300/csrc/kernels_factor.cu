@@ -8,9 +8,10 @@
 //   * update tasks: the submatrix update of Algorithm 5 / Eq. 3 for every
 //     (source j, target k) pair of the level, as
 //     A_s(i,k) -= A_s(i,j) * (A_s(j,k) / A_s(j,j))   for i in L(:,j).
-// Every target entry is written by exactly one warp per level (no atomics);
-// the order of the updates of an entry depends only on the pattern, so a
-// refactorization is deterministic run to run.
+// Every target entry is updated by exactly one warp (or lane) per level,
+// whose additions are L2 reductions issued in a fixed order (separated by
+// warp barriers); the order of the updates of an entry depends only on the
+// pattern, so a refactorization is deterministic run to run.
 #include <cuda_runtime.h>
 
 #include <cstdint>
