@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <array>
 #include <chrono>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <thread>
@@ -514,7 +515,8 @@ void schedule(HostPlan &P, const glu_options &opt, int num_sms) {
     }
     };
     // ranges of levels with about equal numbers of pairs
-    const int nth = std::max(1, std::min<int>(16, (int)std::thread::hardware_concurrency()));
+    int nth = std::max(1, std::min<int>(16, (int)std::thread::hardware_concurrency()));
+    if (const char *e = std::getenv("GLU_ANALYZE_THREADS")) nth = std::max(1, std::min(64, std::atoi(e)));
     std::vector<int32_t> cut(1, 0);
     for (int t = 1; t < nth; t++) {
         const int64_t want = npairs * t / nth;

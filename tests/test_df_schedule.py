@@ -155,3 +155,20 @@ def test_df_schedule_without_blocks(tmp_path, monkeypatch):
     items, nfwd, fch, bch, snf, snb, t0 = load_dump(path)
     assert len(snf) == 0 and len(snb) == 0
     assert not (items[:, 4] & 4).any()
+
+
+def test_schedule_independent_of_analysis_threads(tmp_path, monkeypatch):
+    """The column schedule is built over level ranges on host threads; the
+    result must not depend on their number (per-level summary and the
+    dataflow items compared between 1 and 7 threads)."""
+    m = synth.make("mesh100x200_nets64", 1)
+    out = {}
+    for nth in (1, 7):
+        monkeypatch.setenv("GLU_ANALYZE_THREADS", str(nth))
+        monkeypatch.setenv("GLU_DUMP_SCHEDULE", str(tmp_path / f"s{nth}.txt"))
+        monkeypatch.setenv("GLU_DUMP_DF", str(tmp_path / f"d{nth}.bin"))
+        h = glu.glu_analyze(m.n, m.colptr, m.rowidx, m.perm, glu.default_options(host_only=1))
+        out[nth] = (glu.glu_get_stats(h)["n_updates"], (tmp_path / f"s{nth}.txt").read_bytes(),
+                    (tmp_path / f"d{nth}.bin").read_bytes())
+        glu.glu_destroy(h)
+    assert out[1] == out[7]
