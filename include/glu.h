@@ -98,7 +98,7 @@ typedef struct glu_options {
                                  is factored as a dense matrix by one cooperative
                                  launch instead of one launch per level; 0: off */
     int32_t solve_blocks;     /* 1 (default): in the dataflow solve, dense diagonal blocks of
-                                 4..128 rows are solved by one warp each (their rows'
+                                 4..32 rows are solved by one warp each (their rows'
                                  entries outside the block as parallel partial sums); 0: off */
     int32_t factor_blocks;    /* 1: supernodal factorization -- runs of up to 32 columns with a
                                  dense diagonal block and equal structure below are factored

@@ -105,12 +105,19 @@ struct SolveChunk {
     int64_t p0;
     int64_t p1;
 };
-constexpr int64_t SOLVE_CHUNK = 128;    // single matrix: lanes over a row's entries
+#ifndef GLU_SOLVE_CHUNK
+#define GLU_SOLVE_CHUNK 128
+#endif
+constexpr int64_t SOLVE_CHUNK = GLU_SOLVE_CHUNK;   // single matrix: lanes over a row's entries (<= 128)
 constexpr int64_t SOLVE_CHUNK_B = 32;   // batched: lanes over the sets, entries in sequence
 constexpr int32_t TAIL_MIN = 32, TAIL_MAX = 1024;   // dense-tail solve size range
 constexpr int32_t TAIL_MAX_B = 768;                 // batched: tail rows x 32 sets in shared memory
 constexpr int32_t FTAIL_MIN = 64, FTAIL_MAX = 3200;  // dense-tail factorization size range
-constexpr int32_t SN_MIN = 4, SN_MAX = 128;          // dense diagonal blocks of the dataflow solve
+#ifndef GLU_SN_MAX
+#define GLU_SN_MAX 32
+#endif
+constexpr int32_t SN_MIN = 4, SN_MAX = GLU_SN_MAX;   // dense diagonal blocks of the dataflow solve
+                                                     // (a multiple of 32, <= 128; 32 measured best)
 constexpr int32_t SN_MAX_B = 32;                     // the same in the batched solve (rows in registers)
 
 // Everything glu_analyze computes on the host.

@@ -68,7 +68,7 @@ def replay(n, t0, items, ptr, cols, chunks, snx, backward):
         elif fl & 4:                          # a dense diagonal block [row, cb)
             c0, c1, off = row, cb, ce
             nblocks += 1
-            assert 4 <= c1 - c0 <= 128
+            assert 4 <= c1 - c0 <= 32
             for r in range(c0, c1):
                 b, e = ptr[r], ptr[r + 1]
                 if backward:
