@@ -58,7 +58,8 @@ extern "C" {
 #define GLU_ERR_TIMEOUT -7          /* a bounded device-side wait gave up */
 #define GLU_ERR_NOT_FACTORED -8     /* solve before a successful factorization */
 #define GLU_ERR_INTERNAL -9         /* an internal consistency check failed */
-#define GLU_ERR_TOO_LARGE -10       /* the problem does not fit glu_solve_noalloc's fixed scratch */
+#define GLU_ERR_TOO_LARGE -10       /* a fixed limit is exceeded: glu_solve_noalloc's scratch, or
+                                       2^31 segments / tasks in the factorization schedule */
 
 /* Size, in doubles, of the fixed device scratch array behind
  * glu_solve_noalloc (32 MiB). */
@@ -151,7 +152,9 @@ void glu_default_options(glu_options *opts);
  * among its dependencies) and the per-level update schedule, then uploads the
  * schedule to the current CUDA device.  On success *out holds a new handle.
  * Errors: GLU_ERR_INVALID (malformed input), GLU_ERR_STRUCT_SINGULAR,
- * GLU_ERR_OOM, GLU_ERR_CUDA. */
+ * GLU_ERR_OOM (host or device memory, including allocations on the
+ * analysis's worker threads), GLU_ERR_TOO_LARGE (the schedule's 32-bit record
+ * indices would overflow), GLU_ERR_CUDA. */
 int glu_analyze(int32_t n, const int32_t *colptr, const int32_t *rowidx,
                 const int32_t *perm, glu_handle **out);
 

@@ -10,16 +10,31 @@
 // triangular solves.
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <chrono>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <numeric>
+#include <system_error>
 #include <thread>
 
 #include "glu_internal.h"
 
 namespace glu {
 namespace {
+
+// Starts fn on a new thread (th must have room reserved), or runs it here
+// when no thread can be created: the analysis's results never depend on how
+// many threads ran it.
+template <class F>
+void spawn_or_run(std::vector<std::thread> &th, F fn) {
+    try {
+        th.emplace_back(fn);
+    } catch (const std::system_error &) {
+        fn();
+    }
+}
 
 double now_ms() {
     return std::chrono::duration<double, std::milli>(
@@ -237,8 +252,7 @@ void levelize(HostPlan &P) {
 // becomes KIND_ROW tasks (split by row ranges when large), a group with many
 // sources becomes one KIND_SRC task per touched 32-position chunk of column
 // k.  Each level's kernel also normalizes the previous level's L columns.
-void schedule(HostPlan &P, const glu_options &opt, int num_sms) {
-    P.has_schedule = true;
+int schedule(HostPlan &P, const glu_options &opt, int num_sms) {
     const int32_t n = P.n;
     const int32_t nl = (int32_t)P.level_ptr.size() - 1;
     const int64_t piece = opt.piece_updates > 0 ? opt.piece_updates : 1024;
@@ -280,6 +294,10 @@ void schedule(HostPlan &P, const glu_options &opt, int num_sms) {
     }
     P.pair_map[npairs] = acc;
     P.n_updates = acc;
+    if (opt.verbose)
+        std::fprintf(stderr, "glu_analyze: column schedule: %lld pairs, %lld updates\n", (long long)npairs,
+                     (long long)acc);
+    if (npairs > INT32_MAX) return GLU_ERR_TOO_LARGE;   // PSeg.pair is 32-bit
 
     P.tasks.clear();
     P.lvl_task_ptr.assign((size_t)nl + 1, 0);
@@ -298,6 +316,10 @@ void schedule(HostPlan &P, const glu_options &opt, int num_sms) {
         std::vector<int32_t> tend, rowp, lanep;   // per level, relative to tasks
         std::vector<int8_t> mode;
     };
+    // host-side fault injection for tests: GLU_TEST_FAIL_LEVEL=<l> makes the
+    // scheduling of level l fail as an allocation would
+    const char *fail_env = std::getenv("GLU_TEST_FAIL_LEVEL");
+    const int32_t fail_level = fail_env ? std::atoi(fail_env) : -1;
     auto run_levels = [&](int32_t l0, int32_t l1, Part &pt) {
     std::vector<PSeg> &psegs = pt.psegs;
     std::vector<Task> lvl_tasks;
@@ -306,6 +328,7 @@ void schedule(HostPlan &P, const glu_options &opt, int num_sms) {
     std::vector<std::vector<PSeg>> chunk_segs;
     std::vector<int32_t> touched;
     for (int32_t l = l0; l < l1; l++) {
+        if (l == fail_level) throw std::bad_alloc();
         lvl_tasks.clear();
         int64_t g = lvl_pair_ptr[l];
         const int64_t ge_l = lvl_pair_ptr[l + 1];
@@ -526,13 +549,25 @@ void schedule(HostPlan &P, const glu_options &opt, int num_sms) {
     }
     cut.push_back(nl);
     std::vector<Part> parts(cut.size() - 1);
+    // an allocation failure on a worker is handed to the caller's thread
+    std::atomic<bool> failed{false};
+    auto guarded = [&failed](auto &&fn) {
+        try {
+            fn();
+        } catch (const std::bad_alloc &) {
+            failed = true;
+        }
+    };
     {
         std::vector<std::thread> th;
+        th.reserve(parts.size());
         for (size_t t = 1; t < parts.size(); t++)
-            if (cut[t + 1] > cut[t]) th.emplace_back(run_levels, cut[t], cut[t + 1], std::ref(parts[t]));
-        run_levels(cut[0], cut[1], parts[0]);
+            if (cut[t + 1] > cut[t])
+                spawn_or_run(th, [&, t] { guarded([&] { run_levels(cut[t], cut[t + 1], parts[t]); }); });
+        guarded([&] { run_levels(cut[0], cut[1], parts[0]); });
         for (std::thread &x : th) x.join();
     }
+    if (failed) throw std::bad_alloc();
     // concatenate: each part's tasks and segments go to their offsets (the
     // segments flattened into self-contained records), in parallel
     std::vector<int64_t> sbase(parts.size() + 1, 0), tbase(parts.size() + 1, 0);
@@ -540,6 +575,8 @@ void schedule(HostPlan &P, const glu_options &opt, int num_sms) {
         sbase[t + 1] = sbase[t] + (int64_t)parts[t].psegs.size();
         tbase[t + 1] = tbase[t] + (int64_t)parts[t].tasks.size();
     }
+    // segment and task indices are 32-bit in the device records
+    if (sbase[parts.size()] > INT32_MAX || tbase[parts.size()] > INT32_MAX) return GLU_ERR_TOO_LARGE;
     P.tasks.resize((size_t)tbase[parts.size()]);
     P.segs.resize((size_t)sbase[parts.size()]);
     auto place = [&](size_t t) {
@@ -563,7 +600,8 @@ void schedule(HostPlan &P, const glu_options &opt, int num_sms) {
     };
     {
         std::vector<std::thread> th;
-        for (size_t t = 1; t < parts.size(); t++) th.emplace_back(place, t);
+        th.reserve(parts.size());
+        for (size_t t = 1; t < parts.size(); t++) spawn_or_run(th, [&place, t] { place(t); });
         place(0);
         for (std::thread &x : th) x.join();
     }
@@ -597,6 +635,8 @@ void schedule(HostPlan &P, const glu_options &opt, int num_sms) {
         }
         P.lvl_norm_ptr[l + 1] = (int32_t)P.norms.size();
     }
+    P.has_schedule = true;
+    return GLU_OK;
 }
 
 // Dense diagonal blocks ("supernodes") of the solve among the rows [0, t0):
@@ -970,6 +1010,8 @@ void factor_tail(HostPlan &P, const glu_options &opt) {
 // Solve levels: forward lf(i) = 1 + max lf(j) over L(i,j) != 0 (0 if none);
 // backward lb(i) = 1 + max lb(k) over U(i,k) != 0, k > i (0 if none).
 void solve_levels(HostPlan &P, const glu_options &opt) {
+    // host-side fault injection for tests (as GLU_TEST_FAIL_LEVEL)
+    if (std::getenv("GLU_TEST_FAIL_SOLVE")) throw std::bad_alloc();
     const int32_t n = P.n;
     std::vector<int32_t> lf((size_t)n, 0), lb((size_t)n, 0);
     int32_t nf = n ? 1 : 0, nb = n ? 1 : 0;
@@ -1041,8 +1083,8 @@ void solve_levels(HostPlan &P, const glu_options &opt) {
 
 }  // namespace
 
-void column_schedule(HostPlan &P, const glu_options &opt, int num_sms) {
-    if (!P.has_schedule) schedule(P, opt, num_sms);
+int column_schedule(HostPlan &P, const glu_options &opt, int num_sms) {
+    return P.has_schedule ? GLU_OK : schedule(P, opt, num_sms);
 }
 
 int analyze_host(int32_t n, const int32_t *colptr, const int32_t *rowidx, const int32_t *perm,
@@ -1094,6 +1136,9 @@ int analyze_host(int32_t n, const int32_t *colptr, const int32_t *rowidx, const 
     if (rc != GLU_OK) return rc;
     rc = symbolic(P, bptr, brow);
     if (rc != GLU_OK) return rc;
+    if (opt.verbose)
+        std::fprintf(stderr, "glu_analyze: symbolic fill %.0f ms, nnz(L+U) = %lld\n", now_ms() - t0,
+                     (long long)P.lu_colptr[n]);
     // value gather map: each B entry's position in its LU column
     const int64_t nnz = P.lu_colptr[n];
     P.gsrc.assign((size_t)nnz, -1);
@@ -1113,16 +1158,49 @@ int analyze_host(int32_t n, const int32_t *colptr, const int32_t *rowidx, const 
     double t2 = now_ms();
     levelize(P);
     double t3 = now_ms();
+    if (opt.verbose)
+        std::fprintf(stderr, "glu_analyze: row views %.0f ms, deps %.0f ms (%lld), levels %.0f ms (%d)\n",
+                     t1 - t0, t2 - t1, (long long)P.dep_ptr[n], t3 - t2, (int)P.level_ptr.size() - 1);
     // the column schedule (and its position map) is only built here for the
     // column-level factorization; the supernodal one builds it on demand
     // (the batched path runs column levels)
     // the solve's schedule reads only the fill and its row views: it is built
     // on its own thread while the factorization's schedule is built
-    std::thread solve_thread([&P, &opt] { solve_levels(P, opt); });
-    if (opt.factor_blocks == 0) schedule(P, opt, num_sms);
-    factor_tail(P, opt);
-    if (opt.factor_blocks != 0) block_schedule(P);
-    solve_thread.join();
+    // (an allocation failure on either thread is rethrown here once both
+    // have finished)
+    std::atomic<bool> solve_failed{false};
+    auto solve_job = [&P, &opt, &solve_failed] {
+        try {
+            solve_levels(P, opt);
+        } catch (const std::bad_alloc &) {
+            solve_failed = true;
+        }
+    };
+    std::thread solve_thread;
+    try {
+        solve_thread = std::thread(solve_job);
+    } catch (const std::system_error &) {
+    }
+    rc = GLU_OK;
+    bool failed = false;
+    try {
+        if (opt.factor_blocks == 0) rc = schedule(P, opt, num_sms);
+        if (rc == GLU_OK) {
+            factor_tail(P, opt);
+            if (opt.factor_blocks != 0) block_schedule(P);
+        }
+    } catch (const std::bad_alloc &) {
+        failed = true;
+    }
+    if (solve_thread.joinable())
+        solve_thread.join();
+    else if (!failed)
+        solve_job();
+    if (failed || solve_failed) throw std::bad_alloc();
+    if (rc != GLU_OK) {
+        why = "the column schedule has more than 2^31 segments, tasks or pairs";
+        return rc;
+    }
     // A in compressed rows (original numbering), for residuals
     P.acsr_ptr.assign((size_t)n + 1, 0);
     for (int64_t p = 0; p < P.nnz_a; p++) P.acsr_ptr[P.a_rowidx[p] + 1]++;

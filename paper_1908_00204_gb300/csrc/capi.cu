@@ -553,7 +553,12 @@ SolveArgs<double> sargs(glu_handle *h) {
 int setup_column_plan(glu_handle *h) {
     if (h->col_ready) return GLU_OK;
     HostPlan &P = h->P;
-    column_schedule(P, h->opt, h->num_sms);
+    try {
+        const int rc = column_schedule(P, h->opt, h->num_sms);
+        if (rc != GLU_OK) return rc;
+    } catch (const std::bad_alloc &) {
+        return GLU_ERR_OOM;
+    }
     Carve c;
     const size_t o_pj = c.take<int32_t>(P.pair_j.size()), o_ppos = c.take<int64_t>(P.pair_pos.size()),
                  o_pmap = c.take<int64_t>(P.pair_map.size()), o_segs = c.take<Seg>(P.segs.size()),
@@ -800,6 +805,7 @@ int glu_analyze_opts(int32_t n, const int32_t *colptr, const int32_t *rowidx, co
     try {
         rc = analyze_host(n, colptr, rowidx, perm, h->opt, sms, h->P, h->why);
     } catch (const std::bad_alloc &) {
+        h->why = "a host allocation failed";
         rc = GLU_ERR_OOM;
     }
     if (rc != GLU_OK) {
@@ -1260,7 +1266,7 @@ const char *glu_strerror(int code) {
         case GLU_ERR_TIMEOUT: return "bounded device wait timed out";
         case GLU_ERR_NOT_FACTORED: return "no successful factorization to solve with";
         case GLU_ERR_INTERNAL: return "internal consistency check failed";
-        case GLU_ERR_TOO_LARGE: return "problem exceeds the fixed scratch array of glu_solve_noalloc";
+        case GLU_ERR_TOO_LARGE: return "problem exceeds a fixed limit (glu_solve_noalloc's scratch, or 2^31 schedule records)";
         default: return "unknown error code";
     }
 }

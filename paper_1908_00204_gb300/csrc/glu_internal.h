@@ -218,7 +218,8 @@ int analyze_host(int32_t n, const int32_t *colptr, const int32_t *rowidx, const 
 int order_nested_dissection(int32_t n, const int32_t *colptr, const int32_t *rowidx, int32_t *perm);
 
 // The column-level update schedule (pairs, segments, tasks, normalization
-// items) if analyze_host skipped it.
-void column_schedule(HostPlan &P, const glu_options &opt, int num_sms);
+// items) if analyze_host skipped it.  GLU_OK, or GLU_ERR_TOO_LARGE when a
+// 32-bit index of the device records would overflow; throws std::bad_alloc.
+int column_schedule(HostPlan &P, const glu_options &opt, int num_sms);
 
 }  // namespace glu
