@@ -854,6 +854,31 @@ int glu_analyze_opts(int32_t n, const int32_t *colptr, const int32_t *rowidx, co
             std::fclose(fp);
         }
     }
+    if (const char *dump = std::getenv("GLU_DUMP_COLUMNS")) {
+        // the column-level schedule as int64 words: counts (levels, pairs,
+        // segments, tasks, normalization items), the dense block (ftail_t0,
+        // ftail_level), then lvl_task_ptr, lvl_row_ptr, lvl_lane_ptr,
+        // lvl_norm_ptr, pairs (j, k, pos, map start), segments (pos, dj, mb,
+        // t0, t1), tasks (seg_begin, seg_end, kind, nslots, base),
+        // normalization items (col, t0, t1)
+        if (FILE *fp = std::fopen(dump, "wb")) {
+            const HostPlan &P = h->P;
+            std::vector<int64_t> w = {(int64_t)P.level_ptr.size() - 1, (int64_t)P.pair_j.size(),
+                                      (int64_t)P.segs.size(), (int64_t)P.tasks.size(), (int64_t)P.norms.size(),
+                                      P.ftail_t0, P.ftail_level};
+            for (int32_t v : P.lvl_task_ptr) w.push_back(v);
+            for (int32_t v : P.lvl_row_ptr) w.push_back(v);
+            for (int32_t v : P.lvl_lane_ptr) w.push_back(v);
+            for (int32_t v : P.lvl_norm_ptr) w.push_back(v);
+            for (size_t q = 0; q < P.pair_j.size(); q++)
+                w.insert(w.end(), {P.pair_j[q], P.pair_k[q], P.pair_pos[q], P.pair_map[q]});
+            for (const Seg &g : P.segs) w.insert(w.end(), {g.pos, g.dj, g.mb, g.t0, g.t1});
+            for (const Task &t : P.tasks) w.insert(w.end(), {t.seg_begin, t.seg_end, t.kind, t.nslots, t.base});
+            for (const NormItem &it : P.norms) w.insert(w.end(), {it.col, it.t0, it.t1});
+            std::fwrite(w.data(), sizeof(int64_t), w.size(), fp);
+            std::fclose(fp);
+        }
+    }
     if (const char *dump = std::getenv("GLU_DUMP_BLOCKS")) {
         // the supernodal schedule as int64 words: counts (supernodes, block
         // levels, diagonal list, panel items, pairs, segments, tasks), then
