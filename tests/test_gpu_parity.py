@@ -77,6 +77,13 @@ def test_mesh100x200(glu):
              device_inputs=True)
 
 
+def test_mesh100x200_under_builtin_order(glu):
+    # the same matrix in the library's own nested-dissection order
+    m = synth.make("mesh100x200_nets64", 1)
+    perm = glu.glu_order_nd(m.n, m.colptr, m.rowidx)
+    run_case(glu, m.n, m.colptr, m.rowidx, perm, m.values(2002), synth.rhs(m.n, 2, 2002))
+
+
 @pytest.mark.parametrize("mode", [0, 1, 2])
 def test_mode_invariance(glu, mode):
     m = synth.CircuitMatrix(synth.CircuitSpec(20, 30, 4, 30, 0.02, 0.05, "nd"), 9)
