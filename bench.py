@@ -59,6 +59,10 @@ def parse():
     ap.add_argument("--batched", action="store_true",
                     help="instead of the step: the batched FP64 refactorization of 256 value sets of the "
                          "20k-unknown matrix, timed per factorization, with its bandwidth roofline")
+    ap.add_argument("--latency", action="store_true",
+                    help="instead of the step: the launch/latency-bound small patterns (32x32 grid in natural "
+                         "order, the 5k serving pattern): microseconds per level against the floor of a CUDA "
+                         "graph of as many dependent one-element kernels")
     ap.add_argument("--precision", metavar="WORKLOAD", default=None,
                     help="instead of the step: FP32 factor + FP64 refinement against FP64 and the CPU "
                          "oracle on one workload (backward errors, differences, times)")
@@ -509,6 +513,84 @@ def run_batched(args):
     return 0
 
 
+def run_latency(args):
+    """Small patterns whose refactorization is a chain of short levels: the
+    32 x 32 grid in natural order (1,024 levels of one column) and the
+    5k-unknown serving pattern.  Per pattern: device time of one
+    refactorization (one graph launch; the matrix stays in L2) and of one
+    solve, the kernels one refactorization launches, and the floor -- a CUDA
+    graph of as many dependent one-element kernels, timed the same way."""
+    import torch
+    import paper_1908_00204_gb300 as g
+    g.build.build()
+    g.load_library()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    reps = max(args.steps, 20)
+    cases = []
+
+    def median_ms(fn):
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+    for name in ("grid32_natural", "serve5k"):
+        m = synth.make(name, 1)
+        h = g.glu_analyze(m.n, m.colptr, m.rowidx, m.perm)
+        g.glu_set_stream(h, stream)
+        v = torch.from_numpy(m.values(7)).to(dev)
+        b = torch.from_numpy(synth.rhs(m.n, 1, 7)).to(dev)
+        x = torch.empty_like(b)
+        for _ in range(max(args.warmup, 3)):
+            g.glu_factor(h, v)
+            g.glu_solve(h, b, x)
+        g.glu_sync(h)
+        torch.cuda.synchronize()
+        k0 = g.glu_get_stats(h)["kernel_launches"]
+        g.glu_factor(h, v)
+        g.glu_sync(h)
+        nk = int(g.glu_get_stats(h)["kernel_launches"] - k0)
+        f_ms = median_ms(lambda: g.glu_factor(h, v))
+        s_ms = median_ms(lambda: g.glu_solve(h, b, x))
+        g.glu_sync(h)
+        st = g.glu_get_stats(h)
+        # the floor: nk dependent one-element kernels in one graph
+        z = torch.zeros(1, device=dev)
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            for _ in range(3):
+                z.add_(1.0)
+        stream.wait_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            for _ in range(nk):
+                z.add_(1.0)
+        for _ in range(3):
+            graph.replay()
+        torch.cuda.synchronize()
+        floor_ms = median_ms(graph.replay)
+        cases.append({"workload": name, "n": m.n, "levels": st["nlevels"],
+                      "dense_block_columns": st["factor_tail_cols"], "kernels_per_refactor": nk,
+                      "refactor_us": f_ms * 1e3, "us_per_kernel": f_ms * 1e3 / max(nk, 1),
+                      "solve_us": s_ms * 1e3, "floor_us_per_node": floor_ms * 1e3 / max(nk, 1),
+                      "refactor_over_floor": f_ms / floor_ms if floor_ms > 0 else None})
+        g.glu_destroy(h)
+        del graph
+    line = {"metric": "latency-bound refactorization: microseconds per level kernel vs a graph-node floor",
+            "unit": "us", "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+            "config": {"l2": "warm (the matrices fit in L2)", "reps": reps,
+                       "floor": "CUDA graph of as many dependent one-element torch kernels"},
+            "cases": cases}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_precision(args):
     """FP32 factorization + FP64 iterative refinement to 1e-12 against the
     FP64 factorization and the CPU oracle on one workload: backward errors
@@ -582,6 +664,8 @@ def main():
         return run_precision(args)
     if args.batched:
         return run_batched(args)
+    if args.latency:
+        return run_latency(args)
     return run_ours(args)
 
 
