@@ -142,6 +142,39 @@ def cpu_oracle_steps(m, values, b, min_seconds=10.0, max_reps=5):
     return reps / el, reps, el
 
 
+def _oracle_refactor_worker(job):
+    """One process of the parallel oracle baseline: the oracle's numeric
+    refactorization of its share of the value sets, timed in the process."""
+    name, seeds, sigma, base_seed = job
+    import oracle
+    m = synth.make(name, 1)
+    vals = [m.values(s, sigma=sigma, base_seed=base_seed) for s in seeds]
+    f = oracle.Factorization(m.n, m.colptr, m.rowidx, m.perm)
+    t0 = time.perf_counter()
+    for v in vals:
+        f.factor(v)
+    return time.perf_counter() - t0, len(vals)
+
+
+def cpu_batched_baseline(name, seeds, sigma=0.1, base_seed=5, cores=None):
+    """The oracle on a batch of same-pattern value sets, spread one process
+    per host core (the sets are independent): sets / the slowest process's
+    time.  Processes are spawned, never forked."""
+    import multiprocessing as mp
+    if cores is None:
+        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    cores = max(1, min(int(cores), len(seeds)))
+    jobs = [(name, seeds[i::cores], sigma, base_seed) for i in range(cores)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_refactor_worker, jobs)
+    slowest = max(t for t, _ in res)
+    done = sum(c for _, c in res)
+    return {"value": done / slowest if slowest > 0 else None, "unit": "refactorizations/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"{done} value sets of {name} (the oracle's numeric refactorization), "
+                      f"one process per core, {slowest:.2f} s for the slowest"}
+
+
 def kernel_source_hash():
     """Hash of the file holding the level kernel (k_level)."""
     h = hashlib.sha256()
@@ -466,13 +499,16 @@ def run_batched(args):
     flushed between them.  Lanes run over value sets, so every update streams
     the target (read + write) and L(i,j) of 32 sets at a time: the algorithmic
     bytes per update and set are 16 (targets only, L from cache) to 24."""
+    B = 256
+    # the oracle baseline first: its processes start before any GPU call
+    cpu = None if args.no_cpu_baseline else cpu_batched_baseline("mesh100x200_nets64",
+                                                                 [100 + i for i in range(B)])
     import torch
     import paper_1908_00204_gb300 as g
     g.build.build()
     g.load_library()
     dev = torch.device("cuda", 0)
     mb = synth.make("mesh100x200_nets64", 1)
-    B = 256
     V = torch.from_numpy(np.stack([mb.values(100 + i, sigma=0.1, base_seed=5) for i in range(B)])).to(dev)
     hb = g.glu_analyze(mb.n, mb.colptr, mb.rowidx, mb.perm)
     stream = torch.cuda.current_stream(dev)
@@ -507,7 +543,7 @@ def run_batched(args):
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
             "config": {"workload": "mesh100x200_nets64", "sets": B, "updates_per_set": st["n_updates"],
                        "l2": "flushed between factorizations"},
-            "steps": args.steps, "data": "synthetic"}
+            "cpu_baseline": cpu, "steps": args.steps, "data": "synthetic"}
     print(json.dumps(line), flush=True)
     g.glu_destroy(hb)
     return 0

@@ -55,3 +55,12 @@ def test_single_process_and_reference_arm_rank_gate(monkeypatch):
     monkeypatch.setenv("RANK", "1")
     # a non-zero rank of the reference arm returns at once, without work
     assert bench.run_reference(type("A", (), {})()) == 0
+
+
+def test_parallel_oracle_baseline_counts_every_set():
+    # the batched workload's CPU baseline: value sets spread over processes
+    cpu = bench.cpu_batched_baseline("grid32_natural", list(range(5)), sigma=0.0, base_seed=None, cores=2)
+    assert cpu["cores"] == 2 and cpu["kind"] == "oracle" and cpu["value"] > 0
+    assert cpu["sample"].startswith("5 value sets")
+    one = bench.cpu_batched_baseline("grid32_natural", [3], sigma=0.0, base_seed=None, cores=8)
+    assert one["cores"] == 1                  # never more processes than sets
