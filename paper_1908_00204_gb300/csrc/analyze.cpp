@@ -294,6 +294,7 @@ int schedule(HostPlan &P, const glu_options &opt, int num_sms) {
     }
     P.pair_map[npairs] = acc;
     P.n_updates = acc;
+    const double ts_pairs = now_ms();
     if (opt.verbose)
         std::fprintf(stderr, "glu_analyze: column schedule: %lld pairs, %lld updates\n", (long long)npairs,
                      (long long)acc);
@@ -537,37 +538,44 @@ int schedule(HostPlan &P, const glu_options &opt, int num_sms) {
         pt.mode.push_back(mode);
     }
     };
-    // ranges of levels with about equal numbers of pairs
+    // Ranges of levels ("parts") with about equal numbers of pairs, several
+    // per thread: threads take the next part as they finish (a pair's work
+    // varies a lot), and the parts are concatenated in level order
+    // afterwards -- the result depends on neither the thread count nor the
+    // cut.
     int nth = std::max(1, std::min<int>(16, (int)std::thread::hardware_concurrency()));
     if (const char *e = std::getenv("GLU_ANALYZE_THREADS")) nth = std::max(1, std::min(64, std::atoi(e)));
+    const int32_t nparts = std::max(1, std::min(nl, nth * 8));
     std::vector<int32_t> cut(1, 0);
-    for (int t = 1; t < nth; t++) {
-        const int64_t want = npairs * t / nth;
+    for (int32_t t = 1; t < nparts; t++) {
+        const int64_t want = npairs * t / nparts;
         const int32_t l = (int32_t)(std::lower_bound(lvl_pair_ptr.begin(), lvl_pair_ptr.end(), want) -
                                     lvl_pair_ptr.begin());
         cut.push_back(std::max(cut.back(), std::min(l, nl)));
     }
     cut.push_back(nl);
     std::vector<Part> parts(cut.size() - 1);
-    // an allocation failure on a worker is handed to the caller's thread
-    std::atomic<bool> failed{false};
-    auto guarded = [&failed](auto &&fn) {
-        try {
-            fn();
-        } catch (const std::bad_alloc &) {
-            failed = true;
-        }
-    };
-    {
+    // runs fn(t) for every part t on nth threads (this one included); an
+    // allocation failure on any of them is rethrown here after all joined
+    auto for_parts = [&](auto fn) {
+        std::atomic<size_t> next{0};
+        std::atomic<bool> failed{false};
+        auto worker = [&] {
+            try {
+                for (size_t t; !failed && (t = next.fetch_add(1)) < parts.size();) fn(t);
+            } catch (const std::bad_alloc &) {
+                failed = true;
+            }
+        };
         std::vector<std::thread> th;
-        th.reserve(parts.size());
-        for (size_t t = 1; t < parts.size(); t++)
-            if (cut[t + 1] > cut[t])
-                spawn_or_run(th, [&, t] { guarded([&] { run_levels(cut[t], cut[t + 1], parts[t]); }); });
-        guarded([&] { run_levels(cut[0], cut[1], parts[0]); });
+        th.reserve((size_t)nth);
+        for (int t = 1; t < nth; t++) spawn_or_run(th, worker);
+        worker();
         for (std::thread &x : th) x.join();
-    }
-    if (failed) throw std::bad_alloc();
+        if (failed) throw std::bad_alloc();
+    };
+    for_parts([&](size_t t) { run_levels(cut[t], cut[t + 1], parts[t]); });
+    const double ts_tasks = now_ms();
     // concatenate: each part's tasks and segments go to their offsets (the
     // segments flattened into self-contained records), in parallel
     std::vector<int64_t> sbase(parts.size() + 1, 0), tbase(parts.size() + 1, 0);
@@ -598,13 +606,7 @@ int schedule(HostPlan &P, const glu_options &opt, int num_sms) {
             sg.t1 = ps.t1;
         }
     };
-    {
-        std::vector<std::thread> th;
-        th.reserve(parts.size());
-        for (size_t t = 1; t < parts.size(); t++) spawn_or_run(th, [&place, t] { place(t); });
-        place(0);
-        for (std::thread &x : th) x.join();
-    }
+    for_parts(place);
     for (size_t t = 0; t < parts.size(); t++) {
         const Part &pt = parts[t];
         const int32_t tb = (int32_t)tbase[t];
@@ -618,6 +620,7 @@ int schedule(HostPlan &P, const glu_options &opt, int num_sms) {
         }
     }
     parts.clear();
+    const double ts_flat = now_ms();
 
     // normalization items: level l's columns run in level l+1's kernel; the
     // last level's columns in the final pass
@@ -635,6 +638,10 @@ int schedule(HostPlan &P, const glu_options &opt, int num_sms) {
         }
         P.lvl_norm_ptr[l + 1] = (int32_t)P.norms.size();
     }
+    if (opt.verbose)
+        std::fprintf(stderr, "glu_analyze: schedule phases: tasks %.0f ms (%d threads), flatten %.0f ms, "
+                     "normalization items %.0f ms\n", ts_tasks - ts_pairs, nth, ts_flat - ts_tasks,
+                     now_ms() - ts_flat);
     P.has_schedule = true;
     return GLU_OK;
 }
@@ -1169,12 +1176,15 @@ int analyze_host(int32_t n, const int32_t *colptr, const int32_t *rowidx, const 
     // (an allocation failure on either thread is rethrown here once both
     // have finished)
     std::atomic<bool> solve_failed{false};
-    auto solve_job = [&P, &opt, &solve_failed] {
+    double t_solve = 0.0;
+    auto solve_job = [&P, &opt, &solve_failed, &t_solve] {
+        const double ts = now_ms();
         try {
             solve_levels(P, opt);
         } catch (const std::bad_alloc &) {
             solve_failed = true;
         }
+        t_solve = now_ms() - ts;
     };
     std::thread solve_thread;
     try {
@@ -1192,8 +1202,12 @@ int analyze_host(int32_t n, const int32_t *colptr, const int32_t *rowidx, const 
     } catch (const std::bad_alloc &) {
         failed = true;
     }
+    const double t_sched = now_ms() - t3;
     if (solve_thread.joinable())
         solve_thread.join();
+    if (opt.verbose)
+        std::fprintf(stderr, "glu_analyze: factorization schedule %.0f ms, solve schedule %.0f ms (concurrent)\n",
+                     t_sched, t_solve);
     else if (!failed)
         solve_job();
     if (failed || solve_failed) throw std::bad_alloc();

@@ -180,8 +180,8 @@ struct Carve {
 template <typename T>
 T *at(char *base, size_t off) { return reinterpret_cast<T *>(base + off); }
 
-template <typename T>
-cudaError_t upload(T *dst, const std::vector<T> &src) {
+template <typename T, typename A>
+cudaError_t upload(T *dst, const std::vector<T, A> &src) {
     if (src.empty()) return cudaSuccess;
     return cudaMemcpy(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
 }

@@ -3,12 +3,40 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <memory>
+#include <new>
 #include <string>
+#include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "../../include/glu.h"
 
 namespace glu {
+
+// An allocator that default-initializes: resize() leaves trivially
+// constructible elements unwritten, so large host arrays that are filled
+// right after sizing are not zeroed first (and their pages are first touched
+// by the threads that fill them).
+template <class T>
+struct NoInitAllocator : std::allocator<T> {
+    using value_type = T;
+    template <class U>
+    struct rebind {
+        using other = NoInitAllocator<U>;
+    };
+    NoInitAllocator() noexcept = default;
+    template <class U>
+    NoInitAllocator(const NoInitAllocator<U> &) noexcept {}
+    template <class U>
+    void construct(U *p) noexcept(std::is_nothrow_default_constructible<U>::value) {
+        ::new ((void *)p) U;
+    }
+    template <class U, class... Args>
+    void construct(U *p, Args &&...args) {
+        ::new ((void *)p) U(std::forward<Args>(args)...);
+    }
+};
 
 // Task kinds of a level's work list.
 //   KIND_SRC:  many short segments on one 32-position chunk: lanes over
@@ -141,8 +169,8 @@ struct HostPlan {
     std::vector<int64_t> pair_pos, pair_map;
     int64_t n_updates = 0, n_pairs = 0;
     bool has_schedule = false;           // the column-level schedule is built
-    std::vector<Seg> segs;
-    std::vector<Task> tasks;
+    std::vector<Seg, NoInitAllocator<Seg>> segs;
+    std::vector<Task, NoInitAllocator<Task>> tasks;
     std::vector<int32_t> lvl_task_ptr;  // nlevels + 1
     // inside level l: [lvl_task_ptr[l], lvl_row_ptr[l]) KIND_SRC,
     // [lvl_row_ptr[l], lvl_lane_ptr[l]) KIND_ROW, [lvl_lane_ptr[l], lvl_task_ptr[l+1]) KIND_LANE

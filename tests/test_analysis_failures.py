@@ -37,8 +37,8 @@ def analyze(m):
 @pytest.mark.parametrize("where", ["first", "last"])
 def test_schedule_level_failure_reports_oom(mat, monkeypatch, where):
     (lp0, lc0), nl = analyze(mat)
-    # four threads: level 0 is scheduled on the calling thread, the last
-    # level on a worker
+    # four threads take ranges of levels as they finish: the failing level
+    # may be scheduled on the calling thread or on a worker
     monkeypatch.setenv("GLU_ANALYZE_THREADS", "4")
     monkeypatch.setenv("GLU_TEST_FAIL_LEVEL", "0" if where == "first" else str(nl - 1))
     with pytest.raises(glu.GluError) as e:
