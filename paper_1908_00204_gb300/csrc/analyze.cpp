@@ -36,6 +36,49 @@ void spawn_or_run(std::vector<std::thread> &th, F fn) {
     }
 }
 
+// Host threads of the analysis: the machine's, at most 16, or
+// GLU_ANALYZE_THREADS (1..64).
+int analysis_threads() {
+    int nth = std::max(1, std::min<int>(16, (int)std::thread::hardware_concurrency()));
+    if (const char *e = std::getenv("GLU_ANALYZE_THREADS")) nth = std::max(1, std::min(64, std::atoi(e)));
+    return nth;
+}
+
+// Cuts the columns [0, n) into nth consecutive ranges of about equal weight
+// (ptr[n+1] a prefix sum of the columns' weights); returns nth + 1 bounds.
+template <class I>
+std::vector<int32_t> column_ranges(int32_t n, const I *ptr, int nth) {
+    std::vector<int32_t> cut(1, 0);
+    const int64_t total = (int64_t)ptr[n];
+    for (int t = 1; t < nth; t++) {
+        const int64_t want = total * t / nth;
+        const int32_t j = (int32_t)(std::lower_bound(ptr, ptr + n + 1, (I)want) - ptr);
+        cut.push_back(std::max(cut.back(), std::min(j, n)));
+    }
+    cut.push_back(n);
+    return cut;
+}
+
+// Runs fn(t) for t in [0, nth) on nth threads (this one included).  An
+// allocation failure on any of them is rethrown here once all have joined.
+template <class F>
+void run_threads(int nth, F fn) {
+    std::atomic<bool> failed{false};
+    auto job = [&](int t) {
+        try {
+            fn(t);
+        } catch (const std::bad_alloc &) {
+            failed = true;
+        }
+    };
+    std::vector<std::thread> th;
+    th.reserve((size_t)nth);
+    for (int t = 1; t < nth; t++) spawn_or_run(th, [&job, t] { job(t); });
+    job(0);
+    for (std::thread &x : th) x.join();
+    if (failed) throw std::bad_alloc();
+}
+
 double now_ms() {
     return std::chrono::duration<double, std::milli>(
                std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -155,38 +198,60 @@ int symbolic(HostPlan &P, const std::vector<int64_t> &bptr, const std::vector<in
 }
 
 // Compressed-row views of the strict lower and strict upper parts.
+// Each thread counts, then places, the entries of one range of columns;
+// a row's entries from an earlier range come first, so every row lists its
+// columns in ascending order.
 void row_views(HostPlan &P) {
     const int32_t n = P.n;
+    const int nth = analysis_threads();
+    const std::vector<int32_t> cut = column_ranges(n, P.lu_colptr.data(), nth);
+    // per thread, per row: entries of the thread's columns (then its offsets)
+    std::vector<std::vector<int64_t>> lc((size_t)nth), uc((size_t)nth);
+    run_threads(nth, [&](int t) {
+        lc[t].assign((size_t)n, 0);
+        uc[t].assign((size_t)n, 0);
+        for (int32_t j = cut[t]; j < cut[t + 1]; j++) {
+            for (int64_t p = P.lu_colptr[j]; p < P.diag_pos[j]; p++) uc[t][P.lu_rowidx[p]]++;
+            for (int64_t p = P.diag_pos[j] + 1; p < P.lu_colptr[j + 1]; p++) lc[t][P.lu_rowidx[p]]++;
+        }
+    });
     P.lrow_ptr.assign((size_t)n + 1, 0);
     P.urow_ptr.assign((size_t)n + 1, 0);
-    for (int32_t j = 0; j < n; j++) {
-        for (int64_t p = P.lu_colptr[j]; p < P.diag_pos[j]; p++) P.urow_ptr[P.lu_rowidx[p] + 1]++;
-        for (int64_t p = P.diag_pos[j] + 1; p < P.lu_colptr[j + 1]; p++) P.lrow_ptr[P.lu_rowidx[p] + 1]++;
-    }
+    int64_t la = 0, ua = 0;
     for (int32_t i = 0; i < n; i++) {
-        P.lrow_ptr[i + 1] += P.lrow_ptr[i];
-        P.urow_ptr[i + 1] += P.urow_ptr[i];
-    }
-    P.nnz_l = P.lrow_ptr[n];
-    P.nnz_u = P.urow_ptr[n] + n;
-    P.lrow_col.resize((size_t)P.lrow_ptr[n]);
-    P.lrow_pos.resize((size_t)P.lrow_ptr[n]);
-    P.urow_col.resize((size_t)P.urow_ptr[n]);
-    P.urow_pos.resize((size_t)P.urow_ptr[n]);
-    std::vector<int64_t> lf(P.lrow_ptr.begin(), P.lrow_ptr.end() - 1);
-    std::vector<int64_t> uf(P.urow_ptr.begin(), P.urow_ptr.end() - 1);
-    for (int32_t j = 0; j < n; j++) {
-        for (int64_t p = P.lu_colptr[j]; p < P.diag_pos[j]; p++) {
-            int64_t q = uf[P.lu_rowidx[p]]++;
-            P.urow_col[q] = j;
-            P.urow_pos[q] = p;
-        }
-        for (int64_t p = P.diag_pos[j] + 1; p < P.lu_colptr[j + 1]; p++) {
-            int64_t q = lf[P.lu_rowidx[p]]++;
-            P.lrow_col[q] = j;
-            P.lrow_pos[q] = p;
+        P.lrow_ptr[i] = la;
+        P.urow_ptr[i] = ua;
+        for (int t = 0; t < nth; t++) {
+            const int64_t l = lc[t][i], u = uc[t][i];
+            lc[t][i] = la;
+            uc[t][i] = ua;
+            la += l;
+            ua += u;
         }
     }
+    P.lrow_ptr[n] = la;
+    P.urow_ptr[n] = ua;
+    P.nnz_l = la;
+    P.nnz_u = ua + n;
+    P.lrow_col.resize((size_t)la);
+    P.lrow_pos.resize((size_t)la);
+    P.urow_col.resize((size_t)ua);
+    P.urow_pos.resize((size_t)ua);
+    run_threads(nth, [&](int t) {
+        std::vector<int64_t> &lf = lc[t], &uf = uc[t];
+        for (int32_t j = cut[t]; j < cut[t + 1]; j++) {
+            for (int64_t p = P.lu_colptr[j]; p < P.diag_pos[j]; p++) {
+                const int64_t q = uf[P.lu_rowidx[p]]++;
+                P.urow_col[q] = j;
+                P.urow_pos[q] = p;
+            }
+            for (int64_t p = P.diag_pos[j] + 1; p < P.lu_colptr[j + 1]; p++) {
+                const int64_t q = lf[P.lu_rowidx[p]]++;
+                P.lrow_col[q] = j;
+                P.lrow_pos[q] = p;
+            }
+        }
+    });
 }
 
 // ---------------------------------------------------------------------------
@@ -263,35 +328,64 @@ int schedule(HostPlan &P, const glu_options &opt, int num_sms) {
     // pairs, bucketed by the source's level; scanning targets k ascending
     // (and rows j ascending inside column k) leaves every bucket sorted by
     // (k, j).
+    // (a counting sort by level over ranges of target columns, one per
+    // thread; a thread's columns precede the next thread's, so the order
+    // within a bucket is the same as a sequential scan's)
+    const int nth = analysis_threads();
+    const std::vector<int32_t> kcut = column_ranges(n, P.lu_colptr.data(), nth);
+    std::vector<std::vector<int64_t>> lcnt((size_t)nth);
+    run_threads(nth, [&](int t) {
+        lcnt[t].assign((size_t)nl, 0);
+        for (int32_t k = kcut[t]; k < kcut[t + 1]; k++)
+            for (int64_t p = P.lu_colptr[k]; p < P.diag_pos[k]; p++) {
+                const int32_t j = P.lu_rowidx[p];
+                if (lcount(j) > 0) lcnt[t][P.level_of[j]]++;
+            }
+    });
     std::vector<int64_t> lvl_pair_ptr((size_t)nl + 1, 0);
-    for (int32_t k = 0; k < n; k++)
-        for (int64_t p = P.lu_colptr[k]; p < P.diag_pos[k]; p++) {
-            int32_t j = P.lu_rowidx[p];
-            if (lcount(j) > 0) lvl_pair_ptr[P.level_of[j] + 1]++;
+    for (int32_t l = 0; l < nl; l++) {
+        int64_t at = lvl_pair_ptr[l];
+        for (int t = 0; t < nth; t++) {
+            const int64_t c = lcnt[t][l];
+            lcnt[t][l] = at;     // now this thread's first slot in bucket l
+            at += c;
         }
-    for (int32_t l = 0; l < nl; l++) lvl_pair_ptr[l + 1] += lvl_pair_ptr[l];
+        lvl_pair_ptr[l + 1] = at;
+    }
     const int64_t npairs = lvl_pair_ptr[nl];
     P.pair_j.resize((size_t)npairs);
     P.pair_k.resize((size_t)npairs);
     P.pair_pos.resize((size_t)npairs);
     P.pair_map.resize((size_t)npairs + 1);
-    {
-        std::vector<int64_t> f(lvl_pair_ptr.begin(), lvl_pair_ptr.end() - 1);
-        for (int32_t k = 0; k < n; k++)
+    run_threads(nth, [&](int t) {
+        std::vector<int64_t> &f = lcnt[t];
+        for (int32_t k = kcut[t]; k < kcut[t + 1]; k++)
             for (int64_t p = P.lu_colptr[k]; p < P.diag_pos[k]; p++) {
-                int32_t j = P.lu_rowidx[p];
+                const int32_t j = P.lu_rowidx[p];
                 if (lcount(j) == 0) continue;
-                int64_t q = f[P.level_of[j]]++;
+                const int64_t q = f[P.level_of[j]]++;
                 P.pair_j[q] = j;
                 P.pair_k[q] = k;
                 P.pair_pos[q] = p;
             }
-    }
-    int64_t acc = 0;
-    for (int64_t q = 0; q < npairs; q++) {
-        P.pair_map[q] = acc;
-        acc += lcount(P.pair_j[q]);
-    }
+    });
+    // pair_map: exclusive prefix sum of the sources' L counts, by chunks
+    std::vector<int64_t> csum((size_t)nth + 1, 0);
+    auto chunk = [&](int t) { return npairs * t / nth; };
+    run_threads(nth, [&](int t) {
+        int64_t s = 0;
+        for (int64_t q = chunk(t); q < chunk(t + 1); q++) s += lcount(P.pair_j[q]);
+        csum[t + 1] = s;
+    });
+    for (int t = 0; t < nth; t++) csum[t + 1] += csum[t];
+    run_threads(nth, [&](int t) {
+        int64_t a = csum[t];
+        for (int64_t q = chunk(t); q < chunk(t + 1); q++) {
+            P.pair_map[q] = a;
+            a += lcount(P.pair_j[q]);
+        }
+    });
+    const int64_t acc = csum[nth];
     P.pair_map[npairs] = acc;
     P.n_updates = acc;
     const double ts_pairs = now_ms();
@@ -543,8 +637,6 @@ int schedule(HostPlan &P, const glu_options &opt, int num_sms) {
     // varies a lot), and the parts are concatenated in level order
     // afterwards -- the result depends on neither the thread count nor the
     // cut.
-    int nth = std::max(1, std::min<int>(16, (int)std::thread::hardware_concurrency()));
-    if (const char *e = std::getenv("GLU_ANALYZE_THREADS")) nth = std::max(1, std::min(64, std::atoi(e)));
     const int32_t nparts = std::max(1, std::min(nl, nth * 8));
     std::vector<int32_t> cut(1, 0);
     for (int32_t t = 1; t < nparts; t++) {
@@ -1150,14 +1242,22 @@ int analyze_host(int32_t n, const int32_t *colptr, const int32_t *rowidx, const 
     const int64_t nnz = P.lu_colptr[n];
     P.gsrc.assign((size_t)nnz, -1);
     P.max_col_len = 0;
-    for (int32_t j = 0; j < n; j++) {
-        const int32_t *cb = P.lu_rowidx.data() + P.lu_colptr[j];
-        const int32_t *ce = P.lu_rowidx.data() + P.lu_colptr[j + 1];
-        P.max_col_len = std::max<int64_t>(P.max_col_len, ce - cb);
-        for (int64_t q = bptr[j]; q < bptr[j + 1]; q++) {
-            const int32_t *it = std::lower_bound(cb, ce, brow[q]);
-            P.gsrc[it - P.lu_rowidx.data()] = bsrc[q];
-        }
+    {
+        const int nth = analysis_threads();
+        const std::vector<int32_t> cut = column_ranges(n, P.lu_colptr.data(), nth);
+        std::vector<int64_t> longest((size_t)nth, 0);
+        run_threads(nth, [&](int t) {
+            for (int32_t j = cut[t]; j < cut[t + 1]; j++) {
+                const int32_t *cb = P.lu_rowidx.data() + P.lu_colptr[j];
+                const int32_t *ce = P.lu_rowidx.data() + P.lu_colptr[j + 1];
+                longest[t] = std::max<int64_t>(longest[t], ce - cb);
+                for (int64_t q = bptr[j]; q < bptr[j + 1]; q++) {
+                    const int32_t *it = std::lower_bound(cb, ce, brow[q]);
+                    P.gsrc[it - P.lu_rowidx.data()] = bsrc[q];
+                }
+            }
+        });
+        for (int64_t v : longest) P.max_col_len = std::max(P.max_col_len, v);
     }
     row_views(P);
     double t1 = now_ms();

@@ -860,7 +860,8 @@ int glu_analyze_opts(int32_t n, const int32_t *colptr, const int32_t *rowidx, co
         // ftail_level), then lvl_task_ptr, lvl_row_ptr, lvl_lane_ptr,
         // lvl_norm_ptr, pairs (j, k, pos, map start), segments (pos, dj, mb,
         // t0, t1), tasks (seg_begin, seg_end, kind, nslots, base),
-        // normalization items (col, t0, t1)
+        // normalization items (col, t0, t1), the value gather map (one A
+        // index or -1 per entry of L+U)
         if (FILE *fp = std::fopen(dump, "wb")) {
             const HostPlan &P = h->P;
             std::vector<int64_t> w = {(int64_t)P.level_ptr.size() - 1, (int64_t)P.pair_j.size(),
@@ -875,6 +876,7 @@ int glu_analyze_opts(int32_t n, const int32_t *colptr, const int32_t *rowidx, co
             for (const Seg &g : P.segs) w.insert(w.end(), {g.pos, g.dj, g.mb, g.t0, g.t1});
             for (const Task &t : P.tasks) w.insert(w.end(), {t.seg_begin, t.seg_end, t.kind, t.nslots, t.base});
             for (const NormItem &it : P.norms) w.insert(w.end(), {it.col, it.t0, it.t1});
+            w.insert(w.end(), P.gsrc.begin(), P.gsrc.end());
             std::fwrite(w.data(), sizeof(int64_t), w.size(), fp);
             std::fclose(fp);
         }

@@ -15,8 +15,9 @@ level no task writes a position that another task writes or that any task
 reads, and the normalization items touch neither; a KIND_SRC task's targets
 lie in its 32 positions.  Every update (i,j,k) whose source j lies before the
 dense block is applied exactly once, and every L entry outside the block is
-divided exactly once.  The dump is the library's diagnostic copy of the
-schedule (environment variable GLU_DUMP_COLUMNS at glu_analyze).
+divided exactly once.  The library's value gather map must place A's values
+where the replay's own gather does.  The dump is the library's diagnostic
+copy of the schedule (environment variable GLU_DUMP_COLUMNS at glu_analyze).
 """
 import numpy as np
 import pytest
@@ -49,7 +50,7 @@ def load_columns(path):
     d["segs"] = take(nseg, 5).reshape(nseg, 5)
     d["tasks"] = take(ntask, 5).reshape(ntask, 5)
     d["norms"] = take(nnorm, 3).reshape(nnorm, 3)
-    assert q == w.size
+    d["gsrc"] = w[q:]
     return d
 
 
@@ -178,6 +179,10 @@ def run_case(tmp_path, monkeypatch, m, values, mutate=None, **opts):
         for p in range(cp[jo], cp[jo + 1]):
             i, j = pinv[ri[p]], pinv[jo]
             lu[fcp[j] + np.searchsorted(fri[fcp[j]:fcp[j + 1]], i)] = values[p]
+    # the library's value gather map (step a5) places the same values
+    gs = d["gsrc"]
+    assert gs.size == fri.size
+    assert np.array_equal(np.where(gs >= 0, np.asarray(values)[np.maximum(gs, 0)], 0.0), lu)
     got, kinds = replay(fcp, fri, diag, lu, d)
     ref = oracle.Factorization(n, cp, ri, m.perm, values)
     bad, _ = factor_mismatches(ref.lu_colptr, ref.lu_rowidx, got, ref.lu_val)
