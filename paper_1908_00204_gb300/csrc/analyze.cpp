@@ -79,6 +79,21 @@ void run_threads(int nth, F fn) {
     if (failed) throw std::bad_alloc();
 }
 
+// std::lower_bound for a value expected near the start of [first, last):
+// an exponential search from first, then a binary search inside the bracket
+// (everything before lo is known to be < v).
+template <class T>
+const T *gallop_lower_bound(const T *first, const T *last, T v) {
+    const T *lo = first;
+    ptrdiff_t step = 1;
+    for (;;) {
+        if (last - lo <= step) return std::lower_bound(lo, last, v);
+        if (!(lo[step - 1] < v)) return std::lower_bound(lo, lo + step, v);
+        lo += step;
+        step *= 2;
+    }
+}
+
 double now_ms() {
     return std::chrono::duration<double, std::milli>(
                std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -460,9 +475,12 @@ int schedule(HostPlan &P, const glu_options &opt, int num_sms) {
                 const int32_t *L = P.lu_rowidx.data() + lstart(j);
                 const int32_t lj = lcount(j);
                 int32_t t = 0;
+                // rows of L(:,j) lie below row j, which sits at pair_pos in column k;
+                // both lists ascend, so each search starts where the last one ended
+                int64_t pos = P.pair_pos[q] - c0 + 1;
                 while (t < lj) {
                     // position of row L[t] inside column k
-                    int64_t pos = std::lower_bound(krows, krows + clen, L[t]) - krows;
+                    pos = gallop_lower_bound(krows + pos, krows + clen, L[t]) - krows;
                     int64_t ch = pos / SRC_SLOTS;
                     int64_t chend = std::min<int64_t>((ch + 1) * SRC_SLOTS, clen);
                     int32_t t1;
@@ -470,7 +488,7 @@ int schedule(HostPlan &P, const glu_options &opt, int num_sms) {
                         t1 = lj;
                     } else {
                         int32_t endrow = krows[chend];
-                        t1 = (int32_t)(std::lower_bound(L + t, L + lj, endrow) - L);
+                        t1 = (int32_t)(gallop_lower_bound(L + t, L + lj, endrow) - L);
                     }
                     if (chunk_work[ch] == 0 && chunk_segs[ch].empty()) touched.push_back((int32_t)ch);
                     chunk_segs[ch].push_back(PSeg{(int32_t)q, t, t1, 0});
