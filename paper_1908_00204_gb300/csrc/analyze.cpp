@@ -336,7 +336,14 @@ int schedule(HostPlan &P, const glu_options &opt, int num_sms) {
     const int32_t n = P.n;
     const int32_t nl = (int32_t)P.level_ptr.size() - 1;
     const int64_t piece = opt.piece_updates > 0 ? opt.piece_updates : 1024;
-    const int32_t src_min = 5;   // groups with more sources use KIND_SRC
+    // task-size thresholds; the environment overrides them for sweeps (every
+    // value gives a valid schedule)
+    auto env_int = [](const char *name, int64_t dflt, int64_t lo, int64_t hi) {
+        const char *e = std::getenv(name);
+        return e ? std::max(lo, std::min(hi, (int64_t)std::atoll(e))) : dflt;
+    };
+    // groups with at least this many sources use KIND_SRC chunk tasks
+    const int32_t src_min = (int32_t)env_int("GLU_SRC_MIN", 5, 2, 1 << 20);
     auto lstart = [&](int32_t j) { return P.diag_pos[j] + 1; };
     auto lcount = [&](int32_t j) { return (int32_t)(P.lu_colptr[j + 1] - P.diag_pos[j] - 1); };
 
@@ -413,7 +420,9 @@ int schedule(HostPlan &P, const glu_options &opt, int num_sms) {
     P.lvl_task_ptr.assign((size_t)nl + 1, 0);
     P.lvl_row_ptr.assign((size_t)nl, 0);
     P.lvl_lane_ptr.assign((size_t)nl, 0);
-    const int64_t lane_max = 64;    // tasks up to this many updates run on one lane
+    // tasks up to this many updates (and lane_segs segments) run on one lane
+    const int64_t lane_max = env_int("GLU_LANE_MAX", 64, 1, 1 << 20);
+    const int32_t lane_segs = (int32_t)env_int("GLU_LANE_SEGS", 4, 1, 64);
     P.level_mode.assign((size_t)nl, 0);
     (void)num_sms;
     // Levels are scheduled independently: contiguous ranges of levels run on
@@ -618,11 +627,11 @@ int schedule(HostPlan &P, const glu_options &opt, int num_sms) {
         // rows would leave most lanes idle and pay one round trip per segment)
         // The level's time is the longest serial chain of one work item, and
         // every segment applied in sequence adds a few dependent memory round
-        // trips, so a lane task holds at most 4 segments.
+        // trips, so a lane task holds at most lane_segs (4) segments.
         for (Task &t : lvl_tasks) {
             const int32_t ns = t.seg_end - t.seg_begin;
             if (t.kind == KIND_SRC && ns >= 4) continue;
-            t.kind = (t.work <= lane_max && ns <= 4) ? KIND_LANE : KIND_ROW;
+            t.kind = (t.work <= lane_max && ns <= lane_segs) ? KIND_LANE : KIND_ROW;
         }
         // grouped by kind, largest first inside a kind: warps take tasks in order
         std::stable_sort(lvl_tasks.begin(), lvl_tasks.end(), [](const Task &a, const Task &b) {
