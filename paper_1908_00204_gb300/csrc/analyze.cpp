@@ -1033,7 +1033,6 @@ void block_schedule(HostPlan &P) {
     P.btask_ptr.assign((size_t)nbl + 1, 0);
     std::vector<std::vector<int32_t>> by_level((size_t)nbl);
     for (int32_t q = 0; q < nsn; q++) by_level[blev[q]].push_back(q);
-    std::vector<int32_t> krows;
     for (int32_t l = 0; l < nbl; l++) {
         for (int32_t q : by_level[l])
             if (c0v[q + 1] - c0v[q] >= 2) P.bdiag.push_back(q);
@@ -1046,45 +1045,96 @@ void block_schedule(HostPlan &P) {
             if (c0v[bp.sn + 1] - c0v[bp.sn] - bp.f >= 2) P.bitems.push_back(BItem{bp.sn, 1, (int32_t)p, 0});
         }
         P.bitem_ptr[l + 1] = (int32_t)P.bitems.size();
-        // update tasks: the level's pairs grouped by target column; each
-        // BCHUNK-position chunk of the column touched by some R_B is a task,
-        // its segments the pairs' rows inside the chunk, in supernode order
-        int64_t g = lcount[l];
-        while (g < lcount[l + 1]) {
-            const int32_t k = P.bpairs[g].k;
-            int64_t ge = g;
-            while (ge < lcount[l + 1] && P.bpairs[ge].k == k) ge++;
-            const int64_t cb = P.lu_colptr[k], clen = P.lu_colptr[k + 1] - cb;
-            const int32_t *kr = P.lu_rowidx.data() + cb;
-            int64_t qlo = clen, qhi = 0;
-            for (int64_t p = g; p < ge; p++) {
-                const int32_t q = P.bpairs[p].sn;
-                const int32_t r = P.sn_r[q];
-                if (r == 0) continue;
-                const int32_t *R = P.lu_rowidx.data() + P.lu_colptr[c0v[q + 1]] - r;
-                qlo = std::min<int64_t>(qlo, std::lower_bound(kr, kr + clen, R[0]) - kr);
-                qhi = std::max<int64_t>(qhi, (std::lower_bound(kr, kr + clen, R[r - 1]) - kr) + 1);
-            }
-            for (int64_t c = (qlo / BCHUNK) * BCHUNK; c < qhi; c += BCHUNK) {
-                const int32_t rlo = kr[c];
-                const int32_t rhi = c + BCHUNK < clen ? kr[c + BCHUNK] : INT32_MAX;
-                BTask t{(int32_t)P.bsegs.size(), 0};
-                for (int64_t p = g; p < ge; p++) {
-                    const int32_t q = P.bpairs[p].sn;
-                    const int32_t r = P.sn_r[q];
-                    const int32_t *R = P.lu_rowidx.data() + P.lu_colptr[c0v[q + 1]] - r;
-                    const int32_t t0 = (int32_t)(std::lower_bound(R, R + r, rlo) - R);
-                    const int32_t t1 = (int32_t)(std::lower_bound(R, R + r, rhi) - R);
-                    if (t1 > t0) P.bsegs.push_back(BSeg{(int32_t)p, t0, t1, 0});
-                }
-                t.seg_end = (int32_t)P.bsegs.size();
-                if (t.seg_end > t.seg_begin) P.btasks.push_back(t);
-            }
-            g = ge;
-        }
-        P.btask_ptr[l + 1] = (int32_t)P.btasks.size();
     }
-    (void)krows;
+    // Update tasks, level ranges on threads (each into its own lists, task
+    // segment indices relative to them), concatenated in level order: the
+    // result does not depend on the thread count.
+    struct BPart {
+        std::vector<BSeg> segs;
+        std::vector<BTask> tasks;
+        std::vector<int32_t> tend;   // per level, relative to tasks
+    };
+    const int nth = analysis_threads();
+    const int32_t nparts = std::max(1, std::min(nbl, nth * 8));
+    std::vector<int32_t> cut(1, 0);
+    for (int32_t t = 1; t < nparts; t++) {
+        const int64_t want = lcount[nbl] * t / nparts;
+        const int32_t l = (int32_t)(std::lower_bound(lcount.begin(), lcount.end(), want) - lcount.begin());
+        cut.push_back(std::max(cut.back(), std::min(l, nbl)));
+    }
+    cut.push_back(nbl);
+    std::vector<BPart> parts(cut.size() - 1);
+    std::atomic<size_t> next{0};
+    run_threads(nth, [&](int) {
+        std::vector<std::vector<BSeg>> cbucket;   // per chunk of the current target column
+        std::vector<int32_t> touched;
+        for (size_t pi; (pi = next.fetch_add(1)) < parts.size();) {
+            std::vector<BSeg> &segs = parts[pi].segs;
+            std::vector<BTask> &tasks = parts[pi].tasks;
+            for (int32_t l = cut[pi]; l < cut[pi + 1]; l++) {
+                // update tasks: the level's pairs grouped by target column; each
+                // BCHUNK-position chunk of the column touched by some R_B is a task,
+                // its segments the pairs' rows inside the chunk, in supernode order.
+                // Each pair's rows are routed to their chunks in one pass (rows and
+                // positions both ascend, so every search starts where the last ended).
+                int64_t g = lcount[l];
+                while (g < lcount[l + 1]) {
+                    const int32_t k = P.bpairs[g].k;
+                    int64_t ge = g;
+                    while (ge < lcount[l + 1] && P.bpairs[ge].k == k) ge++;
+                    const int64_t cb = P.lu_colptr[k], clen = P.lu_colptr[k + 1] - cb;
+                    const int32_t *kr = P.lu_rowidx.data() + cb;
+                    const int64_t nch = (clen + BCHUNK - 1) / BCHUNK;
+                    if ((int64_t)cbucket.size() < nch) cbucket.resize((size_t)nch);
+                    touched.clear();
+                    for (int64_t p = g; p < ge; p++) {
+                        const int32_t q = P.bpairs[p].sn;
+                        const int32_t r = P.sn_r[q];
+                        const int32_t *R = P.lu_rowidx.data() + P.lu_colptr[c0v[q + 1]] - r;
+                        int64_t pos = 0;
+                        for (int32_t t = 0; t < r;) {
+                            pos = gallop_lower_bound(kr + pos, kr + clen, R[t]) - kr;
+                            const int64_t ch = pos / BCHUNK;
+                            const int64_t chend = (ch + 1) * BCHUNK;
+                            const int32_t t1 =
+                                chend >= clen ? r : (int32_t)(gallop_lower_bound(R + t, R + r, kr[chend]) - R);
+                            if (cbucket[ch].empty()) touched.push_back((int32_t)ch);
+                            cbucket[ch].push_back(BSeg{(int32_t)p, t, t1, 0});
+                            t = t1;
+                        }
+                    }
+                    std::sort(touched.begin(), touched.end());
+                    for (int32_t ch : touched) {
+                        BTask t{(int32_t)segs.size(), 0};
+                        segs.insert(segs.end(), cbucket[ch].begin(), cbucket[ch].end());
+                        t.seg_end = (int32_t)segs.size();
+                        tasks.push_back(t);
+                        cbucket[ch].clear();
+                    }
+                    g = ge;
+                }
+                parts[pi].tend.push_back((int32_t)tasks.size());
+            }
+        }
+    });
+    int64_t sb = 0, tb = 0;
+    for (size_t pi = 0; pi < parts.size(); pi++) {
+        for (int32_t q = 0; q < cut[pi + 1] - cut[pi]; q++)
+            P.btask_ptr[cut[pi] + q + 1] = (int32_t)(tb + parts[pi].tend[q]);
+        sb += (int64_t)parts[pi].segs.size();
+        tb += (int64_t)parts[pi].tasks.size();
+    }
+    P.bsegs.resize((size_t)sb);
+    P.btasks.resize((size_t)tb);
+    sb = tb = 0;
+    for (BPart &pt : parts) {
+        std::copy(pt.segs.begin(), pt.segs.end(), P.bsegs.begin() + sb);
+        for (size_t q = 0; q < pt.tasks.size(); q++)
+            P.btasks[(size_t)tb + q] = BTask{pt.tasks[q].seg_begin + (int32_t)sb, pt.tasks[q].seg_end + (int32_t)sb};
+        sb += (int64_t)pt.segs.size();
+        tb += (int64_t)pt.tasks.size();
+        pt = BPart();
+    }
 }
 
 // Start of the largest trailing block [t0, n), n - t0 <= tmax, in which every
