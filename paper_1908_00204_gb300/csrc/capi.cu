@@ -813,6 +813,14 @@ int glu_analyze_opts(int32_t n, const int32_t *colptr, const int32_t *rowidx, co
         delete h;
         return rc;
     }
+    if (h->opt.verbose && h->opt.factor_blocks) {
+        const HostPlan &P = h->P;
+        std::fprintf(stderr,
+                     "glu_analyze: supernodal schedule: %zu supernodes, %d block levels, %zu pairs, %lld map "
+                     "entries, %zu update segments, %zu update tasks\n",
+                     P.sn_r.size(), (int)P.nblev, P.bpairs.size(), (long long)P.bmap_size, P.bsegs.size(),
+                     P.btasks.size());
+    }
     if (h->opt.verbose) {
         const HostPlan &P = h->P;
         int64_t cnt[3] = {0, 0, 0}, sg[3] = {0, 0, 0}, wk[3] = {0, 0, 0};
