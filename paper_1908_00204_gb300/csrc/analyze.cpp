@@ -11,6 +11,8 @@
 #include <algorithm>
 #include <array>
 #include <atomic>
+#include <condition_variable>
+#include <mutex>
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
@@ -146,69 +148,254 @@ int permute_input(HostPlan &P, std::vector<int64_t> &bptr, std::vector<int32_t> 
 // known, every k < j with U(k,j) != 0 and L(j,k) != 0 can drop from its
 // search list the rows of L(:,k) below j: they are reached through j
 // (symmetric pruning); the result is unchanged.
+//
+// In parallel by subtrees.  struct(L+U) lies inside the Cholesky pattern of
+// B + B^T, so every k < j with U(k,j) != 0 is a descendant of j in the
+// elimination tree of B + B^T: column j reads, and prunes, only columns of
+// its own subtree.  Small disjoint subtrees are computed at once on threads,
+// each into its own row buffer.  The tree above them is cut into chains
+// (paths along which every node has one child in that part of the tree); a
+// chain runs, bottom up, once the chains below it are done, several at once.
+// The buffers are finally copied into column order.  The result is the same
+// for any thread count.
+
+// Elimination tree of B + B^T (Liu's algorithm with path compression):
+// parent[j] > j, or -1 for a root.
+std::vector<int32_t> etree_of_symmetric(int32_t n, const std::vector<int64_t> &bptr,
+                                        const std::vector<int32_t> &brow) {
+    // B's strictly lower entries B(r, i), r > i, listed by row r
+    std::vector<int64_t> lp((size_t)n + 1, 0);
+    for (int32_t i = 0; i < n; i++)
+        for (int64_t q = bptr[i]; q < bptr[i + 1]; q++)
+            if (brow[q] > i) lp[brow[q] + 1]++;
+    for (int32_t r = 0; r < n; r++) lp[r + 1] += lp[r];
+    std::vector<int32_t> lc((size_t)lp[n]);
+    {
+        std::vector<int64_t> f(lp.begin(), lp.end() - 1);
+        for (int32_t i = 0; i < n; i++)
+            for (int64_t q = bptr[i]; q < bptr[i + 1]; q++)
+                if (brow[q] > i) lc[f[brow[q]]++] = i;
+    }
+    std::vector<int32_t> parent((size_t)n, -1), anc((size_t)n, -1);
+    auto link = [&](int32_t i, int32_t j) {
+        int32_t r = i;
+        while (anc[r] != -1 && anc[r] != j) {
+            const int32_t t = anc[r];
+            anc[r] = j;
+            r = t;
+        }
+        if (anc[r] == -1) {
+            anc[r] = j;
+            parent[r] = j;
+        }
+    };
+    for (int32_t j = 0; j < n; j++) {
+        for (int64_t q = bptr[j]; q < bptr[j + 1]; q++)
+            if (brow[q] < j) link(brow[q], j);
+        for (int64_t q = lp[j]; q < lp[j + 1]; q++) link(lc[q], j);
+    }
+    return parent;
+}
+
 int symbolic(HostPlan &P, const std::vector<int64_t> &bptr, const std::vector<int32_t> &brow) {
     const int32_t n = P.n;
-    P.lu_colptr.assign((size_t)n + 1, 0);
-    P.diag_pos.assign((size_t)n, 0);
-    std::vector<int32_t> &rows = P.lu_rowidx;
-    rows.clear();
-    rows.reserve((size_t)bptr[n] * 4 + 16);
-    std::vector<int64_t> lend_pruned((size_t)n);
+    const int nth = analysis_threads();
+    // ---- the subtrees computed in parallel (none with one thread)
+    const std::vector<int32_t> parent = etree_of_symmetric(n, bptr, brow);
+    std::vector<int64_t> size((size_t)n, 1);
+    for (int32_t j = 0; j < n; j++)
+        if (parent[j] >= 0) size[parent[j]] += size[j];
+    std::vector<int32_t> comp((size_t)n, -1);   // subtree task of each column, -1: above them
+    int32_t ntask = 0;
+    if (nth > 1) {
+        const int64_t target = std::max<int64_t>(1, n / ((int64_t)nth * 4));
+        std::vector<int64_t> cptr((size_t)n + 1, 0);
+        for (int32_t j = 0; j < n; j++)
+            if (parent[j] >= 0) cptr[parent[j] + 1]++;
+        for (int32_t j = 0; j < n; j++) cptr[j + 1] += cptr[j];
+        std::vector<int32_t> child((size_t)cptr[n]);
+        {
+            std::vector<int64_t> f(cptr.begin(), cptr.end() - 1);
+            for (int32_t j = 0; j < n; j++)
+                if (parent[j] >= 0) child[f[parent[j]]++] = j;
+        }
+        std::vector<int32_t> stack;
+        for (int32_t j = 0; j < n; j++)
+            if (parent[j] < 0) stack.push_back(j);
+        while (!stack.empty()) {
+            const int32_t v = stack.back();
+            stack.pop_back();
+            if (size[v] <= target) {
+                comp[v] = ntask++;
+            } else {
+                for (int64_t q = cptr[v]; q < cptr[v + 1]; q++) stack.push_back(child[q]);
+            }
+        }
+        for (int32_t j = n - 1; j >= 0; j--)
+            if (comp[j] < 0 && parent[j] >= 0 && comp[parent[j]] >= 0) comp[j] = comp[parent[j]];
+    }
+    std::vector<std::vector<int32_t>> cols((size_t)ntask + 1);   // last: the columns above
+    for (int32_t j = 0; j < n; j++) cols[comp[j] >= 0 ? comp[j] : ntask].push_back(j);
+    // ---- per column: buffer, start in it, length, diagonal and pruned end
+    // (offsets relative to the column's start)
+    std::vector<int32_t> cb((size_t)n);
+    std::vector<int64_t> cs((size_t)n), cl((size_t)n), cd((size_t)n), ce((size_t)n);
     std::vector<uint8_t> pruned((size_t)n, 0);
-    std::vector<int32_t> mark((size_t)n, -1);
-    std::vector<int32_t> stk((size_t)n + 1);
-    std::vector<int64_t> nxt((size_t)n + 1);
-    std::vector<int32_t> found;
-    found.reserve(1024);
-    for (int32_t j = 0; j < n; j++) {
+    std::vector<std::vector<int32_t>> bufs((size_t)ntask + 1);
+    struct Scratch {
+        std::vector<int32_t> mark, stk, found;
+        std::vector<int64_t> nxt;
+    };
+    auto column = [&](int32_t j, int32_t bid, Scratch &sc) {
+        std::vector<int32_t> &mark = sc.mark, &stk = sc.stk, &found = sc.found;
+        std::vector<int64_t> &nxt = sc.nxt;
         found.clear();
         for (int64_t q = bptr[j]; q < bptr[j + 1]; q++) {
-            int32_t s = brow[q];
+            const int32_t s = brow[q];
             if (mark[s] == j) continue;
             mark[s] = j;
             found.push_back(s);
             if (s >= j) continue;
             int32_t top = 0;
             stk[0] = s;
-            nxt[0] = P.diag_pos[s] + 1;
+            nxt[0] = cd[s] + 1;
             while (top >= 0) {
-                int32_t v = stk[top];
-                int64_t e = lend_pruned[v];
+                const int32_t v = stk[top];
+                const int32_t *rv = bufs[cb[v]].data() + cs[v];
+                const int64_t e = ce[v];
                 int64_t t = nxt[top];
-                while (t < e && mark[rows[t]] == j) t++;
-                if (t == e) { top--; continue; }
-                int32_t w = rows[t];
+                while (t < e && mark[rv[t]] == j) t++;
+                if (t == e) {
+                    top--;
+                    continue;
+                }
+                const int32_t w = rv[t];
                 nxt[top] = t + 1;
                 mark[w] = j;
                 found.push_back(w);
                 if (w < j) {
                     top++;
                     stk[top] = w;
-                    nxt[top] = P.diag_pos[w] + 1;
+                    nxt[top] = cd[w] + 1;
                 }
             }
         }
         std::sort(found.begin(), found.end());
-        int64_t base = (int64_t)rows.size();
-        rows.insert(rows.end(), found.begin(), found.end());
-        int64_t end = (int64_t)rows.size();
-        P.lu_colptr[j + 1] = end;
-        int64_t d = base + (std::lower_bound(found.begin(), found.end(), j) - found.begin());
-        P.diag_pos[j] = d;
-        lend_pruned[j] = end;
+        std::vector<int32_t> &out = bufs[bid];
+        cb[j] = bid;
+        cs[j] = (int64_t)out.size();
+        out.insert(out.end(), found.begin(), found.end());
+        const int64_t d = std::lower_bound(found.begin(), found.end(), j) - found.begin();
+        cl[j] = (int64_t)found.size();
+        cd[j] = d;
+        ce[j] = (int64_t)found.size();
         // symmetric pruning of the columns k with U(k,j) != 0
-        for (int64_t q = base; q < d; q++) {
-            int32_t k = rows[q];
+        for (int64_t q = 0; q < d; q++) {
+            const int32_t k = found[q];
             if (pruned[k]) continue;
-            const int32_t *lb = rows.data() + P.diag_pos[k] + 1;
-            const int32_t *le = rows.data() + P.lu_colptr[k + 1];
+            const int32_t *rk = bufs[cb[k]].data() + cs[k];
+            const int32_t *lb = rk + cd[k] + 1;
+            const int32_t *le = rk + cl[k];
             const int32_t *it = std::lower_bound(lb, le, j);
             if (it != le && *it == j) {
-                lend_pruned[k] = (it - rows.data()) + 1;
+                ce[k] = (it - rk) + 1;
                 pruned[k] = 1;
             }
         }
+    };
+    auto scratch = [n](Scratch &sc) {
+        sc.mark.assign((size_t)n, -1);
+        sc.stk.resize((size_t)n + 1);
+        sc.nxt.resize((size_t)n + 1);
+        sc.found.reserve(1024);
+    };
+    // subtrees, largest first, taken by threads as they finish
+    std::vector<int32_t> order((size_t)ntask);
+    for (int32_t t = 0; t < ntask; t++) order[t] = t;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t a, int32_t b) { return cols[a].size() > cols[b].size(); });
+    // the columns above the subtrees: chains, each continuing the chain of
+    // its node's only child there
+    const std::vector<int32_t> &top = cols[ntask];
+    std::vector<int32_t> ntop((size_t)n, 0), only((size_t)n, -1), chain_of((size_t)n, -1);
+    for (int32_t j : top)
+        if (parent[j] >= 0) {
+            ntop[parent[j]]++;
+            only[parent[j]] = j;
+        }
+    std::vector<std::vector<int32_t>> chains;
+    for (int32_t j : top) {
+        if (ntop[j] == 1) {
+            chain_of[j] = chain_of[only[j]];
+        } else {
+            chain_of[j] = (int32_t)chains.size();
+            chains.emplace_back();
+        }
+        chains[chain_of[j]].push_back(j);
     }
+    const int32_t nchain = (int32_t)chains.size();
+    std::vector<int32_t> pending((size_t)nchain);
+    for (int32_t c = 0; c < nchain; c++) pending[c] = ntop[chains[c][0]];
+    bufs.resize((size_t)ntask + nchain);
+    std::vector<Scratch> scr((size_t)nth);
+    // subtrees first, taken by threads as they finish
+    std::atomic<int32_t> next{0};
+    run_threads(ntask > 0 ? nth : 1, [&](int t) {
+        scratch(scr[t]);
+        for (int32_t i; (i = next.fetch_add(1)) < ntask;)
+            for (int32_t j : cols[order[i]]) column(j, order[i], scr[t]);
+    });
+    // then the chains, each once the chains below it are done
+    std::mutex mu;
+    std::condition_variable cv;
+    std::vector<int32_t> ready;
+    for (int32_t c = 0; c < nchain; c++)
+        if (pending[c] == 0) ready.push_back(c);
+    int32_t remaining = nchain;
+    bool aborted = false;
+    run_threads(nchain > 0 ? nth : 1, [&](int t) {
+        if (scr[t].mark.empty()) scratch(scr[t]);
+        try {
+            for (;;) {
+                int32_t c;
+                {
+                    std::unique_lock<std::mutex> lk(mu);
+                    cv.wait(lk, [&] { return !ready.empty() || remaining == 0 || aborted; });
+                    if (ready.empty()) return;
+                    c = ready.back();
+                    ready.pop_back();
+                }
+                for (int32_t j : chains[c]) column(j, ntask + c, scr[t]);
+                {
+                    std::lock_guard<std::mutex> lk(mu);
+                    remaining--;
+                    const int32_t p = parent[chains[c].back()];
+                    if (p >= 0 && --pending[chain_of[p]] == 0) ready.push_back(chain_of[p]);
+                }
+                cv.notify_all();
+            }
+        } catch (...) {
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                aborted = true;
+            }
+            cv.notify_all();
+            throw;
+        }
+    });
+    scr.clear();
+    // ---- column order
+    P.lu_colptr.assign((size_t)n + 1, 0);
+    P.diag_pos.assign((size_t)n, 0);
+    for (int32_t j = 0; j < n; j++) P.lu_colptr[j + 1] = P.lu_colptr[j] + cl[j];
+    P.lu_rowidx.resize((size_t)P.lu_colptr[n]);
+    const std::vector<int32_t> cut = column_ranges(n, P.lu_colptr.data(), nth);
+    run_threads(nth, [&](int t) {
+        for (int32_t j = cut[t]; j < cut[t + 1]; j++) {
+            std::copy_n(bufs[cb[j]].data() + cs[j], cl[j], P.lu_rowidx.data() + P.lu_colptr[j]);
+            P.diag_pos[j] = P.lu_colptr[j] + cd[j];
+        }
+    });
     return GLU_OK;
 }
 
