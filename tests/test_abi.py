@@ -66,7 +66,9 @@ def test_host_analysis_bit_exact(glu, name):
 
 
 @pytest.mark.parametrize("seed", range(25))
-def test_host_analysis_random(glu, seed):
+def test_host_analysis_random(glu, seed, monkeypatch):
+    # the analysis runs on host threads: vary their number (1, 3, 16)
+    monkeypatch.setenv("GLU_ANALYZE_THREADS", str([1, 3, 16][(seed // 3) % 3]))
     n = 1 + seed * 7
     cp, ri, _ = synth.random_pattern_matrix(n, [0.02, 0.1, 0.3][seed % 3], 700 + seed, extra=2)
     perm = np.random.default_rng(seed).permutation(n).astype(np.int32)

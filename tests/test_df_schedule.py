@@ -158,17 +158,26 @@ def test_df_schedule_without_blocks(tmp_path, monkeypatch):
 
 
 def test_schedule_independent_of_analysis_threads(tmp_path, monkeypatch):
-    """The column schedule is built over level ranges on host threads; the
-    result must not depend on their number (per-level summary and the
-    dataflow items compared between 1 and 7 threads)."""
+    """The symbolic fill, the row views, the gather map and both
+    factorization schedules are built on host threads; the result must not
+    depend on their number (the fill, the full column schedule with its
+    gather map, the dataflow items and the supernodal schedule compared
+    between 1, 2 and 7 threads)."""
     m = synth.make("mesh100x200_nets64", 1)
     out = {}
-    for nth in (1, 7):
+    for nth in (1, 2, 7):
         monkeypatch.setenv("GLU_ANALYZE_THREADS", str(nth))
-        monkeypatch.setenv("GLU_DUMP_SCHEDULE", str(tmp_path / f"s{nth}.txt"))
+        monkeypatch.setenv("GLU_DUMP_COLUMNS", str(tmp_path / f"c{nth}.bin"))
         monkeypatch.setenv("GLU_DUMP_DF", str(tmp_path / f"d{nth}.bin"))
         h = glu.glu_analyze(m.n, m.colptr, m.rowidx, m.perm, glu.default_options(host_only=1))
-        out[nth] = (glu.glu_get_stats(h)["n_updates"], (tmp_path / f"s{nth}.txt").read_bytes(),
-                    (tmp_path / f"d{nth}.bin").read_bytes())
+        cp, ri = glu.glu_get_fill(h)
+        out[nth] = [np.asarray(cp).tobytes(), np.asarray(ri).tobytes(),
+                    (tmp_path / f"c{nth}.bin").read_bytes(), (tmp_path / f"d{nth}.bin").read_bytes()]
         glu.glu_destroy(h)
-    assert out[1] == out[7]
+        monkeypatch.delenv("GLU_DUMP_COLUMNS")
+        monkeypatch.setenv("GLU_DUMP_BLOCKS", str(tmp_path / f"b{nth}.bin"))
+        h = glu.glu_analyze(m.n, m.colptr, m.rowidx, m.perm, glu.default_options(host_only=1, factor_blocks=1))
+        out[nth].append((tmp_path / f"b{nth}.bin").read_bytes())
+        glu.glu_destroy(h)
+        monkeypatch.delenv("GLU_DUMP_BLOCKS")
+    assert out[1] == out[2] == out[7]
