@@ -206,6 +206,37 @@ def test_replay_covers_every_task_kind_and_the_dense_block(tmp_path, monkeypatch
     assert d0["ftail_t0"] == m.n                    # the final normalization pass instead
 
 
+@pytest.mark.parametrize("n", [64, 100])
+def test_replay_fully_dense_matrix(tmp_path, monkeypatch, n):
+    # degenerate: the whole matrix is the dense trailing block (it starts at
+    # column 0, so no level runs before it)
+    cp, ri, v = synth.random_pattern_matrix(n, 1.0, 31 + n)
+
+    class M:
+        pass
+    m = M()
+    m.n, m.colptr, m.rowidx, m.perm = n, cp, ri, None
+    d, kinds = run_case(tmp_path, monkeypatch, m, v)
+    assert d["ftail_t0"] == 0 and d["ftail_level"] == 0 and kinds.sum() == 0
+
+
+def test_replay_triangular_patterns(tmp_path, monkeypatch):
+    # degenerate: no U (no updates, only normalizations) and no L (one level)
+    n = 80
+    cp, ri, v = synth.random_pattern_matrix(n, 0.2, 77)
+
+    class M:
+        pass
+    for keep in (np.greater_equal, np.less_equal):      # lower / upper triangle of A
+        cols = np.repeat(np.arange(n), np.diff(cp))
+        sel = keep(ri, cols)
+        ncp = np.concatenate([[0], np.cumsum(np.bincount(cols[sel], minlength=n))]).astype(np.int32)
+        m = M()
+        m.n, m.colptr, m.rowidx, m.perm = n, ncp, ri[sel].astype(np.int32), None
+        d, kinds = run_case(tmp_path, monkeypatch, m, v[sel])
+        assert kinds.sum() == 0 and len(d["pairs"]) == 0
+
+
 def test_replay_random_pattern_with_permutation(tmp_path, monkeypatch):
     cp, ri, v = synth.random_pattern_matrix(150, 0.04, 11)
 
