@@ -111,12 +111,32 @@ def replay(n, t0, items, ptr, cols, chunks, snx, backward):
     return read, nblocks
 
 
-@pytest.mark.parametrize("case", ["grid32", "mesh_nets", "mesh100x200"])
+class _Pattern:
+    def __init__(self, n, colptr, rowidx):
+        self.n, self.colptr, self.rowidx, self.perm = n, colptr, rowidx, None
+
+
+def _triangle(n, upper):
+    cp, ri, _ = synth.random_pattern_matrix(n, 0.2, 78)
+    cols = np.repeat(np.arange(n), np.diff(cp))
+    sel = ri <= cols if upper else ri >= cols
+    ncp = np.concatenate([[0], np.cumsum(np.bincount(cols[sel], minlength=n))]).astype(np.int32)
+    return _Pattern(n, ncp, ri[sel].astype(np.int32))
+
+
+@pytest.mark.parametrize("case", ["grid32", "mesh_nets", "mesh100x200", "dense100", "lower", "upper"])
 def test_df_schedule_topological_and_complete(tmp_path, monkeypatch, case):
     if case == "grid32":
         m = synth.make("grid32_natural", 0)
     elif case == "mesh_nets":
         m = synth.CircuitMatrix(synth.CircuitSpec(30, 40, 8, 60, 0.02, 0.05, "nd"), 3)
+    elif case == "dense100":
+        # degenerate: the dense tail is the whole matrix, no dataflow item
+        cp, ri, _ = synth.random_pattern_matrix(100, 1.0, 5)
+        m = _Pattern(100, cp, ri)
+    elif case in ("lower", "upper"):
+        # degenerate: one of the two sweeps has only diagonal rows
+        m = _triangle(90, case == "upper")
     else:
         m = synth.make("mesh100x200_nets64", 1)
     path = tmp_path / "df.bin"
@@ -144,6 +164,8 @@ def test_df_schedule_topological_and_complete(tmp_path, monkeypatch, case):
     assert nbf == nbb
     if case == "mesh100x200":
         assert nbf > 10                       # separators give dense blocks
+    if case == "dense100":
+        assert t0 == 0 and len(items) == 0
 
 
 def test_df_schedule_without_blocks(tmp_path, monkeypatch):
