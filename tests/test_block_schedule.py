@@ -100,9 +100,14 @@ def replay(cp, ri, diag, lu, d):
     return lu
 
 
-@pytest.mark.parametrize("case", ["random", "mesh_nets", "arrow"])
+@pytest.mark.parametrize("case", ["random", "mesh_nets", "arrow", "dense"])
 def test_block_schedule_replay_matches_oracle(tmp_path, monkeypatch, case):
-    if case == "random":
+    if case == "dense":
+        # degenerate: every column in supernodes of 32 with nothing below the last
+        n = 100
+        cp, ri, v = synth.random_pattern_matrix(n, 1.0, 9)
+        perm = None
+    elif case == "random":
         n = 60
         cp, ri, v = synth.random_pattern_matrix(n, 0.12, 7)
         perm = np.random.default_rng(3).permutation(n).astype(np.int32)
