@@ -914,23 +914,33 @@ int glu_analyze_opts(int32_t n, const int32_t *colptr, const int32_t *rowidx, co
             std::fclose(fp);
         }
     }
-    if (const char *dump = std::getenv("GLU_DUMP_DF")) {
-        // the dataflow solve schedule as int64 words: counts (items, forward
-        // items, forward chunks, backward chunks, block tables f / b, tail
-        // start), then items (8 each), chunks (p0, p1), block tables
-        if (FILE *fp = std::fopen(dump, "wb")) {
-            const HostPlan &P = h->P;
-            std::vector<int64_t> w = {(int64_t)P.df_items.size() / 8, P.df_nfwd, (int64_t)P.df_fchunks.size(),
-                                      (int64_t)P.df_bchunks.size(), (int64_t)P.df_snx_f.size(),
-                                      (int64_t)P.df_snx_b.size(), P.tail_t0};
-            for (int32_t v : P.df_items) w.push_back(v);
-            for (const SolveChunk &c : P.df_fchunks) { w.push_back(c.p0); w.push_back(c.p1); }
-            for (const SolveChunk &c : P.df_bchunks) { w.push_back(c.p0); w.push_back(c.p1); }
-            for (int32_t v : P.df_snx_f) w.push_back(v);
-            for (int32_t v : P.df_snx_b) w.push_back(v);
+    // the dataflow solve schedules (single and batched) as int64 words:
+    // counts (items, forward items, forward chunks, backward chunks, block
+    // tables f / b, tail start), then items (8 each), chunks (p0, p1), block
+    // tables
+    auto dump_df = [](const char *path, const std::vector<int32_t> &items, int64_t nfwd,
+                      const std::vector<SolveChunk> &fch, const std::vector<SolveChunk> &bch,
+                      const std::vector<int32_t> &snf, const std::vector<int32_t> &snb, int64_t t0) {
+        if (FILE *fp = std::fopen(path, "wb")) {
+            std::vector<int64_t> w = {(int64_t)items.size() / 8, nfwd, (int64_t)fch.size(), (int64_t)bch.size(),
+                                      (int64_t)snf.size(), (int64_t)snb.size(), t0};
+            for (int32_t v : items) w.push_back(v);
+            for (const SolveChunk &c : fch) { w.push_back(c.p0); w.push_back(c.p1); }
+            for (const SolveChunk &c : bch) { w.push_back(c.p0); w.push_back(c.p1); }
+            for (int32_t v : snf) w.push_back(v);
+            for (int32_t v : snb) w.push_back(v);
             std::fwrite(w.data(), sizeof(int64_t), w.size(), fp);
             std::fclose(fp);
         }
+    };
+    if (const char *dump = std::getenv("GLU_DUMP_DF")) {
+        const HostPlan &P = h->P;
+        dump_df(dump, P.df_items, P.df_nfwd, P.df_fchunks, P.df_bchunks, P.df_snx_f, P.df_snx_b, P.tail_t0);
+    }
+    if (const char *dump = std::getenv("GLU_DUMP_DF_BATCHED")) {
+        const HostPlan &P = h->P;
+        dump_df(dump, P.df_items_b, P.bdf_nfwd, P.bdf_fchunks, P.bdf_bchunks, P.bdf_snx_f, P.bdf_snx_b,
+                P.btail_t0);
     }
     if (h->opt.host_only) {
         h->analyze_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

@@ -6,7 +6,7 @@ partial-sum chunks), every entry of L and U outside the dense tail must be
 read exactly once (by a row's dot product, a chunk, or the triangle sweep of
 a dense diagonal block), and every row before the tail must be produced once
 per sweep.  The dump is the library's diagnostic copy of the schedule
-(environment variable GLU_DUMP_DF at glu_analyze).
+(environment variables GLU_DUMP_DF and GLU_DUMP_DF_BATCHED at glu_analyze).
 """
 import numpy as np
 import pytest
@@ -124,8 +124,11 @@ def _triangle(n, upper):
     return _Pattern(n, ncp, ri[sel].astype(np.int32))
 
 
+@pytest.mark.parametrize("variant", ["single", "batched"])
 @pytest.mark.parametrize("case", ["grid32", "mesh_nets", "mesh100x200", "dense100", "lower", "upper"])
-def test_df_schedule_topological_and_complete(tmp_path, monkeypatch, case):
+def test_df_schedule_topological_and_complete(tmp_path, monkeypatch, case, variant):
+    # "batched": the schedule of the batched solves (longer chunks, a dense
+    # tail of at most 768 rows), dumped by GLU_DUMP_DF_BATCHED
     if case == "grid32":
         m = synth.make("grid32_natural", 0)
     elif case == "mesh_nets":
@@ -140,7 +143,7 @@ def test_df_schedule_topological_and_complete(tmp_path, monkeypatch, case):
     else:
         m = synth.make("mesh100x200_nets64", 1)
     path = tmp_path / "df.bin"
-    monkeypatch.setenv("GLU_DUMP_DF", str(path))
+    monkeypatch.setenv("GLU_DUMP_DF" if variant == "single" else "GLU_DUMP_DF_BATCHED", str(path))
     h = glu.glu_analyze(m.n, m.colptr, m.rowidx, m.perm, glu.default_options(host_only=1))
     cp, ri = glu.glu_get_fill(h)
     glu.glu_destroy(h)
