@@ -183,8 +183,9 @@ def kernel_source_hash():
 
 
 def traffic_for(workload):
-    """DRAM bytes per refactorization's level sweep from the committed ncu
-    summary, if it was taken on the current kernel source."""
+    """(DRAM bytes per refactorization's level sweep, note on the schedule it
+    was captured with) from the committed ncu summary, if it was taken on the
+    current kernel source; else None."""
     path = os.path.join(ROOT, "profiles", f"k_level_fp64_{workload}.traffic.json")
     try:
         d = json.load(open(path))
@@ -192,7 +193,7 @@ def traffic_for(workload):
         return None
     if d.get("kernel_source_hash") != kernel_source_hash():
         return None
-    return d.get("dram_bytes_per_factor")
+    return d.get("dram_bytes_per_factor"), d.get("schedule")
 
 
 # ------------------------------------------------------------------- arms
@@ -295,11 +296,18 @@ def measured_hbm_gbs():
 
 def roofline(achieved_tflops, traffic, fac_ms):
     """The level sweep against the FP64 pipe; its measured DRAM traffic (if
-    the committed capture matches the kernel) also as a bandwidth fraction."""
+    the committed capture matches the kernel) also as a bandwidth fraction.
+    ``traffic``: bytes per refactorization, or (bytes, note on the schedule
+    the capture was taken with), or None."""
+    note = None
+    if isinstance(traffic, tuple):
+        traffic, note = traffic
     r = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
          "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
          "kernel": "k_level (FP64 level sweep of one refactorization)",
          "peak_source": "nominal GB300 FP64 rate (the measured peaks cover HBM and bf16 only)"}
+    if note:
+        r["traffic_schedule"] = note
     hbm = measured_hbm_gbs()
     if traffic is not None and fac_ms > 0:
         r["dram_gbs"] = traffic / (fac_ms * 1e-3) / 1e9

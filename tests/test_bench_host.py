@@ -35,3 +35,5 @@ def test_roofline_record(monkeypatch):
     assert abs(r["dram_frac_of_measured_hbm"] - 500.0 / 6785.9) < 1e-12
     r = bench.roofline(0.25, None, 20.0)
     assert r["traffic"] is None and "dram_gbs" not in r
+    r = bench.roofline(0.25, (10.0e9, "captured with another schedule"), 20.0)
+    assert r["traffic"] == 10.0e9 and r["traffic_schedule"] == "captured with another schedule"
