@@ -293,6 +293,23 @@ int glu_solve_noalloc(glu_handle *h, const double *b, double *x, int32_t nrhs);
  * GLU_ERR_INVALID (bad arguments or indices). */
 int glu_order_nd(int32_t n, const int32_t *colptr, const int32_t *rowidx, int32_t *perm);
 
+/* Static pivoting with scaling for callers without one (the step before the
+ * fill-reducing order in the flow of Section II-C and Fig. 5, which names
+ * MC64; this is not MC64's code): a row permutation that maximizes the
+ * product of the diagonal magnitudes -- a minimum-cost perfect matching of
+ * columns to rows, cost log(max_k |a_kj|) - log|a_ij|, by shortest
+ * augmenting paths -- and scalings from its dual variables.  Host only.
+ * colptr[n+1], rowidx[nnz], values[nnz]: A in CSC (0-based; rows need not
+ * be sorted; explicit zeros are not used).  Outputs: row_perm[n] with
+ * row_perm[j] = the row of A matched to column j (B(j,:) = A(row_perm[j],:)
+ * puts the matching on B's diagonal); row_scale[n] (by A's row) and
+ * col_scale[n] such that |row_scale[i] a_ij col_scale[j]| <= 1 for every
+ * entry and = 1 on the matching.  Deterministic.  Errors: GLU_ERR_INVALID
+ * (bad arguments, indices or non-finite values), GLU_ERR_STRUCT_SINGULAR (no
+ * perfect matching exists), GLU_ERR_OOM. */
+int glu_static_pivot(int32_t n, const int32_t *colptr, const int32_t *rowidx, const double *values,
+                     int32_t *row_perm, double *row_scale, double *col_scale);
+
 /* Free the handle and everything it owns.  NULL is ignored. */
 void glu_destroy(glu_handle *h);
 

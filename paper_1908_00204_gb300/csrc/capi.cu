@@ -1299,6 +1299,15 @@ int glu_order_nd(int32_t n, const int32_t *colptr, const int32_t *rowidx, int32_
     }
 }
 
+int glu_static_pivot(int32_t n, const int32_t *colptr, const int32_t *rowidx, const double *values,
+                     int32_t *row_perm, double *row_scale, double *col_scale) {
+    try {
+        return static_pivot(n, colptr, rowidx, values, row_perm, row_scale, col_scale);
+    } catch (const std::bad_alloc &) {
+        return GLU_ERR_OOM;
+    }
+}
+
 const char *glu_strerror(int code) {
     switch (code) {
         case GLU_OK: return "ok";

@@ -244,6 +244,8 @@ int analyze_host(int32_t n, const int32_t *colptr, const int32_t *rowidx, const 
 // Nested-dissection ordering of the pattern of A + A^T (order.cpp): perm[new]
 // = old.  Returns a GLU_ code.
 int order_nested_dissection(int32_t n, const int32_t *colptr, const int32_t *rowidx, int32_t *perm);
+int static_pivot(int32_t n, const int32_t *colptr, const int32_t *rowidx, const double *values, int32_t *row_perm,
+                 double *row_scale, double *col_scale);
 
 // The column-level update schedule (pairs, segments, tasks, normalization
 // items) if analyze_host skipped it.  GLU_OK, or GLU_ERR_TOO_LARGE when a

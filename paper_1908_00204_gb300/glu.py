@@ -96,6 +96,7 @@ def load_library(path: Optional[str] = None):
             "glu_last_error_info": (C.c_int, [P, C.POINTER(i32)]),
             "glu_destroy": (None, [P]),
             "glu_order_nd": (C.c_int, [i32, P, P, P]),
+            "glu_static_pivot": (C.c_int, [i32, P, P, P, P, P, P]),
             "glu_strerror": (C.c_char_p, [C.c_int]),
         }
         for name, (res, args) in sig.items():
@@ -372,6 +373,36 @@ def glu_order_nd(n: int, colptr, rowidx) -> np.ndarray:
     perm = np.empty(max(n, 1), np.int32)
     _check(load_library().glu_order_nd(int(n), cp.ctypes.data, ri.ctypes.data, perm.ctypes.data), "glu_order_nd")
     return perm[:n]
+
+
+def glu_static_pivot(n: int, colptr, rowidx, values):
+    """Row matching with scaling: (row_perm, row_scale, col_scale), see
+    apply_static_pivot."""
+    cp = np.ascontiguousarray(colptr, np.int32)
+    ri = np.ascontiguousarray(rowidx, np.int32)
+    va = np.ascontiguousarray(values, np.float64)
+    rp = np.empty(max(n, 1), np.int32)
+    rs = np.empty(max(n, 1), np.float64)
+    cs = np.empty(max(n, 1), np.float64)
+    _check(load_library().glu_static_pivot(int(n), cp.ctypes.data, ri.ctypes.data, va.ctypes.data, rp.ctypes.data,
+                                           rs.ctypes.data, cs.ctypes.data), "glu_static_pivot")
+    return rp[:n], rs[:n], cs[:n]
+
+
+def apply_static_pivot(n: int, colptr, rowidx, values, row_perm, row_scale, col_scale):
+    """CSC of B = P_r D_r A D_c, B(k, j) = row_scale[r] A(r, j) col_scale[j]
+    with r = row_perm[k]: the matching on the diagonal, rows sorted.  Pure
+    index bookkeeping on the host."""
+    cp = np.asarray(colptr, np.int64)
+    ri = np.asarray(rowidx, np.int64)
+    va = np.asarray(values, np.float64)
+    new_row = np.empty(n, np.int64)
+    new_row[np.asarray(row_perm, np.int64)] = np.arange(n)
+    cols = np.repeat(np.arange(n), np.diff(cp))
+    rows = new_row[ri]
+    vals = np.asarray(row_scale)[ri] * va * np.asarray(col_scale)[cols]
+    order = np.lexsort((rows, cols))
+    return cp.astype(np.int32), rows[order].astype(np.int32), vals[order]
 
 
 def glu_strerror(code: int) -> str:

@@ -5,7 +5,8 @@
  *   an arrow n = 6 with a dense last row and column: no fill-in,
  *     nnz(L+U) = 3n - 2 = 16, levels = 2 (columns 0..4, then column 5).
  * Also: a malformed input is rejected with GLU_ERR_INVALID and a handle is
- * not returned; glu_order_nd returns a permutation.  Prints "ok" on success,
+ * not returned; glu_order_nd returns a permutation; glu_static_pivot puts a
+ * matrix's large anti-diagonal on the diagonal.  Prints "ok" on success,
  * else the first failed check, and exits non-zero. */
 #include <stdio.h>
 #include <stdlib.h>
@@ -65,6 +66,21 @@ int main(void) {
     for (i = 0; i < 6; i++) {
         CHECK(perm[i] >= 0 && perm[i] < 6 && !seen[perm[i]]);
         seen[perm[i]] = 1;
+    }
+    {
+        /* static pivoting: a full 3 x 3 matrix whose large entries sit on the
+         * anti-diagonal, so the matching reverses the rows */
+        const int32_t fcp[4] = {0, 3, 6, 9};
+        const int32_t fri[9] = {0, 1, 2, 0, 1, 2, 0, 1, 2};
+        const double fv[9] = {1.0, 2.0, 100.0, 3.0, 50.0, 1.0, 20.0, 1.0, 2.0};
+        int32_t rp[3];
+        double rs[3], cs[3];
+        CHECK(glu_static_pivot(3, fcp, fri, fv, rp, rs, cs) == GLU_OK);
+        CHECK(rp[0] == 2 && rp[1] == 1 && rp[2] == 0);
+        for (i = 0; i < 3; i++) {
+            const double d = rs[rp[i]] * fv[3 * i + rp[i]] * cs[i];
+            CHECK(d > 1.0 - 1e-12 && d < 1.0 + 1e-12);
+        }
     }
     printf("ok\n");
     return 0;
