@@ -38,6 +38,27 @@
  * used by two host threads at once; separate handles are independent.
  *
  * Return codes: GLU_OK (0) or one of the negative GLU_ERR_* codes below.
+ *
+ * Environment variables (read by glu_analyze unless noted; none is needed):
+ *   GLU_ANALYZE_THREADS  host threads of the analysis (1..64; default: the
+ *                        machine's, at most 16); the results do not depend on it.
+ *   GLU_SRC_MIN, GLU_LANE_MAX, GLU_LANE_SEGS
+ *                        task-size thresholds of the factorization schedule:
+ *                        the source count from which a target column is split
+ *                        into 32-position chunk tasks (default 5), and the
+ *                        largest task run by one lane, in updates (32) and
+ *                        segments (2).  Every value gives a valid schedule.
+ *   GLU_DUMP_COLUMNS, GLU_DUMP_BLOCKS, GLU_DUMP_DF, GLU_DUMP_DF_BATCHED,
+ *   GLU_DUMP_SCHEDULE    file paths: diagnostic copies of the column-level
+ *                        schedule (with the value gather map), the supernodal
+ *                        schedule, the single and batched solve schedules,
+ *                        and a per-level summary.
+ *   GLU_LEVEL_TIMES      file path: glu_factor without graph capture writes
+ *                        each level's device time (CUDA events).
+ *   GLU_TEST_FAIL_LEVEL, GLU_TEST_FAIL_SOLVE
+ *                        test hooks: make the analysis fail as an allocation
+ *                        would (a level of the column schedule, or the solve
+ *                        schedule), to test the GLU_ERR_OOM path.
  */
 #ifndef GLU_H_
 #define GLU_H_
