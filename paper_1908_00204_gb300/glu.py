@@ -274,6 +274,14 @@ def glu_sync(h: Handle) -> None:
     _check(load_library().glu_sync(h._ptr), "glu_sync", h)
 
 
+def glu_sync_status(h: Handle):
+    """glu_sync without raising: (code, column), column -1 unless the code is
+    GLU_ERR_ZERO_PIVOT or GLU_ERR_NONFINITE."""
+    code = load_library().glu_sync(h._ptr)
+    col = glu_last_error_info(h) if code in (GLU_ERR_ZERO_PIVOT, GLU_ERR_NONFINITE) else -1
+    return code, col
+
+
 def _nrhs(b, n):
     shape = tuple(b.shape)
     if len(shape) == 1:

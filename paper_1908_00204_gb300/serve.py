@@ -15,7 +15,11 @@ right-hand sides.  The loop:
 * runs batches of different patterns at the same time on separate CUDA
   streams ("slots"); a request that arrives while others run is admitted as
   soon as a slot and the memory budget allow it;
-* records each request's latency from submission to result-ready.
+* records each request's latency from submission to result-ready, and its
+  status: a zero or non-finite pivot (or another device error) reaches the
+  request as ``status`` / ``error_column`` instead of a solution.  A batch
+  shares one device error word, so a failed batch is run again one request
+  at a time and each request gets its own status.
 
 The host side is plain Python (argument marshalling and bookkeeping); every
 numeric step runs in the CUDA library.
@@ -51,6 +55,9 @@ class Request:
     t_done: float = 0.0
     x: Optional[np.ndarray] = None
     info: Optional[dict] = None
+    status: int = 0             # GLU_OK, or the GLU_ERR_* code of its factorization / solve
+    error_column: int = -1      # the failing pivot's column for GLU_ERR_ZERO_PIVOT / NONFINITE
+    solo: bool = False          # run alone (set when its batch failed)
 
 
 class _Resident:
@@ -75,6 +82,7 @@ class _Slot:
         self.reqs: List[Request] = []
         self.out = None
         self.info = None
+        self.error = None       # (code, column) raised while enqueueing
 
 
 class Server:
@@ -154,7 +162,7 @@ class Server:
         res = self._resident(best)
         if res is None:
             return False
-        take = min(len(q), self.max_batch)
+        take = 1 if q[0].solo else min(len(q), self.max_batch)
         nrhs = max(r.b.shape[0] for r in list(q)[:take])
         # a batch never evicts other patterns: it shrinks to what the budget
         # leaves (batch buffers stay with the pattern until it is evicted)
@@ -162,55 +170,86 @@ class Server:
         while take > 1 and self._batch_bytes(res, take, nrhs) - res.batch_bytes > free:
             take //= 2
         reqs = [q.popleft() for _ in range(take)]
+        if any(r.solo for r in reqs[1:]):
+            for r in reversed(reqs[1:]):
+                q.appendleft(r)
+            reqs, take = reqs[:1], 1
         nrhs = max(r.b.shape[0] for r in reqs)
         torch = self.torch
         res.busy = True
         res.last_use = time.perf_counter()
         slot.res, slot.reqs = res, reqs
         h = res.h
+        slot.error = None
         with torch.cuda.stream(slot.stream):
             _glu.glu_set_stream(h, slot.stream)
-            if take == 1:
-                r = reqs[0]
-                v = torch.from_numpy(r.values).to(self.device, non_blocking=True)
-                bb = torch.from_numpy(np.ascontiguousarray(r.b)).to(self.device, non_blocking=True)
-                if self.precision == "fp64":
-                    _glu.glu_factor(h, v)
-                    x = _glu.glu_solve(h, bb)
-                    slot.info = None
-                else:
-                    _glu.glu_factor_f32(h, v)
-                    x, slot.info = _glu.glu_solve_refine(h, bb, tol=self.tol, maxit=self.maxit)
-                slot.out = x
-            else:
-                res.batch_bytes = max(res.batch_bytes, self._batch_bytes(res, take, nrhs))
-                V = np.stack([r.values for r in reqs])
-                Bt = np.zeros((take, nrhs, res.pat.n))
-                for i, r in enumerate(reqs):
-                    Bt[i, : r.b.shape[0]] = r.b
-                Vd = torch.from_numpy(V).to(self.device, non_blocking=True)
-                Bd = torch.from_numpy(Bt).to(self.device, non_blocking=True)
-                if self.precision == "fp64":
-                    _glu.glu_factor_batched(h, Vd)
-                    x = _glu.glu_solve_batched(h, Bd)
-                    slot.info = None
-                else:
-                    _glu.glu_factor_batched_f32(h, Vd)
-                    x, slot.info = _glu.glu_solve_batched_refine(h, Bd, tol=self.tol, maxit=self.maxit)
-                slot.out = x
+            try:
+                self._enqueue(slot, res, reqs, nrhs)
+            except _glu.GluError as e:
+                slot.error = (e.code, e.column)
+                slot.out = None
             slot.event = torch.cuda.Event()
             slot.event.record(slot.stream)
         self.batches += 1
         return True
 
+    def _enqueue(self, slot: _Slot, res: _Resident, reqs: List[Request], nrhs: int) -> None:
+        """The batch's factorization and solve, on the slot's stream."""
+        torch = self.torch
+        h = res.h
+        take = len(reqs)
+        if take == 1:
+            r = reqs[0]
+            v = torch.from_numpy(r.values).to(self.device, non_blocking=True)
+            bb = torch.from_numpy(np.ascontiguousarray(r.b)).to(self.device, non_blocking=True)
+            if self.precision == "fp64":
+                _glu.glu_factor(h, v)
+                x = _glu.glu_solve(h, bb)
+                slot.info = None
+            else:
+                _glu.glu_factor_f32(h, v)
+                x, slot.info = _glu.glu_solve_refine(h, bb, tol=self.tol, maxit=self.maxit)
+            slot.out = x
+        else:
+            res.batch_bytes = max(res.batch_bytes, self._batch_bytes(res, take, nrhs))
+            V = np.stack([r.values for r in reqs])
+            Bt = np.zeros((take, nrhs, res.pat.n))
+            for i, r in enumerate(reqs):
+                Bt[i, : r.b.shape[0]] = r.b
+            Vd = torch.from_numpy(V).to(self.device, non_blocking=True)
+            Bd = torch.from_numpy(Bt).to(self.device, non_blocking=True)
+            if self.precision == "fp64":
+                _glu.glu_factor_batched(h, Vd)
+                x = _glu.glu_solve_batched(h, Bd)
+                slot.info = None
+            else:
+                _glu.glu_factor_batched_f32(h, Vd)
+                x, slot.info = _glu.glu_solve_batched_refine(h, Bd, tol=self.tol, maxit=self.maxit)
+            slot.out = x
+
     def _finish(self, slot: _Slot) -> None:
-        x = slot.out.cpu().numpy()
+        # the device error word of the handle: pivots of the factorization,
+        # bounded waits of the solve (device inputs leave it unread until here)
+        code, col = slot.error if slot.error is not None else _glu.glu_sync_status(slot.res.h)
+        if code != _glu.GLU_OK and len(slot.reqs) > 1:
+            q = self.queues[slot.res.pat.key]
+            for r in reversed(slot.reqs):
+                r.solo = True
+                q.appendleft(r)
+            self._release(slot)
+            return
+        x = slot.out.cpu().numpy() if code == _glu.GLU_OK else None
         now = time.perf_counter()
         for i, r in enumerate(slot.reqs):
-            r.x = x if len(slot.reqs) == 1 else x[i, : r.b.shape[0]].copy()
+            if x is not None:
+                r.x = x if len(slot.reqs) == 1 else x[i, : r.b.shape[0]].copy()
+            r.status, r.error_column = code, (col if code != _glu.GLU_OK else -1)
             r.info = slot.info
             r.t_done = now
             self.done.append(r)
+        self._release(slot)
+
+    def _release(self, slot: _Slot) -> None:
         slot.res.busy = False
         slot.res = None
         slot.reqs = []

@@ -79,3 +79,35 @@ def test_budget_evicts_idle_patterns(glu):
     srv.drain()
     assert len(srv.done) == len(reqs)
     assert srv.evictions > 0 and srv._bytes_in_use() <= srv.budget
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_zero_pivot_reaches_its_request(glu, precision):
+    """A request whose values make the first pivot exactly zero comes back with
+    GLU_ERR_ZERO_PIVOT and column 0 (read from the device error word, also when
+    it ran inside a batch); every other request still gets its solution."""
+    from paper_1908_00204_gb300.serve import Server
+    mats, reqs = mixed_requests(24, seed=6)
+    bad = {3, 11}
+    for i in bad:
+        m = mats[reqs[i].key]
+        p0 = int(m.perm[0])          # B(0, 0) = A(perm[0], perm[0]): the first pivot
+        cb, ce = int(m.colptr[p0]), int(m.colptr[p0 + 1])
+        v = reqs[i].values.copy()
+        v[cb + int(np.searchsorted(m.rowidx[cb:ce], p0))] = 0.0
+        reqs[i].values = v
+    tol = 1e-14 if precision == "fp32" else 1e-12
+    srv = Server(device_budget_bytes=8e9, max_batch=16, slots=2, precision=precision, tol=tol, maxit=5)
+    for key, m in mats.items():
+        srv.register(key, m.n, m.colptr, m.rowidx, m.perm)
+    for r in reqs:
+        srv.submit(r)
+    srv.drain()
+    assert sorted(r.rid for r in srv.done) == list(range(len(reqs)))
+    for r in srv.done:
+        if r.rid in bad:
+            assert r.status == glu.glu.GLU_ERR_ZERO_PIVOT and r.error_column == 0 and r.x is None
+        else:
+            m = mats[r.key]
+            assert r.status == 0 and r.error_column == -1
+            assert backward_error(m.n, m.colptr, m.rowidx, r.values, r.b, r.x) <= BERR_TOL

@@ -9,7 +9,9 @@ only after it has been polled a few times, so requests overlap.  Checked:
 every request gets the solution of its own system; a pattern is never evicted
 while its work is in flight; the budget is respected; a batch holds at most
 max_batch requests of one pattern; the pattern whose oldest request waited
-longest runs first.
+longest runs first; a request whose factorization meets a zero pivot gets
+that status and column (its batch is rerun one request at a time, so the
+others still get their solutions).
 """
 import contextlib
 import sys
@@ -41,8 +43,22 @@ class FakeTensor:
         return self.a
 
 
+GLU_OK, GLU_ERR_ZERO_PIVOT = 0, -3
+
+
+class GluError(RuntimeError):
+    def __init__(self, code, where, column=-1):
+        super().__init__(where)
+        self.code, self.column = code, column
+
+
 class FakeDevice:
-    """Handles, in-flight work and events of the fake GPU."""
+    """Handles, in-flight work and events of the fake GPU.  A value set whose
+    first entry is exactly zero stands for one with a zero pivot in column 0:
+    the device error word is set and read at the next sync."""
+
+    GLU_OK = GLU_OK
+    GluError = GluError
 
     def __init__(self, bytes_per_entry=8):
         self.bytes_per_entry = bytes_per_entry
@@ -54,7 +70,7 @@ class FakeDevice:
     # -- the library's calls used by the loop
     def glu_analyze(self, n, colptr, rowidx, perm=None, options=None):
         h = types.SimpleNamespace(n=n, colptr=np.asarray(colptr), rowidx=np.asarray(rowidx),
-                                  perm=perm, inflight=False, vals=None)
+                                  perm=perm, inflight=False, vals=None, err=GLU_OK)
         self.live[id(h)] = h
         self.analyses += 1
         return h
@@ -81,30 +97,48 @@ class FakeDevice:
         self.last = h
         self.log.append((h.n, batch))
 
+    def glu_sync_status(self, h):
+        code, h.err = h.err, GLU_OK
+        return code, (0 if code != GLU_OK else -1)
+
     def glu_factor(self, h, v):
         self._launch(h, 1)
         h.vals = v.a
+        if v.a[0] == 0.0:
+            h.err = GLU_ERR_ZERO_PIVOT
 
     def glu_factor_f32(self, h, v):
         self.glu_factor(h, v)
 
     def glu_solve(self, h, b):
+        if h.err != GLU_OK:
+            return FakeTensor(np.full(b.a.shape, np.nan))
         return FakeTensor(self._solve(h, h.vals, b.a).reshape(b.a.shape))
 
     def glu_solve_refine(self, h, b, tol=1e-12, maxit=10):
+        if h.err != GLU_OK:     # the library's refinement synchronizes and raises
+            code, h.err = h.err, GLU_OK
+            raise GluError(code, "glu_solve_refine", 0)
         return self.glu_solve(h, b), {"iterations": 1, "converged": 1}
 
     def glu_factor_batched(self, h, V):
         self._launch(h, V.a.shape[0])
         h.vals = V.a
+        if np.any(V.a[:, 0] == 0.0):
+            h.err = GLU_ERR_ZERO_PIVOT
 
     def glu_factor_batched_f32(self, h, V):
         self.glu_factor_batched(h, V)
 
     def glu_solve_batched(self, h, B):
+        if h.err != GLU_OK:
+            return FakeTensor(np.full(B.a.shape, np.nan))
         return FakeTensor(np.stack([self._solve(h, h.vals[i], B.a[i]) for i in range(B.a.shape[0])]))
 
     def glu_solve_batched_refine(self, h, B, tol=1e-12, maxit=10):
+        if h.err != GLU_OK:
+            code, h.err = h.err, GLU_OK
+            raise GluError(code, "glu_solve_batched_refine", 0)
         return self.glu_solve_batched(h, B), {"iterations": 1, "converged": 1}
 
 
@@ -159,9 +193,13 @@ def requests(mats, n_req, seed=0):
     return out
 
 
-def check_results(mats, done, n_req):
+def check_results(mats, done, n_req, failed=()):
     assert sorted(r.rid for r in done) == list(range(n_req))
     for r in done:
+        if r.rid in failed:
+            assert r.status == GLU_ERR_ZERO_PIVOT and r.error_column == 0 and r.x is None
+            continue
+        assert r.status == GLU_OK and r.error_column == -1
         m = mats[r.key]
         A = sp.csc_matrix((r.values, m.rowidx, m.colptr), shape=(m.n, m.n))
         x = np.atleast_2d(r.x)
@@ -227,3 +265,21 @@ def test_oldest_waiting_pattern_runs_first(server):
     assert [n for n, _ in dev.log] == [mats["p2"].n, mats["p0"].n, mats["p1"].n]
     assert [b for _, b in dev.log] == [1, 2, 1]
     check_results(mats, srv.done, 4)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_zero_pivot_reaches_its_request(server, precision):
+    mats = patterns()
+    srv, dev = server(device_budget_bytes=1e12, max_batch=8, slots=2, precision=precision)
+    for k, m in mats.items():
+        srv.register(k, m.n, m.colptr, m.rowidx, m.perm)
+    reqs = requests(mats, 24, seed=5)
+    bad = {reqs[3].rid, reqs[17].rid}
+    for r in reqs:
+        if r.rid in bad:
+            r.values = r.values.copy()
+            r.values[0] = 0.0
+        srv.submit(r)
+    srv.drain()
+    check_results(mats, srv.done, 24, failed=bad)
+    assert any(b > 1 for _, b in dev.log)       # batches ran, and the failed ones again one by one
