@@ -325,11 +325,25 @@ int glu_order_nd(int32_t n, const int32_t *colptr, const int32_t *rowidx, int32_
  * row_perm[j] = the row of A matched to column j (B(j,:) = A(row_perm[j],:)
  * puts the matching on B's diagonal); row_scale[n] (by A's row) and
  * col_scale[n] such that |row_scale[i] a_ij col_scale[j]| <= 1 for every
- * entry and = 1 on the matching.  Deterministic.  Errors: GLU_ERR_INVALID
+ * entry and = 1 on the matching, both up to rounding (within a few units in
+ * the last place: the scalings are exponentials of dual variables).  Deterministic.  Errors: GLU_ERR_INVALID
  * (bad arguments, indices or non-finite values), GLU_ERR_STRUCT_SINGULAR (no
  * perfect matching exists), GLU_ERR_OOM. */
 int glu_static_pivot(int32_t n, const int32_t *colptr, const int32_t *rowidx, const double *values,
                      int32_t *row_perm, double *row_scale, double *col_scale);
+
+/* Apply glu_static_pivot's result: B = P_r D_r A D_c in CSC, with
+ * B(k, j) = row_scale[r] * A(r, j) * col_scale[j] for r = row_perm[k], so the
+ * matching sits on B's diagonal (the first step of the flow of Section II-C,
+ * Fig. 5).  Host only.  B has A's column pointers: out_rowidx[nnz] and
+ * out_values[nnz] (caller-allocated, nnz = colptr[n]) receive its rows,
+ * ascending in every column, and values.  row_scale / col_scale may be NULL
+ * (no scaling).  A x = b is then B y = P_r D_r b with x = D_c y.  Errors:
+ * GLU_ERR_INVALID (bad arguments, row_perm not a permutation, an index out of
+ * range, a row twice in one column), GLU_ERR_OOM. */
+int glu_apply_static_pivot(int32_t n, const int32_t *colptr, const int32_t *rowidx, const double *values,
+                           const int32_t *row_perm, const double *row_scale, const double *col_scale,
+                           int32_t *out_rowidx, double *out_values);
 
 /* Free the handle and everything it owns.  NULL is ignored. */
 void glu_destroy(glu_handle *h);

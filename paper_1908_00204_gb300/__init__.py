@@ -10,4 +10,4 @@ from .glu import (GluError, Handle, default_options, glu_analyze, glu_destroy, g
                   glu_solve_batched_refine, glu_get_factors_batched,
                   glu_get_deps, glu_get_factors, glu_get_fill, glu_get_levels, glu_get_stats,
                   glu_last_error_info, glu_order_nd, glu_set_stream, glu_solve, glu_solve_noalloc, glu_strerror, glu_sync, load_library,
-                  glu_static_pivot, apply_static_pivot)
+                  glu_static_pivot, glu_apply_static_pivot, apply_static_pivot)

@@ -1308,6 +1308,17 @@ int glu_static_pivot(int32_t n, const int32_t *colptr, const int32_t *rowidx, co
     }
 }
 
+int glu_apply_static_pivot(int32_t n, const int32_t *colptr, const int32_t *rowidx, const double *values,
+                           const int32_t *row_perm, const double *row_scale, const double *col_scale,
+                           int32_t *out_rowidx, double *out_values) {
+    try {
+        return apply_static_pivot(n, colptr, rowidx, values, row_perm, row_scale, col_scale, out_rowidx,
+                                  out_values);
+    } catch (const std::bad_alloc &) {
+        return GLU_ERR_OOM;
+    }
+}
+
 const char *glu_strerror(int code) {
     switch (code) {
         case GLU_OK: return "ok";

@@ -246,6 +246,9 @@ int analyze_host(int32_t n, const int32_t *colptr, const int32_t *rowidx, const 
 int order_nested_dissection(int32_t n, const int32_t *colptr, const int32_t *rowidx, int32_t *perm);
 int static_pivot(int32_t n, const int32_t *colptr, const int32_t *rowidx, const double *values, int32_t *row_perm,
                  double *row_scale, double *col_scale);
+int apply_static_pivot(int32_t n, const int32_t *colptr, const int32_t *rowidx, const double *values,
+                       const int32_t *row_perm, const double *row_scale, const double *col_scale,
+                       int32_t *out_rowidx, double *out_values);
 
 // The column-level update schedule (pairs, segments, tasks, normalization
 // items) if analyze_host skipped it.  GLU_OK, or GLU_ERR_TOO_LARGE when a

@@ -143,11 +143,59 @@ int static_pivot(int32_t n, const int32_t *colptr, const int32_t *rowidx, const 
             done[i] = 0;
         }
     }
+    // The potentials were updated in floating point over many augmentations:
+    // take each v_j again as the smallest c_ij - u_i of its column, so every
+    // reduced cost computed from the final u and v is >= 0 (the scaled
+    // entries are then <= 1 up to the rounding of exp and the products).
     for (int32_t j = 0; j < n; j++) {
+        double vj = INF;
+        for (int32_t p = colptr[j]; p < colptr[j + 1]; p++) {
+            if (values[p] == 0.0) continue;
+            vj = std::min(vj, (lmax[j] - std::log(std::fabs(values[p]))) - u[rowidx[p]]);
+        }
         row_perm[j] = mate_col[j];
-        col_scale[j] = std::exp(v[j] - lmax[j]);
+        col_scale[j] = std::exp(vj - lmax[j]);
     }
     for (int32_t i = 0; i < n; i++) row_scale[i] = std::exp(u[i]);
+    return GLU_OK;
+}
+
+int apply_static_pivot(int32_t n, const int32_t *colptr, const int32_t *rowidx, const double *values,
+                       const int32_t *row_perm, const double *row_scale, const double *col_scale,
+                       int32_t *out_rowidx, double *out_values) {
+    if (n < 0 || (n > 0 && (!colptr || !rowidx || !values || !row_perm || !out_rowidx || !out_values)))
+        return GLU_ERR_INVALID;
+    if (n == 0) return GLU_OK;
+    if (colptr[0] != 0) return GLU_ERR_INVALID;
+    // new_row[row_perm[k]] = k: row_perm must be a permutation
+    std::vector<int32_t> new_row((size_t)n, -1);
+    for (int32_t k = 0; k < n; k++) {
+        const int32_t r = row_perm[k];
+        if (r < 0 || r >= n || new_row[r] >= 0) return GLU_ERR_INVALID;
+        new_row[r] = k;
+    }
+    std::vector<std::pair<int32_t, double>> col;
+    for (int32_t j = 0; j < n; j++) {
+        const int32_t b = colptr[j], e = colptr[j + 1];
+        if (e < b) return GLU_ERR_INVALID;
+        col.clear();
+        const double cs = col_scale ? col_scale[j] : 1.0;
+        for (int32_t p = b; p < e; p++) {
+            const int32_t r = rowidx[p];
+            if (r < 0 || r >= n) return GLU_ERR_INVALID;
+            const double rs = row_scale ? row_scale[r] : 1.0;
+            col.emplace_back(new_row[r], rs * values[p] * cs);
+        }
+        std::sort(col.begin(), col.end(),
+                  [](const std::pair<int32_t, double> &x, const std::pair<int32_t, double> &y) {
+                      return x.first < y.first;
+                  });
+        for (size_t q = 0; q < col.size(); q++) {
+            if (q > 0 && col[q].first == col[q - 1].first) return GLU_ERR_INVALID;   // duplicate row
+            out_rowidx[b + (int32_t)q] = col[q].first;
+            out_values[b + (int32_t)q] = col[q].second;
+        }
+    }
     return GLU_OK;
 }
 

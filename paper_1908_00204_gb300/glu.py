@@ -97,6 +97,7 @@ def load_library(path: Optional[str] = None):
             "glu_destroy": (None, [P]),
             "glu_order_nd": (C.c_int, [i32, P, P, P]),
             "glu_static_pivot": (C.c_int, [i32, P, P, P, P, P, P]),
+            "glu_apply_static_pivot": (C.c_int, [i32, P, P, P, P, P, P, P, P]),
             "glu_strerror": (C.c_char_p, [C.c_int]),
         }
         for name, (res, args) in sig.items():
@@ -397,20 +398,25 @@ def glu_static_pivot(n: int, colptr, rowidx, values):
     return rp[:n], rs[:n], cs[:n]
 
 
-def apply_static_pivot(n: int, colptr, rowidx, values, row_perm, row_scale, col_scale):
-    """CSC of B = P_r D_r A D_c, B(k, j) = row_scale[r] A(r, j) col_scale[j]
-    with r = row_perm[k]: the matching on the diagonal, rows sorted.  Pure
-    index bookkeeping on the host."""
-    cp = np.asarray(colptr, np.int64)
-    ri = np.asarray(rowidx, np.int64)
-    va = np.asarray(values, np.float64)
-    new_row = np.empty(n, np.int64)
-    new_row[np.asarray(row_perm, np.int64)] = np.arange(n)
-    cols = np.repeat(np.arange(n), np.diff(cp))
-    rows = new_row[ri]
-    vals = np.asarray(row_scale)[ri] * va * np.asarray(col_scale)[cols]
-    order = np.lexsort((rows, cols))
-    return cp.astype(np.int32), rows[order].astype(np.int32), vals[order]
+def glu_apply_static_pivot(n: int, colptr, rowidx, values, row_perm, row_scale=None, col_scale=None):
+    """CSC of B = P_r D_r A D_c (glu_apply_static_pivot): (colptr, rowidx, values)."""
+    cp = np.ascontiguousarray(colptr, np.int32)
+    ri = np.ascontiguousarray(rowidx, np.int32)
+    va = np.ascontiguousarray(values, np.float64)
+    rp = np.ascontiguousarray(row_perm, np.int32)
+    rs = None if row_scale is None else np.ascontiguousarray(row_scale, np.float64)
+    cs = None if col_scale is None else np.ascontiguousarray(col_scale, np.float64)
+    nnz = int(cp[n]) if n > 0 else 0
+    out_ri = np.empty(max(nnz, 1), np.int32)
+    out_va = np.empty(max(nnz, 1), np.float64)
+    _check(load_library().glu_apply_static_pivot(int(n), cp.ctypes.data, ri.ctypes.data, va.ctypes.data,
+                                                 rp.ctypes.data, None if rs is None else rs.ctypes.data,
+                                                 None if cs is None else cs.ctypes.data, out_ri.ctypes.data,
+                                                 out_va.ctypes.data), "glu_apply_static_pivot")
+    return cp.copy(), out_ri[:nnz], out_va[:nnz]
+
+
+apply_static_pivot = glu_apply_static_pivot
 
 
 def glu_strerror(code: int) -> str:

@@ -136,3 +136,34 @@ def test_deterministic():
     a = glu.glu_static_pivot(60, cp, ri, v)
     b = glu.glu_static_pivot(60, cp.copy(), ri.copy(), v.copy())
     assert all(np.array_equal(x, y) for x, y in zip(a, b))
+
+
+def test_apply_static_pivot_matches_scipy():
+    """glu_apply_static_pivot against the same product formed with scipy:
+    B = P_r D_r A D_c, rows ascending in every column."""
+    cp, ri, v, A = random_nonsingular(80, 0.06, 21)
+    rp, rs, cs = glu.glu_static_pivot(80, cp, ri, v)
+    bcp, bri, bva = glu.glu_apply_static_pivot(80, cp, ri, v, rp, rs, cs)
+    want = (sp.diags(rs) @ sp.csc_matrix(A) @ sp.diags(cs)).tocsr()[rp, :].tocsc()
+    want.sort_indices()
+    assert np.array_equal(bcp, want.indptr) and np.array_equal(bri, want.indices)
+    np.testing.assert_allclose(bva, want.data, rtol=1e-15, atol=0)
+    assert np.all(np.diff(bri[bcp[0]:bcp[1]]) > 0)
+    # without scalings: a pure row permutation
+    bcp, bri, bva = glu.glu_apply_static_pivot(80, cp, ri, v, rp)
+    want = sp.csc_matrix(A).tocsr()[rp, :].tocsc()
+    want.sort_indices()
+    assert np.array_equal(bri, want.indices) and np.array_equal(bva, want.data)
+
+
+def test_apply_static_pivot_invalid():
+    cp = np.array([0, 2, 3], np.int32)
+    ri = np.array([0, 1, 1], np.int32)
+    v = np.ones(3)
+    for rp in ([0, 0], [0, 2], [-1, 1]):        # not a permutation
+        with pytest.raises(glu.GluError) as e:
+            glu.glu_apply_static_pivot(2, cp, ri, v, np.array(rp, np.int32))
+        assert e.value.code == glu.GLU_ERR_INVALID
+    with pytest.raises(glu.GluError) as e:          # a row twice in one column
+        glu.glu_apply_static_pivot(2, cp, np.array([1, 1, 0], np.int32), v, np.array([1, 0], np.int32))
+    assert e.value.code == glu.GLU_ERR_INVALID
