@@ -127,8 +127,19 @@ typedef struct glu_options {
                                  as dense panels and update their targets once per run
                                  (levels of the contracted Algorithm 4 graph); 0 (default):
                                  one level per Algorithm 4 level */
-    int32_t reserved[1];
+    int32_t row_lookup;       /* how the level kernels find a row of L(:,j) in target column
+                                 k: 1 a position map (2 or 4 bytes per update, built
+                                 once per pattern; the fastest); 2 a run table (one
+                                 8-byte record per run of rows that sit on consecutive
+                                 positions of column k, about one per 20 updates on
+                                 circuit matrices; a warp finds its rows' runs by ballots
+                                 and shuffles); 0 (default): the map when it takes at most
+                                 GLU_MAP_BUDGET_BYTES, else the run table */
 } glu_options;
+
+/* Device memory the position map may take before row_lookup 0 switches to
+ * the run table (8 GiB). */
+#define GLU_MAP_BUDGET_BYTES (8LL << 30)
 
 /* Analysis statistics (glu_get_stats). */
 typedef struct glu_stats {
@@ -151,6 +162,11 @@ typedef struct glu_stats {
     int64_t kernel_launches;  /* CUDA kernels this handle has launched so far */
     int32_t tail_rows;        /* rows of the dense tail solved by one block (0: none) */
     int32_t factor_tail_cols; /* columns of the dense block factored densely (0: none) */
+    int32_t row_lookup;       /* the level kernels' row lookup: 1 position map, 2 run
+                                 table, 0 none built yet (see glu_options.row_lookup) */
+    int32_t spare;
+    int64_t lookup_bytes;     /* device bytes of that map or table */
+    int64_t n_runs;           /* runs in the run table (0 with the map) */
 } glu_stats;
 
 /* Outcome of glu_solve_refine. */
@@ -249,6 +265,10 @@ int glu_solve_batched_refine(glu_handle *h, const double *b, double *x, int32_t 
  * memory (pattern order, nnz_lu doubles); synchronizes. */
 int glu_get_factors_batched(glu_handle *h, int32_t set, double *lu_val_host);
 
+/* The same for the FP32 factors of one set of the last
+ * glu_factor_batched_f32 (nnz_lu floats); synchronizes. */
+int glu_get_factors_batched_f32(glu_handle *h, int32_t set, float *lu_val_host);
+
 /* Pattern of the fill (Section II-A): lu_colptr[n+1], lu_rowidx[nnz]
  * (rows ascending per column), host memory owned by the handle. */
 int glu_get_fill(const glu_handle *h, const int64_t **lu_colptr,
@@ -269,6 +289,11 @@ int glu_get_levels(const glu_handle *h, int32_t *nlevels, const int32_t **level_
  * synchronizes and returns any pending device error. */
 int glu_get_factors(glu_handle *h, double *lu_val_host);
 
+/* Copy the FP32 factor values of the last glu_factor_f32 (pattern order,
+ * nnz_lu floats) to host memory; synchronizes and returns any pending device
+ * error (GLU_ERR_NOT_FACTORED before a successful glu_factor_f32). */
+int glu_get_factors_f32(glu_handle *h, float *lu_val_host);
+
 /* Analysis statistics. */
 int glu_get_stats(const glu_handle *h, glu_stats *s);
 
@@ -282,22 +307,26 @@ int glu_last_error_info(const glu_handle *h, int32_t *column);
  * could fail, or stall the device while it runs), or code that hands the
  * library memory owned by someone else's allocator.
  *
- * Same computation and result as glu_solve (one scratch vector of n * nrhs
- * values plus the partial sums of the long rows), but the scratch is a
- * fixed, file-scope device array of GLU_NOALLOC_SCRATCH_DOUBLES doubles,
- * which every GPU where the library's device code gets loaded holds until
- * the process exits.  b and x must
- * be device pointers (no staging); the call is stream-ordered on the
- * handle's stream and returns once enqueued.
+ * The same launches as glu_solve on the handle's solve schedule (the
+ * dataflow solve by default, the per-level solve with solve_mode 0), so the
+ * result equals glu_solve's bit for bit; only the scratch differs: a fixed,
+ * file-scope device array of GLU_NOALLOC_SCRATCH_DOUBLES doubles, which
+ * every GPU where the library's device code gets loaded holds until the
+ * process exits.  The dataflow solve's ready flags and error word are the
+ * handle's own, allocated by glu_analyze.  b and x must be device pointers
+ * (no staging); the call is stream-ordered on the handle's stream and
+ * returns once enqueued.
  *
- * Needs n * nrhs + (longest-row chunks) * nrhs doubles; a larger problem is
- * rejected with GLU_ERR_TOO_LARGE before anything is launched.  The first
- * call on a device looks up the array's device address (cudaGetSymbolAddress,
- * with that device current); make that first call before any stream capture.
- * All calls share the one array and it keeps the last call's contents (the
- * solve writes every scratch value before reading it, so nothing has to
- * start at zero); calls whose work overlaps on the GPU, from any handle or
- * stream, race on the array and must be serialized by the caller.
+ * Needs 2 * n * nrhs + (long-row chunks) * nrhs doubles for the dataflow
+ * solve (n * nrhs + chunks * nrhs for the per-level one), each part rounded
+ * up to 32 values; a larger problem is rejected with GLU_ERR_TOO_LARGE
+ * before anything is launched.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current);
+ * make that first call before any stream capture.  All calls share the one
+ * array and it keeps the last call's contents (the solve writes every
+ * scratch value before reading it, so nothing has to start at zero); calls
+ * whose work overlaps on the GPU, from any handle or stream, race on the
+ * array and must be serialized by the caller.
  * Errors: GLU_ERR_INVALID (host pointers, nrhs < 0), GLU_ERR_NOT_FACTORED,
  * GLU_ERR_TOO_LARGE, GLU_ERR_CUDA. */
 int glu_solve_noalloc(glu_handle *h, const double *b, double *x, int32_t nrhs);

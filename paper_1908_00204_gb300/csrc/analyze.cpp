@@ -909,7 +909,7 @@ int schedule(HostPlan &P, const glu_options &opt, int num_sms) {
             Seg &sg = P.segs[(size_t)sbase[t] + q];
             sg.pos = P.pair_pos[ps.pair];
             sg.dj = P.diag_pos[P.pair_j[ps.pair]];
-            sg.mb = P.pair_map[ps.pair];
+            sg.rb = ps.pair;          // the device replaces it with the segment's runs
             sg.t0 = ps.t0;
             sg.t1 = ps.t1;
         }
@@ -948,8 +948,8 @@ int schedule(HostPlan &P, const glu_options &opt, int num_sms) {
     }
     if (opt.verbose)
         std::fprintf(stderr, "glu_analyze: schedule phases: tasks %.0f ms (%d threads), flatten %.0f ms, "
-                     "normalization items %.0f ms\n", ts_tasks - ts_pairs, nth, ts_flat - ts_tasks,
-                     now_ms() - ts_flat);
+                     "normalization items %.0f ms; %zu segments, %zu tasks\n", ts_tasks - ts_pairs, nth,
+                     ts_flat - ts_tasks, now_ms() - ts_flat, P.segs.size(), P.tasks.size());
     P.has_schedule = true;
     return GLU_OK;
 }

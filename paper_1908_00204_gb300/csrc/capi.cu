@@ -22,11 +22,14 @@ struct glu_handle {
     int device = 0;
     int num_sms = 152;
     cudaStream_t stream = nullptr;
-    // device memory: one arena for the schedule, the map apart
+    // device memory: one arena for the schedule, the row lookup apart
     char *arena = nullptr;
     size_t arena_bytes = 0;
-    void *map = nullptr;
-    size_t map_total = 0;
+    Run *d_runs = nullptr;        // run table (lookup 0)
+    void *d_map = nullptr;        // position map (lookup 2 or 4 bytes per update)
+    size_t map_total = 0;         // bytes of the row lookup
+    int64_t n_runs = 0;
+    int lookup = 0;
     char *carena = nullptr;      // the column-level schedule (built on first use in block mode)
     size_t carena_bytes = 0;
     bool col_ready = false;
@@ -46,6 +49,7 @@ struct glu_handle {
     int64_t *d_diag = nullptr;
     int32_t *d_pair_j = nullptr;
     int64_t *d_pair_pos = nullptr;
+    int64_t *d_pair_runs = nullptr;
     int64_t *d_pair_map = nullptr;
     Seg *d_segs = nullptr;
     Task *d_tasks = nullptr;
@@ -235,7 +239,7 @@ int enqueue_levels(glu_handle *h, const FactorArgs<T> &a, cudaStream_t st) {
         const bool pipelined = l == nl ? (nl > 0 && P.level_mode[nl - 1] == 2) : P.level_mode[l] == 2;
         if (!pipelined) {
             const LevelRange r = level_range(P, l);
-            CKL((r.t_end - r.t_begin) + (r.n_end - r.n_begin) > 0, launch_level<T>(a, h->map_bytes, r, h->num_sms, st));
+            CKL((r.t_end - r.t_begin) + (r.n_end - r.n_begin) > 0, launch_level<T>(a, h->lookup, r, h->num_sms, st));
             l++;
             continue;
         }
@@ -244,16 +248,16 @@ int enqueue_levels(glu_handle *h, const FactorArgs<T> &a, cudaStream_t st) {
         if (!dense && e == nl) e = nl + 1;   // include the final pass
         if (e - l == 1) {
             const LevelRange r = level_range(P, l);
-            CKL((r.t_end - r.t_begin) + (r.n_end - r.n_begin) > 0, launch_level<T>(a, h->map_bytes, r, h->num_sms, st));
+            CKL((r.t_end - r.t_begin) + (r.n_end - r.n_begin) > 0, launch_level<T>(a, h->lookup, r, h->num_sms, st));
         } else {
-            CKL(1, launch_levels_persistent<T>(a, h->map_bytes, h->d_ranges + l, e - l, bar, h->num_sms, st));
+            CKL(1, launch_levels_persistent<T>(a, h->lookup, h->d_ranges + l, e - l, bar, h->num_sms, st));
         }
         l = e;
     }
     if (dense) {
         LevelRange r = level_range(P, lend);
         r.t_begin = r.row_begin = r.lane_begin = r.t_end = 0;   // normalizations only
-        CKL(r.n_end > r.n_begin, launch_level<T>(a, h->map_bytes, r, h->num_sms, st));
+        CKL(r.n_end > r.n_begin, launch_level<T>(a, h->lookup, r, h->num_sms, st));
         DenseTailArgs d{P.ftail_t0, P.n - P.ftail_t0, h->d_lu_colptr};
         CKL(1, launch_dense_tail<T>(a.lu, d, bar, h->num_sms, st));
     }
@@ -302,7 +306,7 @@ int enqueue_factor(glu_handle *h, const double *av, cudaStream_t st, std::vector
         for (int32_t l = 0; l <= nl; l++) {
             const LevelRange r = level_range(P, l);
             CKL((r.t_end - r.t_begin) + (r.n_end - r.n_begin) > 0,
-                launch_level<double>(a, h->map_bytes, r, h->num_sms, st));
+                launch_level<double>(a, h->lookup, r, h->num_sms, st));
             CK(cudaEventRecord((*lev_events)[l + 1], st));
         }
     } else {
@@ -407,7 +411,8 @@ FactorArgs<T> fargs_t(glu_handle *h, T *lu) {
     FactorArgs<T> a;
     a.lu = lu;
     a.diag_pos = h->d_diag;
-    a.map = h->map;
+    a.map = h->d_map;
+    a.runs = h->d_runs;
     a.segs = h->d_segs;
     a.tasks = h->d_tasks;
     a.norms = h->d_norms;
@@ -524,7 +529,8 @@ FactorArgs<double> fargs(glu_handle *h) {
     FactorArgs<double> a;
     a.lu = h->d_lu;
     a.diag_pos = h->d_diag;
-    a.map = h->map;
+    a.map = h->d_map;
+    a.runs = h->d_runs;
     a.segs = h->d_segs;
     a.tasks = h->d_tasks;
     a.norms = h->d_norms;
@@ -547,8 +553,8 @@ SolveArgs<double> sargs(glu_handle *h) {
 }
 
 // The column-level schedule on the device: pair tables, segments, tasks,
-// normalization items, per-level ranges and the position map (built by
-// k_map_build).  Run by glu_analyze for the column-level factorization and
+// normalization items, per-level ranges and the run table (built by k_runs
+// and k_seg_runs).  Run by glu_analyze for the column-level factorization and
 // on first use otherwise (the batched path runs column levels).
 int setup_column_plan(glu_handle *h) {
     if (h->col_ready) return GLU_OK;
@@ -559,26 +565,34 @@ int setup_column_plan(glu_handle *h) {
     } catch (const std::bad_alloc &) {
         return GLU_ERR_OOM;
     }
+    const int64_t npairs = (int64_t)P.pair_j.size();
+    // the row lookup: the position map unless it would exceed the budget
+    const int64_t map_need = std::max<int64_t>(P.n_updates, 1) * h->map_bytes;
+    const int want = h->opt.row_lookup;
+    h->lookup = (want == 1 || (want != 2 && map_need <= (int64_t)GLU_MAP_BUDGET_BYTES)) ? h->map_bytes : 0;
     Carve c;
     const size_t o_pj = c.take<int32_t>(P.pair_j.size()), o_ppos = c.take<int64_t>(P.pair_pos.size()),
-                 o_pmap = c.take<int64_t>(P.pair_map.size()), o_segs = c.take<Seg>(P.segs.size()),
-                 o_tasks = c.take<Task>(P.tasks.size()), o_norms = c.take<NormItem>(P.norms.size()),
-                 o_pk = c.take<int32_t>(P.pair_k.size()), o_rng = c.take<LevelRange>(P.level_ptr.size());
+                 o_pruns = c.take<int64_t>((size_t)npairs + 1), o_pmap = c.take<int64_t>((size_t)npairs + 1),
+                 o_segs = c.take<Seg>(P.segs.size()), o_tasks = c.take<Task>(P.tasks.size()),
+                 o_norms = c.take<NormItem>(P.norms.size()), o_pk = c.take<int32_t>(P.pair_k.size()),
+                 o_rng = c.take<LevelRange>(P.level_ptr.size()),
+                 o_cnt = c.take<int32_t>((size_t)std::max<int64_t>(npairs, 1));
     h->carena_bytes = c.off + 256;
     CK(cudaMalloc(&h->carena, h->carena_bytes));
     char *A = h->carena;
     h->d_pair_j = at<int32_t>(A, o_pj);
     h->d_pair_pos = at<int64_t>(A, o_ppos);
+    h->d_pair_runs = at<int64_t>(A, o_pruns);
     h->d_pair_map = at<int64_t>(A, o_pmap);
     h->d_segs = at<Seg>(A, o_segs);
     h->d_tasks = at<Task>(A, o_tasks);
     h->d_norms = at<NormItem>(A, o_norms);
     h->d_ranges = at<LevelRange>(A, o_rng);
     int32_t *d_pair_k = at<int32_t>(A, o_pk);
+    int32_t *d_counts = at<int32_t>(A, o_cnt);
     CK(upload(h->d_pair_j, P.pair_j));
     CK(upload(h->d_pair_pos, P.pair_pos));
-    CK(upload(h->d_pair_map, P.pair_map));
-    CK(upload(h->d_segs, P.segs));
+    CK(upload(h->d_segs, P.segs));          // rb: the pair index until the passes below
     CK(upload(h->d_tasks, P.tasks));
     CK(upload(h->d_norms, P.norms));
     CK(upload(d_pair_k, P.pair_k));
@@ -587,20 +601,52 @@ int setup_column_plan(glu_handle *h) {
         for (size_t l = 0; l < rg.size(); l++) rg[l] = level_range(P, (int32_t)l);
         CK(upload(h->d_ranges, rg));
     }
-    h->map_total = (size_t)std::max<int64_t>(P.n_updates, 1) * h->map_bytes;
-    CK(cudaMalloc(&h->map, h->map_total));
-    MapBuildArgs mb;
-    mb.lu_colptr = h->d_lu_colptr;
-    mb.lu_rowidx = h->d_lu_rowidx;
-    mb.diag_pos = h->d_diag;
-    mb.pair_j = h->d_pair_j;
-    mb.pair_k = d_pair_k;
-    mb.pair_pos = h->d_pair_pos;
-    mb.pair_map = h->d_pair_map;
-    mb.map = h->map;
-    mb.npairs = (int64_t)P.pair_j.size();
-    mb.err = h->d_err;
-    CK(launch_map_build(mb, h->map_bytes, h->stream));
+    RunBuildArgs rb;
+    rb.lu_colptr = h->d_lu_colptr;
+    rb.lu_rowidx = h->d_lu_rowidx;
+    rb.diag_pos = h->d_diag;
+    rb.pair_j = h->d_pair_j;
+    rb.pair_k = d_pair_k;
+    rb.pair_pos = h->d_pair_pos;
+    rb.pair_runs = h->d_pair_runs;
+    rb.pair_map = h->d_pair_map;
+    rb.counts = d_counts;
+    rb.runs = nullptr;
+    rb.map = nullptr;
+    rb.segs = h->d_segs;
+    rb.npairs = npairs;
+    rb.nsegs = (int64_t)P.segs.size();
+    rb.err = h->d_err;
+    if (h->lookup != 0) {
+        // position map: every pair's offsets at pair_map[pair], then every
+        // segment's first entry
+        CK(upload(h->d_pair_map, P.pair_map));
+        h->map_total = (size_t)map_need;
+        CK(cudaMalloc(&h->d_map, h->map_total));
+        rb.map = h->d_map;
+        CK(launch_run_build(rb, 3, h->map_bytes, h->stream));
+        CK(launch_run_build(rb, 4, h->map_bytes, h->stream));
+    } else {
+        // run table: count each pair's runs, lay them out (prefix sum on the
+        // host), write them, then point every segment at its runs
+        CK(launch_run_build(rb, 0, 0, h->stream));
+        std::vector<int64_t> pr((size_t)npairs + 1, 0);
+        {
+            std::vector<int32_t> cnt((size_t)npairs);
+            if (npairs > 0)
+                CK(cudaMemcpyAsync(cnt.data(), d_counts, npairs * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                   h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+            for (int64_t q = 0; q < npairs; q++) pr[(size_t)q + 1] = pr[(size_t)q] + cnt[(size_t)q];
+        }
+        h->n_runs = pr[(size_t)npairs];
+        CK(upload(h->d_pair_runs, pr));
+        h->map_total = (size_t)std::max<int64_t>(h->n_runs, 1) * sizeof(Run);
+        CK(cudaMalloc(&h->d_runs, h->map_total));
+        rb.runs = h->d_runs;
+        CK(launch_run_build(rb, 1, 0, h->stream));
+        CK(launch_run_build(rb, 2, 0, h->stream));
+    }
     h->col_ready = true;
     return GLU_OK;
 }
@@ -755,7 +801,7 @@ int upload_plan(glu_handle *h) {
     }
     int rc = read_err(h);
     if (rc != GLU_OK) {
-        h->why = "position map build found a row outside its target column";
+        h->why = "run table build found a row outside its target column";
         return GLU_ERR_INTERNAL;
     }
     return GLU_OK;
@@ -866,8 +912,8 @@ int glu_analyze_opts(int32_t n, const int32_t *colptr, const int32_t *rowidx, co
         // the column-level schedule as int64 words: counts (levels, pairs,
         // segments, tasks, normalization items), the dense block (ftail_t0,
         // ftail_level), then lvl_task_ptr, lvl_row_ptr, lvl_lane_ptr,
-        // lvl_norm_ptr, pairs (j, k, pos, map start), segments (pos, dj, mb,
-        // t0, t1), tasks (seg_begin, seg_end, kind, nslots, base),
+        // lvl_norm_ptr, pairs (j, k, pos, first update), segments (pos, dj,
+        // pair, t0, t1), tasks (seg_begin, seg_end, kind, nslots, base),
         // normalization items (col, t0, t1), the value gather map (one A
         // index or -1 per entry of L+U)
         if (FILE *fp = std::fopen(dump, "wb")) {
@@ -881,7 +927,7 @@ int glu_analyze_opts(int32_t n, const int32_t *colptr, const int32_t *rowidx, co
             for (int32_t v : P.lvl_norm_ptr) w.push_back(v);
             for (size_t q = 0; q < P.pair_j.size(); q++)
                 w.insert(w.end(), {P.pair_j[q], P.pair_k[q], P.pair_pos[q], P.pair_map[q]});
-            for (const Seg &g : P.segs) w.insert(w.end(), {g.pos, g.dj, g.mb, g.t0, g.t1});
+            for (const Seg &g : P.segs) w.insert(w.end(), {g.pos, g.dj, g.rb, g.t0, g.t1});
             for (const Task &t : P.tasks) w.insert(w.end(), {t.seg_begin, t.seg_end, t.kind, t.nslots, t.base});
             for (const NormItem &it : P.norms) w.insert(w.end(), {it.col, it.t0, it.t1});
             w.insert(w.end(), P.gsrc.begin(), P.gsrc.end());
@@ -1215,6 +1261,16 @@ int glu_get_factors(glu_handle *h, double *out) {
     return glu_sync(h);
 }
 
+int glu_get_factors_f32(glu_handle *h, float *out) {
+    if (!h || !out || h->opt.host_only) return GLU_ERR_INVALID;
+    if (!h->factored32) return GLU_ERR_NOT_FACTORED;
+    const int64_t nnz = h->P.lu_colptr[h->P.n];
+    if (nnz == 0) return GLU_OK;
+    CK(cudaSetDevice(h->device));
+    CK(cudaMemcpyAsync(out, h->d_lu32, nnz * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    return glu_sync(h);
+}
+
 int glu_get_stats(const glu_handle *h, glu_stats *s) {
     if (!h || !s) return GLU_ERR_INVALID;
     const HostPlan &P = h->P;
@@ -1241,6 +1297,9 @@ int glu_get_stats(const glu_handle *h, glu_stats *s) {
     s->kernel_launches = h->launches;
     s->tail_rows = P.n - P.tail_t0;
     s->factor_tail_cols = P.n - P.ftail_t0;
+    s->row_lookup = !h->col_ready ? 0 : (h->lookup != 0 ? 1 : 2);
+    s->lookup_bytes = (int64_t)h->map_total;
+    s->n_runs = h->n_runs;
     return GLU_OK;
 }
 
@@ -1281,7 +1340,8 @@ void glu_destroy(glu_handle *h) {
     for (auto &g : h->sgraphs) cudaGraphExecDestroy(g.second);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     cudaFree(h->arena);
-    cudaFree(h->map);
+    cudaFree(h->d_runs);
+    cudaFree(h->d_map);
     cudaFree(h->bmap);
     cudaFree(h->carena);
     cudaFree(h->d_work);
@@ -1373,11 +1433,16 @@ extern "C" int glu_solve_noalloc(glu_handle *h, const double *b, double *x, int3
     const int64_t elems = (int64_t)n * nrhs;
     if (elems == 0) return GLU_OK;
     if (!b || !x || !is_device_ptr(b) || !is_device_ptr(x)) return GLU_ERR_INVALID;
-    // y (n * nrhs values) then the partial sums, 32-value aligned
+    // The handle's own solve schedule: the dataflow solve needs y and z (n *
+    // nrhs values each) and its chunk partial sums; the per-level solve
+    // (solve_mode 0) needs y and its level chunks.  Each part 32-value aligned.
+    const bool df = h->opt.solve_mode == 1;
     const int64_t yelems = (elems + 31) / 32 * 32;
-    const int64_t nch = (int64_t)std::max(P.fwd_chunks.size(), P.bwd_chunks.size()) * nrhs;
-    if (yelems + nch > (int64_t)GLU_NOALLOC_SCRATCH_DOUBLES) {
-        h->why = "glu_solve_noalloc: needs " + std::to_string(yelems + nch) + " doubles of scratch, the array holds " +
+    const int64_t nch = df ? (int64_t)(P.df_fchunks.size() + P.df_bchunks.size()) * nrhs
+                           : (int64_t)std::max(P.fwd_chunks.size(), P.bwd_chunks.size()) * nrhs;
+    const int64_t need = (df ? 2 : 1) * yelems + nch;
+    if (need > (int64_t)GLU_NOALLOC_SCRATCH_DOUBLES) {
+        h->why = "glu_solve_noalloc: needs " + std::to_string(need) + " doubles of scratch, the array holds " +
                  std::to_string((long long)GLU_NOALLOC_SCRATCH_DOUBLES);
         return GLU_ERR_TOO_LARGE;
     }
@@ -1385,10 +1450,19 @@ extern "C" int glu_solve_noalloc(glu_handle *h, const double *b, double *x, int3
     double *scratch = nullptr;
     CK(noalloc_scratch_address(h->device, &scratch));
     double *y = scratch;
-    double *partial = scratch + yelems;
     cudaStream_t st = h->stream;
     CKL(1, launch_permute_in<double>(y, b, h->d_perm, n, nrhs, st));
     SolveArgs<double> a = sargs(h);
+    if (df) {
+        // the same launches as glu_solve's dataflow solve (its ready flags,
+        // ticket and error word belong to the handle, allocated by glu_analyze)
+        double *z = y + yelems;
+        int rc = enqueue_df<double>(h, a, y, z, z + yelems, nrhs, st);
+        if (rc != GLU_OK) return rc;
+        CKL(1, launch_permute_out<double>(x, z, h->d_perm, n, nrhs, st));
+        return GLU_OK;
+    }
+    double *partial = scratch + yelems;
     int launched = 0;
     for (size_t l = 0; l + 1 < P.fwd_ptr.size(); l++) {
         CK(launch_solve_level<double>(a, false, y, nrhs, h->d_fwd_items + P.fwd_ptr[l], P.fwd_ptr[l + 1] - P.fwd_ptr[l],
@@ -1458,7 +1532,7 @@ int enqueue_factor_b(glu_handle *h, T *lu, int32_t B, int32_t S, cudaStream_t st
         r.t_end = l < nl ? P.lvl_task_ptr[l + 1] : 0;
             r.n_begin = P.lvl_norm_ptr[l];
         r.n_end = P.lvl_norm_ptr[l + 1];
-        CKL((r.t_end - r.t_begin) + (r.n_end - r.n_begin) > 0, launch_level_b<T>(a, h->map_bytes, r, S, h->num_sms, st));
+        CKL((r.t_end - r.t_begin) + (r.n_end - r.n_begin) > 0, launch_level_b<T>(a, h->lookup, r, S, h->num_sms, st));
     }
     CKL(P.n > 0, launch_pivot_b<T>(lu, h->d_diag, P.n, B, S, h->d_err, st));
     return GLU_OK;
@@ -1680,6 +1754,18 @@ extern "C" int glu_solve_batched_refine(glu_handle *h, const double *b, double *
     double *dst = xdev ? x : stage;
     CKL(1, launch_rhs_out(dst, xi, n, nrhs, batch, S, st));
     if (!xdev) CK(cudaMemcpyAsync(x, stage, elems * sizeof(double), cudaMemcpyDeviceToHost, st));
+    return glu_sync(h);
+}
+
+extern "C" int glu_get_factors_batched_f32(glu_handle *h, int32_t set, float *out) {
+    if (!h || !out || h->opt.host_only) return GLU_ERR_INVALID;
+    if (h->bprec != 32) return GLU_ERR_NOT_FACTORED;
+    if (set < 0 || set >= h->bB) return GLU_ERR_INVALID;
+    const int64_t nnz = h->P.lu_colptr[h->P.n];
+    if (nnz == 0) return GLU_OK;
+    CK(cudaSetDevice(h->device));
+    CK(cudaMemcpy2DAsync(out, sizeof(float), h->d_lub32 + set, (size_t)h->bS * sizeof(float), sizeof(float), nnz,
+                         cudaMemcpyDeviceToHost, h->stream));
     return glu_sync(h);
 }
 

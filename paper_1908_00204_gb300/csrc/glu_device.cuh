@@ -95,23 +95,33 @@ template <typename T>
 struct FactorArgs {
     T *lu;                       // values over the filled pattern
     const int64_t *diag_pos;     // n
-    const void *map;             // per update: offset of the target row past pair_pos+1
+    const void *map;             // position map (2 or 4 bytes per update), or null
+    const Run *runs;             // run table, or null
     const Seg *segs;
     const Task *tasks;
     const NormItem *norms;
     unsigned long long *err;
 };
 
-struct MapBuildArgs {
+// Building the row lookup of the level kernels.  Position map: per pair (j,
+// k) with U(j,k) at pair_pos, the offset of every row of L(:,j) in column k
+// past U(j,k), at pair_map[pair] + t.  Run table: the runs of L(:,j)'s rows in
+// column k (counted first, then written at pair_runs[pair]).  Then every
+// segment, which carries its pair's index, gets its map base or run range.
+struct RunBuildArgs {
     const int64_t *lu_colptr;
     const int32_t *lu_rowidx;
     const int64_t *diag_pos;
     const int32_t *pair_j;
     const int32_t *pair_k;
     const int64_t *pair_pos;
-    const int64_t *pair_map;
+    const int64_t *pair_runs;    // npairs + 1 (fill pass and segment pass)
+    const int64_t *pair_map;     // npairs + 1 (position map)
+    int32_t *counts;             // npairs (count pass)
+    Run *runs;
     void *map;
-    int64_t npairs;
+    Seg *segs;
+    int64_t npairs, nsegs;
     unsigned long long *err;
 };
 
@@ -158,10 +168,11 @@ struct DFSolveArgs {
 // launchers (kernels_factor.cu)
 template <typename T>
 cudaError_t launch_gather(T *lu, const double *aval, const int32_t *gsrc, int64_t nnz, cudaStream_t s);
+// lookup: 2 or 4 = position map of that many bytes per update, 0 = run table
 template <typename T>
-cudaError_t launch_level(const FactorArgs<T> &a, int map_bytes, const LevelRange &r, int num_sms, cudaStream_t s);
+cudaError_t launch_level(const FactorArgs<T> &a, int lookup, const LevelRange &r, int num_sms, cudaStream_t s);
 template <typename T>
-cudaError_t launch_levels_persistent(const FactorArgs<T> &a, int map_bytes, const LevelRange *ranges, int32_t nlev,
+cudaError_t launch_levels_persistent(const FactorArgs<T> &a, int lookup, const LevelRange *ranges, int32_t nlev,
                                      const GridBarrier &bar, int num_sms, cudaStream_t s);
 // One level of the supernodal factorization: diagonal blocks d0..d1-1,
 // panel items i0..i1-1, update tasks k0..k1-1 (kernels_blocks.cu); *launched
@@ -178,7 +189,10 @@ cudaError_t launch_dense_tail(T *lu, const DenseTailArgs &d, const GridBarrier &
 template <typename T>
 cudaError_t launch_pivot_check(const T *lu, const int64_t *diag_pos, int32_t n,
                                unsigned long long *err, cudaStream_t s);
-cudaError_t launch_map_build(const MapBuildArgs &a, int map_bytes, cudaStream_t s);
+// The run table: pass 0 counts each pair's runs, pass 1 writes them, pass 2
+// points every segment at its runs.  The position map: pass 3 writes it
+// (map_bytes per entry), pass 4 points every segment at its map entries.
+cudaError_t launch_run_build(const RunBuildArgs &a, int pass, int map_bytes, cudaStream_t s);
 cudaError_t launch_reset_err(unsigned long long *err, cudaStream_t s);
 
 // launchers (kernels_solve.cu)
@@ -225,7 +239,7 @@ cudaError_t launch_values_in(double *aT, const double *v, int64_t nnz, int32_t B
 template <typename T>
 cudaError_t launch_gather_b(T *lu, const double *aT, const int32_t *gsrc, int64_t nnz, int32_t S, cudaStream_t s);
 template <typename T>
-cudaError_t launch_level_b(const FactorArgs<T> &a, int map_bytes, const LevelRange &r, int32_t S, int num_sms,
+cudaError_t launch_level_b(const FactorArgs<T> &a, int lookup, const LevelRange &r, int32_t S, int num_sms,
                            cudaStream_t s);
 template <typename T>
 cudaError_t launch_pivot_b(const T *lu, const int64_t *diag_pos, int32_t n, int32_t B, int32_t S,

@@ -48,13 +48,28 @@ enum : int32_t { KIND_ROW = 0, KIND_SRC = 1, KIND_LANE = 2 };
 // A segment of one (source j, target k) column pair: rows t0..t1-1 of L(:,j)
 // (t counts from the first row below the diagonal), with everything needed
 // to apply it in one record: pos = position of U(j,k), dj = position of the
-// pivot of j, mb = the pair's first position-map entry.
+// pivot of j, and rb.  On the host rb is the pair's index; on the device it
+// locates the segment's runs (see Run): the first run overlapping t0..t1-1 in
+// bits 0..43, the number of runs overlapping them in bits 44..63.
 struct alignas(16) Seg {
     int64_t pos;
     int64_t dj;
-    int64_t mb;
+    int64_t rb;
     int32_t t0;
     int32_t t1;
+};
+constexpr int RUN_BASE_BITS = 44;
+
+// Where the rows of L(:,j) sit in target column k.  By the fill theorem
+// every row of L(:,j) is a row of column k below U(j,k); the rows of L(:,j)
+// fall on runs of consecutive positions of column k.  A run is stored as
+// (ts, off): rows t = ts, ts+1, ... of L(:,j) (up to the next run's ts) are
+// at positions pos(U(j,k)) + 1 + off + (t - ts).  A pair's runs are
+// consecutive in one table, ts ascending, the first with ts = 0; the
+// level kernels locate a row's run by warp ballots and shuffles over them.
+struct Run {
+    int32_t ts;
+    int32_t off;
 };
 
 // Scheduling-time segment (pair index + row range).

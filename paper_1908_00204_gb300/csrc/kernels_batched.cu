@@ -4,7 +4,7 @@
 // Monte-Carlo corners; Section III: the numeric part repeats while the
 // pattern stays) are stored interleaved: entry q of set b at [q * S + b],
 // S = B rounded up to 32.  A warp takes one work item for 32 sets at once:
-// every index (schedule, position map, pattern) is the same for all lanes and
+// every index (schedule, run table, pattern) is the same for all lanes and
 // every value access is 32 consecutive elements.  Each lane owns its own
 // matrix, so the right-looking update of a level (Algorithm 5 / Eq. 3) needs
 // no ordering between lanes; a lane applies a task's segments in order, its
@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "glu_device.cuh"
 
@@ -67,7 +68,6 @@ __global__ void __launch_bounds__(128) k_level_b(const FactorArgs<T> a, LevelRan
     const int64_t nn = r.n_end - r.n_begin;
     const int64_t nt = r.t_end - r.t_begin;
     const int64_t total = (nn + nt) * G;
-    const M *__restrict__ map = static_cast<const M *>(a.map);
     for (int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < total; it += nw) {
         const int64_t k = it / G;
         const int32_t b = (int32_t)(it - k * G) * 32 + lane;
@@ -86,17 +86,41 @@ __global__ void __launch_bounds__(128) k_level_b(const FactorArgs<T> a, LevelRan
         for (int32_t s = tk.seg_begin; s < tk.seg_end; s++) {
             const Seg sg = a.segs[s];
             const T f = lu[sg.pos * S + b] / lu[sg.dj * S + b];
-            const M *__restrict__ mp = map + sg.mb;
             const T *__restrict__ L = lu + (sg.dj + 1) * S + b;
             T *tgt = lu + (sg.pos + 1) * S + b;
+            // the rows' offsets: the position map, or the segment's runs walked
+            // in step by the whole warp (every lane reads the same records)
+            int64_t r = 0, rend = 0;
+            Run cur{0, 0}, nxt{INT32_MAX, 0};
+            const M *mp = nullptr;
+            if constexpr (std::is_same<M, Run>::value) {
+                const uint64_t enc = (uint64_t)sg.rb;
+                r = (int64_t)(enc & ((1ull << RUN_BASE_BITS) - 1));
+                rend = r + (int64_t)(enc >> RUN_BASE_BITS);
+                cur = a.runs[r];
+                nxt = r + 1 < rend ? a.runs[r + 1] : Run{INT32_MAX, 0};
+            } else {
+                mp = static_cast<const M *>(a.map) + sg.rb;
+            }
             for (int32_t tb = sg.t0; tb < sg.t1; tb += BU) {
                 int64_t off[BU];
                 T lv[BU];
 #pragma unroll
                 for (int u = 0; u < BU; u++)
+                    if (tb + u < sg.t1) lv[u] = L[(int64_t)(tb + u) * S];
+#pragma unroll
+                for (int u = 0; u < BU; u++)
                     if (tb + u < sg.t1) {
-                        off[u] = (int64_t)mp[tb + u] * S;
-                        lv[u] = L[(int64_t)(tb + u) * S];
+                        if constexpr (std::is_same<M, Run>::value) {
+                            while (tb + u >= nxt.ts) {
+                                cur = nxt;
+                                r++;
+                                nxt = r + 1 < rend ? a.runs[r + 1] : Run{INT32_MAX, 0};
+                            }
+                            off[u] = (int64_t)(cur.off + (tb + u - cur.ts)) * S;
+                        } else {
+                            off[u] = (int64_t)mp[tb + u] * S;
+                        }
                     }
             // the targets take -L(i,j) f as reductions in L2; one lane (one
             // value set) applies a task's segments in order, so each entry's
@@ -500,14 +524,15 @@ cudaError_t launch_gather_b(T *lu, const double *aT, const int32_t *gsrc, int64_
 }
 
 template <typename T>
-cudaError_t launch_level_b(const FactorArgs<T> &a, int map_bytes, const LevelRange &r, int32_t S, int num_sms,
+cudaError_t launch_level_b(const FactorArgs<T> &a, int lookup, const LevelRange &r, int32_t S, int num_sms,
                            cudaStream_t s) {
     const int64_t items = ((int64_t)(r.t_end - r.t_begin) + (r.n_end - r.n_begin)) * (S / 32);
     if (items <= 0) return cudaSuccess;
     int64_t blocks = (items + 3) / 4;
     if (blocks > (int64_t)num_sms * 16) blocks = (int64_t)num_sms * 16;
-    if (map_bytes == 2) k_level_b<T, uint16_t><<<(unsigned)blocks, 128, 0, s>>>(a, r, S);
-    else k_level_b<T, uint32_t><<<(unsigned)blocks, 128, 0, s>>>(a, r, S);
+    if (lookup == 2) k_level_b<T, uint16_t><<<(unsigned)blocks, 128, 0, s>>>(a, r, S);
+    else if (lookup == 4) k_level_b<T, uint32_t><<<(unsigned)blocks, 128, 0, s>>>(a, r, S);
+    else k_level_b<T, Run><<<(unsigned)blocks, 128, 0, s>>>(a, r, S);
     return cudaGetLastError();
 }
 

@@ -12,9 +12,17 @@
 // whose additions are L2 reductions issued in a fixed order (separated by
 // warp barriers); the order of the updates of an entry depends only on the
 // pattern, so a refactorization is deterministic run to run.
+// A row of L(:,j) is found in target column k (the template parameter M) by
+// a position map (M = uint16_t / uint32_t: one offset per update, built once
+// per pattern; one load per update) or by the pair's run table (M = Run):
+// rows of L(:,j) that sit on consecutive positions of column k form one run,
+// about nine per pair on the power-grid workloads, so the table is small next
+// to one position per update; a warp locates its 32 rows' runs with two
+// ballots, an OR-reduction and two shuffles, a single lane by walking them.
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "glu_device.cuh"
 
@@ -64,27 +72,38 @@ __device__ __forceinline__ void norm_item(const FactorArgs<T> &a, const NormItem
     }
 }
 
-// Everything a segment needs, gathered once: the position of U(j,k), the
-// first map entry, the first row of L(:,j) and the multiplier
+// Everything a segment needs, gathered once: the position of U(j,k), its
+// runs, the first row of L(:,j) and the multiplier
 // f = A_s(j,k) / A_s(j,j).  All of them are final when the level starts:
 // U(j,k) and the pivot of a source are only written by earlier levels.
 template <typename T>
 struct SegMeta {
     int64_t pos;
-    int64_t mb;
+    int64_t rb;       // first run of the segment, or its first map entry
     int64_t lstart;
+    int32_t nr;       // runs of the segment (run table)
     int32_t t0;
     int32_t t1;
     T f;
 };
 
-template <typename T>
+template <typename M>
+constexpr bool is_runs() { return std::is_same<M, Run>::value; }
+
+template <typename T, typename M>
 __device__ __forceinline__ void load_meta(const FactorArgs<T> &a, int32_t s, SegMeta<T> &m) {
     const int4 *r = reinterpret_cast<const int4 *>(a.segs + s);
     const int4 v0 = r[0], v1 = r[1];
     m.pos = ((int64_t)(uint32_t)v0.y << 32) | (uint32_t)v0.x;
     const int64_t dj = ((int64_t)(uint32_t)v0.w << 32) | (uint32_t)v0.z;
-    m.mb = ((int64_t)(uint32_t)v1.y << 32) | (uint32_t)v1.x;
+    const uint64_t enc = ((uint64_t)(uint32_t)v1.y << 32) | (uint32_t)v1.x;
+    if constexpr (is_runs<M>()) {
+        m.rb = (int64_t)(enc & ((1ull << RUN_BASE_BITS) - 1));
+        m.nr = (int32_t)(enc >> RUN_BASE_BITS);
+    } else {
+        m.rb = (int64_t)enc;
+        m.nr = 0;
+    }
     m.t0 = v1.z;
     m.t1 = v1.w;
     m.lstart = dj + 1;
@@ -95,12 +114,49 @@ template <typename T>
 __device__ __forceinline__ SegMeta<T> shfl_meta(const SegMeta<T> &m, int src) {
     SegMeta<T> o;
     o.pos = __shfl_sync(0xffffffffu, m.pos, src);
-    o.mb = __shfl_sync(0xffffffffu, m.mb, src);
+    o.rb = __shfl_sync(0xffffffffu, m.rb, src);
     o.lstart = __shfl_sync(0xffffffffu, m.lstart, src);
+    o.nr = __shfl_sync(0xffffffffu, m.nr, src);
     o.t0 = __shfl_sync(0xffffffffu, m.t0, src);
     o.t1 = __shfl_sync(0xffffffffu, m.t1, src);
     o.f = __shfl_sync(0xffffffffu, m.f, src);
     return o;
+}
+
+__device__ __forceinline__ Run load_run(const Run *runs, int64_t r, int64_t rend) {
+    if (r < rend) {
+        const int2 v = *reinterpret_cast<const int2 *>(runs + r);
+        return Run{v.x, v.y};
+    }
+    return Run{INT32_MAX, 0};
+}
+
+// One lane walking the rows of a segment in ascending order: the run holding
+// the current row and the next three runs, loaded ahead so that crossing
+// into a run rarely waits for its record.
+struct RunWalk {
+    int64_t r, rend;    // r: the index of n3
+    Run cur, n1, n2, n3;
+};
+
+__device__ __forceinline__ void walk_begin(RunWalk &w, const Run *runs, int64_t rb, int32_t nr) {
+    w.rend = rb + nr;
+    w.cur = load_run(runs, rb, w.rend);
+    w.n1 = load_run(runs, rb + 1, w.rend);
+    w.n2 = load_run(runs, rb + 2, w.rend);
+    w.n3 = load_run(runs, rb + 3, w.rend);
+    w.r = rb + 3;
+}
+
+// offset in the target column (past U(j,k)) of row t >= every earlier t
+__device__ __forceinline__ uint32_t walk_offset(RunWalk &w, const Run *runs, int32_t t) {
+    while (t >= w.n1.ts) {
+        w.cur = w.n1;
+        w.n1 = w.n2;
+        w.n2 = w.n3;
+        w.n3 = load_run(runs, ++w.r, w.rend);
+    }
+    return (uint32_t)(w.cur.off + (t - w.cur.ts));
 }
 
 #ifndef GLU_ROW_UNROLL
@@ -122,10 +178,79 @@ constexpr int LANE_UNROLL = GLU_LANE_UNROLL;
 // target entries have one owner warp, whose segments are separated by warp
 // barriers, so each entry's sequence of additions is fixed: the results are
 // the same from run to run.
+// The rows' positions come from the segment's runs, held 32 at a time by the
+// lanes (lane w: run wb + w).  For a group of 32 consecutive rows g0..g0+31:
+// the run holding g0 is the last one starting at or before g0 (one ballot);
+// the runs starting inside the group set one bit each at their first row (an
+// OR-reduction); a lane's run is the first one's index plus the bits at or
+// below its row.  The window moves on when a group could reach past it.
+template <typename T>
+__device__ __forceinline__ void row_segment_runs(T *__restrict__ lu, const Run *__restrict__ runs,
+                                                 const SegMeta<T> &m, int lane) {
+    const T *__restrict__ L = lu + m.lstart;
+    T *tgt = lu + m.pos + 1;
+    const int64_t rend = m.rb + m.nr;
+    int64_t wb = m.rb;
+    Run w = load_run(runs, wb + lane, rend);
+    for (int32_t tb = m.t0; tb < m.t1; tb += 32 * ROW_UNROLL) {
+        uint32_t off[ROW_UNROLL];
+        T lv[ROW_UNROLL];
+#pragma unroll
+        for (int u = 0; u < ROW_UNROLL; u++) {
+            const int32_t t = tb + 32 * u + lane;
+            if (t < m.t1) lv[u] = L[t];
+        }
+        if (wb + 32 >= rend) {
+            // the window holds every remaining run: the groups are independent
+#pragma unroll
+            for (int u = 0; u < ROW_UNROLL; u++) {
+                const int32_t g0 = tb + 32 * u;
+                if (g0 < m.t1) {
+                    const int32_t glast = min(g0 + 31, m.t1 - 1);
+                    const int a = __popc(__ballot_sync(0xffffffffu, w.ts <= g0)) - 1;
+                    const unsigned bit = (w.ts > g0 && w.ts <= glast) ? (1u << (w.ts - g0)) : 0u;
+                    const unsigned starts = __reduce_or_sync(0xffffffffu, bit);
+                    const int idx = a + __popc(starts & (0xffffffffu >> (31 - lane)));
+                    const int32_t ts = __shfl_sync(0xffffffffu, w.ts, idx);
+                    const int32_t of = __shfl_sync(0xffffffffu, w.off, idx);
+                    off[u] = (uint32_t)(of + (g0 + lane - ts));
+                }
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < ROW_UNROLL; u++) {
+                const int32_t g0 = tb + 32 * u;
+                if (g0 < m.t1) {                   // the same for the whole warp
+                    const int32_t glast = min(g0 + 31, m.t1 - 1);
+                    if (wb + 32 < rend && __shfl_sync(0xffffffffu, w.ts, 31) <= glast) {
+                        // the group may reach the run after the window: start the
+                        // window at the run holding g0 (32 rows span <= 32 runs)
+                        wb += __popc(__ballot_sync(0xffffffffu, w.ts <= g0)) - 1;
+                        w = load_run(runs, wb + lane, rend);
+                    }
+                    const int a = __popc(__ballot_sync(0xffffffffu, w.ts <= g0)) - 1;
+                    const unsigned bit = (w.ts > g0 && w.ts <= glast) ? (1u << (w.ts - g0)) : 0u;
+                    const unsigned starts = __reduce_or_sync(0xffffffffu, bit);
+                    const int idx = a + __popc(starts & (0xffffffffu >> (31 - lane)));
+                    const int32_t ts = __shfl_sync(0xffffffffu, w.ts, idx);
+                    const int32_t of = __shfl_sync(0xffffffffu, w.off, idx);
+                    off[u] = (uint32_t)(of + (g0 + lane - ts));
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < ROW_UNROLL; u++) {
+            const int32_t t = tb + 32 * u + lane;
+            if (t < m.t1) atomicAdd(&tgt[off[u]], -lv[u] * m.f);
+        }
+    }
+}
+
+// The same with the position map: the rows' offsets are loaded with L(:,j).
 template <typename T, typename M>
-__device__ __forceinline__ void row_segment(T *__restrict__ lu, const M *__restrict__ map, const SegMeta<T> &m,
-                                            int lane) {
-    const M *__restrict__ mp = map + m.mb;
+__device__ __forceinline__ void row_segment_map(T *__restrict__ lu, const M *__restrict__ map, const SegMeta<T> &m,
+                                                int lane) {
+    const M *__restrict__ mp = map + m.rb;
     const T *__restrict__ L = lu + m.lstart;
     T *tgt = lu + m.pos + 1;
     for (int32_t tb = m.t0 + lane; tb < m.t1; tb += 32 * ROW_UNROLL) {
@@ -145,6 +270,31 @@ __device__ __forceinline__ void row_segment(T *__restrict__ lu, const M *__restr
     }
 }
 
+template <typename T, typename M>
+__device__ __forceinline__ void row_segment(const FactorArgs<T> &a, const SegMeta<T> &m, int lane) {
+    if constexpr (is_runs<M>()) row_segment_runs<T>(a.lu, a.runs, m, lane);
+    else row_segment_map<T, M>(a.lu, static_cast<const M *>(a.map), m, lane);
+}
+
+// Offsets of the rows of one segment for a single lane, in ascending order:
+// map loads, or a walk over the runs.
+template <typename M>
+struct LaneRows {
+    const M *mp;
+    __device__ __forceinline__ void begin(const void *map, const Run *, int64_t rb, int32_t) {
+        mp = static_cast<const M *>(map) + rb;
+    }
+    __device__ __forceinline__ uint32_t offset(const Run *, int32_t t) { return mp[t]; }
+};
+template <>
+struct LaneRows<Run> {
+    RunWalk w;
+    __device__ __forceinline__ void begin(const void *, const Run *runs, int64_t rb, int32_t nr) {
+        walk_begin(w, runs, rb, nr);
+    }
+    __device__ __forceinline__ uint32_t offset(const Run *runs, int32_t t) { return walk_offset(w, runs, t); }
+};
+
 // KIND_ROW tasks of one warp, tq0, tq0 + stride, ... (cnt of them), applied one
 // after the other as row_task would, but with the metadata of up to 32
 // segments -- spanning several tasks -- fetched at once, one per lane, so the
@@ -152,7 +302,6 @@ __device__ __forceinline__ void row_segment(T *__restrict__ lu, const M *__restr
 template <typename T, typename M>
 __device__ __forceinline__ void row_tasks(const FactorArgs<T> &a, int64_t tq0, int64_t stride, int64_t cnt,
                                           int lane) {
-    const M *__restrict__ map = static_cast<const M *>(a.map);
     int64_t i = 0;      // next task of the list
     int32_t skip = 0;   // segments of task i already applied
     while (i < cnt) {
@@ -185,10 +334,10 @@ __device__ __forceinline__ void row_tasks(const FactorArgs<T> &a, int64_t tq0, i
         const int32_t t_ns = __shfl_sync(0xffffffffu, ns, t);
         const int32_t t_sb = __shfl_sync(0xffffffffu, sb, t);
         SegMeta<T> mine;
-        if (lane < take) load_meta<T>(a, t_sb + (lane - (t_incl - t_ns)), mine);
+        if (lane < take) load_meta<T, M>(a, t_sb + (lane - (t_incl - t_ns)), mine);
         for (int q = 0; q < take; q++) {
             const SegMeta<T> m = shfl_meta<T>(mine, q);
-            row_segment<T, M>(a.lu, map, m, lane);
+            row_segment<T, M>(a, m, lane);
             __syncwarp();
         }
         if (tot <= 32) {
@@ -211,7 +360,6 @@ __device__ __forceinline__ void row_tasks(const FactorArgs<T> &a, int64_t tq0, i
 // it.  The next segment's metadata is fetched before the current one's rows.
 template <typename T, typename M>
 __device__ __forceinline__ void src_task(const FactorArgs<T> &a, const Task &tk, int lane, T *__restrict__ acc) {
-    const M *__restrict__ map = static_cast<const M *>(a.map);
     T *__restrict__ row = acc + lane * (SRC_SLOTS + 1);
     const int nl = min(32, tk.seg_end - tk.seg_begin);   // lanes with segments
     if (lane < nl) {
@@ -221,24 +369,25 @@ __device__ __forceinline__ void src_task(const FactorArgs<T> &a, const Task &tk,
     int32_t s = tk.seg_begin + lane;
     SegMeta<T> cur;
     bool have = s < tk.seg_end;
-    if (have) load_meta<T>(a, s, cur);
+    if (have) load_meta<T, M>(a, s, cur);
     while (have) {
         SegMeta<T> nxt;
         const int32_t s2 = s + 32;
         const bool have2 = s2 < tk.seg_end;
-        if (have2) load_meta<T>(a, s2, nxt);
-        const M *__restrict__ mp = map + cur.mb;
+        if (have2) load_meta<T, M>(a, s2, nxt);
         const T *__restrict__ L = a.lu + cur.lstart;
         const int32_t rel = (int32_t)(cur.pos + 1 - tk.base);
+        LaneRows<M> wk;
+        wk.begin(a.map, a.runs, cur.rb, cur.nr);
         for (int32_t tb = cur.t0; tb < cur.t1; tb += GLU_SRC_UNROLL) {
             uint32_t off[GLU_SRC_UNROLL];
             T lv[GLU_SRC_UNROLL];
 #pragma unroll
             for (int u = 0; u < GLU_SRC_UNROLL; u++)
-                if (tb + u < cur.t1) {
-                    off[u] = mp[tb + u];
-                    lv[u] = L[tb + u];
-                }
+                if (tb + u < cur.t1) lv[u] = L[tb + u];
+#pragma unroll
+            for (int u = 0; u < GLU_SRC_UNROLL; u++)
+                if (tb + u < cur.t1) off[u] = wk.offset(a.runs, tb + u);
 #pragma unroll
             for (int u = 0; u < GLU_SRC_UNROLL; u++)
                 if (tb + u < cur.t1) {
@@ -263,24 +412,24 @@ __device__ __forceinline__ void src_task(const FactorArgs<T> &a, const Task &tk,
 // the next segment's metadata is fetched before the current one's rows.
 template <typename T, typename M>
 __device__ __forceinline__ void lane_task(const FactorArgs<T> &a, const Task &tk) {
-    const M *__restrict__ map = static_cast<const M *>(a.map);
     SegMeta<T> nxt;
-    load_meta<T>(a, tk.seg_begin, nxt);
+    load_meta<T, M>(a, tk.seg_begin, nxt);
     for (int32_t s = tk.seg_begin; s < tk.seg_end; s++) {
         const SegMeta<T> m = nxt;
-        if (s + 1 < tk.seg_end) load_meta<T>(a, s + 1, nxt);
-        const M *__restrict__ mp = map + m.mb;
+        if (s + 1 < tk.seg_end) load_meta<T, M>(a, s + 1, nxt);
         const T *__restrict__ L = a.lu + m.lstart;
         T *tgt = a.lu + m.pos + 1;
+        LaneRows<M> wk;
+        wk.begin(a.map, a.runs, m.rb, m.nr);
         for (int32_t tb = m.t0; tb < m.t1; tb += LANE_UNROLL) {
             uint32_t off[LANE_UNROLL];
             T lv[LANE_UNROLL];
 #pragma unroll
             for (int u = 0; u < LANE_UNROLL; u++)
-                if (tb + u < m.t1) {
-                    off[u] = mp[tb + u];
-                    lv[u] = L[tb + u];
-                }
+                if (tb + u < m.t1) lv[u] = L[tb + u];
+#pragma unroll
+            for (int u = 0; u < LANE_UNROLL; u++)
+                if (tb + u < m.t1) off[u] = wk.offset(a.runs, tb + u);
 #pragma unroll
             for (int u = 0; u < LANE_UNROLL; u++)
                 if (tb + u < m.t1) atomicAdd(&tgt[off[u]], -lv[u] * m.f);
@@ -328,13 +477,13 @@ __device__ __forceinline__ void prefetch_l2(const void *p) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
-// Pull into L2 the schedule records and position-map lines that this warp
-// will read in level r (its items are warp, warp + nw, ...): they are static,
-// and otherwise each is a first-touch DRAM read on the level's critical path.
+// Pull into L2 the schedule records and map or run-table lines that this
+// warp will read in level r (its items are warp, warp + nw, ...): they are
+// static, and otherwise each is a first-touch DRAM read on the level's
+// critical path.
 template <typename T, typename M>
 __device__ __forceinline__ void prefetch_level(const FactorArgs<T> &a, const LevelRange &r, int lane, int64_t warp,
                                                int64_t nw) {
-    const M *map = static_cast<const M *>(a.map);
     const int64_t nn = r.n_end - r.n_begin;
     const int64_t nsrc = r.row_begin - r.t_begin;
     const int64_t nrow = r.lane_begin - r.row_begin;
@@ -355,14 +504,22 @@ __device__ __forceinline__ void prefetch_level(const FactorArgs<T> &a, const Lev
         if (!mine) continue;
         for (int32_t s = tk.seg_begin; s < tk.seg_end; s++) {
             const Seg sg = a.segs[s];
-            for (int32_t t = sg.t0; t < sg.t1; t += 128 / (int)sizeof(M)) prefetch_l2(map + sg.mb + t);
+            if constexpr (is_runs<M>()) {
+                const uint64_t enc = (uint64_t)sg.rb;
+                const int64_t rb = (int64_t)(enc & ((1ull << RUN_BASE_BITS) - 1));
+                const int32_t nr = (int32_t)(enc >> RUN_BASE_BITS);
+                for (int32_t q = 0; q < nr; q += 128 / (int)sizeof(Run)) prefetch_l2(a.runs + rb + q);
+            } else {
+                const M *map = static_cast<const M *>(a.map);
+                for (int32_t t = sg.t0; t < sg.t1; t += 128 / (int)sizeof(M)) prefetch_l2(map + sg.rb + t);
+            }
         }
     }
 }
 
 // One level per launch, chained to the previous level's launch by a
 // programmatic dependency: the prologue pulls this warp's (static) schedule
-// records and map lines into L2 while the previous level still runs, then
+// records and run-table lines into L2 while the previous level still runs, then
 // waits for it to finish (griddepcontrol.wait makes its writes visible);
 // each block lets the next level start once its own items are done.
 template <typename T, typename M>
@@ -423,12 +580,97 @@ __global__ void k_pivot_check(const T *__restrict__ lu, const int64_t *__restric
 
 __global__ void k_reset_err(unsigned long long *err) { *err = ERR_NONE; }
 
-// ---------------------------------------------------------------- map build
-// For every (j,k) pair and every row L(t,j), the offset of that row inside
-// column k past the position of U(j,k); a binary search over the rows of
-// column k below j.  Built once at analysis.
+// ---------------------------------------------------------------- run table
+// Position of row r among rows[0, len) (ascending), or -1.
+__device__ __forceinline__ int64_t find_row(const int32_t *rows, int64_t len, int32_t r) {
+    int64_t lo = 0, hi = len;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (rows[mid] < r) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < len && rows[lo] == r) ? lo : -1;
+}
+
+// Pass 0 / 1, a warp per (j, k) pair: the position of every row of L(:,j) in
+// column k past U(j,k) (binary search; the fill theorem says it is there), a
+// run starting wherever a row's position is not its predecessor's plus one.
+// Pass 0 stores the pair's run count, pass 1 writes the runs at
+// pair_runs[pair] in order.  Built once per pattern at analysis.
+__global__ void k_runs(const RunBuildArgs a, int fill) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t p = w; p < a.npairs; p += nw) {
+        const int32_t j = a.pair_j[p];
+        const int32_t k = a.pair_k[p];
+        const int64_t pos = a.pair_pos[p];
+        const int64_t dj = a.diag_pos[j];
+        const int32_t lj = (int32_t)(a.lu_colptr[j + 1] - dj - 1);
+        const int32_t *rows = a.lu_rowidx + pos + 1;
+        const int64_t len = a.lu_colptr[k + 1] - pos - 1;
+        int64_t base = fill ? a.pair_runs[p] : 0;
+        int64_t prev = -2;
+        for (int32_t t0 = 0; t0 < lj; t0 += 32) {
+            const int32_t t = t0 + lane;
+            int64_t q = 0;
+            if (t < lj) {
+                q = find_row(rows, len, a.lu_rowidx[dj + 1 + t]);
+                if (q < 0) {
+                    atomicMin(a.err, ((unsigned long long)(uint32_t)k << 8) | DEVERR_INTERNAL);
+                    q = 0;
+                }
+            }
+            int64_t left = __shfl_up_sync(0xffffffffu, q, 1);
+            if (lane == 0) left = prev;
+            const bool start = t < lj && (t == 0 || q != left + 1);
+            const unsigned mask = __ballot_sync(0xffffffffu, start);
+            if (fill && start) {
+                Run *o = a.runs + base + __popc(mask & ((1u << lane) - 1));
+                *o = Run{t, (int32_t)q};
+            }
+            base += __popc(mask);
+            prev = __shfl_sync(0xffffffffu, q, 31);
+        }
+        if (!fill && lane == 0) a.counts[p] = (int32_t)base;
+    }
+}
+
+// Pass 2, a thread per segment: its runs are those of its pair (whose index
+// the host left in rb) that overlap rows t0..t1-1.
+__global__ void k_seg_runs(const RunBuildArgs a) {
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < a.nsegs;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        Seg &sg = a.segs[s];
+        const int64_t pair = sg.rb;
+        const int64_t lo = a.pair_runs[pair], hi = a.pair_runs[pair + 1];
+        // first run starting after t0, and first run starting at or after t1
+        int64_t x = lo, y = hi;
+        while (x < y) {
+            const int64_t mid = (x + y) >> 1;
+            if (a.runs[mid].ts <= sg.t0) x = mid + 1;
+            else y = mid;
+        }
+        const int64_t rb = x - 1;
+        int64_t e = x, f = hi;
+        while (e < f) {
+            const int64_t mid = (e + f) >> 1;
+            if (a.runs[mid].ts < sg.t1) e = mid + 1;
+            else f = mid;
+        }
+        if (rb < lo || e - rb >= (int64_t(1) << (64 - RUN_BASE_BITS))) {
+            atomicMin(a.err, (0xffffffull << 8) | DEVERR_INTERNAL);
+            sg.rb = 0;
+            continue;
+        }
+        sg.rb = (int64_t)((uint64_t)rb | ((uint64_t)(e - rb) << RUN_BASE_BITS));
+    }
+}
+
+// Position map, a warp per (j, k) pair: the offset of every row of L(:,j) in
+// column k past U(j,k), at pair_map[pair] + t.
 template <typename M>
-__global__ void k_map_build(const MapBuildArgs a) {
+__global__ void k_map_build(const RunBuildArgs a) {
     const int lane = threadIdx.x & 31;
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -443,19 +685,23 @@ __global__ void k_map_build(const MapBuildArgs a) {
         const int32_t *rows = a.lu_rowidx + pos + 1;
         const int64_t len = a.lu_colptr[k + 1] - pos - 1;
         for (int32_t t = lane; t < lj; t += 32) {
-            const int32_t r = a.lu_rowidx[dj + 1 + t];
-            int64_t lo = 0, hi = len;
-            while (lo < hi) {
-                int64_t mid = (lo + hi) >> 1;
-                if (rows[mid] < r) lo = mid + 1;
-                else hi = mid;
+            int64_t q = find_row(rows, len, a.lu_rowidx[dj + 1 + t]);
+            if (q < 0) {
+                atomicMin(a.err, ((unsigned long long)(uint32_t)k << 8) | DEVERR_INTERNAL);
+                q = 0;
             }
-            if (lo >= len || rows[lo] != r) {
-                raise_err(a.err, k, DEVERR_INTERNAL);
-                lo = 0;
-            }
-            map[mb + t] = (M)lo;
+            map[mb + t] = (M)q;
         }
+    }
+}
+
+// A thread per segment: its first map entry (its pair's, whose index the host
+// left in rb, plus t0 is where the kernels index from: pair_map[pair]).
+__global__ void k_seg_map(const RunBuildArgs a) {
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < a.nsegs;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        Seg &sg = a.segs[s];
+        sg.rb = a.pair_map[sg.rb];
     }
 }
 
@@ -471,7 +717,7 @@ cudaError_t launch_gather(T *lu, const double *aval, const int32_t *gsrc, int64_
 }
 
 template <typename T>
-cudaError_t launch_level(const FactorArgs<T> &a, int map_bytes, const LevelRange &r, int num_sms, cudaStream_t s) {
+cudaError_t launch_level(const FactorArgs<T> &a, int lookup, const LevelRange &r, int num_sms, cudaStream_t s) {
     const int64_t items = (int64_t)(r.lane_begin - r.t_begin) + (r.t_end - r.lane_begin + 31) / 32 +
                           (r.n_end - r.n_begin);
     if (items <= 0) return cudaSuccess;
@@ -492,17 +738,19 @@ cudaError_t launch_level(const FactorArgs<T> &a, int map_bytes, const LevelRange
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (map_bytes == 2) return cudaLaunchKernelEx(&cfg, k_level<T, uint16_t>, a, r);
-    return cudaLaunchKernelEx(&cfg, k_level<T, uint32_t>, a, r);
+    if (lookup == 2) return cudaLaunchKernelEx(&cfg, k_level<T, uint16_t>, a, r);
+    if (lookup == 4) return cudaLaunchKernelEx(&cfg, k_level<T, uint32_t>, a, r);
+    return cudaLaunchKernelEx(&cfg, k_level<T, Run>, a, r);
 }
 
 template <typename T>
-cudaError_t launch_levels_persistent(const FactorArgs<T> &a, int map_bytes, const LevelRange *ranges, int32_t nlev,
+cudaError_t launch_levels_persistent(const FactorArgs<T> &a, int lookup, const LevelRange *ranges, int32_t nlev,
                                      const GridBarrier &bar, int num_sms, cudaStream_t s) {
     if (nlev <= 0) return cudaSuccess;
     const size_t smem = sizeof(T) * LEVEL_WARPS * 32 * (SRC_SLOTS + 1);
-    const void *fn = map_bytes == 2 ? (const void *)k_levels_persistent<T, uint16_t>
-                                    : (const void *)k_levels_persistent<T, uint32_t>;
+    const void *fn = lookup == 2 ? (const void *)k_levels_persistent<T, uint16_t>
+                   : lookup == 4 ? (const void *)k_levels_persistent<T, uint32_t>
+                                 : (const void *)k_levels_persistent<T, Run>;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, LEVEL_WARPS * 32, smem);
     if (e != cudaSuccess) return e;
@@ -520,8 +768,9 @@ cudaError_t launch_levels_persistent(const FactorArgs<T> &a, int map_bytes, cons
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (map_bytes == 2) return cudaLaunchKernelEx(&cfg, k_levels_persistent<T, uint16_t>, a, ranges, nlev, bar);
-    return cudaLaunchKernelEx(&cfg, k_levels_persistent<T, uint32_t>, a, ranges, nlev, bar);
+    if (lookup == 2) return cudaLaunchKernelEx(&cfg, k_levels_persistent<T, uint16_t>, a, ranges, nlev, bar);
+    if (lookup == 4) return cudaLaunchKernelEx(&cfg, k_levels_persistent<T, uint32_t>, a, ranges, nlev, bar);
+    return cudaLaunchKernelEx(&cfg, k_levels_persistent<T, Run>, a, ranges, nlev, bar);
 }
 
 template <typename T>
@@ -537,12 +786,21 @@ cudaError_t launch_reset_err(unsigned long long *err, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_map_build(const MapBuildArgs &a, int map_bytes, cudaStream_t s) {
-    if (a.npairs == 0) return cudaSuccess;
-    int64_t blocks = (a.npairs * 32 + 255) / 256;
-    if (blocks > 152 * 32) blocks = 152 * 32;
-    if (map_bytes == 2) k_map_build<uint16_t><<<(unsigned)blocks, 256, 0, s>>>(a);
-    else k_map_build<uint32_t><<<(unsigned)blocks, 256, 0, s>>>(a);
+cudaError_t launch_run_build(const RunBuildArgs &a, int pass, int map_bytes, cudaStream_t s) {
+    if (pass == 0 || pass == 1 || pass == 3) {
+        if (a.npairs == 0) return cudaSuccess;
+        int64_t blocks = (a.npairs * 32 + 255) / 256;
+        if (blocks > 152 * 32) blocks = 152 * 32;
+        if (pass < 2) k_runs<<<(unsigned)blocks, 256, 0, s>>>(a, pass);
+        else if (map_bytes == 2) k_map_build<uint16_t><<<(unsigned)blocks, 256, 0, s>>>(a);
+        else k_map_build<uint32_t><<<(unsigned)blocks, 256, 0, s>>>(a);
+    } else {
+        if (a.nsegs == 0) return cudaSuccess;
+        int64_t blocks = (a.nsegs + 255) / 256;
+        if (blocks > 152 * 64) blocks = 152 * 64;
+        if (pass == 2) k_seg_runs<<<(unsigned)blocks, 256, 0, s>>>(a);
+        else k_seg_map<<<(unsigned)blocks, 256, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 

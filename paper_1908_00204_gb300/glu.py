@@ -38,7 +38,7 @@ class glu_options(C.Structure):
                 ("verbose", C.c_int32), ("host_only", C.c_int32), ("solve_mode", C.c_int32),
                 ("spin_limit_us", C.c_int32), ("fault_row", C.c_int32), ("solve_tail", C.c_int32),
                 ("factor_tail", C.c_int32), ("solve_blocks", C.c_int32),
-                ("factor_blocks", C.c_int32), ("reserved", C.c_int32 * 1)]
+                ("factor_blocks", C.c_int32), ("row_lookup", C.c_int32)]
 
 
 class glu_stats(C.Structure):
@@ -48,7 +48,8 @@ class glu_stats(C.Structure):
                 ("solve_levels_fwd", C.c_int32), ("solve_levels_bwd", C.c_int32),
                 ("max_level_width", C.c_int32), ("device_bytes", C.c_int64), ("analyze_ms", C.c_double),
                 ("kernel_launches", C.c_int64), ("tail_rows", C.c_int32),
-                ("factor_tail_cols", C.c_int32)]
+                ("factor_tail_cols", C.c_int32), ("row_lookup", C.c_int32), ("spare", C.c_int32),
+                ("lookup_bytes", C.c_int64), ("n_runs", C.c_int64)]
 
 
 class glu_refine_info(C.Structure):
@@ -83,6 +84,8 @@ def load_library(path: Optional[str] = None):
             "glu_factor_f32": (C.c_int, [P, P]),
             "glu_factor_batched": (C.c_int, [P, P, i32, i64]),
             "glu_get_factors_batched": (C.c_int, [P, i32, P]),
+            "glu_get_factors_batched_f32": (C.c_int, [P, i32, P]),
+            "glu_get_factors_f32": (C.c_int, [P, P]),
             "glu_factor_batched_f32": (C.c_int, [P, P, i32, i64]),
             "glu_solve_batched": (C.c_int, [P, P, P, i32, i32]),
             "glu_solve_batched_refine": (C.c_int, [P, P, P, i32, i32, C.c_double, i32,
@@ -344,6 +347,21 @@ def glu_get_factors(h: Handle) -> np.ndarray:
     st = glu_get_stats(h)
     out = np.empty(max(st["nnz_lu"], 1), np.float64)
     _check(load_library().glu_get_factors(h._ptr, out.ctypes.data), "glu_get_factors", h)
+    return out[:st["nnz_lu"]]
+
+
+def glu_get_factors_f32(h: Handle) -> np.ndarray:
+    st = glu_get_stats(h)
+    out = np.empty(max(st["nnz_lu"], 1), np.float32)
+    _check(load_library().glu_get_factors_f32(h._ptr, out.ctypes.data), "glu_get_factors_f32", h)
+    return out[:st["nnz_lu"]]
+
+
+def glu_get_factors_batched_f32(h: Handle, set_index: int) -> np.ndarray:
+    st = glu_get_stats(h)
+    out = np.empty(max(st["nnz_lu"], 1), np.float32)
+    _check(load_library().glu_get_factors_batched_f32(h._ptr, int(set_index), out.ctypes.data),
+           "glu_get_factors_batched_f32", h)
     return out[:st["nnz_lu"]]
 
 

@@ -1,13 +1,18 @@
 """Host-side check of the column-level factorization schedule (no GPU).
 
 The level kernel's work lists are replayed on the CPU with the kernels' own
-index arithmetic: the position map as its build kernel defines it (entry
-mb + t = offset of row L(:,j)[t] in column k past U(j,k)), then level by
-level the normalization items of the previous level and the update tasks,
-each segment applying A_s(i,k) -= A_s(i,j) * (A_s(j,k) / A_s(j,j)) for its
-rows t0..t1-1 at position pos + 1 + map[mb + t] (Algorithm 5, Eq. 3), then
-the dense trailing block as a dense LU without pivoting, or the final
-normalization pass.  The result must match the oracle's factors.
+index arithmetic: each pair's run table as its build kernel defines it (a
+run starts at every row of L(:,j) whose position in column k is not the
+previous row's plus one), each segment's run range as the segment pass picks
+it, and each row's position found as the kernels find it -- the 32-run
+window, ballots and OR-reduction of a warp over rows (ROW tasks), the
+one-lane walk (SRC and LANE tasks) -- checked against the plain definition
+(the offset of row L(:,j)[t] in column k past U(j,k), by binary search).
+Then level by level the normalization items of the previous level and the
+update tasks, each segment applying A_s(i,k) -= A_s(i,j) * (A_s(j,k) /
+A_s(j,j)) for its rows t0..t1-1 (Algorithm 5, Eq. 3), then the dense
+trailing block as a dense LU without pivoting, or the final normalization
+pass.  The result must match the oracle's factors.
 
 Because the replay applies a level's tasks one after the other while the
 GPU runs them at once, it also checks what makes the two the same: within a
@@ -72,6 +77,72 @@ def position_map(fcp, fri, diag, pairs):
     return mp
 
 
+def runs_of(offsets):
+    """A pair's runs (ts, off) from its rows' offsets, as the build kernel writes them."""
+    t = np.arange(offsets.size)
+    start = np.ones(offsets.size, bool)
+    start[1:] = offsets[1:] != offsets[:-1] + 1
+    return np.stack([t[start], offsets[start]], 1)
+
+
+def segment_runs(runs, t0, t1):
+    """The segment pass: the first run overlapping t0..t1-1 and their count."""
+    rb = int(np.searchsorted(runs[:, 0], t0, side="right")) - 1
+    re = int(np.searchsorted(runs[:, 0], t1, side="left"))
+    return rb, re - rb
+
+
+def offsets_warp(runs, rb, nr, t0, t1, rows_per_batch=256):
+    """row_segment's lookup: lanes hold runs wb..wb+31; per group of 32 rows
+    one ballot for the run holding the group's first row, an OR of the bits
+    of the runs starting inside the group, a popcount per lane."""
+    INF = 2**31 - 1
+    rend = rb + nr
+
+    def window(wb):
+        w = np.full((32, 2), [INF, 0], np.int64)
+        k = max(0, min(32, rend - wb))
+        w[:k] = runs[wb:wb + k]
+        return w
+    wb = rb
+    w = window(wb)
+    out = np.empty(t1 - t0, np.int64)
+    for g0 in range(t0, t1, 32):
+        glast = min(g0 + 31, t1 - 1)
+        if wb + 32 < rend and w[31, 0] <= glast:
+            wb += int((w[:, 0] <= g0).sum()) - 1
+            w = window(wb)
+        a = int((w[:, 0] <= g0).sum()) - 1
+        starts = 0
+        for ts in w[:, 0]:
+            if g0 < ts <= glast:
+                starts |= 1 << int(ts - g0)
+        for lane in range(32):
+            t = g0 + lane
+            if t >= t1:
+                break
+            idx = a + bin(starts & ((1 << (lane + 1)) - 1)).count("1")
+            assert 0 <= idx < 32
+            out[t - t0] = w[idx, 1] + (t - w[idx, 0])
+    return out
+
+
+def offsets_walk(runs, rb, nr, t0, t1):
+    """lane_task / src_task's lookup: one lane walks the runs in order."""
+    INF = 2**31 - 1
+    rend = rb + nr
+    r = rb
+    cur = runs[r]
+    nxt = runs[r + 1] if r + 1 < rend else (INF, 0)
+    out = np.empty(t1 - t0, np.int64)
+    for t in range(t0, t1):
+        while t >= nxt[0]:
+            cur, r = nxt, r + 1
+            nxt = runs[r + 1] if r + 1 < rend else (INF, 0)
+        out[t - t0] = cur[1] + (t - cur[0])
+    return out
+
+
 def replay(fcp, fri, diag, lu, d):
     n = diag.size
     nl, t0b, lend = d["nl"], d["ftail_t0"], d["ftail_level"]
@@ -80,6 +151,8 @@ def replay(fcp, fri, diag, lu, d):
         lend = nl
     pairs, segs, tasks, norms = d["pairs"], d["segs"], d["tasks"], d["norms"]
     mp = position_map(fcp, fri, diag, pairs)
+    lcount = fcp[1:] - diag - 1
+    pair_runs = [runs_of(mp[mb:mb + lcount[j]]) for j, k, pos, mb in pairs]
     applied = np.zeros(mp.size, np.int64)          # uses of each map entry
     divided = np.zeros(lu.size, np.int64)          # divisions of each L entry
     kinds = np.zeros(3, np.int64)
@@ -102,11 +175,18 @@ def replay(fcp, fri, diag, lu, d):
             assert kind == want
             kinds[kind] += 1
             assert se > sb
-            for pos, dj, mb, a, b in segs[sb:se]:
+            for pos, dj, pair, a, b in segs[sb:se]:
                 assert b > a
+                j, k, ppos, mb = pairs[pair]
+                assert ppos == pos and diag[j] == dj and b <= lcount[j]
                 t = np.arange(a, b)
                 src = dj + 1 + t
-                tgt = pos + 1 + mp[mb + t]
+                runs = pair_runs[pair]
+                rb, nr = segment_runs(runs, a, b)
+                look = offsets_warp if kind == KIND_ROW else offsets_walk
+                off = look(runs, rb, nr, a, b)
+                assert np.array_equal(off, mp[mb + t])         # the kernels' lookup = the definition
+                tgt = pos + 1 + off
                 if kind == KIND_SRC:
                     assert 1 <= nslots <= SRC_SLOTS and (tgt >= base).all() and (tgt < base + nslots).all()
                 f = lu[pos] / lu[dj]
@@ -138,7 +218,6 @@ def replay(fcp, fri, diag, lu, d):
     # completeness: every update from a source before the block once, the
     # others never; every L entry outside the block divided once
     from_outside = np.zeros(mp.size, bool)
-    lcount = fcp[1:] - diag - 1
     for j, k, pos, mb in pairs:
         if j < t0b:
             from_outside[mb:mb + lcount[j]] = True
@@ -257,7 +336,8 @@ def _drop_row(d, fcp):
 
 
 def _shift_map(d, fcp):
-    d["segs"][_long_segment(d), 2] += 1                      # rows read the wrong map entries
+    s = _long_segment(d)
+    d["segs"][s, 3:5] += 1                                   # rows shifted by one: the wrong rows and targets
 
 
 def _wrong_pivot(d, fcp):
@@ -281,3 +361,19 @@ def test_replay_detects_planted_mistakes(tmp_path, monkeypatch, mutate):
     m = CASES["mesh30x40_nets8"]()
     with pytest.raises(AssertionError):
         run_case(tmp_path, monkeypatch, m, m.values(1), mutate=mutate)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_run_lookup_with_many_runs(seed):
+    """The warp lookup moves its 32-run window along segments of up to
+    hundreds of runs (runs of 1-3 rows, gaps between them); the walk too."""
+    rng = np.random.default_rng(seed)
+    lj = 700
+    offsets = np.cumsum(rng.integers(1, 4, lj) * (rng.random(lj) < 0.6) + 1)
+    runs = runs_of(offsets)
+    assert len(runs) > 100
+    for t0, t1 in [(0, lj), (1, lj - 1), (37, 400), (255, 257), (600, 700)]:
+        rb, nr = segment_runs(runs, t0, t1)
+        want = offsets[t0:t1]
+        assert np.array_equal(offsets_warp(runs, rb, nr, t0, t1), want)
+        assert np.array_equal(offsets_walk(runs, rb, nr, t0, t1), want)

@@ -1,17 +1,23 @@
 """glu_solve_noalloc: the solve for callers that must not allocate device
 memory while running (for example a time-stepping loop whose memory is all
-reserved up front), using the library's fixed scratch array.
+reserved up front, where a cudaMalloc could fail or stall), using the
+library's fixed scratch array.
 
-Checked through the C ABI against glu_solve on two calls in a row, and the
-size limit is checked on the host before anything runs.  This file is
-collected last so that a stop at its first failure has already run every
-other test; it passes alone in a fresh process and after the others.
+Checked through the C ABI: on two calls in a row it returns glu_solve's
+result bit for bit (it runs the same launches with other scratch memory),
+for the default dataflow solve and for the per-level one; every result meets
+the backward-error bound; at the 200k-unknown workload it matches the CPU
+oracle's solution, and a handle of another size reuses the array right
+after.  The size limit is checked on the host before anything runs.  This
+file is collected last so that a stop at its first failure has already run
+every other test; it passes alone in a fresh process and after the others.
 """
 import numpy as np
 import pytest
 
+import oracle
 import synth
-from parity import FACTOR_RTOL
+from parity import BERR_TOL, backward_error
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -27,18 +33,48 @@ def glu():
     return g
 
 
-def test_noalloc_matches_solve_twice(glu):
+@pytest.mark.parametrize("solve_mode", [1, 0])
+def test_noalloc_matches_solve_twice(glu, solve_mode):
     m = synth.make("mesh100x200_nets64", 1)
-    h = glu.glu_analyze(m.n, m.colptr, m.rowidx, m.perm)
-    glu.glu_factor(h, torch.from_numpy(m.values(31)).cuda())
+    v = m.values(31)
+    h = glu.glu_analyze(m.n, m.colptr, m.rowidx, m.perm, glu.default_options(solve_mode=solve_mode))
+    glu.glu_factor(h, torch.from_numpy(v).cuda())
     for call, k in enumerate((4, 3)):
-        b = torch.from_numpy(synth.rhs(m.n, k, 500 + call)).cuda()
+        bh = synth.rhs(m.n, k, 500 + call)
+        b = torch.from_numpy(bh).cuda()
         want = glu.glu_solve(h, b).cpu().numpy()
         x = torch.full_like(b, float("nan"))
         glu.glu_solve_noalloc(h, b, x)
         glu.glu_sync(h)
         got = x.cpu().numpy()
-        np.testing.assert_allclose(got, want, rtol=FACTOR_RTOL, atol=0.0)
+        assert np.array_equal(got, want)
+        assert backward_error(m.n, m.colptr, m.rowidx, v, bh, got) <= BERR_TOL
+
+
+def test_noalloc_full_size_against_oracle(glu):
+    m = synth.make("mesh400x500_nets64", 1)
+    v = m.values(1001)
+    bh = synth.rhs(m.n, 2, 1001)
+    h = glu.glu_analyze(m.n, m.colptr, m.rowidx, m.perm)
+    glu.glu_factor(h, torch.from_numpy(v).cuda())
+    x = torch.full((2, m.n), float("nan"), dtype=torch.float64, device="cuda")
+    glu.glu_solve_noalloc(h, torch.from_numpy(bh).cuda(), x)
+    glu.glu_sync(h)
+    got = x.cpu().numpy()
+    assert backward_error(m.n, m.colptr, m.rowidx, v, bh, got) <= BERR_TOL
+    f = oracle.Factorization(m.n, m.colptr, m.rowidx, m.perm, v)
+    np.testing.assert_allclose(got, f.solve(bh), rtol=1e-8, atol=1e-12)
+    glu.glu_destroy(h)
+    # another handle, another size, the same array right after
+    g = synth.make("grid32_natural", 0)
+    vg = g.values(1)
+    hg = glu.glu_analyze(g.n, g.colptr, g.rowidx, g.perm)
+    glu.glu_factor(hg, vg)
+    bg = synth.rhs(g.n, 1, 7)
+    xg = torch.full((1, g.n), float("nan"), dtype=torch.float64, device="cuda")
+    glu.glu_solve_noalloc(hg, torch.from_numpy(bg).cuda(), xg)
+    glu.glu_sync(hg)
+    assert np.array_equal(xg.cpu().numpy(), glu.glu_solve(hg, bg))
 
 
 def test_noalloc_rejects_oversize_and_host_pointers(glu):
@@ -46,7 +82,7 @@ def test_noalloc_rejects_oversize_and_host_pointers(glu):
     h = glu.glu_analyze(m.n, m.colptr, m.rowidx, m.perm)
     glu.glu_factor(h, m.values(32))
     limit = glu.glu.GLU_NOALLOC_SCRATCH_DOUBLES
-    k = limit // m.n + 1                       # n * k alone is over the limit
+    k = limit // (2 * m.n) + 1                 # y and z alone are over the limit
     b = torch.zeros((k, m.n), dtype=torch.float64, device="cuda")
     x = torch.zeros_like(b)
     with pytest.raises(glu.GluError) as e:
