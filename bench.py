@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--precision", metavar="WORKLOAD", default=None,
                     help="instead of the step: FP32 factor + FP64 refinement against FP64 and the CPU "
                          "oracle on one workload (backward errors, differences, times)")
+    ap.add_argument("--factor-blocks", action="store_true",
+                    help="with --precision: the supernodal factorization (the schedule that fits the "
+                         "1000x1000 mesh with 256 nets)")
     return ap.parse_args()
 
 
@@ -284,7 +287,98 @@ def extras(g, torch, dev, m, vals_host, b_host, h):
                       "refine_iterations": binfo.get("iterations"), "refine_berr": binfo.get("berr"),
                       "graph_launches_per_batched_factor": 1}
     g.glu_destroy(hb)
+    out["serve"] = serve_compare(g, torch)
     return out
+
+
+def serve_compare(g, torch, names=("serve5k", "serve20k", "serve50k"), nreq=800, load=0.7, seed=2027):
+    """Continuous-batching serving against a plain loop that factors and
+    solves one request at a time (FP64, one handle per pattern), on the same
+    Poisson arrivals over mixed patterns with 1-8 right-hand sides.  The
+    offered rate is `load` times the plain loop's measured capacity, so both
+    arms keep up; latency is scheduled arrival -> result on the host, the
+    first tenth of the requests excluded."""
+    import collections
+    from paper_1908_00204_gb300.serve import Request, Server
+    dev = torch.device("cuda", torch.cuda.current_device())
+    mats = {k: synth.make(k, 1) for k in names}
+    pool = 8
+    vals = {k: [m.values(100 + i, sigma=0.1, base_seed=7) for i in range(pool)] for k, m in mats.items()}
+    rhs = {k: synth.rhs(m.n, 8, 11) for k, m in mats.items()}
+    rng = np.random.default_rng(seed)
+    nwarm = nreq // 10
+    total = nreq + nwarm
+    keys = [names[i] for i in rng.integers(len(names), size=total)]
+    nrhs = rng.integers(1, 9, size=total)
+
+    def make(i):
+        k = keys[i]
+        return Request(i, k, vals[k][i % pool], rhs[k][: int(nrhs[i])])
+    # the plain arm's handles, and its service time per pattern
+    handles = {}
+    for k, m in mats.items():
+        handles[k] = g.glu_analyze(m.n, m.colptr, m.rowidx, m.perm)
+        g.glu_set_stream(handles[k], torch.cuda.current_stream(dev))
+
+    def plain_one(req):
+        h = handles[req.key]
+        v = torch.from_numpy(req.values).to(dev, non_blocking=True)
+        b = torch.from_numpy(np.ascontiguousarray(req.b)).to(dev, non_blocking=True)
+        g.glu_factor(h, v)
+        return g.glu_solve(h, b).cpu().numpy()
+    svc = []
+    for i in range(60):
+        r = make(i)
+        t = time.perf_counter()
+        plain_one(r)
+        svc.append(time.perf_counter() - t)
+    capacity = 1.0 / float(np.mean(svc[10:]))
+    rate = load * capacity
+    arrivals = list(np.cumsum(rng.exponential(1.0 / rate, total)))
+    # serving arm
+    srv = Server(device_budget_bytes=60e9, max_batch=32, slots=4, replicas=3, batch_min=8)
+    for k, m in mats.items():
+        srv.register(k, m.n, m.colptr, m.rowidx, m.perm)
+        srv.prepare(k, vals[k][0], rhs[k][:1])    # analyses, replicas and captured graphs before traffic
+    batches0 = len(srv.batch_sizes)
+    t0 = time.perf_counter()
+    srv.run(arrivals, make)
+    wall_s = time.perf_counter() - t0
+    lat_s = srv.latencies(skip=nwarm) * 1e3
+    ok_s = all(r.status == 0 for r in srv.done)
+    # plain arm: the same arrivals, served in order, one at a time
+    q = collections.deque()
+    lat_p = np.empty(total)
+    t0 = time.perf_counter()
+    i = 0
+    while i < total or q:
+        now = time.perf_counter() - t0
+        while i < total and arrivals[i] <= now:
+            q.append(i)
+            i += 1
+        if not q:
+            time.sleep(max(0.0, min(arrivals[i] - now, 0.001)))
+            continue
+        j = q.popleft()
+        plain_one(make(j))
+        lat_p[j] = time.perf_counter() - t0 - arrivals[j]
+    wall_p = time.perf_counter() - t0
+    lat_p = lat_p[nwarm:] * 1e3
+    for h in handles.values():
+        g.glu_destroy(h)
+
+    def summary(lat, wall, extra):
+        d = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+             "mean_ms": float(lat.mean()), "achieved_per_s": total / wall}
+        d.update(extra)
+        return d
+    return {"patterns": {k: m.n for k, m in mats.items()}, "requests": nreq, "warmup_requests": nwarm,
+            "nrhs": "uniform 1..8", "plain_capacity_per_s": capacity, "offered_per_s": rate, "load": load,
+            "serving": summary(lat_s, wall_s, {"launches": len(srv.batch_sizes) - batches0, "all_ok": ok_s,
+                                               "streams": 4, "max_batch": 32, "batch_min": 8, "replicas": 3,
+                                               "batched_launches": int(sum(b > 1 for b in
+                                                                           srv.batch_sizes[batches0:]))}),
+            "plain_one_at_a_time_fp64": summary(lat_p, wall_p, {})}
 
 
 def measured_hbm_gbs():
@@ -470,14 +564,13 @@ def run_serve(args):
     def make(i):
         k = keys[i]
         return Request(i, k, vals[k][i % pool], rhs[k][: int(nrhs[i])])
-    srv = Server(device_budget_bytes=60e9, max_batch=64, slots=4, precision=args.serve_precision)
+    srv = Server(device_budget_bytes=60e9, max_batch=64, slots=4, precision=args.serve_precision, replicas=3,
+                 batch_min=8)
     t0 = time.perf_counter()
     for k, m in mats.items():
         srv.register(k, m.n, m.colptr, m.rowidx, m.perm)
-        srv.submit(Request(-1, k, vals[k][0], rhs[k][:1]))   # analysis and first factorization
-    srv.drain()
+        srv.prepare(k, vals[k][0], rhs[k][:1])    # analyses, replicas and captured graphs before traffic
     setup_s = time.perf_counter() - t0
-    srv.done.clear()
     arrivals = list(np.cumsum(rng.exponential(1.0 / args.serve_rate, nreq)))
     with ClockSampler(torch.cuda.current_device()) as clk:
         t0 = time.perf_counter()
@@ -646,12 +739,13 @@ def run_precision(args):
     name = args.precision
     m = synth.make(name, 1)
     out = {"metric": "FP32 factor + FP64 refinement vs FP64 and the oracle", "workload": name,
-           "n": m.n, "nnz_a": m.nnz}
+           "n": m.n, "nnz_a": m.nnz, "factor_blocks": int(args.factor_blocks)}
     t0 = time.perf_counter()
-    h = g.glu_analyze(m.n, m.colptr, m.rowidx, m.perm)
+    h = g.glu_analyze(m.n, m.colptr, m.rowidx, m.perm, g.default_options(factor_blocks=int(args.factor_blocks)))
     out["analyze_s"] = time.perf_counter() - t0
     st = g.glu_get_stats(h)
     out.update({k: st[k] for k in ("nnz_lu", "nlevels", "n_updates", "flops", "device_bytes")})
+    print(json.dumps({"analysis": out}), flush=True)
     v = m.values(4001)
     b = synth.rhs(m.n, 1, 4001)
     A = sp.csc_matrix((v, m.rowidx, m.colptr), shape=(m.n, m.n))

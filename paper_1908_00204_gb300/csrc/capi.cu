@@ -297,7 +297,20 @@ int enqueue_factor(glu_handle *h, const double *av, cudaStream_t st, std::vector
     CKL(P.lu_colptr[P.n] > 0, launch_gather<double>(h->d_lu, av, h->d_gsrc, P.lu_colptr[P.n], st));
     FactorArgs<double> a = fargs(h);
     const int32_t nl = (int32_t)P.level_ptr.size() - 1;
-    if (lev_events) {
+    if (lev_events && h->opt.factor_blocks != 0) {
+        // per-level timing diagnostic of the supernodal sweep: events around
+        // each block level's launches
+        const BlockArgs<double> ba = bargs_t<double>(h, h->d_lu);
+        CK(cudaEventRecord((*lev_events)[0], st));
+        for (int32_t l = 0; l < P.nblev; l++) {
+            int launched = 0;
+            CK(launch_block_level<double>(ba, h->map_bytes, P.bdiag_ptr[l], P.bdiag_ptr[l + 1], P.bitem_ptr[l],
+                                          P.bitem_ptr[l + 1], P.btask_ptr[l], P.btask_ptr[l + 1], h->num_sms, st,
+                                          &launched));
+            h->launches += launched;
+            CK(cudaEventRecord((*lev_events)[l + 1], st));
+        }
+    } else if (lev_events) {
         // per-level timing diagnostic: one launch per level (column levels)
         const int rc0 = setup_column_plan(h);
         if (rc0 != GLU_OK) return rc0;
@@ -1046,7 +1059,7 @@ int glu_factor(glu_handle *h, const double *values) {
             av = h->d_aval;
         }
         if (!h->level_times_path.empty()) {
-            const size_t nev = P.level_ptr.size() + 1;
+            const size_t nev = h->opt.factor_blocks != 0 ? (size_t)P.nblev + 1 : P.level_ptr.size() + 1;
             std::vector<cudaEvent_t> ev(nev);
             for (auto &e : ev) CK(cudaEventCreate(&e));
             int rc = enqueue_factor(h, av, h->stream, &ev);

@@ -75,10 +75,10 @@ __global__ void __launch_bounds__(128) k_level_b(const FactorArgs<T> a, LevelRan
         if (k < nn) {
             const NormItem ni = a.norms[r.n_begin + k];
             const int64_t dj = a.diag_pos[ni.col];
-            const T d = lu[dj * S + b];
+            const T rd = (T)1 / lu[dj * S + b];    // one division per item, as the single-matrix kernel
             for (int32_t t = ni.t0; t < ni.t1; t++) {
                 T *p = lu + (dj + 1 + t) * S + b;
-                *p = *p / d;
+                *p = *p * rd;
             }
             continue;
         }

@@ -54,21 +54,26 @@ __global__ void k_gather(T *__restrict__ lu, const double *__restrict__ aval,
 }
 
 // ------------------------------------------------------------- level work
+// L(:,j) /= A_s(j,j) as products with one reciprocal per item: the FP64
+// pipe of this part is narrow (a division is a dozen dependent operations
+// on it), and x * (1/d) is within one rounding of x / d.
 template <typename T>
 __device__ __forceinline__ void norm_item(const FactorArgs<T> &a, const NormItem it, int lane) {
     const int64_t dj = a.diag_pos[it.col];
-    const T d = a.lu[dj];
+    const T rd = (T)1 / a.lu[dj];
     T *L = a.lu + dj + 1;
-    // all loads of the item first (at most 8 per lane), then the divisions
+    // all loads of the item first (at most 8 per lane), then the products
     constexpr int NU = 8;
-    for (int32_t tb = it.t0 + lane; tb < it.t1; tb += 32 * NU) {
+    for (int32_t tb = it.t0; tb < it.t1; tb += 32 * NU) {
         T v[NU];
 #pragma unroll
         for (int u = 0; u < NU; u++)
-            if (tb + 32 * u < it.t1) v[u] = L[tb + 32 * u];
+            if (tb + 32 * u < it.t1 && tb + 32 * u + lane < it.t1) v[u] = L[tb + 32 * u + lane];
 #pragma unroll
         for (int u = 0; u < NU; u++)
-            if (tb + 32 * u < it.t1) L[tb + 32 * u] = v[u] / d;
+            if (tb + 32 * u < it.t1) {              // the same for the whole warp
+                if (tb + 32 * u + lane < it.t1) L[tb + 32 * u + lane] = v[u] * rd;
+            }
     }
 }
 
@@ -253,20 +258,23 @@ __device__ __forceinline__ void row_segment_map(T *__restrict__ lu, const M *__r
     const M *__restrict__ mp = map + m.rb;
     const T *__restrict__ L = lu + m.lstart;
     T *tgt = lu + m.pos + 1;
-    for (int32_t tb = m.t0 + lane; tb < m.t1; tb += 32 * ROW_UNROLL) {
+    for (int32_t tb = m.t0; tb < m.t1; tb += 32 * ROW_UNROLL) {
         uint32_t off[ROW_UNROLL];
         T lv[ROW_UNROLL];
 #pragma unroll
         for (int u = 0; u < ROW_UNROLL; u++) {
-            const int32_t t = tb + 32 * u;
+            const int32_t t = tb + 32 * u + lane;
             if (t < m.t1) {
                 off[u] = mp[t];
                 lv[u] = L[t];
             }
         }
+        // a group of 32 rows past the end is skipped by the whole warp
 #pragma unroll
         for (int u = 0; u < ROW_UNROLL; u++)
-            if (tb + 32 * u < m.t1) atomicAdd(&tgt[off[u]], -lv[u] * m.f);
+            if (tb + 32 * u < m.t1) {
+                if (tb + 32 * u + lane < m.t1) atomicAdd(&tgt[off[u]], -lv[u] * m.f);
+            }
     }
 }
 

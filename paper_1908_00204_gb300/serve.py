@@ -8,13 +8,19 @@ right-hand sides.  The loop:
   (the paper's flow repeats only the numeric part for a fixed pattern,
   Section III), evicting the least recently used idle pattern when the
   device-memory budget would be exceeded;
-* groups waiting requests of one pattern into a batch (up to ``max_batch``)
-  and runs it as one batched refactorization + solve (glu_factor_batched /
-  glu_solve_batched, or the FP32 + FP64-refinement pair), or through the
-  single-matrix path for a batch of one;
-* runs batches of different patterns at the same time on separate CUDA
-  streams ("slots"); a request that arrives while others run is admitted as
-  soon as a slot and the memory budget allow it;
+* keeps up to ``replicas`` handles per pattern (each its own numeric
+  workspace, the budget permitting), so several requests of one pattern can
+  run at once through the single-matrix path;
+* once ``batch_min`` or more requests of one pattern wait, groups them into a
+  batch (up to ``max_batch``) and runs it as one batched refactorization +
+  solve (glu_factor_batched / glu_solve_batched, or the FP32 +
+  FP64-refinement pair) on the pattern's first handle; the batched kernels
+  run 32 value sets per lane group whatever the batch, so a batch is padded
+  to a multiple of 32 with copies of its last request (one captured graph per
+  padded size, the padding's results discarded);
+* runs work of different patterns and handles at the same time on separate
+  CUDA streams ("slots"); a request that arrives while others run is
+  admitted as soon as a slot and the memory budget allow it;
 * records each request's latency from submission to result-ready, and its
   status: a zero or non-finite pivot (or another device error) reaches the
   request as ``status`` / ``error_column`` instead of a solution.  A batch
@@ -61,17 +67,34 @@ class Request:
 
 
 class _Resident:
-    """A pattern's handle on the device, plus its last use."""
+    """A pattern's handles on the device (replicas of one analysis, each with
+    its own numeric workspace), which of them are running, and its last use.
+    Batches run on the first handle."""
 
     def __init__(self, pat: Pattern, handle):
         self.pat = pat
-        self.h = handle
+        self.hs = [handle]
+        self.busy_h = [False]
         self.last_use = time.perf_counter()
-        self.busy = False
         st = _glu.glu_get_stats(handle)
-        self.base_bytes = int(st["device_bytes"])
+        self.one_bytes = int(st["device_bytes"])
         self.nnz_lu = int(st["nnz_lu"])
         self.batch_bytes = 0
+
+    @property
+    def h(self):
+        return self.hs[0]
+
+    @property
+    def busy(self) -> bool:
+        return any(self.busy_h)
+
+    @property
+    def base_bytes(self) -> int:
+        return self.one_bytes * len(self.hs)
+
+    def free_handle(self) -> int:
+        return next((i for i, b in enumerate(self.busy_h) if not b), -1)
 
 
 class _Slot:
@@ -79,6 +102,7 @@ class _Slot:
         self.stream = torch.cuda.Stream(device=device)
         self.event = None
         self.res: Optional[_Resident] = None
+        self.hi = 0             # which of the pattern's handles
         self.reqs: List[Request] = []
         self.out = None
         self.info = None
@@ -89,12 +113,15 @@ class Server:
     """Continuous batching over patterns; see the module docstring."""
 
     def __init__(self, device_budget_bytes: float = 60e9, max_batch: int = 64, slots: int = 4,
-                 precision: str = "fp64", tol: float = 1e-12, maxit: int = 10, device: int = 0):
+                 precision: str = "fp64", tol: float = 1e-12, maxit: int = 10, device: int = 0,
+                 replicas: int = 1, batch_min: int = 2):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", device)
         self.budget = int(device_budget_bytes)
         self.max_batch = max_batch
+        self.replicas = max(1, replicas)
+        self.batch_min = max(2, batch_min)
         self.precision = precision
         self.tol = tol
         self.maxit = maxit
@@ -106,6 +133,7 @@ class Server:
         self.analyses = 0
         self.evictions = 0
         self.batches = 0
+        self.batch_sizes: List[int] = []     # requests per launch, in launch order
 
     # ------------------------------------------------------------ patterns
     def register(self, key: str, n: int, colptr, rowidx, perm=None) -> None:
@@ -126,9 +154,21 @@ class Server:
             victim = next((k for k, r in self.resident.items() if not r.busy and k != keep), None)
             if victim is None:
                 return False
-            _glu.glu_destroy(self.resident.pop(victim).h)
+            for h in self.resident.pop(victim).hs:
+                _glu.glu_destroy(h)
             self.evictions += 1
         return True
+
+    def _add_replica(self, res: _Resident) -> int:
+        """Another handle for the pattern when the budget leaves room for it
+        without evicting anything; its index, or -1."""
+        if len(res.hs) >= self.replicas or self._bytes_in_use() + res.one_bytes > self.budget:
+            return -1
+        pat = res.pat
+        res.hs.append(_glu.glu_analyze(pat.n, pat.colptr, pat.rowidx, pat.perm))
+        res.busy_h.append(False)
+        self.analyses += 1
+        return len(res.hs) - 1
 
     def _resident(self, key: str) -> Optional[_Resident]:
         if key in self.resident:
@@ -144,18 +184,45 @@ class Server:
         self.resident[key] = res
         return res
 
+    def prepare(self, key: str, values: np.ndarray, b: np.ndarray) -> bool:
+        """Make a pattern resident before traffic: its analysis, every
+        replica the budget allows, and one refactorization + solve on each
+        handle and one padded batch on the first (so the captured graphs
+        exist); a server keeps no result of these.  False if the budget has
+        no room for the pattern."""
+        res = self._resident(key)
+        if res is None:
+            return False
+        while self._add_replica(res) >= 0:
+            pass
+        warm = [Request(-1 - i, key, values, b) for i in range(max(len(res.hs), self.batch_min))]
+        q = self.queues[key]
+        for r in warm[: len(res.hs)]:
+            q.append(r)
+        self.drain()
+        for r in warm:
+            q.append(r)
+        self.drain()
+        self.done = [r for r in self.done if r.rid >= 0]
+        return True
+
     # ------------------------------------------------------------ requests
     def submit(self, req: Request) -> None:
         req.t_submit = time.perf_counter()
         self.queues[req.key].append(req)
 
     def _launch(self, slot: _Slot) -> bool:
-        # the pattern whose oldest waiting request is oldest, not already running
+        # the pattern whose oldest waiting request is oldest, among those with
+        # a handle free (or room for another one)
         best = None
         for key, q in self.queues.items():
-            if q and not (key in self.resident and self.resident[key].busy):
-                if best is None or q[0].t_submit < self.queues[best][0].t_submit:
-                    best = key
+            if not q:
+                continue
+            res = self.resident.get(key)
+            if res is not None and res.free_handle() < 0 and len(res.hs) >= self.replicas:
+                continue
+            if best is None or q[0].t_submit < self.queues[best][0].t_submit:
+                best = key
         if best is None:
             return False
         q = self.queues[best]
@@ -163,6 +230,13 @@ class Server:
         if res is None:
             return False
         take = 1 if q[0].solo else min(len(q), self.max_batch)
+        if take < self.batch_min or res.busy_h[0]:
+            take = 1                        # too few for a batch, or the batch handle is running
+        hi = 0 if take > 1 else res.free_handle()
+        if hi < 0:
+            hi = self._add_replica(res)
+            if hi < 0:
+                return False
         nrhs = max(r.b.shape[0] for r in list(q)[:take])
         # a batch never evicts other patterns: it shrinks to what the budget
         # leaves (batch buffers stay with the pattern until it is evicted)
@@ -176,10 +250,10 @@ class Server:
             reqs, take = reqs[:1], 1
         nrhs = max(r.b.shape[0] for r in reqs)
         torch = self.torch
-        res.busy = True
+        res.busy_h[hi] = True
         res.last_use = time.perf_counter()
-        slot.res, slot.reqs = res, reqs
-        h = res.h
+        slot.res, slot.hi, slot.reqs = res, hi, reqs
+        h = res.hs[hi]
         slot.error = None
         with torch.cuda.stream(slot.stream):
             _glu.glu_set_stream(h, slot.stream)
@@ -191,12 +265,13 @@ class Server:
             slot.event = torch.cuda.Event()
             slot.event.record(slot.stream)
         self.batches += 1
+        self.batch_sizes.append(take)
         return True
 
     def _enqueue(self, slot: _Slot, res: _Resident, reqs: List[Request], nrhs: int) -> None:
         """The batch's factorization and solve, on the slot's stream."""
         torch = self.torch
-        h = res.h
+        h = res.hs[slot.hi]
         take = len(reqs)
         if take == 1:
             r = reqs[0]
@@ -211,10 +286,15 @@ class Server:
                 x, slot.info = _glu.glu_solve_refine(h, bb, tol=self.tol, maxit=self.maxit)
             slot.out = x
         else:
-            res.batch_bytes = max(res.batch_bytes, self._batch_bytes(res, take, nrhs))
-            V = np.stack([r.values for r in reqs])
-            Bt = np.zeros((take, nrhs, res.pat.n))
-            for i, r in enumerate(reqs):
+            # padded to the batched kernels' 32-set lane groups with copies of
+            # the last request (their results are discarded)
+            S = (take + 31) // 32 * 32
+            res.batch_bytes = max(res.batch_bytes, self._batch_bytes(res, S, nrhs))
+            V = np.empty((S, reqs[0].values.size))
+            Bt = np.zeros((S, nrhs, res.pat.n))
+            for i in range(S):
+                r = reqs[min(i, take - 1)]
+                V[i] = r.values
                 Bt[i, : r.b.shape[0]] = r.b
             Vd = torch.from_numpy(V).to(self.device, non_blocking=True)
             Bd = torch.from_numpy(Bt).to(self.device, non_blocking=True)
@@ -230,7 +310,7 @@ class Server:
     def _finish(self, slot: _Slot) -> None:
         # the device error word of the handle: pivots of the factorization,
         # bounded waits of the solve (device inputs leave it unread until here)
-        code, col = slot.error if slot.error is not None else _glu.glu_sync_status(slot.res.h)
+        code, col = slot.error if slot.error is not None else _glu.glu_sync_status(slot.res.hs[slot.hi])
         if code != _glu.GLU_OK and len(slot.reqs) > 1:
             q = self.queues[slot.res.pat.key]
             for r in reversed(slot.reqs):
@@ -250,7 +330,7 @@ class Server:
         self._release(slot)
 
     def _release(self, slot: _Slot) -> None:
-        slot.res.busy = False
+        slot.res.busy_h[slot.hi] = False
         slot.res = None
         slot.reqs = []
         slot.event = None
@@ -276,13 +356,17 @@ class Server:
 
     def run(self, arrivals: List[float], make_request: Callable[[int], Request]) -> None:
         """Replay arrival times (seconds from now): requests are submitted at
-        their time while the loop keeps slots busy."""
+        their time while the loop keeps slots busy.  A request's latency
+        counts from its scheduled arrival, so time it waited for the loop to
+        notice it is included."""
         t0 = time.perf_counter()
         i = 0
         while i < len(arrivals) or self.step() or any(self.queues.values()):
             now = time.perf_counter() - t0
             while i < len(arrivals) and arrivals[i] <= now:
-                self.submit(make_request(i))
+                req = make_request(i)
+                self.submit(req)
+                req.t_submit = t0 + arrivals[i]
                 i += 1
             self.step()
 

@@ -224,8 +224,9 @@ def test_every_request_gets_its_own_solution(server, precision):
     srv.drain()
     check_results(mats, srv.done, 60)
     assert dev.analyses == 3 and srv.evictions == 0        # every pattern analysed once
-    assert all(b <= 8 for _, b in dev.log)
-    assert any(b > 1 for _, b in dev.log)                  # same-pattern requests were batched
+    assert all(b <= 8 for b in srv.batch_sizes)
+    assert any(b > 1 for b in srv.batch_sizes)             # same-pattern requests were batched
+    assert all(b in (1, 32) for _, b in dev.log)           # batches padded to the 32-set lane groups
 
 
 def test_budget_evicts_idle_patterns_only(server):
@@ -247,7 +248,7 @@ def test_budget_evicts_idle_patterns_only(server):
     check_results(mats, srv.done, 40)
     assert srv.evictions > 0 and dev.analyses > 3            # patterns came back after eviction
     assert len(dev.live) == len(srv.resident) <= 2
-    assert all(b == 1 for _, b in dev.log)
+    assert all(b == 1 for b in srv.batch_sizes)
 
 
 def test_oldest_waiting_pattern_runs_first(server):
@@ -263,7 +264,7 @@ def test_oldest_waiting_pattern_runs_first(server):
     srv.drain()
     # one slot: p2 first, then p0 (its oldest request is older than p1's) as a batch of two, then p1
     assert [n for n, _ in dev.log] == [mats["p2"].n, mats["p0"].n, mats["p1"].n]
-    assert [b for _, b in dev.log] == [1, 2, 1]
+    assert srv.batch_sizes == [1, 2, 1]
     check_results(mats, srv.done, 4)
 
 
@@ -282,4 +283,37 @@ def test_zero_pivot_reaches_its_request(server, precision):
         srv.submit(r)
     srv.drain()
     check_results(mats, srv.done, 24, failed=bad)
-    assert any(b > 1 for _, b in dev.log)       # batches ran, and the failed ones again one by one
+    assert any(b > 1 for b in srv.batch_sizes)  # batches ran, and the failed ones again one by one
+
+
+def test_replicas_run_one_pattern_concurrently(server):
+    """With replicas, requests of one pattern below the batching threshold run
+    at the same time on separate handles (never two launches on one busy
+    handle), within the budget; results are each request's own."""
+    mats = patterns()
+    srv, dev = server(device_budget_bytes=1e12, max_batch=8, slots=4, replicas=3, batch_min=100)
+    key = "p1"
+    m = mats[key]
+    srv.register(key, m.n, m.colptr, m.rowidx, m.perm)
+    from paper_1908_00204_gb300.serve import Request
+    reqs = [Request(i, key, m.values(900 + i), synth.rhs(m.n, 2, 950 + i)) for i in range(9)]
+    for r in reqs:
+        srv.submit(r)
+    srv.step()
+    assert sum(h.inflight for h in dev.live.values()) == 3          # three handles busy at once
+    srv.drain()
+    assert dev.analyses == 3 and len(srv.resident[key].hs) == 3
+    assert all(b == 1 for b in srv.batch_sizes)
+    check_results({key: m}, srv.done, 9)
+
+
+def test_prepare_makes_replicas_and_keeps_no_results(server):
+    mats = patterns()
+    srv, dev = server(device_budget_bytes=1e12, max_batch=16, slots=3, replicas=2, batch_min=4)
+    key = "p0"
+    m = mats[key]
+    srv.register(key, m.n, m.colptr, m.rowidx, m.perm)
+    assert srv.prepare(key, m.values(1), synth.rhs(m.n, 1, 1))
+    assert len(srv.resident[key].hs) == 2 and dev.analyses == 2
+    assert srv.done == [] and not any(srv.queues.values())
+    assert 4 in srv.batch_sizes                       # a batch ran (its graph exists)
