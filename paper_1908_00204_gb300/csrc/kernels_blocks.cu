@@ -89,6 +89,9 @@ __global__ void __launch_bounds__(BW * 32) k_bpanel(const BlockArgs<T> a, int32_
                 if (lane <= m) u11[lane * U11_LD + m] = a.lu[base + lane];
             }
             __syncwarp();
+            // the diagonal kept as reciprocals: one division per column, not per row
+            if (lane < s) u11[lane * U11_LD + lane] = (T)1 / u11[lane * U11_LD + lane];
+            __syncwarp();
             // rows bi.a .. bi.b-1 of R_B: x U11 = a, solved left to right
             const int32_t t = bi.a + lane;
             const bool own = t < bi.b;
@@ -98,7 +101,7 @@ __global__ void __launch_bounds__(BW * 32) k_bpanel(const BlockArgs<T> a, int32_
 #pragma unroll
             for (int jj = 0; jj < BSN_MAX; jj++) {
                 if (jj < s) {
-                    x[jj] = x[jj] / u11[jj * U11_LD + jj];
+                    x[jj] = x[jj] * u11[jj * U11_LD + jj];
 #pragma unroll
                     for (int m = jj + 1; m < BSN_MAX; m++)
                         if (m < s) x[m] = x[m] - x[jj] * u11[jj * U11_LD + m];
