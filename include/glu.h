@@ -96,9 +96,10 @@ typedef struct glu_options {
                                  1 block-per-column, 2 pipelined tail, for every level */
     int32_t tail_threshold;   /* levels with at most this many columns run in the
                                  pipelined mode: consecutive such levels share one
-                                 persistent launch with a grid barrier between
-                                 levels (the paper's stream-mode threshold is 16,
-                                 Section III-B.2 item 3); 0 (default): off */
+                                 dataflow launch in which each work item waits only for
+                                 the items it reads (per-column counters, bounded waits)
+                                 instead of a barrier per level (the paper's stream-mode
+                                 threshold is 16, Section III-B.2 item 3); 0: off */
     int32_t piece_updates;    /* target-column updates per warp task (work split size) */
     int32_t wide_threshold;   /* levels with more columns than this run warp-per-column */
     int32_t use_graph;        /* 1: capture the level sequence in a CUDA graph */
@@ -111,7 +112,9 @@ typedef struct glu_options {
     int32_t spin_limit_us;    /* bound on any device-side wait, microseconds
                                  (default 2,000,000); past it GLU_ERR_TIMEOUT */
     int32_t fault_row;        /* testing only: in the dataflow solve this row never
-                                 publishes its result, so waits on it time out
+                                 publishes its result, and in the pipelined levels of
+                                 the factorization the tasks that update this column
+                                 never publish theirs, so waits on them time out
                                  (-1: off) */
     int32_t solve_tail;       /* 1 (default): a trailing fully dense block of 32..1024
                                  rows is solved by one block in shared memory; 0: off */

@@ -1448,6 +1448,67 @@ void solve_levels(HostPlan &P, const glu_options &opt) {
 
 }  // namespace
 
+// Dataflow runs: maximal runs of consecutive mode-2 levels before the dense
+// trailing block (the last run also takes the final normalization pass when
+// there is no dense block) run as one launch whose work items wait on
+// counters instead of level barriers.  A task of level l in a run needs
+// (a) the columns of level l final -- every task of the run that targets
+// them done -- and (b) every task of an earlier level of the run that
+// targets its own column done (U(j,k) final, and the additions into the
+// column in level order).  Tasks before the run are complete when it starts.
+void dataflow_tables(HostPlan &P) {
+    const int32_t nl = (int32_t)P.level_ptr.size() - 1;
+    const int64_t ntask = (int64_t)P.tasks.size();
+    P.task_col.assign((size_t)ntask, 0);
+    P.task_before.assign((size_t)ntask, 0);
+    P.lvl_total.assign((size_t)nl + 1, 0);
+    P.lvl_ntasks.assign((size_t)nl + 1, 0);
+    P.lvl_item_ptr.assign((size_t)nl + 2, 0);
+    for (int64_t t = 0; t < ntask; t++) {
+        const Task &tk = P.tasks[(size_t)t];
+        P.task_col[(size_t)t] = tk.seg_end > tk.seg_begin ? P.pair_k[(size_t)P.segs[(size_t)tk.seg_begin].rb] : 0;
+    }
+    for (int32_t l = 0; l <= nl; l++) {
+        const int64_t nn = P.lvl_norm_ptr[l + 1] - P.lvl_norm_ptr[l];
+        int64_t nsrc = 0, nrow = 0, nlane = 0;
+        if (l < nl) {
+            nsrc = P.lvl_row_ptr[l] - P.lvl_task_ptr[l];
+            nrow = P.lvl_lane_ptr[l] - P.lvl_row_ptr[l];
+            nlane = P.lvl_task_ptr[l + 1] - P.lvl_lane_ptr[l];
+            P.lvl_ntasks[l] = P.lvl_task_ptr[l + 1] - P.lvl_task_ptr[l];
+        }
+        P.lvl_item_ptr[l + 1] = P.lvl_item_ptr[l] + (int32_t)(nn + nsrc + nrow + (nlane + 31) / 32);
+    }
+    const bool dense = P.ftail_t0 < P.n;
+    const int32_t lend = dense ? P.ftail_level : nl;
+    std::vector<int32_t> cnt((size_t)P.n, 0);
+    std::vector<int32_t> touched;
+    int32_t l = 0;
+    while (l < lend) {
+        if (P.level_mode[l] != 2) {
+            l++;
+            continue;
+        }
+        int32_t e = l;
+        while (e < lend && P.level_mode[e] == 2) e++;
+        for (int32_t q = l; q < e; q++) {
+            // before-counts from the earlier levels of the run, then this level's
+            for (int32_t t = P.lvl_task_ptr[q]; t < P.lvl_task_ptr[q + 1]; t++)
+                P.task_before[(size_t)t] = cnt[(size_t)P.task_col[(size_t)t]];
+            for (int32_t t = P.lvl_task_ptr[q]; t < P.lvl_task_ptr[q + 1]; t++) {
+                const int32_t k = P.task_col[(size_t)t];
+                if (cnt[(size_t)k]++ == 0) touched.push_back(k);
+                // only targets inside the run: a later run starts with its
+                // counters at zero, everything before it being complete
+                if (P.level_of[(size_t)k] < e) P.lvl_total[(size_t)P.level_of[(size_t)k]]++;
+            }
+        }
+        for (int32_t k : touched) cnt[(size_t)k] = 0;
+        touched.clear();
+        l = e;
+    }
+}
+
 int column_schedule(HostPlan &P, const glu_options &opt, int num_sms) {
     return P.has_schedule ? GLU_OK : schedule(P, opt, num_sms);
 }

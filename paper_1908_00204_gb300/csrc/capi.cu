@@ -77,6 +77,13 @@ struct glu_handle {
     // grid-barrier words
     LevelRange *d_ranges = nullptr;
     unsigned *d_gbar = nullptr;          // count, abort
+    // dataflow level runs (the pipelined mode): tables and counters
+    char *dfarena = nullptr;
+    size_t dfarena_bytes = 0;
+    int32_t *d_task_col = nullptr, *d_task_before = nullptr, *d_lvl_total = nullptr, *d_lvl_ntasks = nullptr;
+    int32_t *d_item_ptr = nullptr, *d_level_of = nullptr;
+    int32_t *d_dfcnt = nullptr;          // cdone (n), ldone (nlevels + 1), tdone (nlevels + 1)
+    unsigned *d_dfword = nullptr;        // ticket, abort
     // FP32 factors and the refinement path
     float *d_lu32 = nullptr;
     cudaGraphExec_t fgraph32 = nullptr;
@@ -250,7 +257,31 @@ int enqueue_levels(glu_handle *h, const FactorArgs<T> &a, cudaStream_t st) {
             const LevelRange r = level_range(P, l);
             CKL((r.t_end - r.t_begin) + (r.n_end - r.n_begin) > 0, launch_level<T>(a, h->lookup, r, h->num_sms, st));
         } else {
-            CKL(1, launch_levels_persistent<T>(a, h->lookup, h->d_ranges + l, e - l, bar, h->num_sms, st));
+            // one dataflow launch for the run, its counters zeroed first
+            CK(cudaMemsetAsync(h->d_dfcnt, 0, ((size_t)P.n + 2 * ((size_t)nl + 1)) * sizeof(int32_t), st));
+            CK(cudaMemsetAsync(h->d_dfword, 0, 2 * sizeof(unsigned), st));
+            DFFactorArgs d;
+            d.ranges = h->d_ranges;
+            d.item_ptr = h->d_item_ptr;
+            d.l0 = l;
+            d.l1 = e;
+            d.task_col = h->d_task_col;
+            d.task_before = h->d_task_before;
+            d.lvl_total = h->d_lvl_total;
+            d.lvl_ntasks = h->d_lvl_ntasks;
+            d.level_of = h->d_level_of;
+            d.cdone = h->d_dfcnt;
+            d.ldone = h->d_dfcnt + P.n;
+            d.tdone = d.ldone + nl + 1;
+            d.ticket = h->d_dfword;
+            d.abort = h->d_dfword + 1;
+            d.err = h->d_err;
+            d.spin_limit_cycles = h->spin_cycles;
+            d.fault_col = h->opt.fault_row;
+            d.max_items = 0;
+            for (int32_t q = l; q < e; q++)
+                d.max_items = std::max(d.max_items, P.lvl_item_ptr[q + 1] - P.lvl_item_ptr[q]);
+            CKL(1, launch_levels_df<T>(a, h->lookup, d, h->num_sms, st));
         }
         l = e;
     }
@@ -659,6 +690,35 @@ int setup_column_plan(glu_handle *h) {
         rb.runs = h->d_runs;
         CK(launch_run_build(rb, 1, 0, h->stream));
         CK(launch_run_build(rb, 2, 0, h->stream));
+    }
+    // the dataflow runs' tables, when some level runs in the pipelined mode
+    bool any_df = false;
+    for (int8_t md : P.level_mode) any_df = any_df || md == 2;
+    if (any_df) {
+        dataflow_tables(P);
+        const size_t nlev1 = P.level_ptr.size();
+        Carve c2;
+        const size_t o_tc = c2.take<int32_t>(P.task_col.size()), o_tb = c2.take<int32_t>(P.task_before.size()),
+                     o_lt = c2.take<int32_t>(nlev1), o_ln = c2.take<int32_t>(nlev1),
+                     o_ip = c2.take<int32_t>(nlev1 + 1), o_lo = c2.take<int32_t>((size_t)P.n),
+                     o_cn = c2.take<int32_t>((size_t)P.n + 2 * nlev1), o_w = c2.take<unsigned>(2);
+        h->dfarena_bytes = c2.off + 256;
+        CK(cudaMalloc(&h->dfarena, h->dfarena_bytes));
+        char *D = h->dfarena;
+        h->d_task_col = at<int32_t>(D, o_tc);
+        h->d_task_before = at<int32_t>(D, o_tb);
+        h->d_lvl_total = at<int32_t>(D, o_lt);
+        h->d_lvl_ntasks = at<int32_t>(D, o_ln);
+        h->d_item_ptr = at<int32_t>(D, o_ip);
+        h->d_level_of = at<int32_t>(D, o_lo);
+        h->d_dfcnt = at<int32_t>(D, o_cn);
+        h->d_dfword = at<unsigned>(D, o_w);
+        CK(upload(h->d_task_col, P.task_col));
+        CK(upload(h->d_task_before, P.task_before));
+        CK(upload(h->d_lvl_total, P.lvl_total));
+        CK(upload(h->d_lvl_ntasks, P.lvl_ntasks));
+        CK(upload(h->d_item_ptr, P.lvl_item_ptr));
+        CK(upload(h->d_level_of, P.level_of));
     }
     h->col_ready = true;
     return GLU_OK;
@@ -1302,7 +1362,7 @@ int glu_get_stats(const glu_handle *h, glu_stats *s) {
     s->solve_levels_fwd = (int32_t)P.fwd_ptr.size() - 1;
     s->solve_levels_bwd = (int32_t)P.bwd_ptr.size() - 1;
     s->max_level_width = P.max_level_width;
-    s->device_bytes = (int64_t)(h->arena_bytes + h->carena_bytes + h->map_total + h->bmap_total +
+    s->device_bytes = (int64_t)(h->arena_bytes + h->carena_bytes + h->map_total + h->bmap_total + h->dfarena_bytes +
                                 4 * h->work_elems * sizeof(double) +
                                 (int64_t)std::max(P.fwd_chunks.size(), P.bwd_chunks.size()) * h->work_nrhs *
                                     sizeof(double));
@@ -1355,6 +1415,7 @@ void glu_destroy(glu_handle *h) {
     cudaFree(h->arena);
     cudaFree(h->d_runs);
     cudaFree(h->d_map);
+    cudaFree(h->dfarena);
     cudaFree(h->bmap);
     cudaFree(h->carena);
     cudaFree(h->d_work);

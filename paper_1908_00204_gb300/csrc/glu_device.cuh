@@ -168,12 +168,30 @@ struct DFSolveArgs {
 // launchers (kernels_factor.cu)
 template <typename T>
 cudaError_t launch_gather(T *lu, const double *aval, const int32_t *gsrc, int64_t nnz, cudaStream_t s);
+// A dataflow run of levels [l0, l1) (see k_levels_df): the per-level work
+// ranges and item prefix (global level indices), the per-task and per-level
+// tables of dataflow_tables, and the counters (zeroed before the launch).
+struct DFFactorArgs {
+    const LevelRange *ranges;     // nlevels + 1
+    const int32_t *item_ptr;      // nlevels + 2
+    int32_t l0, l1;
+    const int32_t *task_col, *task_before, *lvl_total, *lvl_ntasks, *level_of;
+    int32_t *cdone;               // per column: tasks of the run done that target it
+    int32_t *ldone;               // per level: tasks of the run done that target its columns
+    int32_t *tdone;               // per level: its tasks done
+    unsigned *ticket;
+    unsigned *abort;
+    unsigned long long *err;
+    long long spin_limit_cycles;
+    int32_t fault_col;            // test hook: tasks targeting this column never publish (-1: none)
+    int32_t max_items;            // the most work items of one level of the run (sizes the grid)
+};
+
 // lookup: 2 or 4 = position map of that many bytes per update, 0 = run table
 template <typename T>
 cudaError_t launch_level(const FactorArgs<T> &a, int lookup, const LevelRange &r, int num_sms, cudaStream_t s);
 template <typename T>
-cudaError_t launch_levels_persistent(const FactorArgs<T> &a, int lookup, const LevelRange *ranges, int32_t nlev,
-                                     const GridBarrier &bar, int num_sms, cudaStream_t s);
+cudaError_t launch_levels_df(const FactorArgs<T> &a, int lookup, const DFFactorArgs &d, int num_sms, cudaStream_t s);
 // One level of the supernodal factorization: diagonal blocks d0..d1-1,
 // panel items i0..i1-1, update tasks k0..k1-1 (kernels_blocks.cu); *launched
 // counts the kernels launched.

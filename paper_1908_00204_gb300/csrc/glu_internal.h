@@ -193,6 +193,13 @@ struct HostPlan {
     std::vector<NormItem> norms;
     std::vector<int32_t> lvl_norm_ptr;  // nlevels + 2: level l's kernel runs [l, l+1); [L, L+1) is the final pass
     std::vector<int8_t> level_mode;
+    // dataflow runs (consecutive mode-2 levels in one launch, see
+    // dataflow_tables): per task its target column and how many tasks of
+    // earlier levels of its run target that column; per level (nlevels + 1)
+    // the run's tasks that target the level's columns, the level's own tasks,
+    // and the global prefix of work items (warp items) per level
+    std::vector<int32_t> task_col, task_before;
+    std::vector<int32_t> lvl_total, lvl_ntasks, lvl_item_ptr;
     // solve schedule (row views of L and U, levels)
     std::vector<int64_t> lrow_ptr, urow_ptr;
     std::vector<int32_t> lrow_col, urow_col;
@@ -264,6 +271,10 @@ int static_pivot(int32_t n, const int32_t *colptr, const int32_t *rowidx, const 
 int apply_static_pivot(int32_t n, const int32_t *colptr, const int32_t *rowidx, const double *values,
                        const int32_t *row_perm, const double *row_scale, const double *col_scale,
                        int32_t *out_rowidx, double *out_values);
+
+// The tables of the dataflow level runs (task_col, task_before, lvl_total,
+// lvl_ntasks, lvl_item_ptr) for the column-level schedule.
+void dataflow_tables(HostPlan &P);
 
 // The column-level update schedule (pairs, segments, tasks, normalization
 // items) if analyze_host skipped it.  GLU_OK, or GLU_ERR_TOO_LARGE when a

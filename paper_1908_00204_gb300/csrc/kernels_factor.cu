@@ -41,6 +41,16 @@ __device__ __forceinline__ void raise_err(unsigned long long *err, int32_t col, 
     atomicMin(err, ((unsigned long long)(uint32_t)col << 8) | code);
 }
 
+// A factor value.  CG: from L2 (ld.global.cg), for the dataflow kernel, where
+// other SMs write the values during the same launch and a line this SM's L1
+// holds may be stale; otherwise an ordinary load (the level launches see
+// every earlier write at the kernel boundary).
+template <bool CG, typename T>
+__device__ __forceinline__ T ldv(const T *p) {
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
+
 // ----------------------------------------------------------------- gather
 template <typename T>
 __global__ void k_gather(T *__restrict__ lu, const double *__restrict__ aval,
@@ -57,10 +67,10 @@ __global__ void k_gather(T *__restrict__ lu, const double *__restrict__ aval,
 // L(:,j) /= A_s(j,j) as products with one reciprocal per item: the FP64
 // pipe of this part is narrow (a division is a dozen dependent operations
 // on it), and x * (1/d) is within one rounding of x / d.
-template <typename T>
+template <typename T, bool CG = false>
 __device__ __forceinline__ void norm_item(const FactorArgs<T> &a, const NormItem it, int lane) {
     const int64_t dj = a.diag_pos[it.col];
-    const T rd = (T)1 / a.lu[dj];
+    const T rd = (T)1 / ldv<CG>(a.lu + dj);
     T *L = a.lu + dj + 1;
     // all loads of the item first (at most 8 per lane), then the products
     constexpr int NU = 8;
@@ -68,7 +78,7 @@ __device__ __forceinline__ void norm_item(const FactorArgs<T> &a, const NormItem
         T v[NU];
 #pragma unroll
         for (int u = 0; u < NU; u++)
-            if (tb + 32 * u < it.t1 && tb + 32 * u + lane < it.t1) v[u] = L[tb + 32 * u + lane];
+            if (tb + 32 * u < it.t1 && tb + 32 * u + lane < it.t1) v[u] = ldv<CG>(L + tb + 32 * u + lane);
 #pragma unroll
         for (int u = 0; u < NU; u++)
             if (tb + 32 * u < it.t1) {              // the same for the whole warp
@@ -95,7 +105,7 @@ struct SegMeta {
 template <typename M>
 constexpr bool is_runs() { return std::is_same<M, Run>::value; }
 
-template <typename T, typename M>
+template <typename T, typename M, bool CG = false>
 __device__ __forceinline__ void load_meta(const FactorArgs<T> &a, int32_t s, SegMeta<T> &m) {
     const int4 *r = reinterpret_cast<const int4 *>(a.segs + s);
     const int4 v0 = r[0], v1 = r[1];
@@ -112,7 +122,7 @@ __device__ __forceinline__ void load_meta(const FactorArgs<T> &a, int32_t s, Seg
     m.t0 = v1.z;
     m.t1 = v1.w;
     m.lstart = dj + 1;
-    m.f = a.lu[m.pos] / a.lu[dj];
+    m.f = ldv<CG>(a.lu + m.pos) / ldv<CG>(a.lu + dj);
 }
 
 template <typename T>
@@ -189,7 +199,7 @@ constexpr int LANE_UNROLL = GLU_LANE_UNROLL;
 // the runs starting inside the group set one bit each at their first row (an
 // OR-reduction); a lane's run is the first one's index plus the bits at or
 // below its row.  The window moves on when a group could reach past it.
-template <typename T>
+template <typename T, bool CG = false>
 __device__ __forceinline__ void row_segment_runs(T *__restrict__ lu, const Run *__restrict__ runs,
                                                  const SegMeta<T> &m, int lane) {
     const T *__restrict__ L = lu + m.lstart;
@@ -203,7 +213,7 @@ __device__ __forceinline__ void row_segment_runs(T *__restrict__ lu, const Run *
 #pragma unroll
         for (int u = 0; u < ROW_UNROLL; u++) {
             const int32_t t = tb + 32 * u + lane;
-            if (t < m.t1) lv[u] = L[t];
+            if (t < m.t1) lv[u] = ldv<CG>(L + t);
         }
         if (wb + 32 >= rend) {
             // the window holds every remaining run: the groups are independent
@@ -252,7 +262,7 @@ __device__ __forceinline__ void row_segment_runs(T *__restrict__ lu, const Run *
 }
 
 // The same with the position map: the rows' offsets are loaded with L(:,j).
-template <typename T, typename M>
+template <typename T, typename M, bool CG = false>
 __device__ __forceinline__ void row_segment_map(T *__restrict__ lu, const M *__restrict__ map, const SegMeta<T> &m,
                                                 int lane) {
     const M *__restrict__ mp = map + m.rb;
@@ -266,7 +276,7 @@ __device__ __forceinline__ void row_segment_map(T *__restrict__ lu, const M *__r
             const int32_t t = tb + 32 * u + lane;
             if (t < m.t1) {
                 off[u] = mp[t];
-                lv[u] = L[t];
+                lv[u] = ldv<CG>(L + t);
             }
         }
         // a group of 32 rows past the end is skipped by the whole warp
@@ -278,10 +288,10 @@ __device__ __forceinline__ void row_segment_map(T *__restrict__ lu, const M *__r
     }
 }
 
-template <typename T, typename M>
+template <typename T, typename M, bool CG = false>
 __device__ __forceinline__ void row_segment(const FactorArgs<T> &a, const SegMeta<T> &m, int lane) {
-    if constexpr (is_runs<M>()) row_segment_runs<T>(a.lu, a.runs, m, lane);
-    else row_segment_map<T, M>(a.lu, static_cast<const M *>(a.map), m, lane);
+    if constexpr (is_runs<M>()) row_segment_runs<T, CG>(a.lu, a.runs, m, lane);
+    else row_segment_map<T, M, CG>(a.lu, static_cast<const M *>(a.map), m, lane);
 }
 
 // Offsets of the rows of one segment for a single lane, in ascending order:
@@ -307,7 +317,7 @@ struct LaneRows<Run> {
 // after the other as row_task would, but with the metadata of up to 32
 // segments -- spanning several tasks -- fetched at once, one per lane, so the
 // multiplier divisions of a warp's many short tasks share instructions.
-template <typename T, typename M>
+template <typename T, typename M, bool CG = false>
 __device__ __forceinline__ void row_tasks(const FactorArgs<T> &a, int64_t tq0, int64_t stride, int64_t cnt,
                                           int lane) {
     int64_t i = 0;      // next task of the list
@@ -342,10 +352,10 @@ __device__ __forceinline__ void row_tasks(const FactorArgs<T> &a, int64_t tq0, i
         const int32_t t_ns = __shfl_sync(0xffffffffu, ns, t);
         const int32_t t_sb = __shfl_sync(0xffffffffu, sb, t);
         SegMeta<T> mine;
-        if (lane < take) load_meta<T, M>(a, t_sb + (lane - (t_incl - t_ns)), mine);
+        if (lane < take) load_meta<T, M, CG>(a, t_sb + (lane - (t_incl - t_ns)), mine);
         for (int q = 0; q < take; q++) {
             const SegMeta<T> m = shfl_meta<T>(mine, q);
-            row_segment<T, M>(a, m, lane);
+            row_segment<T, M, CG>(a, m, lane);
             __syncwarp();
         }
         if (tot <= 32) {
@@ -366,7 +376,7 @@ __device__ __forceinline__ void row_tasks(const FactorArgs<T> &a, int64_t tq0, i
 // of a 32 x 33 shared-memory tile (slot = target position - base); then lane
 // s sums column s over the lanes that had segments, in order, and applies
 // it.  The next segment's metadata is fetched before the current one's rows.
-template <typename T, typename M>
+template <typename T, typename M, bool CG = false>
 __device__ __forceinline__ void src_task(const FactorArgs<T> &a, const Task &tk, int lane, T *__restrict__ acc) {
     T *__restrict__ row = acc + lane * (SRC_SLOTS + 1);
     const int nl = min(32, tk.seg_end - tk.seg_begin);   // lanes with segments
@@ -377,12 +387,12 @@ __device__ __forceinline__ void src_task(const FactorArgs<T> &a, const Task &tk,
     int32_t s = tk.seg_begin + lane;
     SegMeta<T> cur;
     bool have = s < tk.seg_end;
-    if (have) load_meta<T, M>(a, s, cur);
+    if (have) load_meta<T, M, CG>(a, s, cur);
     while (have) {
         SegMeta<T> nxt;
         const int32_t s2 = s + 32;
         const bool have2 = s2 < tk.seg_end;
-        if (have2) load_meta<T, M>(a, s2, nxt);
+        if (have2) load_meta<T, M, CG>(a, s2, nxt);
         const T *__restrict__ L = a.lu + cur.lstart;
         const int32_t rel = (int32_t)(cur.pos + 1 - tk.base);
         LaneRows<M> wk;
@@ -392,7 +402,7 @@ __device__ __forceinline__ void src_task(const FactorArgs<T> &a, const Task &tk,
             T lv[GLU_SRC_UNROLL];
 #pragma unroll
             for (int u = 0; u < GLU_SRC_UNROLL; u++)
-                if (tb + u < cur.t1) lv[u] = L[tb + u];
+                if (tb + u < cur.t1) lv[u] = ldv<CG>(L + tb + u);
 #pragma unroll
             for (int u = 0; u < GLU_SRC_UNROLL; u++)
                 if (tb + u < cur.t1) off[u] = wk.offset(a.runs, tb + u);
@@ -411,20 +421,20 @@ __device__ __forceinline__ void src_task(const FactorArgs<T> &a, const Task &tk,
     if (lane < tk.nslots) {
         T sum = (T)0;
         for (int l = 0; l < nl; l++) sum += acc[l * (SRC_SLOTS + 1) + lane];
-        a.lu[tk.base + lane] -= sum;
+        a.lu[tk.base + lane] = ldv<CG>(a.lu + tk.base + lane) - sum;
     }
     __syncwarp();
 }
 
 // KIND_LANE: one lane applies the task's segments in order, rows batched;
 // the next segment's metadata is fetched before the current one's rows.
-template <typename T, typename M>
+template <typename T, typename M, bool CG = false>
 __device__ __forceinline__ void lane_task(const FactorArgs<T> &a, const Task &tk) {
     SegMeta<T> nxt;
-    load_meta<T, M>(a, tk.seg_begin, nxt);
+    load_meta<T, M, CG>(a, tk.seg_begin, nxt);
     for (int32_t s = tk.seg_begin; s < tk.seg_end; s++) {
         const SegMeta<T> m = nxt;
-        if (s + 1 < tk.seg_end) load_meta<T, M>(a, s + 1, nxt);
+        if (s + 1 < tk.seg_end) load_meta<T, M, CG>(a, s + 1, nxt);
         const T *__restrict__ L = a.lu + m.lstart;
         T *tgt = a.lu + m.pos + 1;
         LaneRows<M> wk;
@@ -434,7 +444,7 @@ __device__ __forceinline__ void lane_task(const FactorArgs<T> &a, const Task &tk
             T lv[LANE_UNROLL];
 #pragma unroll
             for (int u = 0; u < LANE_UNROLL; u++)
-                if (tb + u < m.t1) lv[u] = L[tb + u];
+                if (tb + u < m.t1) lv[u] = ldv<CG>(L + tb + u);
 #pragma unroll
             for (int u = 0; u < LANE_UNROLL; u++)
                 if (tb + u < m.t1) off[u] = wk.offset(a.runs, tb + u);
@@ -549,28 +559,154 @@ k_level(const FactorArgs<T> a, LevelRange r) {
     asm volatile("griddepcontrol.launch_dependents;");
 }
 
-// Consecutive levels in one launch (the pipelined tail mode): all blocks are
-// resident (cooperative launch) and meet at a grid barrier between levels, a
-// monotone arrival counter.  Every wait is bounded: past the limit the block records GLU_ERR_TIMEOUT,
-// raises the abort word and returns; the other blocks see the abort word and
-// return too, so the launch always ends.
+// Consecutive levels in one launch (the pipelined mode, run by dataflow):
+// the run's work items -- each level's normalization items, KIND_SRC and
+// KIND_ROW tasks, groups of 32 KIND_LANE tasks, in level order -- are handed
+// out by an atomic ticket, and instead of a barrier between levels each item
+// waits for what it reads:
+//   * a task of level l: every task of the run that targets a column of
+//     level l done (its sources final), and the tasks of earlier levels of
+//     the run that target its own column done (U(j,k) final, and its
+//     additions after theirs: each target entry's additions keep the level
+//     order, so the results equal the level launches' bit for bit);
+//   * a normalization item of level l's columns (run in level l + 1): every
+//     task of level l done (they read the columns raw) and the columns final.
+// A finished task publishes with release semantics (fence, then the counter
+// additions); a waiter acquires.  A warp only waits on items of earlier
+// levels, handed out before its own, so the launch needs no co-residency.
+// Factor values are read through L2 (other SMs write them meanwhile).  Every
+// wait is bounded: past the limit the kernel records GLU_ERR_TIMEOUT and
+// raises the abort word, which ends every other wait; the launch always ends.
+__device__ __forceinline__ int ld_acquire_i32(const int32_t *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Lane 0 waits until *p >= target (or gives up); the warp agrees on the
+// outcome and acquires.
+__device__ __forceinline__ bool wait_ge(const int32_t *p, int32_t target, const DFFactorArgs &d, int lane) {
+    int ok = 1;
+    if (lane == 0 && target > 0 && ld_acquire_i32(p) < target) {
+        const long long t0 = clock64();
+        int spins = 0;
+        unsigned nap = 32;             // polls back off: many warps may wait on one counter
+        while (true) {
+            __nanosleep(nap);
+            nap = nap < 1024 ? nap * 2 : 1024;
+            if (ld_acquire_i32(p) >= target) break;
+            if ((++spins & 63) == 0) {
+                if (*(volatile const unsigned *)d.abort) {
+                    ok = 0;
+                    break;
+                }
+                if (clock64() - t0 > d.spin_limit_cycles) {
+                    atomicOr(d.abort, 1u);
+                    atomicMin(d.err, (0xffffffull << 8) | DEVERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    return ok != 0;
+}
+
+// One lane's wait (KIND_LANE tasks): the same, without the warp.
+__device__ __forceinline__ bool wait_ge_lane(const int32_t *p, int32_t target, const DFFactorArgs &d) {
+    if (target <= 0 || ld_acquire_i32(p) >= target) return true;
+    const long long t0 = clock64();
+    int spins = 0;
+    unsigned nap = 32;
+    while (true) {
+        __nanosleep(nap);
+        nap = nap < 1024 ? nap * 2 : 1024;
+        if (ld_acquire_i32(p) >= target) return true;
+        if ((++spins & 63) == 0) {
+            if (*(volatile const unsigned *)d.abort) return false;
+            if (clock64() - t0 > d.spin_limit_cycles) {
+                atomicOr(d.abort, 1u);
+                atomicMin(d.err, (0xffffffull << 8) | DEVERR_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+// A finished task: its additions, then its counters.
+__device__ __forceinline__ void publish_task(const DFFactorArgs &d, int32_t task) {
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    const int32_t k = d.task_col[task];
+    if (k == d.fault_col) return;          // test hook: this column's tasks never publish
+    atomicAdd(d.cdone + k, 1);
+    atomicAdd(d.ldone + d.level_of[k], 1);
+}
+
 template <typename T, typename M>
-__global__ void __launch_bounds__(LEVEL_WARPS * 32, 4)
-k_levels_persistent(const FactorArgs<T> a, const LevelRange *__restrict__ ranges, int32_t nlev,
-                    GridBarrier bar) {
+__global__ void __launch_bounds__(LEVEL_WARPS * 32, 3)
+k_levels_df(const FactorArgs<T> a, const DFFactorArgs d) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     T *acc = reinterpret_cast<T *>(smem_raw) + wib * (32 * (SRC_SLOTS + 1));
-    const int64_t warp = (int64_t)blockIdx.x * LEVEL_WARPS + wib;
-    const int64_t nw = (int64_t)gridDim.x * LEVEL_WARPS;
-    __shared__ int s_stop;
-    for (int32_t li = 0; li < nlev; li++) {
-        const LevelRange r = ranges[li];
-        run_level<T, M>(a, r, lane, warp, nw, acc);
-        if (li + 1 == nlev) break;
-        prefetch_level<T, M>(a, ranges[li + 1], lane, warp, nw);
-        if (!grid_sync(bar, (unsigned)(li + 1) * gridDim.x, &s_stop)) return;
+    const int32_t i0 = d.item_ptr[d.l0];
+    const int32_t nitems = d.item_ptr[d.l1] - i0;
+    while (true) {
+        int32_t t = 0;
+        if (lane == 0) t = (int32_t)atomicAdd(d.ticket, 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= nitems) break;
+        const int32_t g = i0 + t;
+        int32_t lo = d.l0, hi = d.l1;      // the item's level: item_ptr[lo] <= g < item_ptr[lo + 1]
+        while (hi - lo > 1) {
+            const int32_t mid = (lo + hi) >> 1;
+            if (d.item_ptr[mid] <= g) lo = mid;
+            else hi = mid;
+        }
+        const int32_t l = lo;
+        const LevelRange r = d.ranges[l];
+        const int64_t nn = r.n_end - r.n_begin;
+        const int64_t nsrc = r.row_begin - r.t_begin;
+        const int64_t nrow = r.lane_begin - r.row_begin;
+        int64_t k = g - d.item_ptr[l];
+        if (k < nn) {
+            bool ok = true;
+            if (l - 1 >= d.l0)
+                ok = wait_ge(d.tdone + (l - 1), d.lvl_ntasks[l - 1], d, lane) &&
+                     wait_ge(d.ldone + (l - 1), d.lvl_total[l - 1], d, lane);
+            if (ok) norm_item<T, true>(a, a.norms[r.n_begin + k], lane);
+            continue;
+        }
+        k -= nn;
+        if (k < nsrc + nrow) {
+            const int32_t task = (int32_t)(r.t_begin + k);
+            const bool ok = wait_ge(d.ldone + l, d.lvl_total[l], d, lane) &&
+                            wait_ge(d.cdone + d.task_col[task], d.task_before[task], d, lane);
+            if (ok) {
+                if (k < nsrc) src_task<T, M, true>(a, a.tasks[task], lane, acc);
+                else row_tasks<T, M, true>(a, task, 1, 1, lane);
+            }
+            __syncwarp();
+            if (lane == 0) {
+                publish_task(d, task);
+                atomicAdd(d.tdone + l, 1);
+            }
+            continue;
+        }
+        // a group of up to 32 KIND_LANE tasks, one per lane
+        const int64_t q = r.lane_begin + (k - nsrc - nrow) * 32 + lane;
+        const bool mine = q < r.t_end;
+        if (mine) {
+            const bool ok = wait_ge_lane(d.ldone + l, d.lvl_total[l], d) &&
+                            wait_ge_lane(d.cdone + d.task_col[q], d.task_before[q], d);
+            asm volatile("fence.acq_rel.gpu;" ::: "memory");
+            if (ok) lane_task<T, M, true>(a, a.tasks[q]);
+            publish_task(d, (int32_t)q);
+        }
+        const int cnt = __popc(__ballot_sync(0xffffffffu, mine));
+        if (lane == 0) atomicAdd(d.tdone + l, cnt);
     }
 }
 
@@ -752,33 +888,27 @@ cudaError_t launch_level(const FactorArgs<T> &a, int lookup, const LevelRange &r
 }
 
 template <typename T>
-cudaError_t launch_levels_persistent(const FactorArgs<T> &a, int lookup, const LevelRange *ranges, int32_t nlev,
-                                     const GridBarrier &bar, int num_sms, cudaStream_t s) {
-    if (nlev <= 0) return cudaSuccess;
+cudaError_t launch_levels_df(const FactorArgs<T> &a, int lookup, const DFFactorArgs &d, int num_sms, cudaStream_t s) {
+    if (d.l1 <= d.l0) return cudaSuccess;
     const size_t smem = sizeof(T) * LEVEL_WARPS * 32 * (SRC_SLOTS + 1);
-    const void *fn = lookup == 2 ? (const void *)k_levels_persistent<T, uint16_t>
-                   : lookup == 4 ? (const void *)k_levels_persistent<T, uint32_t>
-                                 : (const void *)k_levels_persistent<T, Run>;
+    const void *fn = lookup == 2 ? (const void *)k_levels_df<T, uint16_t>
+                   : lookup == 4 ? (const void *)k_levels_df<T, uint32_t>
+                                 : (const void *)k_levels_df<T, Run>;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, LEVEL_WARPS * 32, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorLaunchOutOfResources;
-    e = cudaMemsetAsync(bar.count, 0, sizeof(unsigned), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(bar.abort, 0, sizeof(unsigned), s);
-    if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(num_sms * per_sm));
-    cfg.blockDim = dim3(LEVEL_WARPS * 32);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    if (lookup == 2) return cudaLaunchKernelEx(&cfg, k_levels_persistent<T, uint16_t>, a, ranges, nlev, bar);
-    if (lookup == 4) return cudaLaunchKernelEx(&cfg, k_levels_persistent<T, uint32_t>, a, ranges, nlev, bar);
-    return cudaLaunchKernelEx(&cfg, k_levels_persistent<T, Run>, a, ranges, nlev, bar);
+    // no more warps than the run's widest level has items (twice, so the next
+    // level's items are fetched while one runs): idle warps would only poll
+    unsigned blocks = (unsigned)(num_sms * per_sm);
+    if (d.max_items > 0) {
+        const int64_t want = (2 * (int64_t)d.max_items + LEVEL_WARPS - 1) / LEVEL_WARPS;
+        if (want < (int64_t)blocks) blocks = (unsigned)(want < 1 ? 1 : want);
+    }
+    if (lookup == 2) k_levels_df<T, uint16_t><<<blocks, LEVEL_WARPS * 32, smem, s>>>(a, d);
+    else if (lookup == 4) k_levels_df<T, uint32_t><<<blocks, LEVEL_WARPS * 32, smem, s>>>(a, d);
+    else k_levels_df<T, Run><<<blocks, LEVEL_WARPS * 32, smem, s>>>(a, d);
+    return cudaGetLastError();
 }
 
 template <typename T>
@@ -816,10 +946,9 @@ template cudaError_t launch_gather<double>(double *, const double *, const int32
 template cudaError_t launch_gather<float>(float *, const double *, const int32_t *, int64_t, cudaStream_t);
 template cudaError_t launch_level<double>(const FactorArgs<double> &, int, const LevelRange &, int, cudaStream_t);
 template cudaError_t launch_level<float>(const FactorArgs<float> &, int, const LevelRange &, int, cudaStream_t);
-template cudaError_t launch_levels_persistent<double>(const FactorArgs<double> &, int, const LevelRange *, int32_t,
-                                                     const GridBarrier &, int, cudaStream_t);
-template cudaError_t launch_levels_persistent<float>(const FactorArgs<float> &, int, const LevelRange *, int32_t,
-                                                    const GridBarrier &, int, cudaStream_t);
+template cudaError_t launch_levels_df<double>(const FactorArgs<double> &, int, const DFFactorArgs &, int,
+                                             cudaStream_t);
+template cudaError_t launch_levels_df<float>(const FactorArgs<float> &, int, const DFFactorArgs &, int, cudaStream_t);
 template cudaError_t launch_pivot_check<double>(const double *, const int64_t *, int32_t, unsigned long long *,
                                                 cudaStream_t);
 template cudaError_t launch_pivot_check<float>(const float *, const int64_t *, int32_t, unsigned long long *,

@@ -182,3 +182,44 @@ def test_batched_fp64_run_table_matches_oracle(glu):
     for s in (0, 21, B - 1):
         assert backward_error(m.n, m.colptr, m.rowidx, V[s], rhs[s], x[s]) <= BERR_TOL
     glu.glu_destroy(h)
+
+
+@pytest.mark.parametrize("name", WORKLOADS)
+@pytest.mark.parametrize("opts", [dict(tail_threshold=16), dict(mode_force=2)])
+def test_dataflow_levels_equal_level_launches(glu, name, opts):
+    """The pipelined levels run as one dataflow launch per run of narrow levels
+    (mode_force=2: every level in one launch).  Every target entry takes its
+    additions in the same order as with one launch per level, so the factors
+    are bitwise equal."""
+    m, v, b, f, xr = reference(name)
+    base = glu.glu_analyze(m.n, m.colptr, m.rowidx, m.perm)
+    glu.glu_factor(base, torch.from_numpy(v).cuda())
+    ref = glu.glu_get_factors(base)
+    glu.glu_destroy(base)
+    h = glu.glu_analyze(m.n, m.colptr, m.rowidx, m.perm, glu.default_options(**opts))
+    assert glu.glu_get_stats(h)["levels_by_mode"][2] > 0
+    for _ in range(2):
+        glu.glu_factor(h, torch.from_numpy(v).cuda())
+        assert np.array_equal(glu.glu_get_factors(h), ref)
+    glu.glu_destroy(h)
+
+
+def test_dataflow_factor_wait_timeout_reported_and_context_survives(glu):
+    """A dataflow wait that can never be met (the test hook: the tasks that
+    update one column never publish) ends the launch with GLU_ERR_TIMEOUT
+    after the configured bound; a fresh handle then factors correctly."""
+    m = synth.make("mesh100x200_nets64", 1)
+    v = m.values(5)
+    bad = glu.glu_analyze(m.n, m.colptr, m.rowidx, m.perm,
+                          glu.default_options(mode_force=2, factor_tail=0, fault_row=m.n - 1,
+                                              spin_limit_us=100000))
+    with pytest.raises(glu.GluError) as e:
+        glu.glu_factor(bad, v)
+    assert e.value.code == glu.glu.GLU_ERR_TIMEOUT
+    glu.glu_destroy(bad)
+    good = glu.glu_analyze(m.n, m.colptr, m.rowidx, m.perm, glu.default_options(mode_force=2, factor_tail=0))
+    glu.glu_factor(good, v)
+    f = oracle.Factorization(m.n, m.colptr, m.rowidx, m.perm, v)
+    bad_entries, _ = factor_mismatches(f.lu_colptr, f.lu_rowidx, glu.glu_get_factors(good), f.lu_val)
+    assert bad_entries.size == 0
+    glu.glu_destroy(good)
