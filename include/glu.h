@@ -42,7 +42,7 @@
  * Environment variables (read by glu_analyze unless noted; none is needed):
  *   GLU_ANALYZE_THREADS  host threads of the analysis (1..64; default: the
  *                        machine's, at most 16); the results do not depend on it.
- *   GLU_SRC_MIN, GLU_LANE_MAX, GLU_LANE_SEGS
+ *   GLU_SRC_MIN, GLU_LANE_MAX, GLU_LANE_SEGS (unless set in glu_options)
  *                        task-size thresholds of the factorization schedule:
  *                        the source count from which a target column is split
  *                        into 32-position chunk tasks (default 5), and the
@@ -100,7 +100,8 @@ typedef struct glu_options {
                                  the items it reads (per-column counters, bounded waits)
                                  instead of a barrier per level (the paper's stream-mode
                                  threshold is 16, Section III-B.2 item 3); 0: off */
-    int32_t piece_updates;    /* target-column updates per warp task (work split size) */
+    int32_t piece_updates;    /* target-column updates per warp task (work split size;
+                                 default 1024) */
     int32_t wide_threshold;   /* levels with more columns than this run warp-per-column */
     int32_t use_graph;        /* 1: capture the level sequence in a CUDA graph */
     int32_t verbose;          /* 1: print analysis statistics to stderr */
@@ -138,6 +139,14 @@ typedef struct glu_options {
                                  circuit matrices; a warp finds its rows' runs by ballots
                                  and shuffles); 0 (default): the map when it takes at most
                                  GLU_MAP_BUDGET_BYTES, else the run table */
+    int32_t src_min;          /* task shapes of the level schedule (0: default, or the
+                                 environment variable of the same name):
+                                 a target column hit by at least this many sources of
+                                 one level is cut into 32-position chunk tasks
+                                 (KIND_SRC; GLU_SRC_MIN, default 5) */
+    int32_t lane_max;         /* tasks of at most this many updates ... (GLU_LANE_MAX, 32) */
+    int32_t lane_segs;        /* ... and this many segments run on one lane (KIND_LANE;
+                                 GLU_LANE_SEGS, 2) */
 } glu_options;
 
 /* Device memory the position map may take before row_lookup 0 switches to

@@ -530,7 +530,8 @@ int schedule(HostPlan &P, const glu_options &opt, int num_sms) {
         return e ? std::max(lo, std::min(hi, (int64_t)std::atoll(e))) : dflt;
     };
     // groups with at least this many sources use KIND_SRC chunk tasks
-    const int32_t src_min = (int32_t)env_int("GLU_SRC_MIN", 5, 2, 1 << 20);
+    const int32_t src_min = opt.src_min > 0 ? std::max<int32_t>(2, opt.src_min)
+                                            : (int32_t)env_int("GLU_SRC_MIN", 5, 2, 1 << 20);
     auto lstart = [&](int32_t j) { return P.diag_pos[j] + 1; };
     auto lcount = [&](int32_t j) { return (int32_t)(P.lu_colptr[j + 1] - P.diag_pos[j] - 1); };
 
@@ -610,8 +611,9 @@ int schedule(HostPlan &P, const glu_options &opt, int num_sms) {
     // tasks up to this many updates (and lane_segs segments) run on one lane
     // (32 and 2 measured best on the 200k-unknown mesh: 22.5 ms per FP64
     // refactorization against 23.5 ms with 64 and 4, factors bitwise equal)
-    const int64_t lane_max = env_int("GLU_LANE_MAX", 32, 1, 1 << 20);
-    const int32_t lane_segs = (int32_t)env_int("GLU_LANE_SEGS", 2, 1, 64);
+    const int64_t lane_max = opt.lane_max > 0 ? opt.lane_max : env_int("GLU_LANE_MAX", 32, 1, 1 << 20);
+    const int32_t lane_segs = opt.lane_segs > 0 ? std::min<int32_t>(64, opt.lane_segs)
+                                                : (int32_t)env_int("GLU_LANE_SEGS", 2, 1, 64);
     P.level_mode.assign((size_t)nl, 0);
     (void)num_sms;
     // Levels are scheduled independently: contiguous ranges of levels run on

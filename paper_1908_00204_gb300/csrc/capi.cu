@@ -890,7 +890,7 @@ void glu_default_options(glu_options *o) {
     o->struct_size = (int32_t)sizeof(glu_options);
     o->mode_force = -1;
     o->tail_threshold = 0;
-    o->piece_updates = 2048;
+    o->piece_updates = 1024;
     o->wide_threshold = 256;
     o->use_graph = 1;
     o->verbose = 0;

@@ -38,7 +38,8 @@ class glu_options(C.Structure):
                 ("verbose", C.c_int32), ("host_only", C.c_int32), ("solve_mode", C.c_int32),
                 ("spin_limit_us", C.c_int32), ("fault_row", C.c_int32), ("solve_tail", C.c_int32),
                 ("factor_tail", C.c_int32), ("solve_blocks", C.c_int32),
-                ("factor_blocks", C.c_int32), ("row_lookup", C.c_int32)]
+                ("factor_blocks", C.c_int32), ("row_lookup", C.c_int32),
+                ("src_min", C.c_int32), ("lane_max", C.c_int32), ("lane_segs", C.c_int32)]
 
 
 class glu_stats(C.Structure):
