@@ -489,18 +489,11 @@ void dependencies(HostPlan &P) {
     }
 }
 
-// Longest-path levels; columns of a level ascending.
-void levelize(HostPlan &P) {
+// The levels' column lists from level_of: columns of a level ascending.
+void group_levels(HostPlan &P) {
     const int32_t n = P.n;
-    P.level_of.assign((size_t)n, 0);
     int32_t nl = n > 0 ? 1 : 0;
-    for (int32_t k = 0; k < n; k++) {
-        int32_t lv = 0;
-        for (int64_t p = P.dep_ptr[k]; p < P.dep_ptr[k + 1]; p++)
-            lv = std::max(lv, P.level_of[P.dep_idx[p]] + 1);
-        P.level_of[k] = lv;
-        nl = std::max(nl, lv + 1);
-    }
+    for (int32_t k = 0; k < n; k++) nl = std::max(nl, P.level_of[k] + 1);
     P.level_ptr.assign((size_t)nl + 1, 0);
     for (int32_t k = 0; k < n; k++) P.level_ptr[P.level_of[k] + 1]++;
     for (int32_t l = 0; l < nl; l++) P.level_ptr[l + 1] += P.level_ptr[l];
@@ -510,6 +503,19 @@ void levelize(HostPlan &P) {
     P.max_level_width = 0;
     for (int32_t l = 0; l < nl; l++)
         P.max_level_width = std::max(P.max_level_width, P.level_ptr[l + 1] - P.level_ptr[l]);
+}
+
+// Longest-path levels; columns of a level ascending.
+void levelize(HostPlan &P) {
+    const int32_t n = P.n;
+    P.level_of.assign((size_t)n, 0);
+    for (int32_t k = 0; k < n; k++) {
+        int32_t lv = 0;
+        for (int64_t p = P.dep_ptr[k]; p < P.dep_ptr[k + 1]; p++)
+            lv = std::max(lv, P.level_of[P.dep_idx[p]] + 1);
+        P.level_of[k] = lv;
+    }
+    group_levels(P);
 }
 
 // ---------------------------------------------------------------------------
@@ -1590,9 +1596,18 @@ int analyze_host(int32_t n, const int32_t *colptr, const int32_t *rowidx, const 
     }
     row_views(P);
     double t1 = now_ms();
-    dependencies(P);
-    double t2 = now_ms();
-    levelize(P);
+    double t2 = t1;
+    if (opt.gpu_analysis != 0 && !opt.host_only) {
+        // Algorithm 4 and the levels on the GPU (bit-identical results)
+        const int rc = gpu_dependencies_levels(P, opt.spin_limit_us, why);
+        if (rc != GLU_OK) return rc;
+        t2 = now_ms();
+        group_levels(P);
+    } else {
+        dependencies(P);
+        t2 = now_ms();
+        levelize(P);
+    }
     double t3 = now_ms();
     if (opt.verbose)
         std::fprintf(stderr, "glu_analyze: row views %.0f ms, deps %.0f ms (%lld), levels %.0f ms (%d)\n",

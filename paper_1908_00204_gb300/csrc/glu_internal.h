@@ -272,6 +272,10 @@ int apply_static_pivot(int32_t n, const int32_t *colptr, const int32_t *rowidx, 
                        const int32_t *row_perm, const double *row_scale, const double *col_scale,
                        int32_t *out_rowidx, double *out_values);
 
+// Algorithm 4 and the longest-path levels on the GPU (analyze_gpu.cu): fills
+// P.dep_ptr, P.dep_idx and P.level_of from the fill and the row views of L.
+int gpu_dependencies_levels(HostPlan &P, int32_t spin_limit_us, std::string &why);
+
 // The tables of the dataflow level runs (task_col, task_before, lvl_total,
 // lvl_ntasks, lvl_item_ptr) for the column-level schedule.
 void dataflow_tables(HostPlan &P);

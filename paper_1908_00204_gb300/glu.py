@@ -39,7 +39,8 @@ class glu_options(C.Structure):
                 ("spin_limit_us", C.c_int32), ("fault_row", C.c_int32), ("solve_tail", C.c_int32),
                 ("factor_tail", C.c_int32), ("solve_blocks", C.c_int32),
                 ("factor_blocks", C.c_int32), ("row_lookup", C.c_int32),
-                ("src_min", C.c_int32), ("lane_max", C.c_int32), ("lane_segs", C.c_int32)]
+                ("src_min", C.c_int32), ("lane_max", C.c_int32), ("lane_segs", C.c_int32),
+                ("gpu_analysis", C.c_int32)]
 
 
 class glu_stats(C.Structure):

@@ -45,6 +45,7 @@ OPTIONS = {
     "run_table_pipelined_narrow_32": dict(row_lookup=2, tail_threshold=32),
     "run_table_level_sweep_over_dense_block": dict(row_lookup=2, factor_tail=0),
     "run_table_mode0": dict(row_lookup=2, mode_force=0),
+    "gpu_dependency_analysis": dict(gpu_analysis=1),
 }
 
 
