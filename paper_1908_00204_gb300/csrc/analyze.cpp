@@ -1452,6 +1452,29 @@ void solve_levels(HostPlan &P, const glu_options &opt) {
     P.btail_t0 = (P.tail_t0 < n) ? std::max<int32_t>(P.tail_t0, n - TAIL_MAX_B) : n;
     build_df(P, SOLVE_CHUNK_B, P.btail_t0, opt.solve_blocks != 0 ? SN_MAX_B : 0, P.df_items_b, P.bdf_fchunks,
              P.bdf_bchunks, P.btail_cb, P.btail_ce, P.bdf_nfwd, P.bdf_snx_f, P.bdf_snx_b);
+    // batched: a dense diagonal block item becomes RSPLIT_B adjacent copies,
+    // copy q taking the right-hand sides r = q (mod RSPLIT_B), so that the
+    // block's column sweeps for different right-hand sides run side by side;
+    // the last copy to finish publishes the block's rows
+    std::vector<int32_t> ex;
+    ex.reserve(P.df_items_b.size());
+    int32_t nfwd = 0, nblk = 0;
+    for (size_t k = 0; k < P.df_items_b.size() / 8; k++) {
+        const int32_t *it = &P.df_items_b[8 * k];
+        const int32_t copies = (it[4] & 4) ? RSPLIT_B : 1;
+        for (int32_t q = 0; q < copies; q++) {
+            ex.insert(ex.end(), it, it + 8);
+            if (copies > 1) {
+                ex[ex.size() - 3] = q;
+                ex[ex.size() - 2] = nblk;
+            }
+        }
+        if (copies > 1) nblk++;
+        if ((int64_t)k < P.bdf_nfwd) nfwd += copies;
+    }
+    P.df_items_b.swap(ex);
+    P.bdf_nfwd = nfwd;
+    P.bdf_nblocks = nblk;
 }
 
 }  // namespace

@@ -370,6 +370,7 @@ int enqueue_df(glu_handle *h, const SolveArgs<T> &a, T *y, T *z, T *partial, int
     CK(cudaMemsetAsync(h->d_flags, 0, h->n_flags * sizeof(int32_t), st));
     CK(cudaMemsetAsync(h->d_serr, 0xff, sizeof(unsigned long long), st));
     DFSolveArgs d;
+    d.blk_done = nullptr;
     d.epoch = 1;
     d.fault_row = h->opt.fault_row;
     d.fchunks = h->d_df_fchunks;
@@ -1581,7 +1582,8 @@ int ensure_batch(glu_handle *h, int32_t S, bool f32) {
         CK(cudaMalloc(&h->d_vstage, na * S * sizeof(double)));
         CK(cudaMalloc(&h->d_aT, na * S * sizeof(double)));
         CK(cudaMalloc(&h->d_avb, na * S * sizeof(double)));
-        h->n_bflags = (2 * (int64_t)P.n + (int64_t)P.bdf_fchunks.size() + (int64_t)P.bdf_bchunks.size()) * G;
+        h->n_bflags =
+            (2 * (int64_t)P.n + (int64_t)P.bdf_fchunks.size() + (int64_t)P.bdf_bchunks.size() + P.bdf_nblocks) * G;
         CK(cudaMalloc(&h->d_bflags, std::max<int64_t>(h->n_bflags, 1) * sizeof(int32_t)));
         h->bcap = S;
     }
@@ -1703,6 +1705,7 @@ int enqueue_solve_b(glu_handle *h, const T *lu, const double *in, double *out, i
     d.bready = h->d_bflags + (int64_t)n * G;
     d.fchunk_ready = h->d_bflags + 2 * (int64_t)n * G;
     d.bchunk_ready = d.fchunk_ready + (int64_t)P.bdf_fchunks.size() * G;
+    d.blk_done = d.bchunk_ready + (int64_t)P.bdf_bchunks.size() * G;
     d.ticket = h->d_ticket;
     d.abort = h->d_abort;
     d.err = h->d_serr;
@@ -1710,7 +1713,7 @@ int enqueue_solve_b(glu_handle *h, const T *lu, const double *in, double *out, i
     d.fsnx = h->d_bsnx_f;
     d.bsnx = h->d_bsnx_b;
     TailArgs ta{P.btail_t0, h->d_btail_cb, h->d_btail_ce, d.bready, d.epoch};
-    CKL(4 + (P.btail_t0 < n), launch_solve_b<T>(sa, d, P.bdf_nfwd, h->d_lu_colptr, ta, in, out, y, z, h->d_perm, nrhs, S,
+    CKL(4 + (P.btail_t0 < n), launch_solve_b<T>(sa, d, P.bdf_nfwd, ta, in, out, y, z, h->d_perm, nrhs, S,
                                                 h->num_sms, st));
     return GLU_OK;
 }

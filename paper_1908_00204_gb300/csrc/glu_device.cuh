@@ -147,7 +147,9 @@ struct DFItem {
     int32_t ce;
     int32_t chunk;   // chunk item: index into the chunk list
     int32_t flags;
-    int32_t spare[3];
+    int32_t sub;     // batched block copy: right-hand sides r = sub (mod RSPLIT_B)
+    int32_t blk;     // batched block copy: the block's ordinal (completion counter)
+    int32_t spare;
 };
 
 struct DFSolveArgs {
@@ -163,6 +165,7 @@ struct DFSolveArgs {
     unsigned long long *err;
     long long spin_limit_cycles;
     const int32_t *fsnx, *bsnx;   // dense diagonal blocks: per row, its first outside chunk
+    int32_t *blk_done;            // batched: per (block, lane group), copies finished
 };
 
 // launchers (kernels_factor.cu)
@@ -267,7 +270,7 @@ cudaError_t launch_rhs_in(double *out, const double *in, int32_t n, int32_t nrhs
 cudaError_t launch_rhs_out(double *out, const double *in, int32_t n, int32_t nrhs, int32_t B, int32_t S,
                            cudaStream_t s);
 template <typename T>
-cudaError_t launch_solve_b(const SolveArgs<T> &sa, const DFSolveArgs &a, int32_t nfwd, const int64_t *lu_colptr,
+cudaError_t launch_solve_b(const SolveArgs<T> &sa, const DFSolveArgs &a, int32_t nfwd,
                            const TailArgs &ta, const double *in, double *out, T *y, T *z, const int32_t *perm,
                            int32_t nrhs, int32_t S, int num_sms, cudaStream_t s);
 cudaError_t launch_ir_b(int op, const int64_t *rp, const int32_t *ci, const double *av, const double *aT,

@@ -154,13 +154,14 @@ struct SolveChunk {
 constexpr int64_t SOLVE_CHUNK = GLU_SOLVE_CHUNK;   // single matrix: lanes over a row's entries (<= 128)
 constexpr int64_t SOLVE_CHUNK_B = 32;   // batched: lanes over the sets, entries in sequence
 constexpr int32_t TAIL_MIN = 32, TAIL_MAX = 1024;   // dense-tail solve size range
-constexpr int32_t TAIL_MAX_B = 768;                 // batched: tail rows x 32 sets in shared memory
+constexpr int32_t TAIL_MAX_B = 736;                 // batched: tail rows x 32 sets in shared memory
 constexpr int32_t FTAIL_MIN = 64, FTAIL_MAX = 3200;  // dense-tail factorization size range
 #ifndef GLU_SN_MAX
 #define GLU_SN_MAX 32
 #endif
 constexpr int32_t SN_MIN = 4, SN_MAX = GLU_SN_MAX;   // dense diagonal blocks of the dataflow solve
                                                      // (a multiple of 32, <= 128; 32 measured best)
+constexpr int32_t RSPLIT_B = 4;                     // batched: copies of a dense diagonal block item
 constexpr int32_t SN_MAX_B = 32;                     // the same in the batched solve (rows in registers)
 
 // Everything glu_analyze computes on the host.
@@ -227,7 +228,7 @@ struct HostPlan {
     std::vector<SolveChunk> bfwd_chunks, bbwd_chunks;
     std::vector<int32_t> bfwd_chunk_ptr, bbwd_chunk_ptr;
     std::vector<int32_t> df_items_b;
-    int32_t bdf_nfwd = 0, btail_t0 = 0;
+    int32_t bdf_nfwd = 0, btail_t0 = 0, bdf_nblocks = 0;
     std::vector<SolveChunk> bdf_fchunks, bdf_bchunks;
     std::vector<int32_t> btail_cb, btail_ce;
     std::vector<int32_t> bdf_snx_f, bdf_snx_b;

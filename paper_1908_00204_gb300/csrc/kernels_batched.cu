@@ -21,6 +21,8 @@ namespace glu {
 namespace {
 
 constexpr int BU = 4;   // rows per batch of independent loads
+constexpr int DU = 8;   // entries per batch of independent loads in the solve
+constexpr int PB = 16;  // chunk partial sums per batch of independent loads
 
 __device__ __forceinline__ void raise_err_b(unsigned long long *err, int32_t col, unsigned code) {
     atomicMin(err, ((unsigned long long)(uint32_t)col << 8) | code);
@@ -229,25 +231,218 @@ __device__ __forceinline__ void wait_b(const int32_t *flag, const DFSolveArgs &a
     }
 }
 
-// sum over entries p0..p1-1 of M[pos[p]] * v[col[p]] for this lane's set;
-// entries in sequence, BU independent loads in flight
-template <typename T>
-__device__ __forceinline__ T dot_b(const T *__restrict__ lu, const int64_t *__restrict__ pos,
-                                   const int32_t *__restrict__ col, const T *v, int64_t p0, int64_t p1, int32_t S) {
-    T acc = (T)0;
-    for (int64_t pb = p0; pb < p1; pb += BU) {
-        T lv[BU], yv[BU];
+__device__ __forceinline__ int atomic_add_acq_rel_b(int32_t *p, int v) {
+    int old;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ int ld_relaxed_b(const int32_t *p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Wait until flags[c * G] holds the epoch for every c in [c0, c1), the lanes
+// splitting the range: relaxed polls, four in flight per lane, a bounded
+// acquiring wait on any flag not yet set, then one acquire fence for the lot.
+__device__ __forceinline__ void wait_range_b(const int32_t *flags, int32_t G, int32_t c0, int32_t c1, int lane,
+                                             const DFSolveArgs &a) {
+    for (int32_t c = c0 + lane; c < c1; c += 128) {
+        int v[4];
 #pragma unroll
-        for (int u = 0; u < BU; u++)
-            if (pb + u < p1) {
-                lv[u] = lu[pos[pb + u] * S];
-                yv[u] = __ldcg(v + (int64_t)col[pb + u] * S);
+        for (int u = 0; u < 4; u++) v[u] = c + 32 * u < c1 ? ld_relaxed_b(flags + (int64_t)(c + 32 * u) * G) : a.epoch;
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+            if (v[u] != a.epoch) wait_b(flags + (int64_t)(c + 32 * u) * G, a);
+    }
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+
+// acc[r] += sum over entries p0..p1-1 of M[pos[p]] * v_r[col[p]] for this
+// lane's set and RB right-hand sides (v_r = src + r * rs), entries in
+// sequence.  The warp loads a window of 32 positions and columns once and
+// broadcasts them; each value of M is read once for all RB right-hand sides
+// and DU entries' loads are in flight together.
+template <typename T, int RB>
+__device__ __forceinline__ void dot_win_b(const T *__restrict__ lub, const int64_t *__restrict__ pos,
+                                          const int32_t *__restrict__ col, const T *src, int64_t rs, int64_t p0,
+                                          int64_t p1, int32_t S, int lane, T (&acc)[RB]) {
+    for (int64_t pw = p0; pw < p1; pw += 32) {
+        const int cnt = (int)((p1 - pw) < 32 ? (p1 - pw) : 32);
+        int64_t mq = 0;
+        int32_t mc = 0;
+        if (lane < cnt) {
+            mq = pos[pw + lane];
+            mc = col[pw + lane];
+        }
+        for (int u0 = 0; u0 < cnt; u0 += DU) {
+            T lv[DU], yv[DU][RB];
+#pragma unroll
+            for (int u = 0; u < DU; u++) {
+                const int64_t q = __shfl_sync(0xffffffffu, mq, u0 + u);
+                const int32_t c = __shfl_sync(0xffffffffu, mc, u0 + u);
+                lv[u] = (T)0;
+#pragma unroll
+                for (int r = 0; r < RB; r++) yv[u][r] = (T)0;
+                if (u0 + u < cnt) {
+                    lv[u] = lub[q * S];
+#pragma unroll
+                    for (int r = 0; r < RB; r++) yv[u][r] = __ldcg(src + r * rs + (int64_t)c * S);
+                }
             }
 #pragma unroll
-        for (int u = 0; u < BU; u++)
-            if (pb + u < p1) acc += lv[u] * yv[u];
+            for (int u = 0; u < DU; u++)
+                if (u0 + u < cnt) {
+#pragma unroll
+                    for (int r = 0; r < RB; r++) acc[r] += lv[u] * yv[u][r];
+                }
+        }
     }
-    return acc;
+}
+
+// The arithmetic of a chunk or row item for right-hand sides r0..r0+RB-1
+// (the item's flags already acquired).
+template <typename T, int RB>
+__device__ __forceinline__ void item_rhs_b(const SolveArgs<T> &s, const DFSolveArgs &a, const DFItem &it, T *y, T *z,
+                                           int32_t nrhs, int32_t S, int32_t b, int lane, int32_t r0, T d) {
+    const int n = s.n;
+    const bool bwd = it.flags & DF_BACKWARD;
+    const int64_t *pos = bwd ? s.urow_pos : s.lrow_pos;
+    const int32_t *col = bwd ? s.urow_col : s.lrow_col;
+    const T *src = (bwd ? z : y) + (int64_t)r0 * n * S + b;
+    const int64_t rs = (int64_t)n * S;
+    const T *lub = s.lu + b;
+    T acc[RB];
+#pragma unroll
+    for (int r = 0; r < RB; r++) acc[r] = (T)0;
+    if (it.flags & DF_CHUNK) {
+        const SolveChunk ch = (bwd ? a.bchunks : a.fchunks)[it.chunk];
+        T *partial = static_cast<T *>(bwd ? a.bpartial_v : a.fpartial_v);
+        dot_win_b<T, RB>(lub, pos, col, src, rs, ch.p0, ch.p1, S, lane, acc);
+#pragma unroll
+        for (int r = 0; r < RB; r++) partial[(((int64_t)it.chunk * nrhs) + r0 + r) * S + b] = acc[r];
+        return;
+    }
+    const int32_t i = it.row;
+    if (it.ce > it.cb) {
+        const T *partial = static_cast<const T *>(bwd ? a.bpartial_v : a.fpartial_v);
+        for (int32_t c0 = it.cb; c0 < it.ce; c0 += PB) {
+            T pv[PB][RB];
+#pragma unroll
+            for (int u = 0; u < PB; u++)
+#pragma unroll
+                for (int r = 0; r < RB; r++)
+                    pv[u][r] = c0 + u < it.ce ? __ldcg(partial + (((int64_t)(c0 + u) * nrhs) + r0 + r) * S + b) : (T)0;
+#pragma unroll
+            for (int u = 0; u < PB; u++)
+                if (c0 + u < it.ce) {
+#pragma unroll
+                    for (int r = 0; r < RB; r++) acc[r] += pv[u][r];
+                }
+        }
+    } else {
+        const int64_t *rptr = bwd ? s.urow_ptr : s.lrow_ptr;
+        dot_win_b<T, RB>(lub, pos, col, src, rs, rptr[i], rptr[i + 1], S, lane, acc);
+    }
+#pragma unroll
+    for (int r = 0; r < RB; r++) {
+        const int64_t at = ((int64_t)(r0 + r) * n + i) * S + b;
+        const T v = __ldcg(y + at);
+        (bwd ? z : y)[at] = bwd ? (v - acc[r]) / d : v - acc[r];
+    }
+}
+
+// The sweeps of a dense diagonal block of ns <= NS rows (NS a size class),
+// one column per template step so that every register index is a constant.
+// Forward (unit L): rows below column JJ subtract L(i, JJ) v(JJ); rows from
+// ns to NS - 1 are padding, computed on the block's last row and discarded,
+// so the class runs without per-row branches.  Backward: v(JJ) is divided by
+// U(JJ, JJ), then rows above subtract U(i, JJ) v(JJ).  mybase in lane k: the
+// position of the block's first row in column k of the block.
+template <typename T, int NS, int JJ>
+struct BlockFwd {
+    static __device__ __forceinline__ void run(T (&v)[NS], const T *lub, int64_t mybase, int32_t ns, int32_t S) {
+        if (JJ + 1 < ns) {
+            const int64_t base = __shfl_sync(0xffffffffu, mybase, JJ);
+            T lv[NS - JJ - 1];
+#pragma unroll
+            for (int ii = JJ + 1; ii < NS; ii++) lv[ii - JJ - 1] = lub[(base + min(ii, ns - 1)) * S];
+#pragma unroll
+            for (int ii = JJ + 1; ii < NS; ii++) v[ii] = v[ii] - lv[ii - JJ - 1] * v[JJ];
+            BlockFwd<T, NS, JJ + 1>::run(v, lub, mybase, ns, S);
+        }
+    }
+};
+template <typename T, int NS>
+struct BlockFwd<T, NS, NS - 1> {
+    static __device__ __forceinline__ void run(T (&)[NS], const T *, int64_t, int32_t, int32_t) {}
+};
+
+template <typename T, int NS, int JJ>
+struct BlockBwd {
+    static __device__ __forceinline__ void run(T (&v)[NS], const T *lub, int64_t mybase, int32_t ns, int32_t S) {
+        if (JJ < ns) {
+            const int64_t base = __shfl_sync(0xffffffffu, mybase, JJ);
+            T uv[JJ + 1];
+#pragma unroll
+            for (int ii = 0; ii <= JJ; ii++) uv[ii] = lub[(base + ii) * S];
+            v[JJ] = v[JJ] / uv[JJ];
+#pragma unroll
+            for (int ii = 0; ii < JJ; ii++) v[ii] = v[ii] - uv[ii] * v[JJ];
+        }
+        BlockBwd<T, NS, JJ - 1>::run(v, lub, mybase, ns, S);
+    }
+};
+template <typename T, int NS>
+struct BlockBwd<T, NS, -1> {
+    static __device__ __forceinline__ void run(T (&)[NS], const T *, int64_t, int32_t, int32_t) {}
+};
+
+// A dense diagonal block [c0, c0 + ns) of the dataflow solve for one lane
+// group (lane = set) and the right-hand sides r0, r0 + RSPLIT_B, ..., ns <= NS,
+// the flags of its chunks already acquired.
+// Each row's right-hand side less its chunks' partial sums (subtracted in
+// chunk order, PB loads in flight) is gathered in this warp's shared rows sv,
+// then swept in registers.  Lane kk holds row kk's chunk end and the block's
+// first-row position in column c0 + kk, broadcast by shuffles.
+template <typename T, int NS>
+__device__ __forceinline__ void block_item_b(const T *lub, const T *partial, T *y, T *out_base, T *sv, bool bwd,
+                                             int32_t c0, int32_t ns, int32_t cbeg, int32_t cend, int32_t myend,
+                                             int64_t mybase, int32_t n, int32_t r0, int32_t nrhs, int32_t S,
+                                             int32_t b) {
+    for (int32_t r = r0; r < nrhs; r += RSPLIT_B) {
+        T v[NS];
+#pragma unroll
+        for (int kk = 0; kk < NS; kk++) v[kk] = __ldcg(y + ((int64_t)r * n + c0 + min(kk, ns - 1)) * S + b);
+        if (cend > cbeg) {
+#pragma unroll
+            for (int kk = 0; kk < NS; kk++) sv[kk * 32] = v[kk];
+            int32_t cur = 0, nxt = __shfl_sync(0xffffffffu, myend, 0);
+            for (int32_t c = cbeg; c < cend; c += PB) {
+                T pv[PB];
+#pragma unroll
+                for (int u = 0; u < PB; u++)
+                    pv[u] = __ldcg(partial + (((int64_t)min(c + u, cend - 1) * nrhs) + r) * S + b);
+#pragma unroll
+                for (int u = 0; u < PB; u++)
+                    if (c + u < cend) {
+                        while (c + u >= nxt) nxt = __shfl_sync(0xffffffffu, myend, ++cur);
+                        sv[cur * 32] -= pv[u];
+                    }
+            }
+#pragma unroll
+            for (int kk = 0; kk < NS; kk++) v[kk] = sv[kk * 32];
+        }
+        if (!bwd)
+            BlockFwd<T, NS, 0>::run(v, lub, mybase, ns, S);
+        else
+            BlockBwd<T, NS, NS - 1>::run(v, lub, mybase, ns, S);
+        T *out = out_base + ((int64_t)r * n + c0) * S + b;
+#pragma unroll
+        for (int kk = 0; kk < NS; kk++)
+            if (kk < ns) out[(int64_t)kk * S] = v[kk];
+    }
 }
 
 // Dataflow solve for all sets: work item (DF item, lane group).  Flags are per
@@ -255,8 +450,9 @@ __device__ __forceinline__ T dot_b(const T *__restrict__ lu, const int64_t *__re
 // lanes of a warp acquire the flags of an item's entries together, then each
 // lane runs the entries in sequence for its own set.
 template <typename T>
-__global__ void __launch_bounds__(128) k_solve_df_b(const SolveArgs<T> s, const DFSolveArgs a, T *y, T *z,
+__global__ void __launch_bounds__(128, 4) k_solve_df_b(const SolveArgs<T> s, const DFSolveArgs a, T *y, T *z,
                                                     int32_t nrhs, int32_t S) {
+    __shared__ __align__(16) unsigned char blk_rows[4 * SN_MAX_B * 32 * sizeof(T)];   // per warp: a block's rows
     const int lane = threadIdx.x & 31;
     const int n = s.n;
     const int32_t G = S / 32;
@@ -272,148 +468,200 @@ __global__ void __launch_bounds__(128) k_solve_df_b(const SolveArgs<T> s, const 
         const DFItem it = a.items[k];
         const bool bwd = it.flags & DF_BACKWARD;
         const int64_t *rptr = bwd ? s.urow_ptr : s.lrow_ptr;
-        const int64_t *pos = bwd ? s.urow_pos : s.lrow_pos;
         const int32_t *col = bwd ? s.urow_col : s.lrow_col;
         int32_t *ready = bwd ? a.bready : a.fready;
-        const T *src = bwd ? z : y;
-        const T *lub = s.lu + b;
         if (it.flags & DF_BLOCK) {
-            // a dense diagonal block [c0, c1) of at most SN_MAX_B rows for this
-            // group: lane = set, the block's values of the set in registers,
-            // swept a column at a time (forward: rows below subtract L(i, jj)
-            // y(jj); backward: z(jj) = y(jj) / U(jj, jj), rows above subtract)
+            // a dense diagonal block [c0, c1) of at most SN_MAX_B rows, run by
+            // the code of its size class for the right-hand sides r = it.sub
+            // (mod RSPLIT_B); the last of the block's copies to finish (a
+            // counter per block and lane group) publishes its rows
             const int32_t c0 = it.row, ns = it.cb - it.row;
-            const int32_t *snx = (bwd ? a.bsnx : a.fsnx) + it.ce;
-            const int32_t *crd = bwd ? a.bchunk_ready : a.fchunk_ready;
-            for (int32_t c = snx[0] + lane; c < snx[ns]; c += 32) wait_b(crd + (int64_t)c * G + g, a);
-            __syncwarp();
-            const T *partial = static_cast<const T *>(bwd ? a.bpartial_v : a.fpartial_v);
-            for (int32_t r = 0; r < nrhs; r++) {
-                T v[SN_MAX_B];
-#pragma unroll
-                for (int kk = 0; kk < SN_MAX_B; kk++) {
-                    T x = (T)0;
-                    if (kk < ns) {
-                        x = __ldcg(y + ((int64_t)r * n + c0 + kk) * S + b);
-                        for (int32_t c = snx[kk]; c < snx[kk + 1]; c++)
-                            x -= __ldcg(partial + (((int64_t)c * nrhs) + r) * S + b);
-                    }
-                    v[kk] = x;
-                }
-                if (!bwd) {
-#pragma unroll
-                    for (int jj = 0; jj < SN_MAX_B; jj++) {
-                        if (jj + 1 < ns) {
-                            const int64_t base = s.diag_pos[c0 + jj] - jj;
-#pragma unroll
-                            for (int ii = jj + 1; ii < SN_MAX_B; ii++)
-                                if (ii < ns) v[ii] = v[ii] - lub[(base + ii) * S] * v[jj];
-                        }
-                    }
-                } else {
-#pragma unroll
-                    for (int jj = SN_MAX_B - 1; jj >= 0; jj--) {
-                        if (jj < ns) {
-                            const int64_t dp = s.diag_pos[c0 + jj];
-                            v[jj] = v[jj] / lub[dp * S];
-                            const int64_t base = dp - jj;
-#pragma unroll
-                            for (int ii = 0; ii < jj; ii++) v[ii] = v[ii] - lub[(base + ii) * S] * v[jj];
-                        }
-                    }
-                }
-                T *out = (bwd ? z : y) + ((int64_t)r * n + c0) * S + b;
-#pragma unroll
-                for (int kk = 0; kk < SN_MAX_B; kk++)
-                    if (kk < ns) out[(int64_t)kk * S] = v[kk];
+            if (it.sub < nrhs) {
+                const T *lub = s.lu + b;
+                const int32_t *snx = (bwd ? a.bsnx : a.fsnx) + it.ce;
+                const int32_t *crd = bwd ? a.bchunk_ready : a.fchunk_ready;
+                const int32_t cbeg = snx[0];
+                const int32_t myend = lane < ns ? snx[lane + 1] : 0;
+                const int64_t mybase = lane < ns ? s.diag_pos[c0 + lane] - lane : 0;
+                const int32_t cend = __shfl_sync(0xffffffffu, myend, ns - 1);
+                wait_range_b(crd + g, G, cbeg, cend, lane, a);
+                __syncwarp();
+                const T *partial = static_cast<const T *>(bwd ? a.bpartial_v : a.fpartial_v);
+                T *sv = reinterpret_cast<T *>(blk_rows) + (threadIdx.x >> 5) * (SN_MAX_B * 32) + lane;
+                T *ob = bwd ? z : y;
+                const int32_t q = it.sub;
+                if (ns <= 8)
+                    block_item_b<T, 8>(lub, partial, y, ob, sv, bwd, c0, ns, cbeg, cend, myend, mybase, n, q, nrhs, S,
+                                       b);
+                else if (ns <= 16)
+                    block_item_b<T, 16>(lub, partial, y, ob, sv, bwd, c0, ns, cbeg, cend, myend, mybase, n, q, nrhs,
+                                        S, b);
+                else if (ns <= 24)
+                    block_item_b<T, 24>(lub, partial, y, ob, sv, bwd, c0, ns, cbeg, cend, myend, mybase, n, q, nrhs,
+                                        S, b);
+                else
+                    block_item_b<T, SN_MAX_B>(lub, partial, y, ob, sv, bwd, c0, ns, cbeg, cend, myend, mybase, n, q,
+                                              nrhs, S, b);
             }
             __syncwarp();
-            for (int32_t kk = lane; kk < ns; kk += 32) st_release_b(ready + (int64_t)(c0 + kk) * G + g, a.epoch);
+            int last = 0;
+            if (lane == 0) last = atomic_add_acq_rel_b(a.blk_done + (int64_t)it.blk * G + g, 1) == RSPLIT_B - 1;
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (last)
+                for (int32_t kk = lane; kk < ns; kk += 32) st_release_b(ready + (int64_t)(c0 + kk) * G + g, a.epoch);
             continue;
         }
+        // chunk or row item: acquire the flags of its entries' columns (or of
+        // its chunks), then all right-hand sides, four at a time.  A backward
+        // item runs after the forward launch and the tail have completed.
+        const T d = (bwd && !(it.flags & DF_CHUNK)) ? s.lu[s.diag_pos[it.row] * S + b] : (T)1;
         if (it.flags & DF_CHUNK) {
             const SolveChunk ch = (bwd ? a.bchunks : a.fchunks)[it.chunk];
-            T *partial = static_cast<T *>(bwd ? a.bpartial_v : a.fpartial_v);
             for (int64_t p = ch.p0 + lane; p < ch.p1; p += 32) wait_b(ready + (int64_t)col[p] * G + g, a);
-            __syncwarp();
-            for (int32_t r = 0; r < nrhs; r++)
-                partial[(((int64_t)it.chunk * nrhs) + r) * S + b] =
-                    dot_b<T>(lub, pos, col, src + (int64_t)r * n * S + b, ch.p0, ch.p1, S);
-            __syncwarp();
-            if (lane == 0) st_release_b((bwd ? a.bchunk_ready : a.fchunk_ready) + (int64_t)it.chunk * G + g, a.epoch);
-            continue;
-        }
-        const int32_t i = it.row;
-        const int64_t p0 = rptr[i], p1 = rptr[i + 1];
-        const int32_t *crd = bwd ? a.bchunk_ready : a.fchunk_ready;
-        if (lane == 0 && bwd) wait_b(a.fready + (int64_t)i * G + g, a);
-        if (it.ce > it.cb) {
-            for (int32_t c = it.cb + lane; c < it.ce; c += 32) wait_b(crd + (int64_t)c * G + g, a);
+        } else if (it.ce > it.cb) {
+            wait_range_b((bwd ? a.bchunk_ready : a.fchunk_ready) + g, G, it.cb, it.ce, lane, a);
         } else {
-            for (int64_t p = p0 + lane; p < p1; p += 32) wait_b(ready + (int64_t)col[p] * G + g, a);
+            for (int64_t p = rptr[it.row] + lane; p < rptr[it.row + 1]; p += 32)
+                wait_b(ready + (int64_t)col[p] * G + g, a);
         }
         __syncwarp();
-        const T d = bwd ? s.lu[s.diag_pos[i] * S + b] : (T)1;
-        const T *partial = static_cast<const T *>(bwd ? a.bpartial_v : a.fpartial_v);
-        for (int32_t r = 0; r < nrhs; r++) {
-            T acc = (T)0;
-            if (it.ce > it.cb) {
-                for (int32_t c = it.cb; c < it.ce; c++) acc += __ldcg(partial + (((int64_t)c * nrhs) + r) * S + b);
-            } else {
-                acc = dot_b<T>(lub, pos, col, src + (int64_t)r * n * S + b, p0, p1, S);
-            }
-            const T v = __ldcg(y + ((int64_t)r * n + i) * S + b);
-            (bwd ? z : y)[((int64_t)r * n + i) * S + b] = bwd ? (v - acc) / d : v - acc;
+        int32_t r0 = 0;
+        for (; r0 + 4 <= nrhs; r0 += 4) item_rhs_b<T, 4>(s, a, it, y, z, nrhs, S, b, lane, r0, d);
+        if (r0 + 2 <= nrhs) {
+            item_rhs_b<T, 2>(s, a, it, y, z, nrhs, S, b, lane, r0, d);
+            r0 += 2;
         }
+        if (r0 < nrhs) item_rhs_b<T, 1>(s, a, it, y, z, nrhs, S, b, lane, r0, d);
         __syncwarp();
-        if (lane == 0) st_release_b(ready + (int64_t)i * G + g, a.epoch);
+        if (lane == 0) {
+            if (it.flags & DF_CHUNK)
+                st_release_b((bwd ? a.bchunk_ready : a.fchunk_ready) + (int64_t)it.chunk * G + g, a.epoch);
+            else
+                st_release_b(ready + (int64_t)it.row * G + g, a.epoch);
+        }
     }
 }
 
-// The dense tail [t0, n) for one group of 32 sets per block: warp w takes
-// rows w, w+32, ...; lane = set.  The tail's values of the group stay in
-// shared memory; one barrier per column forward, two backward.
+// The dense tail [t0, n) for one group of 32 sets and one right-hand side per
+// block (lane = set), in panels of TP columns.  Forward: one warp finishes
+// the panel's rows against its strictly lower triangle, then all warps
+// subtract the panel's columns from the rows below, TP independent loads a
+// row.  Backward likewise with the upper triangle, its diagonal and the rows
+// above.  Each row takes its column updates in the same order as a column-
+// at-a-time sweep.  The tail's right-hand side and the positions of its
+// columns stay in shared memory; the next panel's triangle is staged there
+// during the current update, so a panel costs two barriers.
+constexpr int TP = 16;
+constexpr int TRI_B = TP * (TP + 1) / 2;
+
 template <typename T>
-__global__ void __launch_bounds__(1024) k_solve_tail_b(const SolveArgs<T> s, const int64_t *__restrict__ lu_colptr,
-                                                       const TailArgs ta, const T *__restrict__ fpartial, const T *y,
-                                                       T *z, int32_t nrhs, int32_t S) {
+__device__ __forceinline__ void stage_tri_b(T *tri, const T *lub, const int64_t *lb, int32_t j0, int32_t kb, int32_t S,
+                                            bool bwd, int w, int nwarp, int lane) {
+    if (!bwd) {
+        // strictly lower: (i, k), k < i, at i (i - 1) / 2 + k
+        for (int i = 1 + w; i < kb; i += nwarp)
+            for (int k = 0; k < i; k++) tri[(i * (i - 1) / 2 + k) * 32 + lane] = lub[(lb[j0 + k] + j0 + i) * S];
+    } else {
+        // upper with the diagonal: (i, j), i <= j, at j (j + 1) / 2 + i
+        for (int j = w; j < kb; j += nwarp)
+            for (int i = 0; i <= j; i++) tri[(j * (j + 1) / 2 + i) * 32 + lane] = lub[(lb[j0 + j] + j0 + i) * S];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512, 1) k_solve_tail_b(const SolveArgs<T> s, const TailArgs ta,
+                                                      const T *__restrict__ fpartial, const T *y, T *z, int32_t nrhs,
+                                                      int32_t S) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int32_t n = s.n, t0 = ta.t0, NT = n - t0, G = S / 32;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    const int32_t g = blockIdx.x;
+    const int32_t g = blockIdx.x, r = blockIdx.y;
     const int32_t b = g * 32 + lane;
-    T *yt = reinterpret_cast<T *>(smem_raw);      // [NT][32]
-    T *zc = yt + (int64_t)NT * 32;                 // [32]: z of the current column
-    for (int32_t r = 0; r < nrhs; r++) {
-        for (int32_t ii = w; ii < NT; ii += nwarp) {
-            T v = __ldcg(y + ((int64_t)r * n + t0 + ii) * S + b);
-            for (int32_t c = ta.cb[ii]; c < ta.ce[ii]; c++) v -= __ldcg(fpartial + (((int64_t)c * nrhs) + r) * S + b);
-            yt[ii * 32 + lane] = v;
+    int64_t *lb = reinterpret_cast<int64_t *>(smem_raw);   // [NT]: position of tail row 0 in column t0 + j
+    T *yt = reinterpret_cast<T *>(lb + NT);                // [NT][32]
+    T *tri = yt + (int64_t)NT * 32;                        // [TRI_B][32]
+    const T *lub = s.lu + b;
+    for (int32_t j = threadIdx.x; j < NT; j += blockDim.x) lb[j] = s.diag_pos[t0 + j] - j;
+    for (int32_t ii = w; ii < NT; ii += nwarp) {
+        T v = __ldcg(y + ((int64_t)r * n + t0 + ii) * S + b);
+        for (int32_t c = ta.cb[ii]; c < ta.ce[ii]; c++) v -= __ldcg(fpartial + (((int64_t)c * nrhs) + r) * S + b);
+        yt[ii * 32 + lane] = v;
+    }
+    __syncthreads();
+    // forward, panels ascending
+    stage_tri_b<T>(tri, lub, lb, 0, NT < TP ? NT : TP, S, false, w, nwarp, lane);
+    __syncthreads();
+    for (int32_t j0 = 0; j0 < NT; j0 += TP) {
+        const int32_t kb = (NT - j0) < TP ? (NT - j0) : TP;
+        if (w == 0) {
+            T v[TP];
+#pragma unroll
+            for (int i = 0; i < TP; i++) v[i] = i < kb ? yt[(j0 + i) * 32 + lane] : (T)0;
+#pragma unroll
+            for (int k = 0; k < TP; k++)
+#pragma unroll
+                for (int i = k + 1; i < TP; i++)
+                    if (i < kb) v[i] = v[i] - tri[(i * (i - 1) / 2 + k) * 32 + lane] * v[k];
+#pragma unroll
+            for (int i = 0; i < TP; i++)
+                if (i < kb) yt[(j0 + i) * 32 + lane] = v[i];
         }
         __syncthreads();
-        for (int32_t jj = 0; jj < NT; jj++) {
-            const int64_t lb = s.diag_pos[t0 + jj] - jj;
-            const T vj = yt[jj * 32 + lane];
-            for (int32_t ii = jj + 1 + w; ii < NT; ii += nwarp)
-                yt[ii * 32 + lane] = yt[ii * 32 + lane] - s.lu[(lb + ii) * S + b] * vj;
-            __syncthreads();
+        for (int32_t ii = j0 + kb + w; ii < NT; ii += nwarp) {
+            T lv[TP];
+#pragma unroll
+            for (int k = 0; k < TP; k++) lv[k] = k < kb ? lub[(lb[j0 + k] + ii) * S] : (T)0;
+            T acc = yt[ii * 32 + lane];
+#pragma unroll
+            for (int k = 0; k < TP; k++)
+                if (k < kb) acc = acc - lv[k] * yt[(j0 + k) * 32 + lane];
+            yt[ii * 32 + lane] = acc;
         }
-        T *zr = z + (int64_t)r * n * S;
-        for (int32_t jj = NT - 1; jj >= 0; jj--) {
-            const int32_t j = t0 + jj;
-            if (w == 0) {
-                const T zj = yt[jj * 32 + lane] / s.lu[s.diag_pos[j] * S + b];
-                zc[lane] = zj;
-                zr[(int64_t)j * S + b] = zj;
-            }
-            __syncthreads();
-            const int64_t ub = lu_colptr[j + 1] - NT;
-            const T zj = zc[lane];
-            for (int32_t ii = w; ii < jj; ii += nwarp)
-                yt[ii * 32 + lane] = yt[ii * 32 + lane] - s.lu[(ub + ii) * S + b] * zj;
-            __syncthreads();
+        if (j0 + TP < NT) {
+            const int32_t jn = j0 + TP;
+            stage_tri_b<T>(tri, lub, lb, jn, (NT - jn) < TP ? (NT - jn) : TP, S, false, w, nwarp, lane);
         }
+        __syncthreads();
     }
+    // backward, panels descending
+    const int32_t last = ((NT - 1) / TP) * TP;
+    if (NT > 0) stage_tri_b<T>(tri, lub, lb, last, NT - last, S, true, w, nwarp, lane);
+    __syncthreads();
+    for (int32_t j0 = last; j0 >= 0; j0 -= TP) {
+        const int32_t kb = (NT - j0) < TP ? (NT - j0) : TP;
+        if (w == 0) {
+            T v[TP];
+#pragma unroll
+            for (int i = 0; i < TP; i++) v[i] = i < kb ? yt[(j0 + i) * 32 + lane] : (T)0;
+#pragma unroll
+            for (int j = TP - 1; j >= 0; j--)
+                if (j < kb) {
+                    v[j] = v[j] / tri[(j * (j + 1) / 2 + j) * 32 + lane];
+#pragma unroll
+                    for (int i = 0; i < j; i++) v[i] = v[i] - tri[(j * (j + 1) / 2 + i) * 32 + lane] * v[j];
+                }
+#pragma unroll
+            for (int i = 0; i < TP; i++)
+                if (i < kb) yt[(j0 + i) * 32 + lane] = v[i];
+        }
+        __syncthreads();
+        for (int32_t ii = w; ii < j0; ii += nwarp) {
+            T uv[TP];
+#pragma unroll
+            for (int k = 0; k < TP; k++) uv[k] = k < kb ? lub[(lb[j0 + k] + ii) * S] : (T)0;
+            T acc = yt[ii * 32 + lane];
+#pragma unroll
+            for (int k = TP - 1; k >= 0; k--)
+                if (k < kb) acc = acc - uv[k] * yt[(j0 + k) * 32 + lane];
+            yt[ii * 32 + lane] = acc;
+        }
+        if (j0 > 0) stage_tri_b<T>(tri, lub, lb, j0 - TP, TP, S, true, w, nwarp, lane);
+        __syncthreads();
+    }
+    T *zr = z + (int64_t)r * n * S;
+    for (int32_t ii = w; ii < NT; ii += nwarp) zr[(int64_t)(t0 + ii) * S + b] = yt[ii * 32 + lane];
+    // every right-hand side's block stores the same flags; the backward
+    // items read them after this launch has completed
     for (int32_t ii = threadIdx.x; ii < NT; ii += blockDim.x) ta.bready[(int64_t)(t0 + ii) * G + g] = ta.epoch;
 }
 
@@ -557,7 +805,7 @@ cudaError_t launch_rhs_out(double *out, const double *in, int32_t n, int32_t nrh
 }
 
 template <typename T>
-cudaError_t launch_solve_b(const SolveArgs<T> &sa, const DFSolveArgs &a, int32_t nfwd, const int64_t *lu_colptr,
+cudaError_t launch_solve_b(const SolveArgs<T> &sa, const DFSolveArgs &a, int32_t nfwd,
                            const TailArgs &ta, const double *in, double *out, T *y, T *z, const int32_t *perm,
                            int32_t nrhs, int32_t S, int num_sms, cudaStream_t s) {
     const int32_t n = sa.n;
@@ -579,13 +827,14 @@ cudaError_t launch_solve_b(const SolveArgs<T> &sa, const DFSolveArgs &a, int32_t
             k_solve_df_b<T><<<(unsigned)blocks, 128, 0, s>>>(sa, d, y, z, nrhs, S);
         }
         if (part == 0 && ta.t0 < n) {
-            const size_t smem = ((size_t)(n - ta.t0) * 32 + 32) * sizeof(T);
+            const int32_t nt = n - ta.t0;
+            const size_t smem = (size_t)nt * sizeof(int64_t) + ((size_t)nt + TRI_B) * 32 * sizeof(T);
             cudaError_t e = cudaFuncSetAttribute(k_solve_tail_b<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)smem);
             if (e != cudaSuccess) return e;
-            k_solve_tail_b<T><<<(unsigned)(S / 32), 1024, smem, s>>>(sa, lu_colptr, ta,
-                                                                     static_cast<const T *>(a.fpartial_v), y, z,
-                                                                     nrhs, S);
+            if (nrhs > 0)
+                k_solve_tail_b<T><<<dim3((unsigned)(S / 32), (unsigned)nrhs), 512, smem, s>>>(
+                    sa, ta, static_cast<const T *>(a.fpartial_v), y, z, nrhs, S);
         }
     }
     k_perm_out_b<T><<<grid_b((int64_t)n * nrhs * S), 256, 0, s>>>(out, z, perm, n, nrhs, S);
@@ -626,10 +875,10 @@ template cudaError_t launch_pivot_b<double>(const double *, const int64_t *, int
                                             unsigned long long *, cudaStream_t);
 template cudaError_t launch_pivot_b<float>(const float *, const int64_t *, int32_t, int32_t, int32_t,
                                            unsigned long long *, cudaStream_t);
-template cudaError_t launch_solve_b<double>(const SolveArgs<double> &, const DFSolveArgs &, int32_t, const int64_t *,
+template cudaError_t launch_solve_b<double>(const SolveArgs<double> &, const DFSolveArgs &, int32_t,
                                             const TailArgs &, const double *, double *, double *, double *,
                                             const int32_t *, int32_t, int32_t, int, cudaStream_t);
-template cudaError_t launch_solve_b<float>(const SolveArgs<float> &, const DFSolveArgs &, int32_t, const int64_t *,
+template cudaError_t launch_solve_b<float>(const SolveArgs<float> &, const DFSolveArgs &, int32_t,
                                            const TailArgs &, const double *, double *, float *, float *,
                                            const int32_t *, int32_t, int32_t, int, cudaStream_t);
 

@@ -51,6 +51,35 @@ def load_dump(path):
     return items, nfwd, fch, bch, snf, snb, t0
 
 
+RSPLIT_B = 4   # copies of a dense diagonal block item in the batched schedule
+
+
+def block_copies(items, nfwd):
+    """The batched schedule lists each dense diagonal block RSPLIT_B times in
+    a row, copy q (field 5) taking the right-hand sides r = q mod RSPLIT_B,
+    with the block's ordinal (field 6) for its completion counter.  Checks
+    that layout and returns the list with one item per block."""
+    keep, k, nb, nf = [], 0, 0, 0
+    while k < len(items):
+        it = items[k]
+        if it[4] & 4:
+            group = items[k:k + RSPLIT_B]
+            assert len(group) == RSPLIT_B
+            assert (group[:, :5] == it[:5]).all(), "copies differ"
+            assert group[:, 5].tolist() == list(range(RSPLIT_B))
+            assert (group[:, 6] == nb).all(), "block ordinals not consecutive"
+            nb += 1
+            step = RSPLIT_B
+        else:
+            assert it[5] == 0 and it[6] == 0
+            step = 1
+        keep.append(it)
+        if k < nfwd:
+            nf += 1
+        k += step
+    return np.array(keep, dtype=items.dtype).reshape(-1, 8), nf
+
+
 def replay(n, t0, items, ptr, cols, chunks, snx, backward):
     done = np.zeros(n, bool)
     if backward:
@@ -127,8 +156,9 @@ def _triangle(n, upper):
 @pytest.mark.parametrize("variant", ["single", "batched"])
 @pytest.mark.parametrize("case", ["grid32", "mesh_nets", "mesh100x200", "dense100", "lower", "upper"])
 def test_df_schedule_topological_and_complete(tmp_path, monkeypatch, case, variant):
-    # "batched": the schedule of the batched solves (longer chunks, a dense
-    # tail of at most 768 rows), dumped by GLU_DUMP_DF_BATCHED
+    # "batched": the schedule of the batched solves (a dense tail of at most
+    # 736 rows, each block item in RSPLIT_B copies), dumped by
+    # GLU_DUMP_DF_BATCHED
     if case == "grid32":
         m = synth.make("grid32_natural", 0)
     elif case == "mesh_nets":
@@ -148,6 +178,8 @@ def test_df_schedule_topological_and_complete(tmp_path, monkeypatch, case, varia
     cp, ri = glu.glu_get_fill(h)
     glu.glu_destroy(h)
     items, nfwd, fch, bch, snf, snb, t0 = load_dump(path)
+    if variant == "batched":
+        items, nfwd = block_copies(items, nfwd)
     n = m.n
     lptr, lcol, uptr, ucol = row_views(np.asarray(cp, np.int64), np.asarray(ri, np.int64), n)
     fwd = [tuple(int(x) for x in r) for r in items[:nfwd]]
