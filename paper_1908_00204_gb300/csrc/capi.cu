@@ -134,6 +134,9 @@ struct glu_handle {
     cudaGraphExec_t fgraph = nullptr;
     int64_t fgraph_launches = 0;
     std::vector<std::pair<int32_t, cudaGraphExec_t>> sgraphs;
+    std::vector<std::pair<int32_t, cudaGraphExec_t>> rgraphs;   // refinement iteration per nrhs
+    std::vector<int64_t> rgraph_launches;
+    std::vector<double> rgraph_tol;
     std::vector<int64_t> sgraph_launches;
     // per-level timing diagnostic (GLU_LEVEL_TIMES=path)
     std::string level_times_path;
@@ -295,6 +298,15 @@ int enqueue_levels(glu_handle *h, const FactorArgs<T> &a, cudaStream_t st) {
     return GLU_OK;
 }
 
+// Refinement graphs hold the work and refinement buffers; they go when
+// either is reallocated.
+void drop_rgraphs(glu_handle *h) {
+    for (auto &g : h->rgraphs) cudaGraphExecDestroy(g.second);
+    h->rgraphs.clear();
+    h->rgraph_launches.clear();
+    h->rgraph_tol.clear();
+}
+
 int ensure_work(glu_handle *h, int32_t nrhs) {
     if (nrhs <= h->work_nrhs) return GLU_OK;
     const int64_t elems = (int64_t)h->P.n * nrhs;
@@ -304,6 +316,7 @@ int ensure_work(glu_handle *h, int32_t nrhs) {
     for (auto &g : h->sgraphs) cudaGraphExecDestroy(g.second);
     h->sgraphs.clear();
     h->sgraph_launches.clear();
+    drop_rgraphs(h);
     cudaFree(h->d_work);
     cudaFree(h->d_bstage);
     cudaFree(h->d_xstage);
@@ -511,6 +524,7 @@ int enqueue_solve_f32(glu_handle *h, const double *db, double *dx, int32_t nrhs,
 
 int ensure_ir(glu_handle *h, int32_t nrhs) {
     if (nrhs <= h->ir_nrhs) return GLU_OK;
+    drop_rgraphs(h);
     cudaFree(h->d_ir);
     cudaFree(h->d_irnorm);
     cudaFree(h->d_done);
@@ -1253,27 +1267,61 @@ int glu_solve_refine(glu_handle *h, const double *b, double *x, int32_t nrhs, do
     rc = ensure_ir(h, nrhs);
     if (rc != GLU_OK) return rc;
     cudaStream_t st = h->stream;
-    const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
-    const double *db = b;
-    if (!bdev) {
-        CK(cudaMemcpyAsync(h->d_bstage, b, elems * sizeof(double), cudaMemcpyHostToDevice, st));
-        db = h->d_bstage;
-    }
-    double *dx = xdev ? x : h->d_xstage;
+    // b, the iterate x and the residual r live in the handle's buffers, so
+    // that one iteration (FP32 solve of r, x += d on the sides not done,
+    // r = b - A x with its norms, the check) is the same graph every time.
+    // x starts at 0, so the first residual is b itself.
+    double *db = h->d_bstage, *dx = h->d_xstage;
     double *r = h->d_ir, *d = h->d_ir + elems;
+    CK(cudaMemcpyAsync(db, b, elems * sizeof(double),
+                       is_device_ptr(b) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
     unsigned long long *anorm = h->d_irnorm, *rmax = anorm + 1, *xmax = rmax + nrhs, *bmax = xmax + nrhs;
     int32_t *done = h->d_done, *ndone = h->d_done + nrhs;
     CK(cudaMemsetAsync(h->d_irnorm, 0, (1 + 3 * (size_t)nrhs) * sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(done, 0, (size_t)nrhs * sizeof(int32_t), st));
     CKL(1, launch_anorm(h->d_acsr_ptr, h->d_aval_csr, n, anorm, st));
     CKL(1, launch_absmax(db, n, nrhs, bmax, st));
     CK(cudaMemsetAsync(dx, 0, elems * sizeof(double), st));
+    CK(cudaMemcpyAsync(r, db, elems * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    auto step = [&](cudaStream_t cs) -> int {
+        int rc2 = enqueue_solve_f32(h, r, d, nrhs, cs);
+        if (rc2 != GLU_OK) return rc2;
+        CKL(1, launch_update(dx, d, done, n, nrhs, cs));
+        CK(cudaMemsetAsync(rmax, 0, 2 * (size_t)nrhs * sizeof(unsigned long long), cs));
+        CK(cudaMemsetAsync(ndone, 0, sizeof(int32_t), cs));
+        CKL(1, launch_residual(h->d_acsr_ptr, h->d_acsr_col, h->d_aval_csr, db, dx, r, n, nrhs, rmax, xmax, cs));
+        CKL(1, launch_check(rmax, xmax, bmax, anorm, nrhs, tol, done, h->d_berr, ndone, cs));
+        return GLU_OK;
+    };
+    size_t gi = 0;
+    if (h->opt.use_graph) {
+        // the check's tolerance is a kernel argument: one graph per (nrhs, tol)
+        while (gi < h->rgraphs.size() && !(h->rgraphs[gi].first == nrhs && h->rgraph_tol[gi] == tol)) gi++;
+        if (gi == h->rgraphs.size()) {
+            cudaGraphExec_t ex = nullptr;
+            int64_t nl = 0;
+            rc = capture(h, step, &ex, &nl);
+            if (rc != GLU_OK) return rc;
+            h->rgraphs.emplace_back(nrhs, ex);
+            h->rgraph_launches.push_back(nl);
+            h->rgraph_tol.push_back(tol);
+        }
+    }
     std::vector<double> berr((size_t)nrhs);
     int32_t solves = 0;
     while (true) {
-        CK(cudaMemsetAsync(rmax, 0, 2 * (size_t)nrhs * sizeof(unsigned long long), st));
-        CK(cudaMemsetAsync(ndone, 0, sizeof(int32_t), st));
-        CKL(1, launch_residual(h->d_acsr_ptr, h->d_acsr_col, h->d_aval_csr, db, dx, r, n, nrhs, rmax, xmax, st));
-        CKL(1, launch_check(rmax, xmax, bmax, anorm, nrhs, tol, done, h->d_berr, ndone, st));
+        if (solves >= 1 + maxit) {
+            inf.converged = 0;
+            break;
+        }
+        if (h->opt.use_graph) {
+            CK(cudaGraphLaunch(h->rgraphs[gi].second, st));
+            h->launches += h->rgraph_launches[gi];
+        } else {
+            rc = step(st);
+            if (rc != GLU_OK) return rc;
+        }
+        solves++;
         int32_t nd = 0;
         CK(cudaMemcpyAsync(&nd, ndone, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(berr.data(), h->d_berr, (size_t)nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1286,19 +1334,11 @@ int glu_solve_refine(glu_handle *h, const double *b, double *x, int32_t nrhs, do
             inf.converged = 1;
             break;
         }
-        if (solves >= 1 + maxit) {
-            inf.converged = 0;
-            break;
-        }
-        rc = enqueue_solve_f32(h, r, d, nrhs, st);
-        if (rc != GLU_OK) return rc;
-        CKL(1, launch_update(dx, d, done, n, nrhs, st));
-        solves++;
     }
     inf.iterations = std::max(0, solves - 1);
-    if (solves == 0) inf.berr_first = inf.berr;
     if (info) *info = inf;
-    if (!xdev) CK(cudaMemcpyAsync(x, dx, elems * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(x, dx, elems * sizeof(double), is_device_ptr(x) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       st));
     return glu_sync(h);
 }
 
@@ -1411,6 +1451,7 @@ void glu_destroy(glu_handle *h) {
     cudaFree(h->d_irnorm);
     cudaFree(h->d_done);
     cudaFree(h->d_berr);
+    drop_rgraphs(h);
     for (auto &g : h->sgraphs) cudaGraphExecDestroy(g.second);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     cudaFree(h->arena);
@@ -1793,12 +1834,24 @@ extern "C" int glu_solve_batched_refine(glu_handle *h, const double *b, double *
     }
     CKL(1, launch_rhs_in(bin, src, n, nrhs, batch, S, st));
     CK(cudaMemsetAsync(h->d_bnorm, 0, (S + 3 * (size_t)nrhs * S) * sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(done, 0, (size_t)nrhs * S * sizeof(int32_t), st));
     CKL(3, launch_ir_b(0, h->d_acsr_ptr, h->d_acsr_col, h->d_avb, h->d_aT, h->d_acsr_src, P.nnz_a, bin, xi, r, d, n,
                        nrhs, batch, S, anorm, rmax, xmax, bmax, tol, done, h->d_bberr, ndone, st));
+    // x starts at 0, so the first residual is b itself
     CK(cudaMemsetAsync(xi, 0, e * sizeof(double), st));
+    CK(cudaMemcpyAsync(r, bin, e * sizeof(double), cudaMemcpyDeviceToDevice, st));
     std::vector<double> berr((size_t)nrhs * S);
     int32_t solves = 0;
     while (true) {
+        if (solves >= 1 + maxit) {
+            inf.converged = 0;
+            break;
+        }
+        rc = enqueue_solve_b<float>(h, h->d_lub32, r, d, nrhs, st);
+        if (rc != GLU_OK) return rc;
+        CKL(1, launch_ir_b(2, h->d_acsr_ptr, h->d_acsr_col, h->d_avb, h->d_aT, h->d_acsr_src, P.nnz_a, bin, xi, r, d, n,
+                           nrhs, batch, S, anorm, rmax, xmax, bmax, tol, done, h->d_bberr, ndone, st));
+        solves++;
         CK(cudaMemsetAsync(rmax, 0, 2 * (size_t)nrhs * S * sizeof(unsigned long long), st));
         CK(cudaMemsetAsync(ndone, 0, sizeof(int32_t), st));
         CKL(2, launch_ir_b(1, h->d_acsr_ptr, h->d_acsr_col, h->d_avb, h->d_aT, h->d_acsr_src, P.nnz_a, bin, xi, r, d,
@@ -1815,18 +1868,8 @@ extern "C" int glu_solve_batched_refine(glu_handle *h, const double *b, double *
             inf.converged = 1;
             break;
         }
-        if (solves >= 1 + maxit) {
-            inf.converged = 0;
-            break;
-        }
-        rc = enqueue_solve_b<float>(h, h->d_lub32, r, d, nrhs, st);
-        if (rc != GLU_OK) return rc;
-        CKL(1, launch_ir_b(2, h->d_acsr_ptr, h->d_acsr_col, h->d_avb, h->d_aT, h->d_acsr_src, P.nnz_a, bin, xi, r, d, n,
-                           nrhs, batch, S, anorm, rmax, xmax, bmax, tol, done, h->d_bberr, ndone, st));
-        solves++;
     }
     inf.iterations = std::max(0, solves - 1);
-    if (solves == 0) inf.berr_first = inf.berr;
     if (info) *info = inf;
     double *dst = xdev ? x : stage;
     CKL(1, launch_rhs_out(dst, xi, n, nrhs, batch, S, st));

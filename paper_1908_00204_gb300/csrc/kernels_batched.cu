@@ -349,7 +349,7 @@ __device__ __forceinline__ void item_rhs_b(const SolveArgs<T> &s, const DFSolveA
     for (int r = 0; r < RB; r++) {
         const int64_t at = ((int64_t)(r0 + r) * n + i) * S + b;
         const T v = __ldcg(y + at);
-        (bwd ? z : y)[at] = bwd ? (v - acc[r]) / d : v - acc[r];
+        (bwd ? z : y)[at] = bwd ? (v - acc[r]) * d : v - acc[r];
     }
 }
 
@@ -357,9 +357,10 @@ __device__ __forceinline__ void item_rhs_b(const SolveArgs<T> &s, const DFSolveA
 // one column per template step so that every register index is a constant.
 // Forward (unit L): rows below column JJ subtract L(i, JJ) v(JJ); rows from
 // ns to NS - 1 are padding, computed on the block's last row and discarded,
-// so the class runs without per-row branches.  Backward: v(JJ) is divided by
-// U(JJ, JJ), then rows above subtract U(i, JJ) v(JJ).  mybase in lane k: the
-// position of the block's first row in column k of the block.
+// so the class runs without per-row branches.  Backward: v(JJ) is multiplied
+// by the reciprocal of U(JJ, JJ) (taken as soon as it is loaded, off the
+// column chain), then rows above subtract U(i, JJ) v(JJ).  mybase in lane k:
+// the position of the block's first row in column k of the block.
 template <typename T, int NS, int JJ>
 struct BlockFwd {
     static __device__ __forceinline__ void run(T (&v)[NS], const T *lub, int64_t mybase, int32_t ns, int32_t S) {
@@ -387,7 +388,7 @@ struct BlockBwd {
             T uv[JJ + 1];
 #pragma unroll
             for (int ii = 0; ii <= JJ; ii++) uv[ii] = lub[(base + ii) * S];
-            v[JJ] = v[JJ] / uv[JJ];
+            v[JJ] = v[JJ] * ((T)1 / uv[JJ]);
 #pragma unroll
             for (int ii = 0; ii < JJ; ii++) v[ii] = v[ii] - uv[ii] * v[JJ];
         }
@@ -514,7 +515,8 @@ __global__ void __launch_bounds__(128, 4) k_solve_df_b(const SolveArgs<T> s, con
         // chunk or row item: acquire the flags of its entries' columns (or of
         // its chunks), then all right-hand sides, four at a time.  A backward
         // item runs after the forward launch and the tail have completed.
-        const T d = (bwd && !(it.flags & DF_CHUNK)) ? s.lu[s.diag_pos[it.row] * S + b] : (T)1;
+        // d: the reciprocal of U(i, i) for a backward row
+        const T d = (bwd && !(it.flags & DF_CHUNK)) ? (T)1 / s.lu[s.diag_pos[it.row] * S + b] : (T)1;
         if (it.flags & DF_CHUNK) {
             const SolveChunk ch = (bwd ? a.bchunks : a.fchunks)[it.chunk];
             for (int64_t p = ch.p0 + lane; p < ch.p1; p += 32) wait_b(ready + (int64_t)col[p] * G + g, a);
@@ -636,7 +638,7 @@ __global__ void __launch_bounds__(512, 1) k_solve_tail_b(const SolveArgs<T> s, c
 #pragma unroll
             for (int j = TP - 1; j >= 0; j--)
                 if (j < kb) {
-                    v[j] = v[j] / tri[(j * (j + 1) / 2 + j) * 32 + lane];
+                    v[j] = v[j] * ((T)1 / tri[(j * (j + 1) / 2 + j) * 32 + lane]);
 #pragma unroll
                     for (int i = 0; i < j; i++) v[i] = v[i] - tri[(j * (j + 1) / 2 + i) * 32 + lane] * v[j];
                 }
@@ -666,8 +668,25 @@ __global__ void __launch_bounds__(512, 1) k_solve_tail_b(const SolveArgs<T> s, c
 }
 
 // ------------------------------------------------------------ refinement
-__device__ __forceinline__ void max_abs_b(unsigned long long *slot, double v) {
-    atomicMax(slot, (unsigned long long)__double_as_longlong(fabs(v)));
+__device__ __forceinline__ unsigned long long abs_bits_b(double v) {
+    return (unsigned long long)__double_as_longlong(fabs(v));
+}
+
+// Blocks of 32 sets (x) by 8 rows (y): each thread keeps the maximum over
+// its rows of one set; the block's maximum per set goes into slot[x] by one
+// atomicMax (bit patterns of non-negative doubles order like the values).
+__device__ __forceinline__ void block_max_b(unsigned long long *slot, unsigned long long m) {
+    __shared__ unsigned long long sm[8][32];
+    sm[threadIdx.y][threadIdx.x] = m;
+    __syncthreads();
+    if (threadIdx.y == 0) {
+        for (int w = 1; w < (int)blockDim.y; w++) {
+            const unsigned long long u = sm[w][threadIdx.x];
+            m = u > m ? u : m;
+        }
+        if (m) atomicMax(slot + threadIdx.x, m);
+    }
+    __syncthreads();
 }
 
 __global__ void k_csr_values_b(double *__restrict__ out, const double *__restrict__ aT,
@@ -679,44 +698,52 @@ __global__ void k_csr_values_b(double *__restrict__ out, const double *__restric
     }
 }
 
+// ||A_b||_inf per set b (lane group blockIdx.y)
 __global__ void k_anorm_b(const int64_t *__restrict__ rp, const double *__restrict__ av, int32_t n, int32_t S,
                           unsigned long long *anorm) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)n * S) return;
-    const int32_t i = (int32_t)(t / S);
-    const int32_t b = (int32_t)(t - (int64_t)i * S);
-    double s = 0.0;
-    for (int64_t p = rp[i]; p < rp[i + 1]; p++) s += fabs(av[p * S + b]);
-    max_abs_b(anorm + b, s);
+    const int32_t b = blockIdx.y * 32 + threadIdx.x;
+    unsigned long long m = 0;
+    for (int32_t i = blockIdx.x * blockDim.y + threadIdx.y; i < n; i += gridDim.x * blockDim.y) {
+        double s = 0.0;
+        for (int64_t p = rp[i]; p < rp[i + 1]; p++) s += fabs(av[p * S + b]);
+        const unsigned long long u = abs_bits_b(s);
+        m = u > m ? u : m;
+    }
+    block_max_b(anorm + blockIdx.y * 32, m);
 }
 
-// r = b - A x per (row, side, set); max |r|, |x| per (side, set)
+// r = b - A x per (row, side k = blockIdx.z, set); max |r|, |x| per (side, set)
 __global__ void k_residual_b(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
                              const double *__restrict__ av, const double *__restrict__ bb,
-                             const double *__restrict__ x, double *__restrict__ r, int32_t n, int32_t nrhs, int32_t S,
+                             const double *__restrict__ x, double *__restrict__ r, int32_t n, int32_t S,
                              unsigned long long *rmax, unsigned long long *xmax) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)n * nrhs * S) return;
-    const int64_t ri = t / S;
-    const int32_t b = (int32_t)(t - ri * S);
-    const int32_t k = (int32_t)(ri / n);
-    const int32_t i = (int32_t)(ri - (int64_t)k * n);
+    const int32_t k = blockIdx.z;
+    const int32_t b = blockIdx.y * 32 + threadIdx.x;
     const double *xk = x + (int64_t)k * n * S + b;
-    double s = 0.0;
-    for (int64_t p = rp[i]; p < rp[i + 1]; p++) s = fma(av[p * S + b], xk[(int64_t)ci[p] * S], s);
-    const double v = bb[t] - s;
-    r[t] = v;
-    max_abs_b(rmax + (int64_t)k * S + b, v);
-    max_abs_b(xmax + (int64_t)k * S + b, x[t]);
+    unsigned long long mr = 0, mx = 0;
+    for (int32_t i = blockIdx.x * blockDim.y + threadIdx.y; i < n; i += gridDim.x * blockDim.y) {
+        double s = 0.0;
+        for (int64_t p = rp[i]; p < rp[i + 1]; p++) s = fma(av[p * S + b], xk[(int64_t)ci[p] * S], s);
+        const int64_t t = ((int64_t)k * n + i) * S + b;
+        const double v = bb[t] - s;
+        r[t] = v;
+        const unsigned long long ur = abs_bits_b(v), ux = abs_bits_b(x[t]);
+        mr = ur > mr ? ur : mr;
+        mx = ux > mx ? ux : mx;
+    }
+    block_max_b(rmax + (int64_t)k * S + blockIdx.y * 32, mr);
+    block_max_b(xmax + (int64_t)k * S + blockIdx.y * 32, mx);
 }
 
-__global__ void k_absmax_b(const double *__restrict__ v, int32_t n, int32_t nrhs, int32_t S,
-                           unsigned long long *out) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)n * nrhs * S) return;
-    const int64_t ri = t / S;
-    const int32_t b = (int32_t)(t - ri * S);
-    max_abs_b(out + (ri / n) * S + b, v[t]);
+__global__ void k_absmax_b(const double *__restrict__ v, int32_t n, int32_t S, unsigned long long *out) {
+    const int32_t k = blockIdx.z;
+    const int32_t b = blockIdx.y * 32 + threadIdx.x;
+    unsigned long long m = 0;
+    for (int32_t i = blockIdx.x * blockDim.y + threadIdx.y; i < n; i += gridDim.x * blockDim.y) {
+        const unsigned long long u = abs_bits_b(v[((int64_t)k * n + i) * S + b]);
+        m = u > m ? u : m;
+    }
+    block_max_b(out + (int64_t)k * S + blockIdx.y * 32, m);
 }
 
 __global__ void k_check_b(const unsigned long long *rmax, const unsigned long long *xmax,
@@ -746,6 +773,17 @@ __global__ void k_update_b(double *__restrict__ x, const double *__restrict__ d,
     const int64_t ri = t / S;
     const int32_t b = (int32_t)(t - ri * S);
     if (!done[(ri / n) * S + b]) x[t] += d[t];
+}
+
+// row-parallel reductions over (row blocks, lane groups, sides): about eight
+// blocks per SM in all
+dim3 row_grid_b(int32_t n, int32_t nrhs, int32_t S) {
+    const int64_t groups = (int64_t)(S / 32) * (nrhs > 0 ? nrhs : 1);
+    int64_t rb = ((int64_t)n + 7) / 8;
+    const int64_t cap = (int64_t)152 * 8 / groups;
+    if (rb > cap) rb = cap;
+    if (rb < 1) rb = 1;
+    return dim3((unsigned)rb, (unsigned)(S / 32), (unsigned)(nrhs > 0 ? nrhs : 1));
 }
 
 unsigned grid_b(int64_t work) {
@@ -850,11 +888,11 @@ cudaError_t launch_ir_b(int op, const int64_t *rp, const int32_t *ci, const doub
     switch (op) {
         case 0:   // values in compressed-row order, ||A||, ||b||
             if (nnz > 0) k_csr_values_b<<<grid_b(nnz * S), 256, 0, s>>>(const_cast<double *>(av), aT, src, nnz, S);
-            if (n > 0) k_anorm_b<<<(unsigned)(((int64_t)n * S + 255) / 256), 256, 0, s>>>(rp, av, n, S, anorm);
-            if (w > 0) k_absmax_b<<<(unsigned)((w + 255) / 256), 256, 0, s>>>(bb, n, nrhs, S, bmax);
+            if (n > 0) k_anorm_b<<<row_grid_b(n, 1, S), dim3(32, 8), 0, s>>>(rp, av, n, S, anorm);
+            if (w > 0) k_absmax_b<<<row_grid_b(n, nrhs, S), dim3(32, 8), 0, s>>>(bb, n, S, bmax);
             break;
         case 1:   // residual and check
-            if (w > 0) k_residual_b<<<(unsigned)((w + 255) / 256), 256, 0, s>>>(rp, ci, av, bb, x, r, n, nrhs, S, rmax, xmax);
+            if (w > 0) k_residual_b<<<row_grid_b(n, nrhs, S), dim3(32, 8), 0, s>>>(rp, ci, av, bb, x, r, n, S, rmax, xmax);
             k_check_b<<<(unsigned)((nrhs * S + 127) / 128), 128, 0, s>>>(rmax, xmax, bmax, anorm, nrhs, B, S, tol, done,
                                                                          berr, ndone);
             break;

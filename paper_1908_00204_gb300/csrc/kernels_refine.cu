@@ -2,10 +2,12 @@
 //
 // The factors are FP32; the residual r = b - A x, its norms and the update
 // x += d stay in FP64 on the GPU.  Norm maxima use the bit pattern of
-// non-negative doubles, which orders like the values, so an integer
-// atomicMax gives an exact, order-independent maximum.
+// non-negative doubles, which orders like the values, so an integer maximum
+// (within a block by shuffles, across blocks by one atomicMax each) is exact
+// and independent of order.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "glu_device.cuh"
@@ -13,11 +15,35 @@
 namespace glu {
 namespace {
 
-__device__ __forceinline__ void max_abs(unsigned long long *slot, double v) {
-    atomicMax(slot, (unsigned long long)__double_as_longlong(fabs(v)));
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+    return (unsigned long long)__double_as_longlong(fabs(v));
 }
 
 __device__ __forceinline__ double as_double(unsigned long long u) { return __longlong_as_double((long long)u); }
+
+// The block's maximum of m (bit patterns of non-negative doubles) into *slot:
+// shuffles within each warp, then shared memory, one atomic per block.
+__device__ __forceinline__ void block_max(unsigned long long *slot, unsigned long long m) {
+    __shared__ unsigned long long wmax[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long u = __shfl_xor_sync(0xffffffffu, m, o);
+        m = u > m ? u : m;
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) wmax[w] = m;
+    __syncthreads();
+    if (w == 0) {
+        m = lane < (int)(blockDim.x >> 5) ? wmax[lane] : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long u = __shfl_xor_sync(0xffffffffu, m, o);
+            m = u > m ? u : m;
+        }
+        if (lane == 0 && m) atomicMax(slot, m);
+    }
+    __syncthreads();   // wmax is reused by the next call
+}
 
 // A's values in compressed-row order (gathered once per factorization).
 __global__ void k_csr_values(double *__restrict__ out, const double *__restrict__ aval,
@@ -29,35 +55,45 @@ __global__ void k_csr_values(double *__restrict__ out, const double *__restrict_
 // ||A||_inf = max over rows of sum |a_ij|.
 __global__ void k_anorm(const int64_t *__restrict__ rp, const double *__restrict__ av, int32_t n,
                         unsigned long long *anorm) {
-    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double s = 0.0;
-    for (int64_t p = rp[i]; p < rp[i + 1]; p++) s += fabs(av[p]);
-    max_abs(anorm, s);
+    unsigned long long m = 0;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int64_t p = rp[i]; p < rp[i + 1]; p++) s += fabs(av[p]);
+        const unsigned long long u = abs_bits(s);
+        m = u > m ? u : m;
+    }
+    block_max(anorm, m);
 }
 
-// r = b - A x for every right-hand side; also max |r| and max |x| per side.
+// r = b - A x for right-hand side k = blockIdx.y; also max |r| and max |x|.
 __global__ void k_residual(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
                            const double *__restrict__ av, const double *__restrict__ b, const double *__restrict__ x,
-                           double *__restrict__ r, int32_t n, int32_t nrhs, unsigned long long *rmax,
-                           unsigned long long *xmax) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)n * nrhs) return;
-    const int32_t k = (int32_t)(t / n);
-    const int32_t i = (int32_t)(t - (int64_t)k * n);
+                           double *__restrict__ r, int32_t n, unsigned long long *rmax, unsigned long long *xmax) {
+    const int32_t k = blockIdx.y;
     const double *xk = x + (int64_t)k * n;
-    double s = 0.0;
-    for (int64_t p = rp[i]; p < rp[i + 1]; p++) s = fma(av[p], xk[ci[p]], s);
-    const double v = b[t] - s;
-    r[t] = v;
-    max_abs(rmax + k, v);
-    max_abs(xmax + k, xk[i]);
+    unsigned long long mr = 0, mx = 0;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int64_t p = rp[i]; p < rp[i + 1]; p++) s = fma(av[p], xk[ci[p]], s);
+        const int64_t t = (int64_t)k * n + i;
+        const double v = b[t] - s;
+        r[t] = v;
+        const unsigned long long ur = abs_bits(v), ux = abs_bits(xk[i]);
+        mr = ur > mr ? ur : mr;
+        mx = ux > mx ? ux : mx;
+    }
+    block_max(rmax + k, mr);
+    block_max(xmax + k, mx);
 }
 
-__global__ void k_absmax(const double *__restrict__ v, int32_t n, int32_t nrhs, unsigned long long *out) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)n * nrhs) return;
-    max_abs(out + t / n, v[t]);
+__global__ void k_absmax(const double *__restrict__ v, int32_t n, unsigned long long *out) {
+    const int32_t k = blockIdx.y;
+    unsigned long long m = 0;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const unsigned long long u = abs_bits(v[(int64_t)k * n + i]);
+        m = u > m ? u : m;
+    }
+    block_max(out + k, m);
 }
 
 // Normwise backward error per side, ||r|| / (||A|| ||x|| + ||b||); a side is
@@ -88,6 +124,14 @@ unsigned blocks_for(int64_t work) {
     return (unsigned)(b < 1 ? 1 : b);
 }
 
+// row-parallel reductions: at most eight blocks per SM in all
+unsigned row_blocks(int32_t n, int32_t nrhs) {
+    int64_t b = ((int64_t)n + 255) / 256;
+    const int64_t cap = std::max<int64_t>(1, (int64_t)152 * 8 / std::max<int32_t>(nrhs, 1));
+    if (b > cap) b = cap;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
 }  // namespace
 
 cudaError_t launch_csr_values(double *out, const double *aval, const int64_t *src, int64_t nnz, cudaStream_t s) {
@@ -100,23 +144,21 @@ cudaError_t launch_csr_values(double *out, const double *aval, const int64_t *sr
 
 cudaError_t launch_anorm(const int64_t *rp, const double *av, int32_t n, unsigned long long *anorm, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    k_anorm<<<blocks_for(n), 256, 0, s>>>(rp, av, n, anorm);
+    k_anorm<<<row_blocks(n, 1), 256, 0, s>>>(rp, av, n, anorm);
     return cudaGetLastError();
 }
 
 cudaError_t launch_residual(const int64_t *rp, const int32_t *ci, const double *av, const double *b, const double *x,
                             double *r, int32_t n, int32_t nrhs, unsigned long long *rmax, unsigned long long *xmax,
                             cudaStream_t s) {
-    const int64_t w = (int64_t)n * nrhs;
-    if (w == 0) return cudaSuccess;
-    k_residual<<<blocks_for(w), 256, 0, s>>>(rp, ci, av, b, x, r, n, nrhs, rmax, xmax);
+    if ((int64_t)n * nrhs == 0) return cudaSuccess;
+    k_residual<<<dim3(row_blocks(n, nrhs), (unsigned)nrhs), 256, 0, s>>>(rp, ci, av, b, x, r, n, rmax, xmax);
     return cudaGetLastError();
 }
 
 cudaError_t launch_absmax(const double *v, int32_t n, int32_t nrhs, unsigned long long *out, cudaStream_t s) {
-    const int64_t w = (int64_t)n * nrhs;
-    if (w == 0) return cudaSuccess;
-    k_absmax<<<blocks_for(w), 256, 0, s>>>(v, n, nrhs, out);
+    if ((int64_t)n * nrhs == 0) return cudaSuccess;
+    k_absmax<<<dim3(row_blocks(n, nrhs), (unsigned)nrhs), 256, 0, s>>>(v, n, out);
     return cudaGetLastError();
 }
 

@@ -101,7 +101,7 @@ __global__ void k_solve_level(const SolveArgs<T> a, T *y, int32_t nrhs, const So
     const int64_t *rptr = BACKWARD ? a.urow_ptr : a.lrow_ptr;
     const int64_t *pos = BACKWARD ? a.urow_pos : a.lrow_pos;
     const int32_t *col = BACKWARD ? a.urow_col : a.lrow_col;
-    const T d = BACKWARD ? a.lu[a.diag_pos[i]] : (T)1;
+    const T d = BACKWARD ? (T)1 / a.lu[a.diag_pos[i]] : (T)1;   // the reciprocal of U(i, i)
     for (int32_t r = 0; r < nrhs; r++) {
         T *yr = y + (int64_t)r * a.n;
         T s;
@@ -112,7 +112,7 @@ __global__ void k_solve_level(const SolveArgs<T> a, T *y, int32_t nrhs, const So
         } else {
             s = row_dot<T>(a.lu, pos, col, yr, rptr[i], rptr[i + 1], lane);
         }
-        if (lane == 0) yr[i] = BACKWARD ? (yr[i] - s) / d : yr[i] - s;
+        if (lane == 0) yr[i] = BACKWARD ? (yr[i] - s) * d : yr[i] - s;
     }
 }
 

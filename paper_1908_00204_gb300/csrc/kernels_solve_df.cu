@@ -1,7 +1,9 @@
 // kernels_solve_df.cu -- dataflow ("sync-free") triangular solves (sm_103a).
 //
-// The two triangular systems of Section I, forward (unit L) then backward
-// (U), in one launch.  Work items -- a row, or a chunk of a long row's dot
+// The two triangular systems of Section I: forward (unit L) items in one
+// launch, the dense tail, then backward (U) items in a second launch, so a
+// backward row finds its own forward value final.  Work items -- a row, or a
+// chunk of a long row's dot
 // product -- are listed in a topological order (each item after everything it
 // reads) and handed out by an atomic ticket, so a warp waits only on items
 // that running warps already hold: no level barriers, no co-residency
@@ -10,9 +12,9 @@
 // so they need no reset between calls.  Every wait is bounded: past the limit
 // the kernel records GLU_ERR_TIMEOUT, raises an abort flag that ends all other
 // waits, publishes its own result and carries on, so the launch always ends.
-// The backward sweep writes its own vector z: with an unsymmetric pattern a
-// backward row can be ready while a forward row still reads the forward value
-// of that row, so the two sweeps must not share storage.
+// The backward sweep writes its own vector z (y keeps the forward values).
+// A backward step multiplies by the reciprocal of U's diagonal, taken before
+// the step's waits, so no division sits on the dependency chain.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -138,8 +140,8 @@ __device__ __forceinline__ T dot_entries(const int32_t (&j)[DF_PER_LANE], const 
 // rows' entries outside the block (chunk items) are ready, the block's own
 // triangle is swept a column at a time: the owner of row jj holds its final
 // value, a shuffle broadcasts it, every other row of the block subtracts
-// L(i, jj) times it (forward), or, backward, z(jj) = y(jj) / U(jj, jj) and the
-// rows above subtract U(i, jj) z(jj).  The block being dense, column c0+jj's
+// L(i, jj) times it (forward), or, backward, z(jj) = y(jj) times the
+// reciprocal of U(jj, jj) and the rows above subtract U(i, jj) z(jj).  The block being dense, column c0+jj's
 // entries in rows c0..c1-1 are contiguous in the CSC values, at
 // diag_pos[c0+jj] - jj + i; the coefficients of BLK_PF columns are loaded
 // together, ahead of their steps.
@@ -177,7 +179,7 @@ __device__ __forceinline__ void block_item(const SolveArgs<T> &s, const DFSolveA
             ce[k] = snx[ii + 1];
             const int64_t dp = s.diag_pos[c0 + ii];
             bj[k] = dp - ii;
-            if (bwd) d[k] = s.lu[dp];
+            if (bwd) d[k] = (T)1 / s.lu[dp];   // the reciprocal of U(ii, ii)
         }
     }
     for (int32_t r = 0; r < nrhs; r++) {
@@ -188,7 +190,16 @@ __device__ __forceinline__ void block_item(const SolveArgs<T> &s, const DFSolveA
             T x = (T)0;
             if (ii < ns) {
                 x = ld_cg(y + (int64_t)r * n + c0 + ii);
-                for (int32_t c = cb[k]; c < ce[k]; c++) x -= ld_cg(partial + (int64_t)c * nrhs + r);
+                // the row's chunk partial sums in chunk order, eight loads in flight
+                for (int32_t c = cb[k]; c < ce[k]; c += 8) {
+                    T pv[8];
+#pragma unroll
+                    for (int u = 0; u < 8; u++)
+                        pv[u] = c + u < ce[k] ? ld_cg(partial + (int64_t)(c + u) * nrhs + r) : (T)0;
+#pragma unroll
+                    for (int u = 0; u < 8; u++)
+                        if (c + u < ce[k]) x -= pv[u];
+                }
             }
             v[k] = x;
         }
@@ -242,7 +253,7 @@ __device__ __forceinline__ void block_item(const SolveArgs<T> &s, const DFSolveA
                     for (int u = 0; u < BLK_PF; u++) {
                         const int32_t t = tg + BLK_PF - 1 - u;
                         const int32_t jj = kj * 32 + t;
-                        const T zo = v[kj] / d[kj];
+                        const T zo = v[kj] * d[kj];
                         const T zj = __shfl_sync(0xffffffffu, zo, t);
                         if (jj < ns) {
                             if (lane == t) v[kj] = zj;
@@ -304,12 +315,11 @@ __global__ void __launch_bounds__(128) k_solve_df(const SolveArgs<T> s, const DF
             continue;
         }
         const int32_t i = it.row;
-        // the backward row needs the forward result of its own row
-        if (bwd && lane == 0) wait_flag(a.fready + i, a.epoch, a);
-        __syncwarp();
+        // a backward launch follows the forward one and the tail, so its own
+        // row's forward value is final; d: the reciprocal of U(i, i)
         T d = (T)1, v0 = (T)0;
         if (lane == 0) {
-            if (bwd) d = s.lu[s.diag_pos[i]];
+            if (bwd) d = (T)1 / s.lu[s.diag_pos[i]];
             v0 = ld_cg(y + i);    // c(i) forward, y(i) backward, first side
         }
         if (it.ce > it.cb) {
@@ -325,7 +335,7 @@ __global__ void __launch_bounds__(128) k_solve_df(const SolveArgs<T> s, const DF
                     T acc = (T)0;
                     for (int32_t c = it.cb; c < it.ce; c++) acc += ld_cg(partial + (int64_t)c * nrhs + r);
                     const T v = r == 0 ? v0 : ld_cg(y + (int64_t)r * n + i);
-                    (bwd ? z : y)[(int64_t)r * n + i] = bwd ? (v - acc) / d : v - acc;
+                    (bwd ? z : y)[(int64_t)r * n + i] = bwd ? (v - acc) * d : v - acc;
                 }
             }
         } else {
@@ -336,7 +346,7 @@ __global__ void __launch_bounds__(128) k_solve_df(const SolveArgs<T> s, const DF
                 const T acc = dot_entries<T>(j, l, src + (int64_t)r * n);
                 if (lane == 0) {
                     const T v = r == 0 ? v0 : ld_cg(y + (int64_t)r * n + i);
-                    (bwd ? z : y)[(int64_t)r * n + i] = bwd ? (v - acc) / d : v - acc;
+                    (bwd ? z : y)[(int64_t)r * n + i] = bwd ? (v - acc) * d : v - acc;
                 }
             }
         }
@@ -347,15 +357,46 @@ __global__ void __launch_bounds__(128) k_solve_df(const SolveArgs<T> s, const DF
 
 // The dense tail, one block, one tail row per thread (at most 1024 rows),
 // its running value in a register, columns taken TAIL_TB at a time.  For a
-// panel of columns j0..j0+TB-1 every thread loads its coefficients in them;
-// the warp owning the panel's rows solves the panel's triangle with shuffles
-// (row j0+u is final after the panel's columns before u), publishes the
-// values in shared memory, and after one barrier every row below subtracts
-// the panel's columns in order.  The backward sweep mirrors it (z(jj) =
-// y(jj) / U(jj, jj), rows above, columns descending).  Each row applies the
-// columns in the same order as a column-at-a-time sweep.  The tail column
-// jj's entries are contiguous in the CSC values.
-constexpr int TAIL_TB = 16;
+// panel of columns j0..j0+TB-1 the warp owning the panel's rows solves the
+// panel's triangle with shuffles (row j0+u is final after the panel's
+// columns before u), publishes the values in shared memory, and after one
+// barrier every row below subtracts the panel's columns in order.  The
+// backward sweep mirrors it (z(jj) = y(jj) times the reciprocal of U(jj, jj),
+// taken once per row before the sweeps; rows above, columns descending).
+// Each row applies the columns in the same order as a column-at-a-time
+// sweep.  The tail column jj's entries are contiguous in the CSC values: the
+// block is prefetched into L2 first, and every thread copies its own row's
+// coefficients of the next panel into shared memory (cp.async) while the
+// current panel runs.
+constexpr int TAIL_TB = 8;
+
+__device__ __forceinline__ void cp_async_tail(void *dst, const void *src, int bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if (bytes == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// barrier 1 over the first `threads` threads of the block (whole warps)
+__device__ __forceinline__ void tail_bar(int threads) { asm volatile("bar.sync 1, %0;" ::"r"(threads) : "memory"); }
+
+// Row ii's coefficients in the panel at j0 (forward: L(ii, j0+u) for ii > j0+u;
+// backward: U(ii, j0+u) for ii < j0+u) into buf[u * NT + ii], one commit group.
+template <typename T>
+__device__ __forceinline__ void tail_panel_issue(T *buf, const T *lu, const int64_t *colbase, int32_t j0, int32_t NT,
+                                                 int32_t ii, bool bwd) {
+    if (ii < NT) {
+        const int32_t jn = min(TAIL_TB, NT - j0);
+#pragma unroll
+        for (int u = 0; u < TAIL_TB; u++)
+            if (u < jn && (bwd ? ii < j0 + u : ii > j0 + u))
+                cp_async_tail(buf + u * NT + ii, lu + colbase[j0 + u] + ii, (int)sizeof(T));
+    }
+    cp_async_commit();
+}
 
 template <typename T>
 __global__ void __launch_bounds__(1024) k_solve_tail(const SolveArgs<T> s, const int64_t *__restrict__ lu_colptr,
@@ -366,28 +407,66 @@ __global__ void __launch_bounds__(1024) k_solve_tail(const SolveArgs<T> s, const
     int64_t *lcol = reinterpret_cast<int64_t *>(smem_raw);   // L(t0+ii, t0+jj) at lcol[jj] + ii
     int64_t *ucol = lcol + NT;                                // U(t0+ii, t0+jj) at ucol[jj] + ii
     T *bc = reinterpret_cast<T *>(ucol + NT);                 // published values
-    const int32_t ii = threadIdx.x;
+    T *cf = bc + NT;                                          // [2][TAIL_TB][NT]: panel coefficients
+    const int32_t ii = threadIdx.x, nwarp = blockDim.x >> 5;
     const bool own = ii < NT;
     for (int32_t q = ii; q < NT; q += blockDim.x) {
         lcol[q] = s.diag_pos[t0 + q] - q;
         ucol[q] = lu_colptr[t0 + q + 1] - NT;
     }
     __syncthreads();
-    const T d = own ? s.lu[lcol[ii] + ii] : (T)1;
+    // the tail block's values (NT contiguous entries per column) into L2
+    // ahead of the panels, kept there over the streaming sweeps
+    {
+        const int32_t lines = (int32_t)(((int64_t)NT * sizeof(T) + 127) / 128) + 1;
+        for (int64_t q = ii; q < (int64_t)NT * lines; q += blockDim.x) {
+            const int32_t j = (int32_t)(q / lines), k = (int32_t)(q - (int64_t)j * lines);
+            const char *p0 = reinterpret_cast<const char *>(s.lu + lcol[j]);
+            const char *pl = p0 + (int64_t)k * 128;
+            if (pl < reinterpret_cast<const char *>(s.lu + lcol[j] + NT))
+                asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(pl));
+        }
+    }
+    // the reciprocal of the row's diagonal, taken once off the panels' chains
+    const T rd = own ? (T)1 / s.lu[lcol[ii] + ii] : (T)1;
+    const int32_t npanel = (NT + TAIL_TB - 1) / TAIL_TB;
     for (int32_t r = 0; r < nrhs; r++) {
         T v = (T)0;
         if (own) {
             v = __ldcg(y + (int64_t)r * n + t0 + ii);
-            for (int32_t c = ta.cb[ii]; c < ta.ce[ii]; c++) v -= __ldcg(fpartial + (int64_t)c * nrhs + r);
+            // the row's chunk partial sums, in chunk order, eight loads in flight
+            for (int32_t c = ta.cb[ii]; c < ta.ce[ii]; c += 8) {
+                T pv[8];
+#pragma unroll
+                for (int u = 0; u < 8; u++)
+                    pv[u] = c + u < ta.ce[ii] ? __ldcg(fpartial + (int64_t)(c + u) * nrhs + r) : (T)0;
+#pragma unroll
+                for (int u = 0; u < 8; u++)
+                    if (c + u < ta.ce[ii]) v -= pv[u];
+            }
         }
-        // forward, panels j0 = 0, TB, 2TB, ... (a panel's rows lie in one warp)
-        for (int32_t j0 = 0; j0 < NT; j0 += TAIL_TB) {
-            const int32_t jn = min(TAIL_TB, NT - j0);
+        // forward, panels j0 = 0, TB, 2TB, ... (a panel's rows lie in one
+        // warp); a warp whose rows all lie above the panel is done with the
+        // sweep and leaves it, the others meet at a barrier sized to them
+        const int32_t w = ii >> 5;
+        tail_panel_issue<T>(cf, s.lu, lcol, 0, NT, ii, false);
+        for (int32_t p = 0; p < npanel; p++) {
+            const int32_t j0 = p * TAIL_TB, jn = min(TAIL_TB, NT - j0);
+            if (w < (j0 >> 5)) {
+                cp_async_wait_all();
+                break;
+            }
+            T *cur = cf + (p & 1) * TAIL_TB * NT;
+            if (p + 1 < npanel) {
+                tail_panel_issue<T>(cf + ((p + 1) & 1) * TAIL_TB * NT, s.lu, lcol, j0 + TAIL_TB, NT, ii, false);
+                cp_async_wait_prev();
+            } else {
+                cp_async_wait_all();
+            }
             T lv[TAIL_TB];
 #pragma unroll
-            for (int u = 0; u < TAIL_TB; u++)
-                lv[u] = (own && u < jn && ii > j0 + u) ? s.lu[lcol[j0 + u] + ii] : (T)0;
-            if ((ii >> 5) == (j0 >> 5)) {
+            for (int u = 0; u < TAIL_TB; u++) lv[u] = (own && u < jn && ii > j0 + u) ? cur[u * NT + ii] : (T)0;
+            if (w == (j0 >> 5)) {
                 const int base = j0 & 31;
                 const bool inside = own && ii >= j0 && ii < j0 + jn;
 #pragma unroll
@@ -399,7 +478,7 @@ __global__ void __launch_bounds__(1024) k_solve_tail(const SolveArgs<T> s, const
                 }
                 if (inside) bc[ii] = v;
             }
-            __syncthreads();
+            tail_bar((nwarp - (j0 >> 5)) * 32);
             if (own && ii >= j0 + jn) {
 #pragma unroll
                 for (int u = 0; u < TAIL_TB; u++)
@@ -407,21 +486,34 @@ __global__ void __launch_bounds__(1024) k_solve_tail(const SolveArgs<T> s, const
             }
         }
         __syncthreads();
-        // backward, panels from the last (aligned) one down
+        // backward, panels from the last (aligned) one down; a warp whose rows
+        // all lie below the panel is done
         T *zr = z + (int64_t)r * n;
-        for (int32_t j0 = ((NT - 1) / TAIL_TB) * TAIL_TB; j0 >= 0; j0 -= TAIL_TB) {
-            const int32_t jn = min(TAIL_TB, NT - j0);
+        tail_panel_issue<T>(cf, s.lu, ucol, (npanel - 1) * TAIL_TB, NT, ii, true);
+        for (int32_t p = npanel - 1, k = 0; p >= 0; p--, k++) {
+            const int32_t j0 = p * TAIL_TB, jn = min(TAIL_TB, NT - j0);
+            const int32_t wlast = (j0 + jn - 1) >> 5;
+            if (w > wlast) {
+                cp_async_wait_all();
+                break;
+            }
+            T *cur = cf + (k & 1) * TAIL_TB * NT;
+            if (p > 0) {
+                tail_panel_issue<T>(cf + ((k + 1) & 1) * TAIL_TB * NT, s.lu, ucol, j0 - TAIL_TB, NT, ii, true);
+                cp_async_wait_prev();
+            } else {
+                cp_async_wait_all();
+            }
             T lv[TAIL_TB];
 #pragma unroll
-            for (int u = 0; u < TAIL_TB; u++)
-                lv[u] = (own && u < jn && ii < j0 + u) ? s.lu[ucol[j0 + u] + ii] : (T)0;
-            if ((ii >> 5) == (j0 >> 5)) {
+            for (int u = 0; u < TAIL_TB; u++) lv[u] = (own && u < jn && ii < j0 + u) ? cur[u * NT + ii] : (T)0;
+            if (w == (j0 >> 5)) {
                 const int base = j0 & 31;
                 const bool inside = own && ii >= j0 && ii < j0 + jn;
 #pragma unroll
                 for (int u = TAIL_TB - 1; u >= 0; u--) {
                     if (u < jn) {
-                        if (inside && ii == j0 + u) v = v / d;
+                        if (inside && ii == j0 + u) v = v * rd;
                         const T zu = __shfl_sync(0xffffffffu, v, base + u);
                         if (inside && ii < j0 + u) v = v - lv[u] * zu;
                     }
@@ -431,7 +523,7 @@ __global__ void __launch_bounds__(1024) k_solve_tail(const SolveArgs<T> s, const
                     zr[t0 + ii] = v;
                 }
             }
-            __syncthreads();
+            tail_bar((wlast + 1) * 32);
             if (own && ii < j0) {
 #pragma unroll
                 for (int u = TAIL_TB - 1; u >= 0; u--)
@@ -451,8 +543,11 @@ cudaError_t launch_solve_tail(const SolveArgs<T> &s, const int64_t *lu_colptr, c
     const int32_t NT = s.n - t.t0;
     if (NT <= 0) return cudaSuccess;
     if (NT > 1024) return cudaErrorInvalidValue;
-    const size_t smem = 2 * (size_t)NT * sizeof(int64_t) + (size_t)NT * sizeof(T);
-    k_solve_tail<T><<<1, 1024, smem, st>>>(s, lu_colptr, t, fpartial, y, z, nrhs);
+    const size_t smem = 2 * (size_t)NT * sizeof(int64_t) + (size_t)NT * (1 + 2 * TAIL_TB) * sizeof(T);
+    cudaError_t e = cudaFuncSetAttribute(k_solve_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    // one thread per tail row, whole warps
+    k_solve_tail<T><<<1, (unsigned)((NT + 31) / 32 * 32), smem, st>>>(s, lu_colptr, t, fpartial, y, z, nrhs);
     return cudaGetLastError();
 }
 
