@@ -204,8 +204,6 @@ cudaError_t launch_block_level(const BlockArgs<T> &a, int map_bytes, int32_t d0,
 cudaError_t launch_bmap_build(const BlockArgs<double> &a, int map_bytes, int64_t npairs, int num_sms, cudaStream_t s);
 // Dense LU of the trailing block (one cooperative launch, grid barriers).
 template <typename T>
-int32_t dense_tail_panel(int32_t nt);
-template <typename T>
 cudaError_t launch_dense_tail(T *lu, const DenseTailArgs &d, const GridBarrier &bar, int num_sms, cudaStream_t s);
 template <typename T>
 cudaError_t launch_pivot_check(const T *lu, const int64_t *diag_pos, int32_t n,
