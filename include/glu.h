@@ -108,8 +108,9 @@ typedef struct glu_options {
     int32_t host_only;        /* 1: run the host analysis only; no device memory is
                                  touched and the handle can only report the analysis
                                  (glu_get_fill / deps / levels / stats) */
-    int32_t solve_mode;       /* 1 (default): dataflow solve, one launch with per-row
-                                 ready flags; 0: one launch per solve level */
+    int32_t solve_mode;       /* 1 (default): dataflow solve, a forward and a backward
+                                 launch (the dense tail between them), items waiting on
+                                 per-row ready flags; 0: one launch per solve level */
     int32_t spin_limit_us;    /* bound on any device-side wait, microseconds
                                  (default 2,000,000); past it GLU_ERR_TIMEOUT */
     int32_t fault_row;        /* testing only: in the dataflow solve this row never
@@ -244,10 +245,12 @@ int glu_factor_f32(glu_handle *h, const double *values);
 /* Mixed-precision solve: FP32 triangular solves with the glu_factor_f32
  * factors, FP64 iterative refinement on the GPU (r = b - A x with the FP64
  * values, x += d in FP64), until the normwise backward error of every side is
- * <= tol or maxit corrections were applied.  b, x: nrhs vectors of length n,
- * host or device.  info may be NULL.  Not converging is not an error: check
- * info->converged.  Errors: GLU_ERR_NOT_FACTORED (no FP32 factorization),
- * GLU_ERR_INVALID, pending device errors. */
+ * <= tol or maxit corrections were applied.  The iterate starts at x = 0, so
+ * the first FP32 solve is of b itself; each later solve is of the residual.
+ * b, x: nrhs vectors of length n, host or device.  info may be NULL.  Not
+ * converging is not an error: check info->converged.  Errors:
+ * GLU_ERR_NOT_FACTORED (no FP32 factorization), GLU_ERR_INVALID, pending
+ * device errors. */
 int glu_solve_refine(glu_handle *h, const double *b, double *x, int32_t nrhs, double tol, int32_t maxit,
                      glu_refine_info *info);
 
