@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--batched", action="store_true",
                     help="instead of the step: the batched FP64 refactorization of 256 value sets of the "
                          "20k-unknown matrix, timed per factorization, with its bandwidth roofline")
+    ap.add_argument("--sets", type=int, default=256, help="with --batched: the number of value sets")
     ap.add_argument("--latency", action="store_true",
                     help="instead of the step: the launch/latency-bound small patterns (32x32 grid in natural "
                          "order, the 5k serving pattern): microseconds per level against the floor of a CUDA "
@@ -596,12 +597,13 @@ def run_serve(args):
 
 
 def run_batched(args):
-    """The batched refactorization alone: 256 Monte-Carlo value sets of the
+    """The batched refactorization: 256 (--sets) Monte-Carlo value sets of the
     20k-unknown matrix in one graph launch, CUDA events per factorization, L2
     flushed between them.  Lanes run over value sets, so every update streams
     the target (read + write) and L(i,j) of 32 sets at a time: the algorithmic
-    bytes per update and set are 16 (targets only, L from cache) to 24."""
-    B = 256
+    bytes per update and set are 16 (targets only, L from cache) to 24.  Also
+    the batched solve of 4 right-hand sides per set, timed the same way."""
+    B = max(1, args.sets)
     # the oracle baseline first: its processes start before any GPU call
     cpu = None if args.no_cpu_baseline else cpu_batched_baseline("mesh100x200_nets64",
                                                                  [100 + i for i in range(B)])
@@ -630,14 +632,27 @@ def run_batched(args):
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1))
     g.glu_sync(hb)
+    R = torch.from_numpy(np.stack([synth.rhs(mb.n, 4, 300 + i) for i in range(B)])).to(dev)
+    g.glu_solve_batched(hb, R)
+    torch.cuda.synchronize()
+    ts_solve = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.glu_solve_batched(hb, R)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts_solve.append(e0.elapsed_time(e1))
     st = g.glu_get_stats(hb)
     ms = float(np.median(ts))
     upd = float(st["n_updates"]) * B
     hbm = measured_hbm_gbs()
     lo, hi = 16.0 * upd / (ms * 1e-3) / 1e9, 24.0 * upd / (ms * 1e-3) / 1e9
-    line = {"metric": "batched FP64 refactorizations per second (256 value sets, n=20,064)",
+    line = {"metric": f"batched FP64 refactorizations per second ({B} value sets, n=20,064)",
             "value": B * 1e3 / ms, "unit": "refactorizations/s", "higher_is_better": True,
-            "ms_per_batch": ms, "gflops": st["flops"] * B / (ms * 1e-3) / 1e9, "dtype": "f64",
+            "ms_per_batch": ms, "solve_ms_per_batch_4rhs": float(np.median(ts_solve)),
+            "gflops": st["flops"] * B / (ms * 1e-3) / 1e9, "dtype": "f64",
             "roofline": {"bound": "hbm", "achieved": lo, "achieved_upper": hi, "peak": hbm, "unit": "GB/s",
                          "frac": lo / hbm if hbm else None, "frac_upper": hi / hbm if hbm else None,
                          "traffic": None, "kernel": "k_level_b (one level of the batched sweep)",

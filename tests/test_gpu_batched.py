@@ -92,3 +92,24 @@ def test_batched_errors(glu):
     with pytest.raises(glu.GluError) as e:
         glu.glu_factor_batched(h, V)
     assert e.value.code == glu.glu.GLU_ERR_ZERO_PIVOT and e.value.column == 0
+
+
+@pytest.mark.parametrize("nrhs", [1, 3, 5, 8])
+def test_batched_solve_nrhs(glu, nrhs):
+    """The batched dataflow solve for right-hand-side counts that exercise
+    every path: fewer sides than copies of a dense block item (idle copies
+    still publish the block), more (a copy takes sides q and q + 4), and the
+    four/two/one-side forms of the row items; 40 sets, so two lane groups and
+    padded lanes."""
+    m = synth.make("mesh100x200_nets64", 1)
+    B = 40
+    V = value_sets(m, B, base=9)
+    rhs = np.stack([synth.rhs(m.n, nrhs, 900 + b) for b in range(B)])    # (B, nrhs, n)
+    h = glu.glu_analyze(m.n, m.colptr, m.rowidx, m.perm)
+    glu.glu_factor_batched(h, torch.from_numpy(V).cuda())
+    x = glu.glu_solve_batched(h, torch.from_numpy(rhs).cuda()).cpu().numpy()
+    for b in range(B):
+        assert backward_error(m.n, m.colptr, m.rowidx, V[b], rhs[b], x[b]) <= BERR_TOL, b
+    f = oracle.Factorization(m.n, m.colptr, m.rowidx, m.perm, V[B - 1])
+    xr = f.solve(rhs[B - 1])
+    assert np.abs(x[B - 1] - xr).max() <= 1e-10 * np.abs(xr).max()
