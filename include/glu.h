@@ -148,9 +148,10 @@ typedef struct glu_options {
     int32_t lane_max;         /* tasks of at most this many updates ... (GLU_LANE_MAX, 32) */
     int32_t lane_segs;        /* ... and this many segments run on one lane (KIND_LANE;
                                  GLU_LANE_SEGS, 2) */
-    int32_t gpu_analysis;     /* 1: glu_analyze runs Algorithm 4 (the dependency lists)
-                                 and the longest-path levels on the current GPU (the
-                                 same result as the host's); 0 (default): on the host */
+    int32_t gpu_analysis;     /* 1 (default): glu_analyze runs Algorithm 4 (the
+                                 dependency lists) and the longest-path levels on the
+                                 current GPU (the same result as the host's); 0: on the
+                                 host.  A host_only analysis always runs on the host */
 } glu_options;
 
 /* Device memory the position map may take before row_lookup 0 switches to

@@ -1027,7 +1027,7 @@ void build_df(const HostPlan &P, int64_t chunk, int32_t t0, int32_t blocks, std:
         for (int64_t p = b; p < e; p += chunk) ch.push_back(SolveChunk{p, std::min(e, p + chunk)});
     };
     auto chunk_recs = [&](bool bwd, const std::vector<SolveChunk> &ch, int32_t c_begin, const std::vector<int32_t> &lv,
-                          const std::vector<int32_t> &colv, int32_t row, std::vector<Rec> &recs) {
+                          const int32_t *colv, int32_t row, std::vector<Rec> &recs) {
         for (int32_t c = c_begin; c < (int32_t)ch.size(); c++) {
             int32_t m = 0;
             for (int64_t p = ch[c].p0; p < ch[c].p1; p++) m = std::max(m, lv[colv[p]] + 1);
@@ -1054,7 +1054,7 @@ void build_df(const HostPlan &P, int64_t chunk, int32_t t0, int32_t blocks, std:
                 const int32_t cb = (int32_t)dff.size();
                 snx_f.push_back(cb);
                 add_chunks(dff, b, e);
-                chunk_recs(false, dff, cb, lf, P.lrow_col, r, frec);
+                chunk_recs(false, dff, cb, lf, P.lrow_col.data(), r, frec);
             }
             snx_f.push_back((int32_t)dff.size());
             for (int32_t r = c0; r < c1; r++) lf[r] = lev;
@@ -1070,7 +1070,7 @@ void build_df(const HostPlan &P, int64_t chunk, int32_t t0, int32_t blocks, std:
         if (e - b > chunk) {
             add_chunks(dff, b, e);
             ce = (int32_t)dff.size();
-            chunk_recs(false, dff, cb, lf, P.lrow_col, i, frec);
+            chunk_recs(false, dff, cb, lf, P.lrow_col.data(), i, frec);
         }
         frec.push_back(Rec{lev, 1, (int32_t)frec.size(), {i, cb, ce, -1, 0, 0, 0, 0}});
         i++;
@@ -1084,7 +1084,7 @@ void build_df(const HostPlan &P, int64_t chunk, int32_t t0, int32_t blocks, std:
         add_chunks(dff, b, e);
         tcb[i - t0] = cb;
         tce[i - t0] = (int32_t)dff.size();
-        chunk_recs(false, dff, cb, lf, P.lrow_col, i, frec);
+        chunk_recs(false, dff, cb, lf, P.lrow_col.data(), i, frec);
     }
     finish(frec);
     // ---- backward (U), rows descending; the tail is solved before
@@ -1102,7 +1102,7 @@ void build_df(const HostPlan &P, int64_t chunk, int32_t t0, int32_t blocks, std:
                 const int32_t cb = (int32_t)dfb.size();
                 snx_b.push_back(cb);
                 add_chunks(dfb, b, e);
-                chunk_recs(true, dfb, cb, lb, P.urow_col, r, brec);
+                chunk_recs(true, dfb, cb, lb, P.urow_col.data(), r, brec);
             }
             snx_b.push_back((int32_t)dfb.size());
             for (int32_t r = c0; r < c1; r++) lb[r] = lev;
@@ -1118,7 +1118,7 @@ void build_df(const HostPlan &P, int64_t chunk, int32_t t0, int32_t blocks, std:
         if (e - b > chunk) {
             add_chunks(dfb, b, e);
             ce = (int32_t)dfb.size();
-            chunk_recs(true, dfb, cb, lb, P.urow_col, i, brec);
+            chunk_recs(true, dfb, cb, lb, P.urow_col.data(), i, brec);
         }
         brec.push_back(Rec{lev, 1, (int32_t)brec.size(), {i, cb, ce, -1, 1, 0, 0, 0}});
         i--;

@@ -150,8 +150,8 @@ __global__ void k_levels(const LevelArgs a) {
     }
 }
 
-template <typename T>
-cudaError_t up(T **d, const std::vector<T> &v) {
+template <typename T, typename A>
+cudaError_t up(T **d, const std::vector<T, A> &v) {
     cudaError_t e = cudaMalloc(d, std::max<size_t>(v.size(), 1) * sizeof(T));
     if (e == cudaSuccess && !v.empty()) e = cudaMemcpy(*d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
     return e;

@@ -915,6 +915,7 @@ void glu_default_options(glu_options *o) {
     o->solve_tail = 1;
     o->factor_tail = 1;
     o->solve_blocks = 1;
+    o->gpu_analysis = 1;
 }
 
 int glu_analyze_opts(int32_t n, const int32_t *colptr, const int32_t *rowidx, const int32_t *perm,

@@ -203,8 +203,8 @@ struct HostPlan {
     std::vector<int32_t> lvl_total, lvl_ntasks, lvl_item_ptr;
     // solve schedule (row views of L and U, levels)
     std::vector<int64_t> lrow_ptr, urow_ptr;
-    std::vector<int32_t> lrow_col, urow_col;
-    std::vector<int64_t> lrow_pos, urow_pos;
+    std::vector<int32_t, NoInitAllocator<int32_t>> lrow_col, urow_col;
+    std::vector<int64_t, NoInitAllocator<int64_t>> lrow_pos, urow_pos;
     std::vector<int32_t> fwd_ptr, fwd_rows, bwd_ptr, bwd_rows;
     // per solve level: rows (with their chunk ranges) and chunks
     std::vector<SolveRow> fwd_items, bwd_items;
