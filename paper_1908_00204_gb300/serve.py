@@ -107,6 +107,7 @@ class _Slot:
         self.out = None
         self.info = None
         self.error = None       # (code, column) raised while enqueueing
+        self.pinned = {}        # page-locked staging buffers of this slot, by use
 
 
 class Server:
@@ -268,6 +269,23 @@ class Server:
         self.batch_sizes.append(take)
         return True
 
+    def _staged(self, slot: _Slot, name: str, shape):
+        """A host buffer of `shape` doubles for one copy to the device:
+        page-locked and kept by the slot (grown when too small), so the copy
+        runs asynchronously on the slot's stream; reused only once the slot's
+        work has finished.  Returns its numpy view and its tensor."""
+        torch = self.torch
+        count = int(np.prod(shape))
+        if not hasattr(torch, "empty"):          # a host-only stand-in for torch
+            a = np.empty(shape)
+            return a, torch.from_numpy(a)
+        buf = slot.pinned.get(name)
+        if buf is None or buf.numel() < count:
+            buf = torch.empty(max(count, 1), dtype=torch.float64, pin_memory=True)
+            slot.pinned[name] = buf
+        t = buf[:count].view(*shape)
+        return t.numpy(), t
+
     def _enqueue(self, slot: _Slot, res: _Resident, reqs: List[Request], nrhs: int) -> None:
         """The batch's factorization and solve, on the slot's stream."""
         torch = self.torch
@@ -275,8 +293,12 @@ class Server:
         take = len(reqs)
         if take == 1:
             r = reqs[0]
-            v = torch.from_numpy(r.values).to(self.device, non_blocking=True)
-            bb = torch.from_numpy(np.ascontiguousarray(r.b)).to(self.device, non_blocking=True)
+            va, vt = self._staged(slot, "v", r.values.shape)
+            va[...] = r.values
+            ba, bt = self._staged(slot, "b", r.b.shape)
+            ba[...] = r.b
+            v = vt.to(self.device, non_blocking=True)
+            bb = bt.to(self.device, non_blocking=True)
             if self.precision == "fp64":
                 _glu.glu_factor(h, v)
                 x = _glu.glu_solve(h, bb)
@@ -290,14 +312,15 @@ class Server:
             # the last request (their results are discarded)
             S = (take + 31) // 32 * 32
             res.batch_bytes = max(res.batch_bytes, self._batch_bytes(res, S, nrhs))
-            V = np.empty((S, reqs[0].values.size))
-            Bt = np.zeros((S, nrhs, res.pat.n))
+            V, Vt = self._staged(slot, "V", (S, reqs[0].values.size))
+            Bt, Btt = self._staged(slot, "B", (S, nrhs, res.pat.n))
             for i in range(S):
                 r = reqs[min(i, take - 1)]
                 V[i] = r.values
                 Bt[i, : r.b.shape[0]] = r.b
-            Vd = torch.from_numpy(V).to(self.device, non_blocking=True)
-            Bd = torch.from_numpy(Bt).to(self.device, non_blocking=True)
+                Bt[i, r.b.shape[0]:] = 0.0
+            Vd = Vt.to(self.device, non_blocking=True)
+            Bd = Btt.to(self.device, non_blocking=True)
             if self.precision == "fp64":
                 _glu.glu_factor_batched(h, Vd)
                 x = _glu.glu_solve_batched(h, Bd)
