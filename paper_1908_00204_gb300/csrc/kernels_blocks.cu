@@ -156,18 +156,8 @@ __global__ void __launch_bounds__(BW * 32) k_bupdate(const BlockArgs<T> a, int32
                 um = a.lu[bp.upos + (lane - bp.f)];
                 lc = a.colptr[c0 + lane + 1] - r;
             }
-            T acc[BU_ROWS];
-#pragma unroll
-            for (int u = 0; u < BU_ROWS; u++) acc[u] = (T)0;
-            for (int32_t m = bp.f; m < s; m++) {
-                const T um_b = __shfl_sync(0xffffffffu, um, m);
-                const int64_t lcm = __shfl_sync(0xffffffffu, lc, m);
-#pragma unroll
-                for (int u = 0; u < BU_ROWS; u++) {
-                    const int32_t t = seg.t0 + lane + 32 * u;
-                    if (t < seg.t1) acc[u] = fma(a.lu[lcm + t], um_b, acc[u]);
-                }
-            }
+            // the targets' offsets and values first: they do not depend on
+            // the products, so their loads overlap the L21 loop below
             T *tgt = a.lu + a.colptr[bp.k];
             const M *mp = map + bp.mb;
             uint32_t off[BU_ROWS];
@@ -180,6 +170,18 @@ __global__ void __launch_bounds__(BW * 32) k_bupdate(const BlockArgs<T> a, int32
 #pragma unroll
             for (int u = 0; u < BU_ROWS; u++)
                 if (seg.t0 + lane + 32 * u < seg.t1) tv[u] = tgt[off[u]];
+            T acc[BU_ROWS];
+#pragma unroll
+            for (int u = 0; u < BU_ROWS; u++) acc[u] = (T)0;
+            for (int32_t m = bp.f; m < s; m++) {
+                const T um_b = __shfl_sync(0xffffffffu, um, m);
+                const int64_t lcm = __shfl_sync(0xffffffffu, lc, m);
+#pragma unroll
+                for (int u = 0; u < BU_ROWS; u++) {
+                    const int32_t t = seg.t0 + lane + 32 * u;
+                    if (t < seg.t1) acc[u] = fma(a.lu[lcm + t], um_b, acc[u]);
+                }
+            }
 #pragma unroll
             for (int u = 0; u < BU_ROWS; u++)
                 if (seg.t0 + lane + 32 * u < seg.t1) tgt[off[u]] = tv[u] - acc[u];
@@ -220,10 +222,12 @@ __global__ void k_bmap_build(const BlockArgs<double> a, int64_t npairs) {
     }
 }
 
+// One work item per warp: the items' costs vary widely, and the block
+// scheduler balances them better than a grid-stride split (200k workload
+// 65.7 -> 58.5 ms FP64 against 8 blocks per SM)
 unsigned warps_grid(int64_t warps, int num_sms) {
-    int64_t blocks = (warps + BW - 1) / BW;
-    const int64_t cap = (int64_t)num_sms * 8;
-    if (blocks > cap) blocks = cap;
+    (void)num_sms;
+    const int64_t blocks = (warps + BW - 1) / BW;
     return (unsigned)(blocks < 1 ? 1 : blocks);
 }
 
