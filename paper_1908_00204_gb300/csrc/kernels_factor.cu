@@ -455,15 +455,20 @@ __device__ __forceinline__ void lane_task(const FactorArgs<T> &a, const Task &tk
     }
 }
 
-constexpr int LEVEL_WARPS = 4;
+// One warp per block: a block retires, and its slot goes to the next level's
+// blocks, as soon as its own warp is done, and the block scheduler places
+// each warp on its own (200k workload 21.4 -> 20.6 ms FP64, 14.5 -> 13.8 ms
+// FP32 against blocks of 4 warps; 2 warps 21.1 ms, 8 warps 22.4 ms; the same
+// factors bit for bit).
+constexpr int LEVEL_WARPS = 1;
 #ifndef GLU_LEVEL_BLOCKS_PER_SM
-#define GLU_LEVEL_BLOCKS_PER_SM 4   // resident k_level blocks per SM the launch aims for
+#define GLU_LEVEL_BLOCKS_PER_SM 16  // resident k_level blocks per SM the launch aims for
 #endif
 #ifndef GLU_LEVEL_BLOCKS_PER_SM_F32
-#define GLU_LEVEL_BLOCKS_PER_SM_F32 6
+#define GLU_LEVEL_BLOCKS_PER_SM_F32 24
 #endif
 #ifndef GLU_LEVEL_CAP_BIG_F32
-#define GLU_LEVEL_CAP_BIG_F32 6
+#define GLU_LEVEL_CAP_BIG_F32 24
 #endif
 #ifndef GLU_LEVEL_BIG_ITEMS
 #define GLU_LEVEL_BIG_ITEMS 8192
@@ -471,10 +476,11 @@ constexpr int LEVEL_WARPS = 4;
 // By precision: the resident blocks per SM k_level is compiled for (its
 // register budget), the grid cap in blocks per SM, and the cap for a level of
 // at least GLU_LEVEL_BIG_ITEMS work items.  FP32 needs fewer registers: it is
-// compiled for 6 blocks, and a wide level's grid of 6 per SM lets the block
-// scheduler balance its uneven items (200k workload 16.1 -> 14.5 ms); narrower
-// levels keep 4 per SM (a level of 2-8 k items lost with 6).  FP64 stays at 4:
-// 5 gained 1 % at 200k and lost 2-3 % on the 20k and 50k patterns.
+// compiled for 24 warps per SM, and a wide level's grid of 24 per SM lets the
+// block scheduler balance its uneven items (200k workload 16.1 -> 14.5 ms with
+// blocks of 4 warps); narrower levels keep 16 per SM (a level of 2-8 k items
+// lost with 24).  FP64 stays at 16 warps: 20 gained 1-2.5 % at 200k and lost
+// 1-9 % on the 20k and 50k patterns.
 template <typename T>
 struct LevelOcc {
     static constexpr int blocks = GLU_LEVEL_BLOCKS_PER_SM;
@@ -673,7 +679,7 @@ __device__ __forceinline__ void publish_task(const DFFactorArgs &d, int32_t task
 }
 
 template <typename T, typename M>
-__global__ void __launch_bounds__(LEVEL_WARPS * 32, 3)
+__global__ void __launch_bounds__(LEVEL_WARPS * 32, 12 / LEVEL_WARPS)
 k_levels_df(const FactorArgs<T> a, const DFFactorArgs d) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -894,9 +900,9 @@ cudaError_t launch_level(const FactorArgs<T> &a, int lookup, const LevelRange &r
                           (r.n_end - r.n_begin);
     if (items <= 0) return cudaSuccess;
     int64_t blocks = (items + LEVEL_WARPS - 1) / LEVEL_WARPS;
-    // at most the resident capacity (LevelOcc: 4 blocks per SM; FP32 levels
-    // of many items 6): the next level's early blocks then take only slots
-    // this level no longer needs
+    // at most the resident capacity (LevelOcc: 16 one-warp blocks per SM;
+    // FP32 levels of many items 24): the next level's early blocks then take
+    // only slots this level no longer needs
     const int64_t cap = (int64_t)num_sms * (items >= GLU_LEVEL_BIG_ITEMS ? LevelOcc<T>::cap_big : LevelOcc<T>::cap);
     if (blocks > cap) blocks = cap;
     const size_t smem = sizeof(T) * LEVEL_WARPS * 32 * (SRC_SLOTS + 1);
