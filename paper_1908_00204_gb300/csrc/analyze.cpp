@@ -250,11 +250,13 @@ int symbolic(HostPlan &P, const std::vector<int64_t> &bptr, const std::vector<in
         std::vector<int32_t> &mark = sc.mark, &stk = sc.stk, &found = sc.found;
         std::vector<int64_t> &nxt = sc.nxt;
         found.clear();
+        int32_t lo = n;   // smallest row found
         for (int64_t q = bptr[j]; q < bptr[j + 1]; q++) {
             const int32_t s = brow[q];
             if (mark[s] == j) continue;
             mark[s] = j;
             found.push_back(s);
+            lo = std::min(lo, s);
             if (s >= j) continue;
             int32_t top = 0;
             stk[0] = s;
@@ -273,6 +275,7 @@ int symbolic(HostPlan &P, const std::vector<int64_t> &bptr, const std::vector<in
                 nxt[top] = t + 1;
                 mark[w] = j;
                 found.push_back(w);
+                lo = std::min(lo, w);
                 if (w < j) {
                     top++;
                     stk[top] = w;
@@ -280,7 +283,16 @@ int symbolic(HostPlan &P, const std::vector<int64_t> &bptr, const std::vector<in
                 }
             }
         }
-        std::sort(found.begin(), found.end());
+        // ascending order: a set that fills at least 1/8 of its range [lo, n)
+        // (the dense trailing columns) by a scan of the marks, else a sort
+        const int64_t f = (int64_t)found.size();
+        if (f >= 256 && (int64_t)(n - lo) <= 8 * f) {
+            found.clear();
+            for (int32_t i = lo; i < n; i++)
+                if (mark[i] == j) found.push_back(i);
+        } else {
+            std::sort(found.begin(), found.end());
+        }
         std::vector<int32_t> &out = bufs[bid];
         cb[j] = bid;
         cs[j] = (int64_t)out.size();
@@ -643,6 +655,8 @@ int schedule(HostPlan &P, const glu_options &opt, int num_sms) {
     std::vector<int64_t> chunk_work;
     std::vector<std::vector<PSeg>> chunk_segs;
     std::vector<int32_t> touched;
+    std::vector<int32_t> cuts;   // a heavily shared chunk's segment cuts
+    std::vector<PSeg> sub;
     for (int32_t l = l0; l < l1; l++) {
         if (l == fail_level) throw std::bad_alloc();
         lvl_tasks.clear();
@@ -734,35 +748,60 @@ int schedule(HostPlan &P, const glu_options &opt, int num_sms) {
                         // equal parts (16, 8, ... positions) until each part
                         // holds at most piece_l updates.  A segment's rows
                         // split at the parts' first rows.
-                        auto clip = [&](const PSeg &sg, int64_t p0, int64_t p1) {
+                        // a part's updates are the rows of the chunk's segments
+                        // that sit on its positions: count them per position once
+                        // (each segment's rows and the column's rows both ascend)
+                        std::array<int64_t, SRC_SLOTS> at{};
+                        for (const PSeg &sg : cs) {
                             const int32_t *L = P.lu_rowidx.data() + lstart(P.pair_j[sg.pair]);
-                            const int32_t a0 = p0 <= cb ? sg.t0
-                                : (int32_t)(std::lower_bound(L + sg.t0, L + sg.t1, krows[p0]) - L);
-                            const int32_t a1 = p1 >= cb + cl ? sg.t1
-                                : (int32_t)(std::lower_bound(L + sg.t0, L + sg.t1, krows[p1]) - L);
-                            return PSeg{sg.pair, a0, a1, 0};
-                        };
+                            int64_t p = cb;
+                            for (int32_t t = sg.t0; t < sg.t1; t++) {
+                                while (krows[p] < L[t]) p++;
+                                at[(size_t)(p - cb)]++;
+                            }
+                        }
                         int64_t part = SRC_SLOTS;
                         while (part > 1) {
                             int64_t worst = 0;
-                            for (int64_t p0 = cb; p0 < cb + cl; p0 += part) {
+                            for (int64_t p0 = 0; p0 < cl; p0 += part) {
                                 int64_t w = 0;
-                                for (const PSeg &sg : cs) {
-                                    const PSeg c = clip(sg, p0, std::min(p0 + part, cb + cl));
-                                    w += c.t1 - c.t0;
-                                }
+                                for (int64_t q = p0; q < std::min(p0 + part, cl); q++) w += at[(size_t)q];
                                 worst = std::max(worst, w);
                             }
                             if (worst <= piece_l) break;
                             part /= 2;
                         }
-                        for (int64_t p0 = cb; p0 < cb + cl; p0 += part) {
-                            const int64_t p1 = std::min(p0 + part, cb + cl);
-                            std::vector<PSeg> sub;
+                        // each segment cut at the parts' first positions: cut[i] is
+                        // its first row on a position of part i or later
+                        const int64_t nparts = (cl + part - 1) / part;
+                        cuts.resize(cs.size() * (size_t)(nparts + 1));
+                        for (size_t si = 0; si < cs.size(); si++) {
+                            const PSeg &sg = cs[si];
+                            const int32_t *L = P.lu_rowidx.data() + lstart(P.pair_j[sg.pair]);
+                            int32_t *cut = cuts.data() + si * (size_t)(nparts + 1);
+                            int32_t t = sg.t0;
+                            int64_t p = cb;
+                            cut[0] = sg.t0;
+                            for (int64_t i = 1; i < nparts; i++) {
+                                while (t < sg.t1) {
+                                    while (krows[p] < L[t]) p++;
+                                    if (p >= cb + i * part) break;
+                                    t++;
+                                }
+                                cut[i] = t;
+                            }
+                            cut[nparts] = sg.t1;
+                        }
+                        for (int64_t i = 0; i < nparts; i++) {
+                            const int64_t p0 = cb + i * part, p1 = std::min(p0 + part, cb + cl);
+                            sub.clear();
                             int64_t w = 0;
-                            for (const PSeg &sg : cs) {
-                                const PSeg c = clip(sg, p0, p1);
-                                if (c.t1 > c.t0) { sub.push_back(c); w += c.t1 - c.t0; }
+                            for (size_t si = 0; si < cs.size(); si++) {
+                                const int32_t *cut = cuts.data() + si * (size_t)(nparts + 1);
+                                if (cut[i + 1] > cut[i]) {
+                                    sub.push_back(PSeg{cs[si].pair, cut[i], cut[i + 1], 0});
+                                    w += cut[i + 1] - cut[i];
+                                }
                             }
                             if (sub.empty()) continue;
                             if (sub.size() == 1) { add_priv(sub[0]); continue; }
