@@ -400,8 +400,8 @@ def roofline(achieved_tflops, traffic, fac_ms):
     r = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
          "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
          "kernel": "k_level (FP64 level sweep of one refactorization)",
-         "peak_source": "measured FP64 FMA throughput of a GB300 (standalone probe; the driver-measured "
-                        "peaks cover HBM and bf16 only)"}
+         "peak_source": "measured FP64 FMA throughput of a GB300 (standalone probe, "
+                        "profiles/fp64_fma_peak_probe.md; MEASURED_PEAKS.json covers HBM and bf16 only)"}
     if note:
         r["traffic_schedule"] = note
     hbm = measured_hbm_gbs()
