@@ -348,8 +348,151 @@ int symbolic(HostPlan &P, const std::vector<int64_t> &bptr, const std::vector<in
     const int32_t nchain = (int32_t)chains.size();
     std::vector<int32_t> pending((size_t)nchain);
     for (int32_t c = 0; c < nchain; c++) pending[c] = ntop[chains[c][0]];
+    // The chain that ends the matrix -- its columns are [c0, n) -- runs last,
+    // in two phases (top_chain below) when it is long: the dense trailing
+    // block and the nets' columns, whose reach sets cover much of the matrix,
+    // would otherwise be one thread's sequential work.
+    int32_t tc = -1;
+    if (nth > 1 && n > 0 && comp[n - 1] < 0) {
+        const std::vector<int32_t> &cc = chains[chain_of[n - 1]];
+        const int32_t c0 = n - (int32_t)cc.size();
+        bool tail = cc.size() >= 32;
+        for (size_t i = 0; tail && i < cc.size(); i++) tail = cc[i] == c0 + (int32_t)i;
+        if (tail) tc = chain_of[n - 1];
+    }
     bufs.resize((size_t)ntask + nchain);
     std::vector<Scratch> scr((size_t)nth);
+    // The final chain [c0, n): every row of L(:,j) for j >= c0 lies in the
+    // chain, so the rows below c0 that column j reaches are reached through
+    // columns below c0 only, whose structures are final once the other
+    // chains are done.  Phase 1 (columns in parallel): those rows, sorted,
+    // and the rows of the chain met on the way.  Phase 2 (in column order):
+    // the closure of the latter through the chain's own columns, and the
+    // column is the two lists one after the other.  The reach sets are those
+    // of column(); only the columns of the chain are pruned (the others are
+    // searched no more), which changes no set.
+    auto top_chain = [&](const std::vector<int32_t> &cc, int32_t bid) {
+        const int32_t c0 = cc.front();
+        const int32_t len = (int32_t)cc.size();
+        std::vector<std::vector<int32_t>> below((size_t)len), entry((size_t)len);
+        std::atomic<int32_t> nextc{0};
+        run_threads(nth, [&](int t) {
+            Scratch &sc = scr[t];
+            if (sc.mark.empty()) scratch(sc);
+            std::vector<int32_t> &mark = sc.mark, &stk = sc.stk;
+            std::vector<int64_t> &nxt = sc.nxt;
+            for (int32_t i; (i = nextc.fetch_add(1)) < len;) {
+                const int32_t j = c0 + i;
+                std::vector<int32_t> &out = below[(size_t)i], &ent = entry[(size_t)i];
+                int32_t lo = c0;
+                for (int64_t q = bptr[j]; q < bptr[j + 1]; q++) {
+                    const int32_t s = brow[q];
+                    if (mark[s] == j) continue;
+                    mark[s] = j;
+                    if (s >= c0) {
+                        ent.push_back(s);
+                        continue;
+                    }
+                    out.push_back(s);
+                    lo = std::min(lo, s);
+                    int32_t top = 0;
+                    stk[0] = s;
+                    nxt[0] = cd[s] + 1;
+                    while (top >= 0) {
+                        const int32_t v = stk[top];
+                        const int32_t *rv = bufs[cb[v]].data() + cs[v];
+                        const int64_t e = ce[v];
+                        int64_t t2 = nxt[top];
+                        while (t2 < e && mark[rv[t2]] == j) t2++;
+                        if (t2 == e) {
+                            top--;
+                            continue;
+                        }
+                        const int32_t w = rv[t2];
+                        nxt[top] = t2 + 1;
+                        mark[w] = j;
+                        if (w >= c0) {
+                            ent.push_back(w);
+                            continue;
+                        }
+                        out.push_back(w);
+                        lo = std::min(lo, w);
+                        top++;
+                        stk[top] = w;
+                        nxt[top] = cd[w] + 1;
+                    }
+                }
+                const int64_t f = (int64_t)out.size();
+                if (f >= 256 && (int64_t)(c0 - lo) <= 8 * f) {
+                    out.clear();
+                    for (int32_t r = lo; r < c0; r++)
+                        if (mark[r] == j) out.push_back(r);
+                } else {
+                    std::sort(out.begin(), out.end());
+                }
+            }
+        });
+        std::vector<int32_t> cm((size_t)len, -1), cstk, cfound;
+        std::vector<int64_t> cnx;
+        std::vector<int32_t> &buf = bufs[(size_t)bid];
+        for (int32_t i = 0; i < len; i++) {
+            const int32_t j = c0 + i;
+            cfound.clear();
+            for (const int32_t e0 : entry[(size_t)i]) {
+                if (cm[(size_t)(e0 - c0)] == j) continue;
+                cm[(size_t)(e0 - c0)] = j;
+                cfound.push_back(e0);
+                if (e0 >= j) continue;
+                cstk.assign(1, e0);
+                cnx.assign(1, cd[e0] + 1);
+                while (!cstk.empty()) {
+                    const int32_t v = cstk.back();
+                    const int32_t *rv = bufs[cb[v]].data() + cs[v];
+                    const int64_t e = ce[v];
+                    int64_t t2 = cnx.back();
+                    while (t2 < e && cm[(size_t)(rv[t2] - c0)] == j) t2++;
+                    if (t2 == e) {
+                        cstk.pop_back();
+                        cnx.pop_back();
+                        continue;
+                    }
+                    const int32_t w = rv[t2];
+                    cnx.back() = t2 + 1;
+                    cm[(size_t)(w - c0)] = j;
+                    cfound.push_back(w);
+                    if (w < j) {
+                        cstk.push_back(w);
+                        cnx.push_back(cd[w] + 1);
+                    }
+                }
+            }
+            std::sort(cfound.begin(), cfound.end());
+            const std::vector<int32_t> &out = below[(size_t)i];
+            cb[j] = bid;
+            cs[j] = (int64_t)buf.size();
+            buf.insert(buf.end(), out.begin(), out.end());
+            buf.insert(buf.end(), cfound.begin(), cfound.end());
+            const int64_t dc = std::lower_bound(cfound.begin(), cfound.end(), j) - cfound.begin();
+            cl[j] = (int64_t)(out.size() + cfound.size());
+            cd[j] = (int64_t)out.size() + dc;
+            ce[j] = cl[j];
+            // symmetric pruning of the chain's columns k with U(k,j) != 0
+            for (int64_t q = 0; q < dc; q++) {
+                const int32_t k = cfound[(size_t)q];
+                if (pruned[k]) continue;
+                const int32_t *rk = bufs[cb[k]].data() + cs[k];
+                const int32_t *lb = rk + cd[k] + 1;
+                const int32_t *le = rk + cl[k];
+                const int32_t *it = std::lower_bound(lb, le, j);
+                if (it != le && *it == j) {
+                    ce[k] = (it - rk) + 1;
+                    pruned[k] = 1;
+                }
+            }
+            std::vector<int32_t>().swap(below[(size_t)i]);
+            std::vector<int32_t>().swap(entry[(size_t)i]);
+        }
+    };
     // subtrees first, taken by threads as they finish
     std::atomic<int32_t> next{0};
     run_threads(ntask > 0 ? nth : 1, [&](int t) {
@@ -362,8 +505,8 @@ int symbolic(HostPlan &P, const std::vector<int64_t> &bptr, const std::vector<in
     std::condition_variable cv;
     std::vector<int32_t> ready;
     for (int32_t c = 0; c < nchain; c++)
-        if (pending[c] == 0) ready.push_back(c);
-    int32_t remaining = nchain;
+        if (pending[c] == 0 && c != tc) ready.push_back(c);
+    int32_t remaining = nchain - (tc >= 0 ? 1 : 0);
     bool aborted = false;
     run_threads(nchain > 0 ? nth : 1, [&](int t) {
         if (scr[t].mark.empty()) scratch(scr[t]);
@@ -382,7 +525,7 @@ int symbolic(HostPlan &P, const std::vector<int64_t> &bptr, const std::vector<in
                     std::lock_guard<std::mutex> lk(mu);
                     remaining--;
                     const int32_t p = parent[chains[c].back()];
-                    if (p >= 0 && --pending[chain_of[p]] == 0) ready.push_back(chain_of[p]);
+                    if (p >= 0 && --pending[chain_of[p]] == 0 && chain_of[p] != tc) ready.push_back(chain_of[p]);
                 }
                 cv.notify_all();
             }
@@ -395,6 +538,7 @@ int symbolic(HostPlan &P, const std::vector<int64_t> &bptr, const std::vector<in
             throw;
         }
     });
+    if (tc >= 0) top_chain(chains[tc], ntask + tc);
     scr.clear();
     // ---- column order
     P.lu_colptr.assign((size_t)n + 1, 0);
