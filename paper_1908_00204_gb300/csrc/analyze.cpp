@@ -1367,40 +1367,68 @@ void block_schedule(HostPlan &P) {
     }
     P.nblev = nbl;
     // pairs, bucketed by level, each bucket sorted by (k, sn): scanning
-    // columns k ascending and their U rows ascending gives that order
-    std::vector<int64_t> lcount((size_t)nbl + 1, 0);
-    std::vector<int32_t> last_sn((size_t)nsn, -1);   // last column k that recorded a pair for sn
-    for (int32_t k = 0; k < n; k++)
+    // columns k ascending and their U rows ascending gives that order.  On
+    // threads, one range of columns each: count per level, then place; a
+    // thread's columns precede the next thread's, so every bucket comes out
+    // in the order of one sequential scan.
+    const int nth = analysis_threads();
+    const std::vector<int32_t> kc = column_ranges(n, P.lu_colptr.data(), nth);
+    std::vector<std::vector<int64_t>> lcnt((size_t)nth);
+    // a column's pairs: the supernodes of its U rows that end before it, each
+    // once, with its first such row
+    auto column_pairs = [&](int32_t k, std::vector<int32_t> &last, auto emit) {
         for (int64_t p = P.lu_colptr[k]; p < P.diag_pos[k]; p++) {
-            const int32_t q = sof[P.lu_rowidx[p]];
-            if (c0v[q + 1] > k || last_sn[q] == k) continue;
-            last_sn[q] = k;
-            lcount[blev[q] + 1]++;
+            const int32_t j = P.lu_rowidx[p];
+            const int32_t q = sof[j];
+            if (c0v[q + 1] > k || last[q] == k) continue;
+            last[q] = k;
+            emit(q, j, p);
         }
-    for (int32_t l = 0; l < nbl; l++) lcount[l + 1] += lcount[l];
-    P.bpairs.assign((size_t)lcount[nbl], BPair{});
-    {
-        std::vector<int64_t> f(lcount.begin(), lcount.end() - 1);
-        std::fill(last_sn.begin(), last_sn.end(), -1);
-        for (int32_t k = 0; k < n; k++)
-            for (int64_t p = P.lu_colptr[k]; p < P.diag_pos[k]; p++) {
-                const int32_t j = P.lu_rowidx[p];
-                const int32_t q = sof[j];
-                if (c0v[q + 1] > k || last_sn[q] == k) continue;
-                last_sn[q] = k;
-                BPair &bp = P.bpairs[f[blev[q]]++];
-                bp.sn = q;
-                bp.k = k;
-                bp.f = j - c0v[q];
-                bp.upos = p;
-            }
+    };
+    run_threads(nth, [&](int t) {
+        std::vector<int64_t> &cnt = lcnt[t];
+        cnt.assign((size_t)nbl, 0);
+        std::vector<int32_t> last((size_t)nsn, -1);   // last column that recorded a pair for sn
+        for (int32_t k = kc[t]; k < kc[t + 1]; k++)
+            column_pairs(k, last, [&](int32_t q, int32_t, int64_t) { cnt[blev[q]]++; });
+    });
+    std::vector<int64_t> lcount((size_t)nbl + 1, 0);
+    for (int32_t l = 0; l < nbl; l++) {
+        int64_t at = lcount[l];
+        for (int t = 0; t < nth; t++) {
+            const int64_t c = lcnt[t][l];
+            lcnt[t][l] = at;     // now this thread's first slot in bucket l
+            at += c;
+        }
+        lcount[l + 1] = at;
     }
-    int64_t mb = 0;
-    for (BPair &bp : P.bpairs) {
-        bp.mb = mb;
-        mb += P.sn_r[bp.sn];
-    }
-    P.bmap_size = mb;
+    P.bpairs.resize((size_t)lcount[nbl]);
+    run_threads(nth, [&](int t) {
+        std::vector<int64_t> &f = lcnt[t];
+        std::vector<int32_t> last((size_t)nsn, -1);
+        for (int32_t k = kc[t]; k < kc[t + 1]; k++)
+            column_pairs(k, last, [&](int32_t q, int32_t j, int64_t p) {
+                P.bpairs[f[blev[q]]++] = BPair{q, k, j - c0v[q], 0, p, 0};
+            });
+    });
+    // map bases: exclusive prefix sum of the pairs' R_B sizes, by chunks
+    const int64_t npr = lcount[nbl];
+    std::vector<int64_t> msum((size_t)nth + 1, 0);
+    auto pch = [&](int t) { return npr * t / nth; };
+    run_threads(nth, [&](int t) {
+        int64_t s = 0;
+        for (int64_t q = pch(t); q < pch(t + 1); q++) s += P.sn_r[P.bpairs[q].sn];
+        msum[t + 1] = s;
+    });
+    for (int t = 0; t < nth; t++) msum[t + 1] += msum[t];
+    run_threads(nth, [&](int t) {
+        int64_t mb = msum[t];
+        for (int64_t q = pch(t); q < pch(t + 1); q++) {
+            P.bpairs[q].mb = mb;
+            mb += P.sn_r[P.bpairs[q].sn];
+        }
+    });
+    P.bmap_size = msum[nth];
     // per level: diagonal blocks, panel items, update tasks
     P.bdiag.clear();
     P.bdiag_ptr.assign((size_t)nbl + 1, 0);
@@ -1432,7 +1460,6 @@ void block_schedule(HostPlan &P) {
         std::vector<BTask> tasks;
         std::vector<int32_t> tend;   // per level, relative to tasks
     };
-    const int nth = analysis_threads();
     const int32_t nparts = std::max(1, std::min(nbl, nth * 8));
     std::vector<int32_t> cut(1, 0);
     for (int32_t t = 1; t < nparts; t++) {
@@ -1495,24 +1522,27 @@ void block_schedule(HostPlan &P) {
             }
         }
     });
-    int64_t sb = 0, tb = 0;
+    // concatenation: each part's segments and tasks to their offsets, on threads
+    std::vector<int64_t> sbase(parts.size() + 1, 0), tbase(parts.size() + 1, 0);
     for (size_t pi = 0; pi < parts.size(); pi++) {
         for (int32_t q = 0; q < cut[pi + 1] - cut[pi]; q++)
-            P.btask_ptr[cut[pi] + q + 1] = (int32_t)(tb + parts[pi].tend[q]);
-        sb += (int64_t)parts[pi].segs.size();
-        tb += (int64_t)parts[pi].tasks.size();
+            P.btask_ptr[cut[pi] + q + 1] = (int32_t)(tbase[pi] + parts[pi].tend[q]);
+        sbase[pi + 1] = sbase[pi] + (int64_t)parts[pi].segs.size();
+        tbase[pi + 1] = tbase[pi] + (int64_t)parts[pi].tasks.size();
     }
-    P.bsegs.resize((size_t)sb);
-    P.btasks.resize((size_t)tb);
-    sb = tb = 0;
-    for (BPart &pt : parts) {
-        std::copy(pt.segs.begin(), pt.segs.end(), P.bsegs.begin() + sb);
-        for (size_t q = 0; q < pt.tasks.size(); q++)
-            P.btasks[(size_t)tb + q] = BTask{pt.tasks[q].seg_begin + (int32_t)sb, pt.tasks[q].seg_end + (int32_t)sb};
-        sb += (int64_t)pt.segs.size();
-        tb += (int64_t)pt.tasks.size();
-        pt = BPart();
-    }
+    P.bsegs.resize((size_t)sbase[parts.size()]);
+    P.btasks.resize((size_t)tbase[parts.size()]);
+    std::atomic<size_t> nextp{0};
+    run_threads(nth, [&](int) {
+        for (size_t pi; (pi = nextp.fetch_add(1)) < parts.size();) {
+            BPart &pt = parts[pi];
+            const int32_t sb = (int32_t)sbase[pi];
+            std::copy(pt.segs.begin(), pt.segs.end(), P.bsegs.begin() + sbase[pi]);
+            for (size_t q = 0; q < pt.tasks.size(); q++)
+                P.btasks[(size_t)tbase[pi] + q] = BTask{pt.tasks[q].seg_begin + sb, pt.tasks[q].seg_end + sb};
+            pt = BPart();
+        }
+    });
 }
 
 // Start of the largest trailing block [t0, n), n - t0 <= tmax, in which every

@@ -238,9 +238,9 @@ struct HostPlan {
     std::vector<int32_t> bdiag, bdiag_ptr;   // supernodes of >= 2 columns, by block level
     std::vector<BItem> bitems;
     std::vector<int32_t> bitem_ptr;
-    std::vector<BPair> bpairs;
-    std::vector<BSeg> bsegs;
-    std::vector<BTask> btasks;
+    std::vector<BPair, NoInitAllocator<BPair>> bpairs;
+    std::vector<BSeg, NoInitAllocator<BSeg>> bsegs;
+    std::vector<BTask, NoInitAllocator<BTask>> btasks;
     std::vector<int32_t> btask_ptr;
     int64_t bmap_size = 0;
     int32_t nblev = 0;
