@@ -1209,18 +1209,31 @@ void build_df(const HostPlan &P, int64_t chunk, int32_t t0, int32_t blocks, std:
     auto add_chunks = [&](std::vector<SolveChunk> &ch, int64_t b, int64_t e) {
         for (int64_t p = b; p < e; p += chunk) ch.push_back(SolveChunk{p, std::min(e, p + chunk)});
     };
+    // a record per chunk from c_begin on, at 1 + the highest level its
+    // entries read; returns the highest of those (the level of a row made of
+    // these chunks), 0 without chunks
     auto chunk_recs = [&](bool bwd, const std::vector<SolveChunk> &ch, int32_t c_begin, const std::vector<int32_t> &lv,
                           const int32_t *colv, int32_t row, std::vector<Rec> &recs) {
+        int32_t top = 0;
         for (int32_t c = c_begin; c < (int32_t)ch.size(); c++) {
             int32_t m = 0;
             for (int64_t p = ch[c].p0; p < ch[c].p1; p++) m = std::max(m, lv[colv[p]] + 1);
             recs.push_back(Rec{m, 0, (int32_t)recs.size(), {row, 0, 0, c, (bwd ? 1 : 0) | 2, 0, 0, 0}});
+            top = std::max(top, m);
         }
+        return top;
     };
+    // records in (level, type) order, each key's records in the order they
+    // were made: a stable counting sort on 2 * level + type
     auto finish = [](std::vector<Rec> &recs) {
-        std::stable_sort(recs.begin(), recs.end(), [](const Rec &a, const Rec &b) {
-            return a.level != b.level ? a.level < b.level : a.type < b.type;
-        });
+        int32_t maxl = 0;
+        for (const Rec &r : recs) maxl = std::max(maxl, r.level);
+        std::vector<int64_t> at((size_t)2 * ((size_t)maxl + 1) + 1, 0);
+        for (const Rec &r : recs) at[(size_t)(2 * r.level + r.type) + 1]++;
+        for (size_t k = 1; k < at.size(); k++) at[k] += at[k - 1];
+        std::vector<Rec> sorted(recs.size());
+        for (const Rec &r : recs) sorted[(size_t)at[(size_t)(2 * r.level + r.type)]++] = r;
+        recs.swap(sorted);
     };
     // ---- forward (unit L), rows ascending
     std::vector<int32_t> lf((size_t)n, 0);
@@ -1231,13 +1244,12 @@ void build_df(const HostPlan &P, int64_t chunk, int32_t t0, int32_t blocks, std:
             int32_t lev = 0;
             const int32_t off = (int32_t)snx_f.size();
             for (int32_t r = c0; r < c1; r++) {
-                // entries before the block: all but the last r - c0
+                // entries before the block: all but the last r - c0 (all in chunks)
                 const int64_t b = P.lrow_ptr[r], e = P.lrow_ptr[r + 1] - (r - c0);
-                for (int64_t p = b; p < e; p++) lev = std::max(lev, lf[P.lrow_col[p]] + 1);
                 const int32_t cb = (int32_t)dff.size();
                 snx_f.push_back(cb);
                 add_chunks(dff, b, e);
-                chunk_recs(false, dff, cb, lf, P.lrow_col.data(), r, frec);
+                lev = std::max(lev, chunk_recs(false, dff, cb, lf, P.lrow_col.data(), r, frec));
             }
             snx_f.push_back((int32_t)dff.size());
             for (int32_t r = c0; r < c1; r++) lf[r] = lev;
@@ -1247,14 +1259,15 @@ void build_df(const HostPlan &P, int64_t chunk, int32_t t0, int32_t blocks, std:
         }
         const int64_t b = P.lrow_ptr[i], e = P.lrow_ptr[i + 1];
         int32_t lev = 0;
-        for (int64_t p = b; p < e; p++) lev = std::max(lev, lf[P.lrow_col[p]] + 1);
-        lf[i] = lev;
         int32_t cb = (int32_t)dff.size(), ce = cb;
-        if (e - b > chunk) {
+        if (e - b > chunk) {   // the row's level from its chunks' (its entries read columns < i)
             add_chunks(dff, b, e);
             ce = (int32_t)dff.size();
-            chunk_recs(false, dff, cb, lf, P.lrow_col.data(), i, frec);
+            lev = chunk_recs(false, dff, cb, lf, P.lrow_col.data(), i, frec);
+        } else {
+            for (int64_t p = b; p < e; p++) lev = std::max(lev, lf[P.lrow_col[p]] + 1);
         }
+        lf[i] = lev;
         frec.push_back(Rec{lev, 1, (int32_t)frec.size(), {i, cb, ce, -1, 0, 0, 0, 0}});
         i++;
     }
@@ -1279,13 +1292,12 @@ void build_df(const HostPlan &P, int64_t chunk, int32_t t0, int32_t blocks, std:
             int32_t lev = 0;
             const int32_t off = (int32_t)snx_b.size();
             for (int32_t r = c0; r < c1; r++) {
-                // U row r's entries after the block: all but the first c1 - 1 - r
+                // U row r's entries after the block: all but the first c1 - 1 - r (all in chunks)
                 const int64_t b = P.urow_ptr[r] + (c1 - 1 - r), e = P.urow_ptr[r + 1];
-                for (int64_t p = b; p < e; p++) lev = std::max(lev, lb[P.urow_col[p]] + 1);
                 const int32_t cb = (int32_t)dfb.size();
                 snx_b.push_back(cb);
                 add_chunks(dfb, b, e);
-                chunk_recs(true, dfb, cb, lb, P.urow_col.data(), r, brec);
+                lev = std::max(lev, chunk_recs(true, dfb, cb, lb, P.urow_col.data(), r, brec));
             }
             snx_b.push_back((int32_t)dfb.size());
             for (int32_t r = c0; r < c1; r++) lb[r] = lev;
@@ -1295,14 +1307,15 @@ void build_df(const HostPlan &P, int64_t chunk, int32_t t0, int32_t blocks, std:
         }
         const int64_t b = P.urow_ptr[i], e = P.urow_ptr[i + 1];
         int32_t lev = 0;
-        for (int64_t p = b; p < e; p++) lev = std::max(lev, lb[P.urow_col[p]] + 1);
-        lb[i] = lev;
         int32_t cb = (int32_t)dfb.size(), ce = cb;
-        if (e - b > chunk) {
+        if (e - b > chunk) {   // the row's level from its chunks' (its entries read columns > i)
             add_chunks(dfb, b, e);
             ce = (int32_t)dfb.size();
-            chunk_recs(true, dfb, cb, lb, P.urow_col.data(), i, brec);
+            lev = chunk_recs(true, dfb, cb, lb, P.urow_col.data(), i, brec);
+        } else {
+            for (int64_t p = b; p < e; p++) lev = std::max(lev, lb[P.urow_col[p]] + 1);
         }
+        lb[i] = lev;
         brec.push_back(Rec{lev, 1, (int32_t)brec.size(), {i, cb, ce, -1, 1, 0, 0, 0}});
         i--;
     }
