@@ -797,7 +797,24 @@ int schedule(HostPlan &P, const glu_options &opt, int num_sms) {
     std::vector<Task> lvl_tasks;
     // per-chunk scratch for splitting one group
     std::vector<int64_t> chunk_work;
-    std::vector<std::vector<PSeg>> chunk_segs;
+    // a group's segments per chunk: routed in (source, chunk) order into one
+    // list, then placed chunk by chunk keeping that order (a stable counting
+    // sort); chunk ch's are routed[cstart[ch] - ccount[ch], cstart[ch])
+    std::vector<int32_t> ccount;
+    std::vector<int64_t> cstart;
+    std::vector<std::pair<int32_t, PSeg>> flat;
+    std::vector<PSeg> routed;
+    struct SegSpan {
+        const PSeg *b;
+        size_t n;
+        size_t size() const { return n; }
+        const PSeg &operator[](size_t i) const { return b[i]; }
+        const PSeg *begin() const { return b; }
+        const PSeg *end() const { return b + n; }
+    };
+    auto chunk_segs = [&](int32_t ch) {
+        return SegSpan{routed.data() + cstart[(size_t)ch] - ccount[(size_t)ch], (size_t)ccount[(size_t)ch]};
+    };
     std::vector<int32_t> touched;
     std::vector<int32_t> cuts;   // a heavily shared chunk's segment cuts
     std::vector<PSeg> sub;
@@ -830,7 +847,8 @@ int schedule(HostPlan &P, const glu_options &opt, int num_sms) {
             const int64_t nchunks = (clen + SRC_SLOTS - 1) / SRC_SLOTS;
             if ((int64_t)chunk_work.size() < nchunks) {
                 chunk_work.resize((size_t)nchunks, 0);
-                chunk_segs.resize((size_t)nchunks);
+                ccount.resize((size_t)nchunks, 0);
+                cstart.resize((size_t)nchunks, 0);
             }
             touched.clear();
             const int32_t *krows = P.lu_rowidx.data() + c0;
@@ -854,13 +872,23 @@ int schedule(HostPlan &P, const glu_options &opt, int num_sms) {
                         int32_t endrow = krows[chend];
                         t1 = (int32_t)(gallop_lower_bound(L + t, L + lj, endrow) - L);
                     }
-                    if (chunk_work[ch] == 0 && chunk_segs[ch].empty()) touched.push_back((int32_t)ch);
-                    chunk_segs[ch].push_back(PSeg{(int32_t)q, t, t1, 0});
+                    if (ccount[(size_t)ch]++ == 0) touched.push_back((int32_t)ch);
+                    flat.emplace_back((int32_t)ch, PSeg{(int32_t)q, t, t1, 0});
                     chunk_work[ch] += t1 - t;
                     t = t1;
                 }
             }
             std::sort(touched.begin(), touched.end());
+            {
+                int64_t at = 0;
+                for (int32_t ch : touched) {
+                    cstart[(size_t)ch] = at;
+                    at += ccount[(size_t)ch];
+                }
+                routed.resize((size_t)at);
+                for (const auto &e : flat) routed[(size_t)cstart[(size_t)e.first]++] = e.second;
+                flat.clear();
+            }
             if (nsrc >= src_min) {
                 // Chunks reached by two or more segments become KIND_SRC
                 // tasks.  A chunk reached by one segment holds rows that no
@@ -876,7 +904,7 @@ int schedule(HostPlan &P, const glu_options &opt, int num_sms) {
                         priv.push_back(sg);
                 };
                 for (int32_t ch : touched) {
-                    std::vector<PSeg> &cs = chunk_segs[ch];
+                    const SegSpan cs = chunk_segs(ch);
                     const int64_t cb = (int64_t)ch * SRC_SLOTS;
                     const int64_t cl = std::min<int64_t>(SRC_SLOTS, clen - cb);
                     if (cs.size() < 2) {
@@ -955,7 +983,7 @@ int schedule(HostPlan &P, const glu_options &opt, int num_sms) {
                             lvl_tasks.push_back(t);
                         }
                     }
-                    cs.clear();
+                    ccount[(size_t)ch] = 0;
                     chunk_work[ch] = 0;
                 }
                 // (private segments are independent: small packs run on one
@@ -989,7 +1017,7 @@ int schedule(HostPlan &P, const glu_options &opt, int num_sms) {
                     for (int64_t q = g; q < ge; q++) {
                         int32_t lo = INT32_MAX, hi = -1;
                         for (size_t c = a; c < b; c++)
-                            for (const PSeg &s : chunk_segs[touched[c]])
+                            for (const PSeg &s : chunk_segs(touched[c]))
                                 if (s.pair == (int32_t)q) { lo = std::min(lo, s.t0); hi = std::max(hi, s.t1); }
                         if (hi > lo) psegs.push_back(PSeg{(int32_t)q, lo, hi, 0});
                     }
@@ -997,7 +1025,7 @@ int schedule(HostPlan &P, const glu_options &opt, int num_sms) {
                     lvl_tasks.push_back(t);
                     a = b;
                 }
-                for (int32_t ch : touched) { chunk_segs[ch].clear(); chunk_work[ch] = 0; }
+                for (int32_t ch : touched) { ccount[(size_t)ch] = 0; chunk_work[ch] = 0; }
             }
             g = ge;
         }
