@@ -68,8 +68,11 @@ def parse():
                     help="instead of the step: FP32 factor + FP64 refinement against FP64 and the CPU "
                          "oracle on one workload (backward errors, differences, times)")
     ap.add_argument("--factor-blocks", action="store_true",
-                    help="with --precision: the supernodal factorization (the schedule that fits the "
-                         "1000x1000 mesh with 256 nets)")
+                    help="with --precision or --analysis-only: the supernodal factorization (the "
+                         "schedule that fits the 1000x1000 mesh with 256 nets)")
+    ap.add_argument("--analysis-only", metavar="WORKLOAD", default=None,
+                    help="instead of the step: the host analysis alone (host_only, no GPU), timed "
+                         "--steps times after one untimed run")
     return ap.parse_args()
 
 
@@ -744,6 +747,30 @@ def run_latency(args):
     return 0
 
 
+def run_analysis_only(args):
+    """The analysis of one workload on the host cores (option host_only: the
+    fill, Algorithm 4, the levels and the schedules; nothing on the GPU),
+    wall time per call."""
+    import paper_1908_00204_gb300 as g
+    g.build.build()
+    m = synth.make(args.analysis_only, 1)
+    opts = dict(host_only=1, factor_blocks=int(args.factor_blocks))
+    times = []
+    for k in range(max(args.steps, 1) + 1):
+        t0 = time.perf_counter()
+        h = g.glu_analyze(m.n, m.colptr, m.rowidx, m.perm, g.default_options(**opts))
+        dt = time.perf_counter() - t0
+        st = g.glu_get_stats(h)
+        g.glu_destroy(h)
+        if k > 0:
+            times.append(dt)
+    out = {"metric": "host analysis time", "workload": args.analysis_only, "n": m.n, "nnz_a": m.nnz,
+           "factor_blocks": int(args.factor_blocks), "threads": os.cpu_count(),
+           "analyze_s_median": float(np.median(times)), "analyze_s": [round(t, 4) for t in times],
+           "nnz_lu": st["nnz_lu"], "nlevels": st["nlevels"], "n_pairs": st["n_pairs"]}
+    print(json.dumps(out), flush=True)
+
+
 def run_precision(args):
     """FP32 factorization + FP64 iterative refinement to 1e-12 against the
     FP64 factorization and the CPU oracle on one workload: backward errors
@@ -814,6 +841,8 @@ def main():
         return run_reference(args)
     if args.serve:
         return run_serve(args)
+    if args.analysis_only:
+        return run_analysis_only(args)
     if args.precision:
         return run_precision(args)
     if args.batched:
