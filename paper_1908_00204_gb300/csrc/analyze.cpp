@@ -1926,11 +1926,11 @@ int analyze_host(int32_t n, const int32_t *colptr, const int32_t *rowidx, const 
     const double t_sched = now_ms() - t3;
     if (solve_thread.joinable())
         solve_thread.join();
+    else if (!failed)
+        solve_job();   // no thread could be started: the solve schedule on this one
     if (opt.verbose)
         std::fprintf(stderr, "glu_analyze: factorization schedule %.0f ms, solve schedule %.0f ms (concurrent)\n",
                      t_sched, t_solve);
-    else if (!failed)
-        solve_job();
     if (failed || solve_failed) throw std::bad_alloc();
     if (rc != GLU_OK) {
         why = "the column schedule has more than 2^31 segments, tasks or pairs";
